@@ -1,0 +1,155 @@
+"""Pins of the oracle's graphs and colourings (CPU only).
+
+- Lattice neighbourhoods against brute-force enumeration by coordinate distance.
+- Lattice colourings (Sec. 2.3, Fig. 1) proper, with 2 / 4 / 2 colours.
+- The oracle's greedy colouring with priority decreasing in the index equals the paper's greedy
+  algorithm (repeatedly peel off the lexicographically first maximal independent set), written
+  out here independently.
+- With random priorities it equals a round-by-round Jones-Plassmann simulation (the parallel
+  algorithm the CUDA path runs), and every colouring is proper with k <= max degree + 1.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_05518_gb300 import workloads as wl
+
+
+def _proper(rp, ci, colors):
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    return bool(np.all(colors[rows] != colors[ci]))
+
+
+@pytest.mark.parametrize("kind,dims", [(oracle.LAT2D_4, (5, 7)), (oracle.LAT2D_8, (6, 5)),
+                                       (oracle.LAT3D_6, (3, 4, 5)), (oracle.LAT2D_4, (1, 9)),
+                                       (oracle.LAT2D_8, (1, 1)), (oracle.LAT3D_6, (1, 1, 4))])
+def test_lattice_neighbourhood_bruteforce(kind, dims):
+    rp, ci = oracle.lattice_csr(kind, dims)
+    shape = dims if kind == oracle.LAT3D_6 else (1,) + tuple(dims)
+    coords = list(itertools.product(*[range(s) for s in shape]))
+    for s, a in enumerate(coords):
+        want = []
+        for t, b in enumerate(coords):
+            d = np.abs(np.subtract(a, b))
+            if s == t:
+                continue
+            if kind == oracle.LAT2D_8:
+                ok = d.max() == 1
+            else:
+                ok = d.sum() == 1
+            if ok:
+                want.append(t)
+        assert sorted(ci[rp[s]:rp[s + 1]].tolist()) == want
+
+
+@pytest.mark.parametrize("kind,dims,k", [(oracle.LAT2D_4, (8, 9), 2), (oracle.LAT2D_8, (7, 8), 4),
+                                         (oracle.LAT3D_6, (4, 5, 3), 2)])
+def test_lattice_colourings_proper(kind, dims, k):
+    rp, ci = oracle.lattice_csr(kind, dims)
+    colors, kk = oracle.lattice_colors(kind, dims)
+    assert kk == k and colors.max() == k - 1 and colors.min() == 0
+    assert _proper(rp, ci, colors)
+
+
+def _paper_greedy(rp, ci):
+    """The paper's greedy colouring: colour class j is built by scanning the still-uncoloured
+    vertices in increasing index and taking each one not adjacent to a vertex already in the
+    class; repeat until all vertices are coloured."""
+    n = len(rp) - 1
+    colors = -np.ones(n, np.int64)
+    j = 0
+    while (colors < 0).any():
+        cand = set(np.flatnonzero(colors < 0).tolist())
+        while cand:
+            i = min(cand)
+            colors[i] = j
+            cand.discard(i)
+            cand -= set(ci[rp[i]:rp[i + 1]].tolist())
+        j += 1
+    return colors
+
+
+def _jp_rounds(rp, ci, prio):
+    """Jones-Plassmann by rounds: every uncoloured vertex whose (priority, index) beats all its
+    uncoloured neighbours takes the smallest colour absent among its coloured neighbours."""
+    n = len(rp) - 1
+    colors = -np.ones(n, np.int64)
+    rounds = 0
+    while (colors < 0).any():
+        sel = []
+        for v in np.flatnonzero(colors < 0):
+            nb = ci[rp[v]:rp[v + 1]]
+            if all(colors[u] >= 0 or (prio[u], u) < (prio[v], v) for u in nb):
+                sel.append(v)
+        newc = {}
+        for v in sel:
+            used = {colors[u] for u in ci[rp[v]:rp[v + 1]] if colors[u] >= 0}
+            c = 0
+            while c in used:
+                c += 1
+            newc[v] = c
+        for v, c in newc.items():
+            colors[v] = c
+        rounds += 1
+    return colors, rounds
+
+
+def _graphs():
+    g = wl.rng(1)
+    out = [wl.path_graph(9), wl.cycle_graph(7), wl.k4_minus_edge(), wl.star_graph(12),
+           wl.grid_graph(5, 6), wl.grid_graph(4, 5, eight=True), wl.random_graph(60, 0.1, g),
+           wl.random_graph(40, 0.5, g)]
+    rp, ci, _ = wl.delaunay_graph(300, g)
+    out.append((rp, ci))
+    out.append(wl.csr_from_edges(6, np.array([[0, 1], [2, 3]])))  # isolated vertices 4, 5
+    return out
+
+
+@pytest.mark.parametrize("gi", range(10))
+def test_greedy_index_order_equals_paper_algorithm(gi):
+    rp, ci = _graphs()[gi]
+    n = len(rp) - 1
+    prio = (n - 1 - np.arange(n)).astype(np.uint32)  # smaller index = higher priority
+    colors, k = oracle.color_greedy(rp, ci, prio)
+    want = _paper_greedy(rp, ci)
+    assert np.array_equal(colors, want)
+    assert k == want.max() + 1
+
+
+@pytest.mark.parametrize("gi", range(10))
+def test_greedy_equals_jones_plassmann(gi):
+    rp, ci = _graphs()[gi]
+    n = len(rp) - 1
+    prio = oracle.priorities(1234 + gi, n)
+    colors, k = oracle.color_greedy(rp, ci, prio)
+    jp, _ = _jp_rounds(rp, ci, prio)
+    assert np.array_equal(colors, jp)
+    assert _proper(rp, ci, colors)
+    maxdeg = np.diff(rp).max() if n else 0
+    assert k <= maxdeg + 1
+
+
+def test_greedy_ties_broken_by_index():
+    rp, ci = wl.cycle_graph(6)
+    prio = np.zeros(6, np.uint32)  # all equal: larger index wins
+    colors, _ = oracle.color_greedy(rp, ci, prio)
+    jp, _ = _jp_rounds(rp, ci, prio)
+    assert np.array_equal(colors, jp)
+    assert colors[5] == 0
+
+
+def test_priorities_are_philox_word0():
+    p = oracle.priorities(99, 5)
+    blk = oracle.philox_fill(99, 0, 0, 3 << 24, 5)
+    assert np.array_equal(p, blk[:, 0])
+
+
+def test_components():
+    assert oracle.components(*wl.path_graph(5)) == 1
+    assert oracle.components(*wl.csr_from_edges(6, np.array([[0, 1], [2, 3]]))) == 4
+    e = np.array([[0, 1], [1, 2], [2, 0], [3, 4], [4, 5], [5, 3]])
+    assert oracle.components(*wl.csr_from_edges(8, e)) == 4
+    rp, ci = oracle.lattice_csr(oracle.LAT3D_6, (3, 3, 3))
+    assert oracle.components(rp, ci) == 1

@@ -1,0 +1,107 @@
+"""Distributional pins of the oracle sampler (CPU only).
+
+- With tau and sigma^2 fixed, the chain's stationary law is the Gaussian full conditional of
+  Sec. 2.2, x ~ N(Q_p^-1 y / sigma^2, Q_p^-1) with Q_p = tau (D - rho W) + I / sigma^2.  On
+  graphs of at most 12 nodes the empirical mean and covariance of a long chain must agree with
+  it within a few batch-means standard errors.
+- With the hyperparameter draws on, the posterior of (tau, sigma^2) must agree, within Monte
+  Carlo error, with a dense block Gibbs sampler (Sec. 2.2, block updating by a Cholesky
+  factorisation of Q_p) written here with numpy's own generators.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_05518_gb300 import workloads as wl
+
+
+def _dense(rp, ci):
+    n = len(rp) - 1
+    Wm = np.zeros((n, n))
+    Wm[np.repeat(np.arange(n), np.diff(rp)), ci] = 1.0
+    return Wm, np.diag(Wm.sum(1))
+
+
+def _batch_se(samples, nb=50):
+    """Batch-means standard error of the mean of each column of samples [T, ...]."""
+    T = samples.shape[0] // nb * nb
+    b = samples[:T].reshape(nb, T // nb, *samples.shape[1:]).mean(1)
+    return b.std(0, ddof=1) / np.sqrt(nb)
+
+
+GRAPHS = [("path6", lambda: wl.path_graph(6)), ("cycle8", lambda: wl.cycle_graph(8)),
+          ("grid3x4", lambda: wl.grid_graph(3, 4)), ("k4e", wl.k4_minus_edge),
+          ("grid3x4x8", lambda: wl.grid_graph(3, 4, eight=True))]
+
+
+@pytest.mark.parametrize("name,make", GRAPHS)
+@pytest.mark.parametrize("prior,rho", [("icar", 1.0), ("pcar", 0.9)])
+def test_fixed_hyper_stationary_law(name, make, prior, rho):
+    rp, ci = make()
+    n = len(rp) - 1
+    g = wl.rng(21)
+    y = g.normal(0, 1.5, n)
+    tau, sig2 = 1.7, 0.6
+    colors, _ = oracle.color_graph(rp, ci, 3)
+    st = oracle.initial_state(y, 1, tau0=tau, sigma2_0=sig2)
+    T = 120_000
+    out = oracle.run((rp, ci), colors, y, st, seed=31, nsweeps=T, prior=prior, rho=rho,
+                     fix_hyper=True, accumulate=False, record_x=True)
+    xs = out["xtrace"][1000:, 0, :]
+    Wm, D = _dense(rp, ci)
+    Qp = tau * (D - rho * Wm) + np.eye(n) / sig2
+    cov = np.linalg.inv(Qp)
+    mu = cov @ (y / sig2)
+    se = _batch_se(xs)
+    assert np.all(np.abs(xs.mean(0) - mu) < 5 * se + 1e-12)
+    dev = xs - mu
+    outer = dev[:, :, None] * dev[:, None, :]
+    se_cov = _batch_se(outer)
+    assert np.all(np.abs(outer.mean(0) - cov) < 5 * se_cov + 1e-12)
+
+
+def _block_gibbs(rp, ci, y, prior, rho, a_tau, b_tau, a_sig, b_sig, T, seed):
+    """Dense block Gibbs: x | tau, sigma^2 ~ N(Q_p^-1 b, Q_p^-1) by Cholesky (one factorisation
+    and triangular solves), then tau^2 and sigma^2 from their inverse-gamma conditionals."""
+    n = len(rp) - 1
+    Wm, D = _dense(rp, ci)
+    R = D - rho * Wm
+    r = n - oracle.components(rp, ci) if prior == "icar" else n
+    g = np.random.default_rng(seed)
+    tau, sig2 = 1.0, 1.0
+    out = np.zeros((T, 2))
+    for t in range(T):
+        Qp = tau * R + np.eye(n) / sig2
+        L = np.linalg.cholesky(Qp)
+        mean = np.linalg.solve(L.T, np.linalg.solve(L, y / sig2))
+        x = mean + np.linalg.solve(L.T, g.standard_normal(n))
+        S = x @ R @ x
+        tau = g.gamma(a_tau + r / 2, 1.0 / (b_tau + S / 2))
+        sig2 = 1.0 / g.gamma(a_sig + n / 2, 1.0 / (b_sig + np.sum((y - x) ** 2) / 2))
+        out[t] = tau, sig2
+    return out
+
+
+@pytest.mark.parametrize("name,make", [("grid3x4", lambda: wl.grid_graph(3, 4)),
+                                       ("k4e", wl.k4_minus_edge)])
+@pytest.mark.parametrize("prior,rho", [("icar", 1.0), ("pcar", 0.8)])
+def test_hyper_posterior_matches_block_gibbs(name, make, prior, rho):
+    rp, ci = make()
+    n = len(rp) - 1
+    y = wl.rng(5).normal(0, 1.0, n)
+    hp = dict(a_tau=3.0, b_tau=2.0, a_sig=3.0, b_sig=1.0)
+    T = 60_000
+    colors, _ = oracle.color_graph(rp, ci, 1)
+    st = oracle.initial_state(y, 1)
+    out = oracle.run((rp, ci), colors, y, st, seed=2, nsweeps=T, prior=prior, rho=rho,
+                     accumulate=False, **hp)
+    chrom = np.stack([out["tau_trace"][0], out["sigma2_trace"][0]], 1)[2000:]
+    block = _block_gibbs(rp, ci, y, prior, rho, hp["a_tau"], hp["b_tau"], hp["a_sig"],
+                         hp["b_sig"], 30_000, 7)[1000:]
+    se = np.sqrt(_batch_se(chrom) ** 2 + _batch_se(block) ** 2)
+    diff = np.abs(chrom.mean(0) - block.mean(0))
+    assert np.all(diff < 5 * se), (chrom.mean(0), block.mean(0), se)
+    for q in (0.1, 0.5, 0.9):
+        qc, qb = np.quantile(chrom, q, axis=0), np.quantile(block, q, axis=0)
+        spread = chrom.std(0)
+        assert np.all(np.abs(qc - qb) < 0.06 * spread + 5 * se), (q, qc, qb)
