@@ -1,0 +1,434 @@
+#!/usr/bin/env python3
+"""Benchmark of the chromatic Gibbs sampler (site-updates per second) on synthetic workloads.
+
+Default workload: a 1024 x 1024 second-order (8-neighbour) intrinsic CAR lattice with the 2x2
+four-colouring, observations = 20 Gaussian bumps + N(0, 1) noise, FP32 state with FP64
+hyperparameter reductions, one chain, 2000 sweeps (the first 1000 burn-in, the rest accumulated
+into the running posterior mean and variance), tau and sigma^2 drawn every sweep.
+
+One step = one complete MCMC run of the workload on device-resident inputs: restart from the
+initial state, then all sweeps (every colour step, the fused reductions, the conjugate draws,
+the accumulation), replayed as CUDA graphs.  L2 is flushed (a 512 MiB write) between timed
+steps, outside the per-step CUDA events.
+
+Printed: one JSON line with the site-update rate, the end-to-end rate through the C ABI with
+host buffers, the roofline of the colour-step kernel, the clocks seen, and the oracle's CPU rate
+on a bounded sample.  ``--impl reference`` times the oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1702_05518_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "site-updates/sec & HBM GB/s vs peak: batched FP32 vs plain FP64 chromatic Gibbs"
+UNIT = "site-updates/s"
+
+
+# ----------------------------------------------------------------------------------------------
+# Workloads
+# ----------------------------------------------------------------------------------------------
+def workload_spec(name: str):
+    """Fields and run parameters of a named workload."""
+    if name == "image1024":
+        return dict(name="1024x1024 8-neighbour ICAR, 2x2 colouring, 20 Gaussian bumps + N(0,1)",
+                    fields=wl.image_1024_bumps(seed=2), chains=1, sweeps=2000, burn_in=1000,
+                    prior="icar", rho=1.0, seed=2, graph_sweeps=50, cpu_sweeps=20)
+    if name == "image64":
+        return dict(name="64x64 4-neighbour ICAR, checkerboard, 4-level block image + N(0,0.5^2)",
+                    fields=wl.image_64_block(seed=0), chains=1, sweeps=1000, burn_in=500,
+                    prior="icar", rho=1.0, seed=0, graph_sweeps=50, cpu_sweeps=1000)
+    if name == "volume256":
+        return dict(name="256^3 6-neighbour ICAR, parity colouring, 50 ellipsoids + N(0,1), 8 chains",
+                    fields=wl.volume_ellipsoids(seed=5), chains=8, sweeps=500, burn_in=250,
+                    prior="icar", rho=1.0, seed=5, graph_sweeps=25, cpu_sweeps=1)
+    if name == "delaunay16k":
+        f = wl.delaunay_pcar(seed=3)
+        f[0]["color_seed"] = 3
+        return dict(name="Delaunay 16384 points, proper CAR rho=0.95, 8 chains", fields=f, chains=8,
+                    sweeps=5000, burn_in=2500, prior="pcar", rho=0.95, seed=3, graph_sweeps=50,
+                    cpu_sweeps=50)
+    if name == "batched":
+        fields = wl.batched_uneven(seed=4)
+        for i, f in enumerate(fields):
+            f["color_seed"] = 100 + i
+        return dict(name="224 lattices (sides log-U[32,512]) + 32 Delaunay graphs (n log-U[1k,50k])",
+                    fields=fields, chains=1, sweeps=1000, burn_in=500, prior="icar", rho=1.0,
+                    seed=4, graph_sweeps=25, cpu_sweeps=3)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def site_updates_per_step(spec):
+    return sum(f["n"] for f in spec["fields"]) * spec["chains"] * spec["sweeps"]
+
+
+def colour_classes(field):
+    """Sites per colour class of a field (lattice closed forms; CSR via the oracle-free count
+    of the GPU's own colouring is not needed for lattices)."""
+    k = field["kind"]
+    if k == wl.LATTICE2D_8:
+        H, W = field["dims"][:2]
+        return [((H - a + 1) // 2) * ((W - b + 1) // 2) for a in (0, 1) for b in (0, 1)]
+    if k == wl.LATTICE3D_6:
+        L, H, W = field["dims"]
+        even = (L * H * W + 1) // 2
+        return [even, L * H * W - even]
+    H, W = field["dims"][:2]
+    even = (H * W + 1) // 2
+    return [even, H * W - even]
+
+
+def algorithmic_bytes_per_colour_step(spec, colour, state_bytes=4):
+    """Bytes a colour step must move at least: every neighbour value of the class read once
+    (for lattices: all sites of the other colours adjacent to the class), the class's y read
+    once, its new state written once (C chains), no accumulation."""
+    C = spec["chains"]
+    total = 0
+    for f in spec["fields"]:
+        if f["kind"] == wl.CSR:
+            raise ValueError("CSR roofline bytes need the colouring")
+        cls = colour_classes(f)
+        if colour >= len(cls):
+            continue
+        n_c = cls[colour]
+        others = sum(cls) - n_c  # every other-colour site neighbours the class
+        total += others * C * state_bytes + n_c * state_bytes + n_c * C * state_bytes
+    return total
+
+
+# ----------------------------------------------------------------------------------------------
+# Clocks
+# ----------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample of the workload
+# ----------------------------------------------------------------------------------------------
+def oracle_rate(spec, sweeps):
+    import oracle
+    from paper_1702_05518_gb300.workloads import CSR
+
+    kinds = {wl.LATTICE2D_4: oracle.LAT2D_4, wl.LATTICE2D_8: oracle.LAT2D_8, wl.LATTICE3D_6: oracle.LAT3D_6}
+    prepared = []
+    for i, f in enumerate(spec["fields"]):
+        if f["kind"] == CSR:
+            graph = (f["row_ptr"], f["col_idx"])
+            colors = oracle.color_graph(f["row_ptr"], f["col_idx"], f.get("color_seed", 0))[0]
+        else:
+            graph = oracle.lattice_csr(kinds[f["kind"]], f["dims"])
+            colors = oracle.lattice_colors(kinds[f["kind"]], f["dims"])[0]
+        prepared.append((graph, colors, f["y"], i))
+    t0 = time.perf_counter()
+    updates = 0
+    for graph, colors, y, i in prepared:
+        st = oracle.initial_state(y, spec["chains"])
+        oracle.run(graph, colors, y, st, seed=spec["seed"], nsweeps=sweeps, stream=i, prior=spec["prior"],
+                   rho=spec["rho"], burn_in=0, accumulate=True)
+        updates += len(y) * spec["chains"] * sweeps
+    dt = time.perf_counter() - t0
+    return updates / dt, dt, updates
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+# ----------------------------------------------------------------------------------------------
+# Distributed helpers (one process per GPU; replicas with independent seeds, no data exchange)
+# ----------------------------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank runs an independent replica: a different Philox key per rank."""
+    return int(base_seed) + 1000003 * int(rank)
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------------------------
+# Arms
+# ----------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    spec = workload_spec(args.workload)
+    sample = max(1, spec["cpu_sweeps"] // 4) if args.workload != "image64" else 100
+    for _ in range(args.warmup):
+        oracle_rate(spec, sample)
+    times = []
+    updates = 0
+    for _ in range(args.steps):
+        _, dt, u = oracle_rate(spec, sample)
+        times.append(dt)
+        updates += u
+    value = updates / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": spec["name"], "sample": f"{sample} sweeps of the workload per step",
+                       "chains": spec["chains"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{sample} sweeps per step, {args.steps} steps; CPU: {cpu_model()}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1702_05518_gb300 import build as libbuild
+    from paper_1702_05518_gb300 import gmrf as g
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if not os.path.exists(g.LIB_PATH):
+        libbuild.build()
+    spec = workload_spec(args.workload)
+    seed = replica_seed(spec["seed"], rank)
+    prior = g.PRIOR_PCAR if spec["prior"] == "pcar" else g.PRIOR_ICAR
+    kw = dict(precision=g.FP32, chains=spec["chains"], seed=seed, prior=prior, rho=spec["rho"],
+              burn_in=spec["burn_in"], graph_sweeps=spec["graph_sweeps"], trace_capacity=spec["sweeps"])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    units = site_updates_per_step(spec)
+
+    s = g.Sampler(spec["fields"], **kw)
+    info = s.info()
+    for _ in range(args.warmup):
+        s.reset()
+        s.sweep(spec["sweeps"])
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)  # evict the previous step's data from L2 (untimed)
+            starts[k].record(stream)
+            s.reset()
+            s.sweep(spec["sweeps"])
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - w0
+    clocks = clk.summary()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    dev_s = sum(step_ms) / 1e3
+    dev_s_max = max_over_ranks(dev_s, world, device="cuda")
+    value = world * units * args.steps / dev_s_max
+
+    # Colour-step kernel alone: back-to-back launches of each colour class, CUDA events on the
+    # launching stream (accumulation off); average duration per launch.
+    k_colours = info["max_colors"]
+    reps = 50
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for c in range(k_colours):
+        s.launch_colour_step(c)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(reps):
+        for c in range(k_colours):
+            s.launch_colour_step(c)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    kernel_us = ev0.elapsed_time(ev1) * 1e3 / (reps * k_colours)
+    try:
+        algo_bytes = np.mean([algorithmic_bytes_per_colour_step(spec, c) for c in range(k_colours)])
+    except ValueError:
+        algo_bytes = None
+    s.close()
+
+    # End to end through the C ABI with host buffers: create (H2D copy of y), all sweeps, fetch
+    # of the posterior mean (D2H), destroy.
+    e2e_steps = max(1, min(3, args.steps))
+    n_total = sum(f["n"] for f in spec["fields"])
+    h2d = 8 * n_total
+    d2h = 8 * n_total * spec["chains"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with g.Sampler(spec["fields"], **kw) as s2:
+            s2.sweep(spec["sweeps"])
+            for fi in range(len(spec["fields"])):
+                for c in range(spec["chains"]):
+                    s2.fetch(fi, c)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
+    e2e_value = world * units * e2e_steps / e2e_s
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_note = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    roofline = None
+    if algo_bytes is not None:
+        achieved = algo_bytes / (kernel_us * 1e-6) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": None, "peak_source": peak_note,
+                    "kernel": "colour_step_kernel<float,1>", "algorithmic_bytes_per_launch": algo_bytes,
+                    "avg_launch_us": kernel_us}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return 0
+
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        rate, dt, u = oracle_rate(spec, spec["cpu_sweeps"])
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{spec['cpu_sweeps']} sweeps of the full workload ({u} site-updates, {dt:.1f} s); "
+                         f"CPU: {cpu_model()}"}
+    launches = args.steps * spec["sweeps"] * info["launches_per_sweep"] + args.steps  # + reset kernel
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": spec["name"], "chains": spec["chains"], "sweeps_per_step": spec["sweeps"],
+                       "burn_in": spec["burn_in"], "sites": n_total, "graph_sweeps": spec["graph_sweeps"],
+                       "l2": "flushed between steps (512 MiB write), outside the timed events",
+                       "parallelism": f"replicas x{world}"},
+            "wall_ms_per_step": 1e3 * wall / args.steps,
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "cpu_baseline": cpu}
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="image1024",
+                    choices=["image1024", "image64", "volume256", "delaunay16k", "batched"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

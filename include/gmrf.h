@@ -1,0 +1,257 @@
+/*
+ * gmrf.h -- C ABI of libgmrf, a GB300 (sm_103a) library for chromatic Gibbs sampling of
+ * Gaussian Markov random fields, after Brown, McMahan & Self, "Sampling Strategies for Fast
+ * Updating of Gaussian Markov Random Fields" (arXiv 1702.05518).
+ *
+ * Model (Sec. 2.2, Sec. 3.1; Sec. 3.2 for the proper prior).  A field has n sites on an
+ * undirected graph with symmetric weights w_ij > 0 (w_ij = 1 unless given), degrees
+ * d_i = sum_j w_ij, observations y = x + eps, eps ~ N(0, sigma^2 I), and the CAR prior with
+ * precision tau (D - rho W): rho = 1 is the intrinsic CAR ("IAR"), 0 <= rho < 1 the proper CAR.
+ * tau here is a precision: tau = 1 / tau^2 in the paper's notation.  Conjugate priors
+ * tau ~ Gamma(a_tau, rate b_tau), 1/sigma^2 ~ Gamma(a_sigma, rate b_sigma).
+ *
+ * One sweep (Algorithm 1) visits the colour classes A_0..A_{k-1} of a proper colouring in
+ * order and draws every site of the class at once from its full conditional
+ *     x_i | x_-i ~ N((tau rho s_i + y_i / sigma^2) / P_i, 1 / P_i),
+ *     P_i = tau d_i + 1 / sigma^2,  s_i = sum_j w_ij x_j,
+ * then (unless the hyperparameters are fixed) draws
+ *     tau       ~ Gamma(a_tau + r/2,  rate b_tau + x'(D - rho W)x / 2),
+ *     1/sigma^2 ~ Gamma(a_sigma + n/2, rate b_sigma + ||y - x||^2 / 2),
+ * with r = n - (connected components) for the intrinsic prior and r = n for the proper one
+ * (Sec. 3.1 full conditionals).
+ *
+ * Random numbers are Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seed, with
+ * counters that name the draw, so results do not depend on launch shapes or on the order of
+ * sites within a colour class:
+ *     site update      counter (site, sweep, stream, (0 << 24) | chain/4), normal chain mod 4
+ *                      of the block: Box-Muller of (w0,w1) gives normals 0 (cos), 1 (sin),
+ *                      (w2,w3) gives 2 and 3; u = (w + 1/2) 2^-32.
+ *     tau draw         counter (attempt, sweep, stream, (1 << 24) | chain)   [Marsaglia-Tsang]
+ *     1/sigma^2 draw   counter (attempt, sweep, stream, (2 << 24) | chain)
+ *     JP priority      word 0 of counter (vertex, 0, 0, 3 << 24)
+ *     extra hyper draw counter (attempt, k, stream, ((5|6) << 24) | chain), k-th call of
+ *                      gmrf_hyper_update
+ * "site" is the natural (row-major for lattices) index, "stream" the field's stream id.
+ *
+ * Conventions.  Every call returns a gmrf_status and never aborts or prints.  Host pointers
+ * are read during the call only and stay owned by the caller; the library owns every device
+ * buffer it allocates.  A failed create leaves *out == NULL.  After a CUDA error a sampler is
+ * poisoned: later calls on it return GMRF_E_STATE.  gmrf_last_error() describes the last
+ * failure of the calling thread.  A sampler is bound to the device current at creation and to
+ * one CUDA stream; it is not thread-safe.
+ */
+#ifndef GMRF_H
+#define GMRF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GMRF_OK = 0,
+    GMRF_E_INVALID = 1,     /* an argument failed validation; nothing was launched         */
+    GMRF_E_CUDA = 2,        /* a CUDA call failed; the sampler is poisoned                 */
+    GMRF_E_OOM = 3,         /* device allocation failed                                   */
+    GMRF_E_STATE = 4,       /* sampler poisoned by an earlier error, or call out of order  */
+    GMRF_E_TIMEOUT = 5,     /* a bounded device wait gave up (reserved; no kernel waits)   */
+    GMRF_E_UNSUPPORTED = 6  /* valid request that this build does not implement           */
+} gmrf_status;
+
+typedef enum {
+    GMRF_LATTICE2D_4 = 0,   /* H x W lattice, 4 neighbours, 2 colours (i + j) mod 2          */
+    GMRF_LATTICE2D_8 = 1,   /* H x W lattice, 8 neighbours, 4 colours 2 (i mod 2) + (j mod 2) */
+    GMRF_LATTICE3D_6 = 2,   /* L x H x W lattice, 6 neighbours, 2 colours (l + i + j) mod 2  */
+    GMRF_CSR = 3            /* arbitrary graph in compressed sparse rows                   */
+} gmrf_field_kind;
+
+typedef enum { GMRF_PRIOR_ICAR = 0, GMRF_PRIOR_PCAR = 1 } gmrf_prior_kind;
+typedef enum { GMRF_FP32 = 0, GMRF_FP64 = 1 } gmrf_precision;
+typedef enum {
+    GMRF_ALGO_CHROMATIC = 0, /* colour-split layout, fused per-colour kernels (the product)   */
+    GMRF_ALGO_PLAIN = 1      /* natural layout, one unfused pass over all sites per colour;
+                                the plain single-field FP64 reference sweep for speed-ups   */
+} gmrf_algorithm;
+
+/*
+ * One field.  Lattices (Sec. 2.3, Fig. 1: colourings found by inspection) have free,
+ * non-periodic boundaries (Sec. 3.1, edge effects ignored: border sites have fewer
+ * neighbours) and sites in row-major order: 2-D site (i, j) = i*W + j with dims = {H, W, 0};
+ * 3-D site (l, i, j) = (l*H + i)*W + j with dims = {L, H, W}.  A CSR graph (Sec. 2.3) gives
+ * row_ptr[n+1], col_idx[nnz] (int32, host): symmetric, no self-loops, no duplicate entries,
+ * rows in any order; weights[nnz] (host, symmetric, > 0) or NULL for w_ij = 1; colors[n]
+ * (host) a proper colouring, or NULL to colour on the device by Jones-Plassmann with Philox
+ * priorities of `color_seed`.
+ */
+typedef struct {
+    int32_t kind;             /* gmrf_field_kind                                            */
+    int32_t dims[3];          /* lattice extents (see above); unused for CSR                */
+    int32_t n;                /* sites; must equal the product of dims for lattices         */
+    const int32_t *row_ptr;   /* CSR only                                                   */
+    const int32_t *col_idx;   /* CSR only                                                   */
+    const double *weights;    /* CSR only, may be NULL                                      */
+    const int32_t *colors;    /* CSR only, may be NULL                                      */
+    uint64_t color_seed;      /* CSR with colors == NULL: priority seed                     */
+    const double *y;          /* [n] observations, natural order (host)                     */
+    const double *x0;         /* [chains][n] initial states (host) or NULL: x0 = y          */
+    const double *tau0;       /* [chains] initial tau or NULL: model.tau0                   */
+    const double *sigma2_0;   /* [chains] initial sigma^2 or NULL: model.sigma2_0           */
+    uint32_t stream_id;       /* Philox counter word 2 of this field's draws                */
+} gmrf_field_desc;
+
+typedef struct {
+    int32_t prior;            /* gmrf_prior_kind                                            */
+    double rho;               /* proper CAR: 0 <= rho < 1; ignored for the intrinsic prior  */
+    double a_tau, b_tau;      /* tau ~ Gamma(a_tau, rate b_tau); a_tau > 0, b_tau >= 0      */
+    double a_sigma, b_sigma;  /* 1/sigma^2 ~ Gamma(a_sigma, rate b_sigma)                   */
+    int32_t fix_hyper;        /* nonzero: tau, sigma^2 stay at their initial values         */
+    double tau0, sigma2_0;    /* default initial values (tau0 >= 0, sigma2_0 > 0)            */
+} gmrf_model;
+
+typedef struct {
+    int32_t precision;        /* gmrf_precision: state and site arithmetic                  */
+    int32_t chains;           /* independent chains per field, 1..64                        */
+    uint64_t seed;            /* Philox key                                                 */
+    int64_t start_sweep;      /* number of the first sweep (resume); 0 for a fresh run       */
+    int64_t burn_in;          /* sweeps numbered < burn_in are not accumulated              */
+    int32_t thin;             /* accumulate sweeps burn_in, burn_in + thin, ... (>= 1)       */
+    int32_t trace_capacity;   /* tau/sigma^2 trace ring length per chain (>= 1)             */
+    int32_t algorithm;        /* gmrf_algorithm                                             */
+    int32_t graph_sweeps;     /* sweeps captured per CUDA graph; 0 = launch kernels directly */
+} gmrf_opts;
+
+typedef struct {
+    int32_t nfields;
+    int32_t chains;
+    int32_t precision;
+    int32_t max_colors;       /* colour steps per sweep                                     */
+    int64_t sweeps_done;      /* sweeps completed (start_sweep included)                    */
+    int64_t accumulated;      /* sweeps accumulated into the running mean / variance         */
+    int64_t hyper_fallbacks;  /* Gamma draws that hit the 64-attempt limit (normally 0)     */
+    int64_t device_bytes;     /* device memory held by the sampler                          */
+    int64_t launches_per_sweep; /* kernels launched per sweep                               */
+} gmrf_info;
+
+typedef struct gmrf_sampler gmrf_sampler;
+
+/*
+ * Colour a CSR graph by Jones-Plassmann on the device (Sec. 2.3: a colouring is a one-off
+ * pre-computation; the paper's greedy colouring is the special case priority = -index).
+ * Round by round, every uncoloured vertex whose (priority, index) is larger than that of all
+ * its uncoloured neighbours takes the smallest colour absent among its coloured neighbours;
+ * the result equals sequential greedy colouring in decreasing (priority, index) order.
+ *   n, row_ptr[n+1], col_idx[nnz]: host CSR, validated as for gmrf_field_desc.
+ *   priorities: host [n] or NULL for Philox priorities of `seed`.
+ *   colors: host out [n], 0-based; num_colors: out.
+ * Device scratch is allocated and freed inside the call; runs on the legacy default stream
+ * and synchronises.  Errors: GMRF_E_INVALID (bad CSR / NULL outputs), GMRF_E_CUDA, GMRF_E_OOM.
+ */
+gmrf_status gmrf_color_graph(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                             const uint32_t *priorities, uint64_t seed, int32_t *colors,
+                             int32_t *num_colors);
+
+/*
+ * Create a sampler over `nfields` independent fields (each with `opts.chains` chains and its
+ * own tau, sigma^2 per chain), copy y / x0 / graphs to the device in the colour-split layout
+ * (Sec. 3.1: chromatic sampling needs only the lists of sites of each colour), and colour CSR fields that
+ * come without colours.  `cuda_stream` (a cudaStream_t, or NULL for the legacy default
+ * stream) is the stream every later call enqueues on.  All host inputs are copied; none is
+ * retained.  Errors: GMRF_E_INVALID, GMRF_E_UNSUPPORTED (e.g. GMRF_ALGO_PLAIN with more than
+ * one field or non-FP64), GMRF_E_OOM, GMRF_E_CUDA.  On error *out is NULL.
+ */
+gmrf_status gmrf_sampler_create(gmrf_sampler **out, const gmrf_field_desc *fields,
+                                int32_t nfields, const gmrf_model *model, const gmrf_opts *opts,
+                                void *cuda_stream);
+
+/* Release every device buffer and CUDA graph of the sampler (synchronises its stream). */
+void gmrf_sampler_destroy(gmrf_sampler *s);
+
+/*
+ * Enqueue `nsweeps` sweeps (Algorithm 1 over all colours of all fields, then the conjugate
+ * tau, sigma^2 draws unless with_hyper == 0 or model.fix_hyper, then trace and accumulator
+ * updates) on the sampler's stream.  Asynchronous: returns before the work finishes.
+ * Errors: GMRF_E_INVALID (nsweeps < 0), GMRF_E_STATE, GMRF_E_CUDA.
+ */
+gmrf_status gmrf_sweep(gmrf_sampler *s, int32_t nsweeps, int32_t with_hyper);
+
+/*
+ * One extra draw of tau and sigma^2 from their full conditionals (Sec. 3.1) given the current
+ * x of every field and chain, without a sweep (counters: tags 5 and 6, k = number of earlier
+ * calls).  Asynchronous.  Errors: GMRF_E_STATE, GMRF_E_CUDA.
+ */
+gmrf_status gmrf_hyper_update(gmrf_sampler *s);
+
+/*
+ * Copy results of one (field, chain) to host buffers in natural site order (synchronises the
+ * stream).  Any output pointer may be NULL.
+ *   x_last[n]: current state;  x_mean[n], x_var[n]: running mean and sample variance
+ *   (M2 / (count - 1)) over the accumulated sweeps (zeros / NaN when fewer than 1 / 2);
+ *   tau_trace[trace_cap], sigma2_trace[trace_cap]: the last min(trace_cap, available) values,
+ *   oldest first; *n_trace: values available (<= opts.trace_capacity);
+ *   tau_now, sigma2_now: current hyperparameters.
+ * Errors: GMRF_E_INVALID (field/chain out of range), GMRF_E_STATE, GMRF_E_CUDA.
+ */
+gmrf_status gmrf_fetch_samples(gmrf_sampler *s, int32_t field, int32_t chain, double *x_last,
+                               double *x_mean, double *x_var, int64_t trace_cap,
+                               double *tau_trace, double *sigma2_trace, int64_t *n_trace,
+                               double *tau_now, double *sigma2_now);
+
+/*
+ * Restart the run: state, tau and sigma^2 back to their values at creation, sweep counter back
+ * to opts.start_sweep, accumulators cleared.  Asynchronous (device copies on the sampler's
+ * stream); lets one sampler run many independent MCMC runs of the same data without re-upload.
+ * Errors: GMRF_E_STATE, GMRF_E_CUDA.
+ */
+gmrf_status gmrf_sampler_reset(gmrf_sampler *s);
+
+/*
+ * Diagnostic: enqueue exactly one colour step (the kernel and arguments a sweep uses for
+ * colour class `colour` of every field) on the sampler's stream, without the hyperparameter
+ * draw and without advancing the sweep counter; `accumulate` = 0 skips the running-mean update.
+ * For timing the colour-step kernel in isolation; the state moves on as in a sweep.
+ * Errors: GMRF_E_INVALID (colour out of range), GMRF_E_UNSUPPORTED (plain algorithm),
+ * GMRF_E_STATE, GMRF_E_CUDA.
+ */
+gmrf_status gmrf_launch_colour_step(gmrf_sampler *s, int32_t colour, int32_t accumulate);
+
+/* The colouring a field is sampled with (natural order) and its number of colours. */
+gmrf_status gmrf_field_colors(gmrf_sampler *s, int32_t field, int32_t *colors,
+                              int32_t *num_colors);
+
+/* Sizes and counters of the sampler (synchronises the stream). */
+gmrf_status gmrf_sampler_info(gmrf_sampler *s, gmrf_info *out);
+
+/*
+ * Host-only check of a CSR graph against the rules of gmrf_field_desc (no CUDA call).
+ * Returns GMRF_OK or GMRF_E_INVALID; *components (may be NULL) receives the number of
+ * connected components, which sets the rank n - components of the intrinsic prior.
+ */
+gmrf_status gmrf_validate_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                              const double *weights, int32_t *components);
+
+/*
+ * Diagnostics of the device random-number path (same generators the sweep kernels inline).
+ * gmrf_philox_words: out[4i..4i+3] = Philox4x32-10 of counter (i, c1, c2, c3) under the key
+ *   (seed lo, seed hi), i = 0..count-1.  `out` is a DEVICE pointer of 4*count words.
+ * gmrf_site_normals: out[i] = the normal that updates (site i, chain) at `sweep` of a field
+ *   with stream id `stream`, in the given precision; `out` is a DEVICE pointer of `count`
+ *   floats (GMRF_FP32) or doubles (GMRF_FP64).
+ * Both enqueue on `cuda_stream` and return without synchronising.
+ */
+gmrf_status gmrf_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3,
+                              int64_t count, uint32_t *out, void *cuda_stream);
+gmrf_status gmrf_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream, uint32_t chain,
+                              int32_t precision, int64_t count, void *out, void *cuda_stream);
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char *gmrf_last_error(void);
+
+/* Library version, "major.minor.patch". */
+const char *gmrf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMRF_H */

@@ -1,0 +1,1080 @@
+// api.cu -- the C ABI of libgmrf (include/gmrf.h): argument validation on the host, device
+// memory and layout set-up, the sweep driver (direct launches or captured CUDA graphs), and the
+// copy-out of results.  Every compute step runs in the kernels of sweep_kernels.cu,
+// csr_build.cu and plain.cu; this file only validates, allocates, launches and copies.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gmrf.h"
+#include "gmrf_device.cuh"
+#include "gmrf_internal.h"
+
+using namespace gmrf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gmrf_status fail(gmrf_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+struct CudaFail {
+    cudaError_t err;
+    std::string where;
+};
+
+struct HostField {
+    int32_t kind = 0;
+    int32_t dims[3] = {0, 0, 0};
+    int32_t n = 0;
+    int32_t ncolors = 0;
+    int32_t components = 1;
+    std::vector<int32_t> colors;  // CSR: natural-order colouring used
+};
+
+}  // namespace
+
+struct gmrf_sampler {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    gmrf_model model{};
+    gmrf_opts opts{};
+    int precision = 0, C = 1, Cp = 1, V = 1;
+    int algorithm = GMRF_ALGO_CHROMATIC;
+    int nfields = 0;
+    int kmax = 0;
+    int nparts = 0;
+    int64_t slots = 0;
+    int64_t max_n = 0;
+    std::vector<HostField> hf;
+    std::vector<FieldDev> fd;
+    std::vector<int32_t> tile_off, tile_cnt;  // per colour
+    FieldDev *fields_dev = nullptr;
+    Tile *tiles_dev = nullptr;
+    void *x = nullptr, *y = nullptr, *mean = nullptr, *m2 = nullptr;
+    int32_t *rp = nullptr, *ci = nullptr, *perm = nullptr, *perm_inv = nullptr, *coff = nullptr;
+    void *w = nullptr, *deg = nullptr;
+    double *tau = nullptr, *sig2 = nullptr;
+    void *hyp = nullptr;
+    double2 *partials = nullptr;
+    double *trace_tau = nullptr, *trace_sig = nullptr;
+    SweepCtl *ctl = nullptr;
+    double *staging = nullptr;  // [max_n] doubles for fetch
+    void *x_init = nullptr;     // state at creation (for gmrf_sampler_reset)
+    double *tau_init = nullptr, *sig2_init = nullptr;
+    void *hyp_init = nullptr;
+    size_t x_bytes = 0, hyp_bytes = 0, nh = 0;
+    // plain path
+    PlainArgs plain{};
+    int32_t *plain_colors = nullptr;
+    // graphs: [with_hyper][0: graph_sweeps sweeps, 1: single sweep]
+    cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+    bool poisoned = false;
+    int64_t launches_per_sweep = 0;
+
+    cudaError_t alloc(void **p, size_t b)
+    {
+        *p = nullptr;
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(p, b);
+        if (e == cudaSuccess) {
+            allocs.push_back(*p);
+            bytes += static_cast<int64_t>(b);
+        }
+        return e;
+    }
+    template <typename P> cudaError_t alloc_t(P **p, size_t count, size_t elem)
+    {
+        void *v = nullptr;
+        cudaError_t e = alloc(&v, count * elem);
+        *p = static_cast<P *>(v);
+        return e;
+    }
+    void release()
+    {
+        for (auto &row : exec)
+            for (auto &g : row)
+                if (g) {
+                    cudaGraphExecDestroy(g);
+                    g = nullptr;
+                }
+        for (void *p : allocs) cudaFree(p);
+        allocs.clear();
+        if (capture_stream) cudaStreamDestroy(capture_stream);
+        capture_stream = nullptr;
+    }
+};
+
+namespace {
+
+size_t tsize(int precision) { return precision == GMRF_FP32 ? sizeof(float) : sizeof(double); }
+
+bool finite(double v) { return std::isfinite(v); }
+
+// ---------------------------------------------------------------------------------------------
+// Host validation of a CSR graph: in-range columns, no self-loops, no duplicates, symmetric
+// structure and weights, positive finite weights.  Counts connected components (union-find).
+// ---------------------------------------------------------------------------------------------
+gmrf_status validate_csr(int32_t n, const int32_t *rp, const int32_t *ci, const double *w, int32_t *components)
+{
+    if (n < 1) return fail(GMRF_E_INVALID, "CSR: n must be >= 1");
+    if (!rp || !ci) return fail(GMRF_E_INVALID, "CSR: row_ptr and col_idx are required");
+    if (rp[0] != 0) return fail(GMRF_E_INVALID, "CSR: row_ptr[0] must be 0");
+    for (int32_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) return fail(GMRF_E_INVALID, "CSR: row_ptr must be non-decreasing");
+    const int64_t nnz = rp[n];
+    std::vector<int64_t> keys(static_cast<size_t>(nnz));
+    std::vector<int64_t> order(static_cast<size_t>(nnz));
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+            const int32_t j = ci[e];
+            if (j < 0 || j >= n) return fail(GMRF_E_INVALID, "CSR: column index out of range at row " + std::to_string(i));
+            if (j == i) return fail(GMRF_E_INVALID, "CSR: self-loop at row " + std::to_string(i));
+            if (w && !(finite(w[e]) && w[e] > 0.0))
+                return fail(GMRF_E_INVALID, "CSR: weights must be finite and > 0 (row " + std::to_string(i) + ")");
+            keys[e] = static_cast<int64_t>(i) * n + j;
+        }
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return keys[a] < keys[b]; });
+    for (int64_t k = 1; k < nnz; ++k)
+        if (keys[order[k]] == keys[order[k - 1]]) return fail(GMRF_E_INVALID, "CSR: duplicate entry");
+    std::vector<int64_t> sorted(static_cast<size_t>(nnz));
+    for (int64_t k = 0; k < nnz; ++k) sorted[k] = keys[order[k]];
+    for (int64_t k = 0; k < nnz; ++k) {
+        const int64_t i = sorted[k] / n, j = sorted[k] % n;
+        const int64_t rev = j * n + i;
+        auto it = std::lower_bound(sorted.begin(), sorted.end(), rev);
+        if (it == sorted.end() || *it != rev) return fail(GMRF_E_INVALID, "CSR: graph is not symmetric");
+        if (w && w[order[k]] != w[order[it - sorted.begin()]])
+            return fail(GMRF_E_INVALID, "CSR: weights are not symmetric");
+    }
+    if (components) {
+        std::vector<int32_t> parent(static_cast<size_t>(n));
+        std::iota(parent.begin(), parent.end(), 0);
+        auto find = [&](int32_t v) {
+            while (parent[v] != v) {
+                parent[v] = parent[parent[v]];
+                v = parent[v];
+            }
+            return v;
+        };
+        int32_t comps = n;
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+                const int32_t a = find(i), b = find(ci[e]);
+                if (a != b) {
+                    parent[std::max(a, b)] = std::min(a, b);
+                    --comps;
+                }
+            }
+        *components = comps;
+    }
+    return GMRF_OK;
+}
+
+gmrf_status validate_colors(int32_t n, const int32_t *rp, const int32_t *ci, const int32_t *colors, int32_t *k)
+{
+    int32_t mx = -1;
+    for (int32_t i = 0; i < n; ++i) {
+        if (colors[i] < 0 || colors[i] >= n) return fail(GMRF_E_INVALID, "colors: value out of range");
+        mx = std::max(mx, colors[i]);
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e)
+            if (colors[ci[e]] == colors[i]) return fail(GMRF_E_INVALID, "colors: not a proper colouring");
+    }
+    *k = mx + 1;
+    return GMRF_OK;
+}
+
+int lattice_colour_host(int kind, const int32_t *dims, int64_t site)
+{
+    if (kind == GMRF_LATTICE3D_6) {
+        const int64_t W = dims[2], H = dims[1];
+        return static_cast<int>(((site % W) + ((site / W) % H) + site / (W * H)) & 1);
+    }
+    const int64_t W = dims[1];
+    const int64_t i = site / W, j = site % W;
+    if (kind == GMRF_LATTICE2D_8) return static_cast<int>(2 * (i & 1) + (j & 1));
+    return static_cast<int>((i + j) & 1);
+}
+
+gmrf_status check_model(const gmrf_model *m)
+{
+    if (!m) return fail(GMRF_E_INVALID, "model is NULL");
+    if (m->prior != GMRF_PRIOR_ICAR && m->prior != GMRF_PRIOR_PCAR) return fail(GMRF_E_INVALID, "model.prior");
+    if (m->prior == GMRF_PRIOR_PCAR && !(finite(m->rho) && m->rho >= 0.0 && m->rho < 1.0))
+        return fail(GMRF_E_INVALID, "model.rho must be in [0, 1) for the proper CAR prior");
+    if (!(finite(m->a_tau) && m->a_tau > 0) || !(finite(m->a_sigma) && m->a_sigma > 0))
+        return fail(GMRF_E_INVALID, "model: Gamma shapes a_tau, a_sigma must be > 0");
+    if (!(finite(m->b_tau) && m->b_tau > 0) || !(finite(m->b_sigma) && m->b_sigma > 0))
+        return fail(GMRF_E_INVALID, "model: Gamma rates b_tau, b_sigma must be > 0");
+    if (!(finite(m->tau0) && m->tau0 >= 0) || !(finite(m->sigma2_0) && m->sigma2_0 > 0))
+        return fail(GMRF_E_INVALID, "model: tau0 >= 0 and sigma2_0 > 0 required");
+    return GMRF_OK;
+}
+
+gmrf_status check_opts(const gmrf_opts *o)
+{
+    if (!o) return fail(GMRF_E_INVALID, "opts is NULL");
+    if (o->precision != GMRF_FP32 && o->precision != GMRF_FP64) return fail(GMRF_E_INVALID, "opts.precision");
+    if (o->chains < 1 || o->chains > kMaxChains) return fail(GMRF_E_INVALID, "opts.chains must be in 1..64");
+    if (o->thin < 1) return fail(GMRF_E_INVALID, "opts.thin must be >= 1");
+    if (o->trace_capacity < 1) return fail(GMRF_E_INVALID, "opts.trace_capacity must be >= 1");
+    if (o->start_sweep < 0) return fail(GMRF_E_INVALID, "opts.start_sweep must be >= 0");
+    if (o->graph_sweeps < 0) return fail(GMRF_E_INVALID, "opts.graph_sweeps must be >= 0");
+    if (o->algorithm != GMRF_ALGO_CHROMATIC && o->algorithm != GMRF_ALGO_PLAIN)
+        return fail(GMRF_E_INVALID, "opts.algorithm");
+    return GMRF_OK;
+}
+
+gmrf_status check_field(const gmrf_field_desc &f, int idx, int chains, HostField &h)
+{
+    const std::string at = "field " + std::to_string(idx) + ": ";
+    h.kind = f.kind;
+    if (f.kind < GMRF_LATTICE2D_4 || f.kind > GMRF_CSR) return fail(GMRF_E_INVALID, at + "unknown kind");
+    if (f.kind == GMRF_CSR) {
+        h.n = f.n;
+        h.dims[0] = f.n;
+        gmrf_status st = validate_csr(f.n, f.row_ptr, f.col_idx, f.weights, &h.components);
+        if (st != GMRF_OK) return fail(st, at + g_last_error);
+        if (f.colors) {
+            int32_t k = 0;
+            st = validate_colors(f.n, f.row_ptr, f.col_idx, f.colors, &k);
+            if (st != GMRF_OK) return fail(st, at + g_last_error);
+            h.ncolors = k;
+            h.colors.assign(f.colors, f.colors + f.n);
+        }
+    } else {
+        const int nd = f.kind == GMRF_LATTICE3D_6 ? 3 : 2;
+        int64_t prod = 1;
+        for (int d = 0; d < nd; ++d) {
+            if (f.dims[d] < 1) return fail(GMRF_E_INVALID, at + "lattice dims must be >= 1");
+            h.dims[d] = f.dims[d];
+            prod *= f.dims[d];
+        }
+        if (prod >= (int64_t(1) << 31)) return fail(GMRF_E_INVALID, at + "lattice has too many sites");
+        if (f.n != prod) return fail(GMRF_E_INVALID, at + "n must equal the product of dims");
+        h.n = f.n;
+        h.ncolors = f.kind == GMRF_LATTICE2D_8 ? 4 : 2;
+        h.components = 1;
+    }
+    if (!f.y) return fail(GMRF_E_INVALID, at + "y is required");
+    for (int32_t i = 0; i < h.n; ++i)
+        if (!finite(f.y[i])) return fail(GMRF_E_INVALID, at + "y must be finite");
+    if (f.x0)
+        for (int64_t i = 0; i < static_cast<int64_t>(h.n) * chains; ++i)
+            if (!finite(f.x0[i])) return fail(GMRF_E_INVALID, at + "x0 must be finite");
+    if (f.tau0)
+        for (int c = 0; c < chains; ++c)
+            if (!(finite(f.tau0[c]) && f.tau0[c] >= 0)) return fail(GMRF_E_INVALID, at + "tau0 must be >= 0");
+    if (f.sigma2_0)
+        for (int c = 0; c < chains; ++c)
+            if (!(finite(f.sigma2_0[c]) && f.sigma2_0[c] > 0))
+                return fail(GMRF_E_INVALID, at + "sigma2_0 must be > 0");
+    return GMRF_OK;
+}
+
+#define CK(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t _e = (call);                                                                      \
+        if (_e != cudaSuccess) throw CudaFail{_e, #call};                                             \
+    } while (0)
+
+gmrf_status cuda_status(const CudaFail &f)
+{
+    const gmrf_status st = (f.err == cudaErrorMemoryAllocation) ? GMRF_E_OOM : GMRF_E_CUDA;
+    return fail(st, std::string("CUDA error ") + cudaGetErrorString(f.err) + " in " + f.where);
+}
+
+int pow2_at_least(int c)
+{
+    int p = 1;
+    while (p < c) p <<= 1;
+    return p;
+}
+
+// Upload n doubles from the host into a fresh temporary device buffer (freed by the caller).
+double *upload(const double *h, int64_t n, cudaStream_t st, std::vector<void *> &tmp)
+{
+    void *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(double) * static_cast<size_t>(n > 0 ? n : 1)));
+    tmp.push_back(d);
+    CK(cudaMemcpyAsync(d, h, sizeof(double) * static_cast<size_t>(n), cudaMemcpyHostToDevice, st));
+    return static_cast<double *>(d);
+}
+
+template <typename P> P *upload_t(const P *h, int64_t n, cudaStream_t st, std::vector<void *> &tmp)
+{
+    void *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(P) * static_cast<size_t>(n > 0 ? n : 1)));
+    tmp.push_back(d);
+    if (n > 0) CK(cudaMemcpyAsync(d, h, sizeof(P) * static_cast<size_t>(n), cudaMemcpyHostToDevice, st));
+    return static_cast<P *>(d);
+}
+
+void free_tmp(std::vector<void *> &tmp)
+{
+    for (void *p : tmp) cudaFree(p);
+    tmp.clear();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Sweep launches
+// ---------------------------------------------------------------------------------------------
+StepArgs step_args(gmrf_sampler *s, int colour, int update, int accumulate = 1)
+{
+    StepArgs a{};
+    a.fields = s->fields_dev;
+    a.tiles = s->tiles_dev + s->tile_off[colour];
+    a.ntiles = s->tile_cnt[colour];
+    a.colour = colour;
+    a.x = s->x;
+    a.y = s->y;
+    a.mean = s->mean;
+    a.m2 = s->m2;
+    a.rp = s->rp;
+    a.ci = s->ci;
+    a.w = s->w;
+    a.deg = s->deg;
+    a.perm = s->perm;
+    a.coff = s->coff;
+    a.hyp = s->hyp;
+    a.partials = s->partials;
+    a.ctl = s->ctl;
+    a.key = philox_key(s->opts.seed);
+    a.Cp = s->Cp;
+    a.rho = s->model.prior == GMRF_PRIOR_PCAR ? s->model.rho : 1.0;
+    a.burn_in = s->opts.burn_in;
+    a.thin = s->opts.thin;
+    a.acc_enabled = accumulate;
+    a.update = update;
+    return a;
+}
+
+HyperArgs hyper_args(gmrf_sampler *s, int draw, int end_of_sweep)
+{
+    HyperArgs h{};
+    h.fields = s->fields_dev;
+    h.nfields = s->nfields;
+    h.Cp = s->Cp;
+    h.partials = s->partials;
+    h.tau = s->tau;
+    h.sig2 = s->sig2;
+    h.hyp = s->hyp;
+    h.trace_tau = s->trace_tau;
+    h.trace_sig = s->trace_sig;
+    h.trace_cap = s->opts.trace_capacity;
+    h.ctl = s->ctl;
+    h.key = philox_key(s->opts.seed);
+    h.a_tau = s->model.a_tau;
+    h.b_tau = s->model.b_tau;
+    h.a_sig = s->model.a_sigma;
+    h.b_sig = s->model.b_sigma;
+    h.draw = draw;
+    h.end_of_sweep = end_of_sweep;
+    h.burn_in = s->opts.burn_in;
+    h.thin = s->opts.thin;
+    h.acc_enabled = 1;
+    return h;
+}
+
+cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int draw, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < nsweeps && e == cudaSuccess; ++k) {
+        if (s->algorithm == GMRF_ALGO_PLAIN) {
+            PlainArgs a = s->plain;
+            a.draw = draw;
+            int64_t l = 0;
+            e = launch_plain_sweep(a, st, &l);
+            continue;
+        }
+        for (int c = 0; c < s->kmax && e == cudaSuccess; ++c)
+            e = launch_colour_step(s->precision, s->V, step_args(s, c, 1), st);
+        if (e == cudaSuccess) e = launch_hyper(s->precision, hyper_args(s, draw, 1), st);
+    }
+    return e;
+}
+
+cudaError_t get_graph(gmrf_sampler *s, int draw, int which, int nsweeps, cudaGraphExec_t *out)
+{
+    if (s->exec[draw][which]) {
+        *out = s->exec[draw][which];
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaStreamBeginCapture(s->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = enqueue_sweeps(s, nsweeps, draw, s->capture_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s->capture_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return le;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&s->exec[draw][which], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    *out = s->exec[draw][which];
+    return cudaSuccess;
+}
+
+gmrf_status poison(gmrf_sampler *s, cudaError_t e, const char *where)
+{
+    s->poisoned = true;
+    return cuda_status(CudaFail{e, where});
+}
+
+gmrf_status build_plain(gmrf_sampler *s, const gmrf_field_desc &f, std::vector<void *> &tmp)
+{
+    HostField &h = s->hf[0];
+    const int64_t n = h.n;
+    PlainArgs &a = s->plain;
+    a.n = h.n;
+    a.kind = h.kind;
+    for (int d = 0; d < 3; ++d) a.dims[d] = h.dims[d];
+    a.C = s->C;
+    a.rho = s->model.prior == GMRF_PRIOR_PCAR ? s->model.rho : 1.0;
+    a.rank = s->model.prior == GMRF_PRIOR_PCAR ? h.n : h.n - h.components;
+    a.a_tau = s->model.a_tau;
+    a.b_tau = s->model.b_tau;
+    a.a_sig = s->model.a_sigma;
+    a.b_sig = s->model.b_sigma;
+    a.key = philox_key(s->opts.seed);
+    a.stream_id = f.stream_id;
+    a.trace_cap = s->opts.trace_capacity;
+    a.ncolors = h.ncolors;
+    double *x = nullptr, *y = nullptr;
+    CK(s->alloc_t(&x, static_cast<size_t>(n) * s->C, sizeof(double)));
+    CK(s->alloc_t(&y, static_cast<size_t>(n), sizeof(double)));
+    CK(cudaMemcpyAsync(y, f.y, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+    for (int c = 0; c < s->C; ++c)
+        CK(cudaMemcpyAsync(x + c * n, f.x0 ? f.x0 + c * n : f.y, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+    a.x = x;
+    a.y = y;
+    if (h.kind == GMRF_CSR) {
+        int32_t *rp = nullptr, *ci = nullptr;
+        const int64_t nnz = f.row_ptr[h.n];
+        CK(s->alloc_t(&rp, static_cast<size_t>(n + 1), sizeof(int32_t)));
+        CK(s->alloc_t(&ci, static_cast<size_t>(nnz), sizeof(int32_t)));
+        CK(cudaMemcpyAsync(rp, f.row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s->stream));
+        CK(cudaMemcpyAsync(ci, f.col_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s->stream));
+        a.rp = rp;
+        a.ci = ci;
+        if (f.weights) {
+            double *w = nullptr;
+            CK(s->alloc_t(&w, static_cast<size_t>(nnz), sizeof(double)));
+            CK(cudaMemcpyAsync(w, f.weights, sizeof(double) * nnz, cudaMemcpyHostToDevice, s->stream));
+            a.w = w;
+        }
+        CK(s->alloc_t(&s->plain_colors, static_cast<size_t>(n), sizeof(int32_t)));
+        if (h.colors.empty()) {
+            void *scratch = nullptr;
+            CK(cudaMalloc(&scratch, jp_scratch_bytes(h.n)));
+            tmp.push_back(scratch);
+            int32_t k = 0;
+            CK(jp_color(h.n, rp, ci, nullptr, f.color_seed, s->plain_colors, scratch, &k, s->stream));
+            h.ncolors = k;
+            a.ncolors = k;
+            h.colors.resize(static_cast<size_t>(n));
+            CK(cudaMemcpyAsync(h.colors.data(), s->plain_colors, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s->stream));
+        } else {
+            CK(cudaMemcpyAsync(s->plain_colors, h.colors.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s->stream));
+        }
+        a.colors = s->plain_colors;
+    }
+    CK(s->alloc_t(&a.tau, static_cast<size_t>(s->C), sizeof(double)));
+    CK(s->alloc_t(&a.sig2, static_cast<size_t>(s->C), sizeof(double)));
+    std::vector<double> t0(s->C), s0(s->C);
+    for (int c = 0; c < s->C; ++c) {
+        t0[c] = f.tau0 ? f.tau0[c] : s->model.tau0;
+        s0[c] = f.sigma2_0 ? f.sigma2_0[c] : s->model.sigma2_0;
+    }
+    CK(cudaMemcpyAsync(a.tau, t0.data(), sizeof(double) * s->C, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(a.sig2, s0.data(), sizeof(double) * s->C, cudaMemcpyHostToDevice, s->stream));
+    CK(s->alloc_t(&a.trace_tau, static_cast<size_t>(s->C) * s->opts.trace_capacity, sizeof(double)));
+    CK(s->alloc_t(&a.trace_sig, static_cast<size_t>(s->C) * s->opts.trace_capacity, sizeof(double)));
+    s->nh = static_cast<size_t>(s->C);
+    s->x_bytes = sizeof(double) * static_cast<size_t>(n) * s->C;
+    CK(s->alloc(&s->x_init, s->x_bytes));
+    CK(cudaMemcpyAsync(s->x_init, x, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
+    CK(s->alloc_t(&s->tau_init, s->nh, sizeof(double)));
+    CK(s->alloc_t(&s->sig2_init, s->nh, sizeof(double)));
+    CK(cudaMemcpyAsync(s->tau_init, a.tau, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->sig2_init, a.sig2, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    CK(s->alloc_t(&a.red, static_cast<size_t>(s->C) * 2, sizeof(double)));
+    CK(cudaMemsetAsync(a.red, 0, sizeof(double) * 2 * s->C, s->stream));
+    a.ctl = s->ctl;
+    s->kmax = h.ncolors;
+    s->launches_per_sweep = h.ncolors + (s->model.fix_hyper ? 1 : 2);
+    s->tau = a.tau;
+    s->sig2 = a.sig2;
+    s->trace_tau = a.trace_tau;
+    s->trace_sig = a.trace_sig;
+    return GMRF_OK;
+}
+
+gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std::vector<void *> &tmp)
+{
+    const size_t T = tsize(s->precision);
+    // Field geometry and offsets.
+    int64_t slots = 0, csr_sites = 0, csr_rp = 0, csr_nnz = 0, coff_n = 0;
+    bool any_weights = false;
+    s->fd.resize(s->nfields);
+    for (int fi = 0; fi < s->nfields; ++fi) {
+        HostField &h = s->hf[fi];
+        FieldDev &d = s->fd[fi];
+        std::memset(&d, 0, sizeof(d));
+        d.kind = h.kind;
+        d.n = h.n;
+        d.stream = fields[fi].stream_id;
+        for (int k = 0; k < 3; ++k) d.dims[k] = h.dims[k];
+        d.rank = s->model.prior == GMRF_PRIOR_PCAR ? h.n : h.n - h.components;
+        d.slot0 = slots;
+        if (h.kind == GMRF_CSR) {
+            d.nslots = h.n;
+            d.csr0 = csr_sites;
+            d.rp0 = csr_rp;
+            d.nnz0 = csr_nnz;
+            d.coff0 = coff_n;
+            csr_sites += h.n;
+            csr_rp += h.n + 1;
+            csr_nnz += fields[fi].row_ptr[h.n];
+            coff_n += std::max<int64_t>(h.n, 1) + 1;  // room for up to n colours
+            any_weights = any_weights || fields[fi].weights;
+        } else {
+            if (h.kind == GMRF_LATTICE2D_8) {
+                d.rows = (h.dims[0] + 1) / 2;
+                d.cols = (h.dims[1] + 1) / 2;
+            } else if (h.kind == GMRF_LATTICE3D_6) {
+                d.rows = h.dims[0] * h.dims[1];
+                d.cols = (h.dims[2] + 1) / 2;
+            } else {
+                d.rows = h.dims[0];
+                d.cols = (h.dims[1] + 1) / 2;
+            }
+            d.ncolors = h.ncolors;
+            d.nslots = static_cast<int64_t>(h.ncolors) * d.rows * d.cols;
+        }
+        slots += d.nslots;
+        s->max_n = std::max<int64_t>(s->max_n, h.n);
+    }
+    if (csr_nnz >= (int64_t(1) << 31)) return fail(GMRF_E_INVALID, "total CSR entries must be < 2^31");
+    s->slots = slots;
+    const size_t Cp = static_cast<size_t>(s->Cp);
+    CK(s->alloc(&s->x, static_cast<size_t>(slots) * Cp * T));
+    CK(s->alloc(&s->y, static_cast<size_t>(slots) * T));
+    CK(s->alloc(&s->mean, static_cast<size_t>(slots) * Cp * T));
+    CK(s->alloc(&s->m2, static_cast<size_t>(slots) * Cp * T));
+    CK(cudaMemsetAsync(s->x, 0, static_cast<size_t>(slots) * Cp * T, s->stream));
+    CK(cudaMemsetAsync(s->y, 0, static_cast<size_t>(slots) * T, s->stream));
+    CK(cudaMemsetAsync(s->mean, 0, static_cast<size_t>(slots) * Cp * T, s->stream));
+    CK(cudaMemsetAsync(s->m2, 0, static_cast<size_t>(slots) * Cp * T, s->stream));
+    if (csr_sites > 0) {
+        CK(s->alloc_t(&s->rp, static_cast<size_t>(csr_rp), sizeof(int32_t)));
+        CK(s->alloc_t(&s->ci, static_cast<size_t>(csr_nnz), sizeof(int32_t)));
+        CK(s->alloc_t(&s->perm, static_cast<size_t>(csr_sites), sizeof(int32_t)));
+        CK(s->alloc_t(&s->perm_inv, static_cast<size_t>(csr_sites), sizeof(int32_t)));
+        CK(s->alloc_t(&s->coff, static_cast<size_t>(coff_n), sizeof(int32_t)));
+        CK(s->alloc(&s->deg, static_cast<size_t>(csr_sites) * T));
+        if (any_weights) CK(s->alloc(&s->w, static_cast<size_t>(csr_nnz) * T));
+    }
+    CK(s->alloc_t(&s->fields_dev, static_cast<size_t>(s->nfields), sizeof(FieldDev)));
+
+    // CSR fields: upload, colour (JP unless given), colour-permuted layout.
+    std::vector<std::vector<int32_t>> coff_host(s->nfields);
+    for (int fi = 0; fi < s->nfields; ++fi) {
+        HostField &h = s->hf[fi];
+        FieldDev &d = s->fd[fi];
+        if (h.kind != GMRF_CSR) continue;
+        const gmrf_field_desc &f = fields[fi];
+        const int64_t nnz = f.row_ptr[h.n];
+        int32_t *rp_d = upload_t(f.row_ptr, h.n + 1, s->stream, tmp);
+        int32_t *ci_d = upload_t(f.col_idx, nnz, s->stream, tmp);
+        double *w_d = f.weights ? upload(f.weights, nnz, s->stream, tmp) : nullptr;
+        int32_t *col_d = nullptr;
+        {
+            void *p = nullptr;
+            CK(cudaMalloc(&p, sizeof(int32_t) * h.n));
+            tmp.push_back(p);
+            col_d = static_cast<int32_t *>(p);
+        }
+        if (h.colors.empty()) {
+            void *scratch = nullptr;
+            CK(cudaMalloc(&scratch, jp_scratch_bytes(h.n)));
+            tmp.push_back(scratch);
+            int32_t k = 0;
+            CK(jp_color(h.n, rp_d, ci_d, nullptr, f.color_seed, col_d, scratch, &k, s->stream));
+            h.ncolors = k;
+            h.colors.resize(h.n);
+            CK(cudaMemcpyAsync(h.colors.data(), col_d, sizeof(int32_t) * h.n, cudaMemcpyDeviceToHost, s->stream));
+        } else {
+            CK(cudaMemcpyAsync(col_d, h.colors.data(), sizeof(int32_t) * h.n, cudaMemcpyHostToDevice, s->stream));
+        }
+        if (h.ncolors > 1024) return fail(GMRF_E_UNSUPPORTED, "CSR colouring with more than 1024 colours");
+        d.ncolors = h.ncolors;
+        void *scratch = nullptr;
+        CK(cudaMalloc(&scratch, layout_scratch_bytes(h.n, h.ncolors)));
+        tmp.push_back(scratch);
+        char *wbase = any_weights && f.weights ? static_cast<char *>(s->w) + d.nnz0 * T : nullptr;
+        CK(csr_layout(s->precision, h.n, h.ncolors, rp_d, ci_d, w_d, col_d, scratch, s->perm + d.csr0,
+                      s->perm_inv + d.csr0, s->coff + d.coff0, s->rp + d.rp0, s->ci + d.nnz0, wbase,
+                      static_cast<char *>(s->deg) + d.csr0 * T, s->stream));
+        coff_host[fi].resize(h.ncolors + 1);
+        CK(cudaMemcpyAsync(coff_host[fi].data(), s->coff + d.coff0, sizeof(int32_t) * (h.ncolors + 1),
+                           cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        if (!f.weights && any_weights) {
+            // Unit weights for this field inside a batch where another field has weights.
+            std::vector<char> ones(static_cast<size_t>(nnz) * T);
+            for (int64_t k = 0; k < nnz; ++k) {
+                if (s->precision == GMRF_FP32) reinterpret_cast<float *>(ones.data())[k] = 1.0f;
+                else reinterpret_cast<double *>(ones.data())[k] = 1.0;
+            }
+            CK(cudaMemcpyAsync(static_cast<char *>(s->w) + d.nnz0 * T, ones.data(), ones.size(), cudaMemcpyHostToDevice,
+                               s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+        }
+    }
+
+    // Tiles: per colour, each field's colour class cut into tiles of about 2048 (site, chain
+    // vector) elements; partial-sum slots are contiguous per field.
+    const int CV = s->Cp / s->V;
+    const int64_t target = 2048;
+    s->kmax = 0;
+    for (auto &h : s->hf) s->kmax = std::max(s->kmax, h.ncolors);
+    std::vector<std::vector<Tile>> by_colour(s->kmax);
+    int part = 0;
+    for (int fi = 0; fi < s->nfields; ++fi) {
+        FieldDev &d = s->fd[fi];
+        d.part0 = part;
+        for (int c = 0; c < d.ncolors; ++c) {
+            if (d.kind == GMRF_CSR) {
+                const int32_t lo = coff_host[fi][c], hi = coff_host[fi][c + 1];
+                const int64_t per = std::max<int64_t>(1, target / CV);
+                for (int64_t st = lo; st < hi; st += per) {
+                    Tile t{};
+                    t.field = fi;
+                    t.colour = c;
+                    t.start = static_cast<int32_t>(st);
+                    t.count = static_cast<int32_t>(std::min<int64_t>(per, hi - st));
+                    t.part = part++;
+                    by_colour[c].push_back(t);
+                }
+            } else {
+                const int64_t per = std::max<int64_t>(1, target / (static_cast<int64_t>(d.cols) * CV));
+                for (int64_t st = 0; st < d.rows; st += per) {
+                    Tile t{};
+                    t.field = fi;
+                    t.colour = c;
+                    t.start = static_cast<int32_t>(st);
+                    t.count = static_cast<int32_t>(std::min<int64_t>(per, d.rows - st));
+                    t.part = part++;
+                    by_colour[c].push_back(t);
+                }
+            }
+        }
+        d.nparts = part - d.part0;
+    }
+    s->nparts = part;
+    std::vector<Tile> all;
+    s->tile_off.assign(s->kmax, 0);
+    s->tile_cnt.assign(s->kmax, 0);
+    for (int c = 0; c < s->kmax; ++c) {
+        s->tile_off[c] = static_cast<int32_t>(all.size());
+        s->tile_cnt[c] = static_cast<int32_t>(by_colour[c].size());
+        all.insert(all.end(), by_colour[c].begin(), by_colour[c].end());
+    }
+    CK(s->alloc_t(&s->tiles_dev, std::max<size_t>(all.size(), 1), sizeof(Tile)));
+    if (!all.empty())
+        CK(cudaMemcpyAsync(s->tiles_dev, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice, s->stream));
+    CK(s->alloc_t(&s->partials, static_cast<size_t>(std::max(part, 1)) * Cp, sizeof(double2)));
+    CK(cudaMemsetAsync(s->partials, 0, static_cast<size_t>(std::max(part, 1)) * Cp * sizeof(double2), s->stream));
+    CK(cudaMemcpyAsync(s->fields_dev, s->fd.data(), sizeof(FieldDev) * s->nfields, cudaMemcpyHostToDevice, s->stream));
+
+    // y and x0 into the colour-split layout.
+    for (int fi = 0; fi < s->nfields; ++fi) {
+        const gmrf_field_desc &f = fields[fi];
+        const HostField &h = s->hf[fi];
+        double *y_d = upload(f.y, h.n, s->stream, tmp);
+        double *x0_d = f.x0 ? upload(f.x0, static_cast<int64_t>(h.n) * s->C, s->stream, tmp) : nullptr;
+        CK(launch_pack(s->precision, s->fields_dev, s->fd[fi], fi, s->C, s->Cp, y_d, x0_d, s->perm_inv, s->x, s->y,
+                       s->stream));
+    }
+
+    // Hyperparameters and their precision-T copies.
+    const size_t nh = static_cast<size_t>(s->nfields) * Cp;
+    std::vector<double> t0(nh), s0(nh);
+    std::vector<char> hypT(nh * 2 * T);
+    for (int fi = 0; fi < s->nfields; ++fi)
+        for (int c = 0; c < s->Cp; ++c) {
+            const size_t k = static_cast<size_t>(fi) * Cp + c;
+            const gmrf_field_desc &f = fields[fi];
+            t0[k] = (f.tau0 && c < s->C) ? f.tau0[c] : s->model.tau0;
+            s0[k] = (f.sigma2_0 && c < s->C) ? f.sigma2_0[c] : s->model.sigma2_0;
+            if (s->precision == GMRF_FP32) {
+                reinterpret_cast<float *>(hypT.data())[2 * k] = static_cast<float>(t0[k]);
+                reinterpret_cast<float *>(hypT.data())[2 * k + 1] = static_cast<float>(1.0 / s0[k]);
+            } else {
+                reinterpret_cast<double *>(hypT.data())[2 * k] = t0[k];
+                reinterpret_cast<double *>(hypT.data())[2 * k + 1] = 1.0 / s0[k];
+            }
+        }
+    CK(s->alloc_t(&s->tau, nh, sizeof(double)));
+    CK(s->alloc_t(&s->sig2, nh, sizeof(double)));
+    CK(s->alloc(&s->hyp, nh * 2 * T));
+    CK(cudaMemcpyAsync(s->tau, t0.data(), nh * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->sig2, s0.data(), nh * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->hyp, hypT.data(), hypT.size(), cudaMemcpyHostToDevice, s->stream));
+    CK(s->alloc_t(&s->trace_tau, nh * s->opts.trace_capacity, sizeof(double)));
+    CK(s->alloc_t(&s->trace_sig, nh * s->opts.trace_capacity, sizeof(double)));
+    // Initial state kept for gmrf_sampler_reset.
+    s->nh = nh;
+    s->x_bytes = static_cast<size_t>(slots) * Cp * T;
+    s->hyp_bytes = nh * 2 * T;
+    CK(s->alloc(&s->x_init, s->x_bytes));
+    CK(cudaMemcpyAsync(s->x_init, s->x, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
+    CK(s->alloc_t(&s->tau_init, nh, sizeof(double)));
+    CK(s->alloc_t(&s->sig2_init, nh, sizeof(double)));
+    CK(s->alloc(&s->hyp_init, s->hyp_bytes));
+    CK(cudaMemcpyAsync(s->tau_init, s->tau, nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->sig2_init, s->sig2, nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->hyp_init, s->hyp, s->hyp_bytes, cudaMemcpyDeviceToDevice, s->stream));
+    s->launches_per_sweep = s->kmax + 1;
+    CK(cudaStreamSynchronize(s->stream));
+    return GMRF_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+extern "C" {
+
+const char *gmrf_last_error(void) { return g_last_error.c_str(); }
+
+const char *gmrf_version(void) { return "0.1.0"; }
+
+gmrf_status gmrf_validate_csr(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const double *weights,
+                              int32_t *components)
+{
+    g_last_error.clear();
+    return validate_csr(n, row_ptr, col_idx, weights, components);
+}
+
+gmrf_status gmrf_color_graph(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const uint32_t *priorities,
+                             uint64_t seed, int32_t *colors, int32_t *num_colors)
+{
+    g_last_error.clear();
+    if (!colors || !num_colors) return fail(GMRF_E_INVALID, "colors and num_colors are required");
+    gmrf_status st = validate_csr(n, row_ptr, col_idx, nullptr, nullptr);
+    if (st != GMRF_OK) return st;
+    std::vector<void *> tmp;
+    try {
+        cudaStream_t stream = nullptr;
+        int32_t *rp = upload_t(row_ptr, n + 1, stream, tmp);
+        int32_t *ci = upload_t(col_idx, row_ptr[n], stream, tmp);
+        uint32_t *pr = priorities ? upload_t(priorities, n, stream, tmp) : nullptr;
+        void *col = nullptr, *scratch = nullptr;
+        CK(cudaMalloc(&col, sizeof(int32_t) * n));
+        tmp.push_back(col);
+        CK(cudaMalloc(&scratch, jp_scratch_bytes(n)));
+        tmp.push_back(scratch);
+        int32_t k = 0;
+        CK(jp_color(n, rp, ci, pr, seed, static_cast<int32_t *>(col), scratch, &k, stream));
+        CK(cudaMemcpy(colors, col, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        *num_colors = k;
+    } catch (const CudaFail &f) {
+        free_tmp(tmp);
+        return cuda_status(f);
+    }
+    free_tmp(tmp);
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_sampler_create(gmrf_sampler **out, const gmrf_field_desc *fields, int32_t nfields,
+                                const gmrf_model *model, const gmrf_opts *opts, void *cuda_stream)
+{
+    g_last_error.clear();
+    if (!out) return fail(GMRF_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!fields || nfields < 1) return fail(GMRF_E_INVALID, "at least one field is required");
+    gmrf_status st = check_model(model);
+    if (st != GMRF_OK) return st;
+    if ((st = check_opts(opts)) != GMRF_OK) return st;
+    std::vector<HostField> hf(nfields);
+    for (int i = 0; i < nfields; ++i)
+        if ((st = check_field(fields[i], i, opts->chains, hf[i])) != GMRF_OK) return st;
+    if (opts->algorithm == GMRF_ALGO_PLAIN && (nfields != 1 || opts->precision != GMRF_FP64))
+        return fail(GMRF_E_UNSUPPORTED, "the plain sweep takes exactly one field in FP64");
+
+    gmrf_sampler *s = new gmrf_sampler();
+    s->model = *model;
+    s->opts = *opts;
+    s->precision = opts->precision;
+    s->C = opts->chains;
+    s->Cp = pow2_at_least(opts->chains);
+    s->V = std::min(s->Cp, opts->precision == GMRF_FP32 ? 4 : 2);
+    s->algorithm = opts->algorithm;
+    s->nfields = nfields;
+    s->hf = std::move(hf);
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    std::vector<void *> tmp;
+    try {
+        CK(cudaGetDevice(&s->device));
+        CK(cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking));
+        CK(s->alloc_t(&s->ctl, 1, sizeof(SweepCtl)));
+        SweepCtl c0{};
+        c0.sweep = opts->start_sweep;
+        CK(cudaMemcpyAsync(s->ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, s->stream));
+        if (s->algorithm == GMRF_ALGO_PLAIN) st = build_plain(s, fields[0], tmp);
+        else st = build_chromatic(s, fields, tmp);
+        if (st == GMRF_OK) {
+            s->max_n = 0;
+            for (auto &h : s->hf) s->max_n = std::max<int64_t>(s->max_n, h.n);
+            CK(s->alloc_t(&s->staging, static_cast<size_t>(s->max_n), sizeof(double)));
+            CK(cudaStreamSynchronize(s->stream));
+        }
+    } catch (const CudaFail &f) {
+        st = cuda_status(f);
+    }
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    free_tmp(tmp);
+    if (st != GMRF_OK) {
+        const std::string msg = g_last_error;
+        s->release();
+        delete s;
+        g_last_error = msg;
+        return st;
+    }
+    *out = s;
+    return GMRF_OK;
+}
+
+void gmrf_sampler_destroy(gmrf_sampler *s)
+{
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    s->release();
+    delete s;
+}
+
+gmrf_status gmrf_sweep(gmrf_sampler *s, int32_t nsweeps, int32_t with_hyper)
+{
+    g_last_error.clear();
+    if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
+    if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (nsweeps < 0) return fail(GMRF_E_INVALID, "nsweeps must be >= 0");
+    const int draw = (with_hyper && !s->model.fix_hyper) ? 1 : 0;
+    cudaError_t e = cudaSuccess;
+    const int G = s->opts.graph_sweeps;
+    if (G <= 0) {
+        e = enqueue_sweeps(s, nsweeps, draw, s->stream);
+        if (e != cudaSuccess) return poison(s, e, "sweep launch");
+        return GMRF_OK;
+    }
+    int remaining = nsweeps;
+    if (remaining >= G) {
+        cudaGraphExec_t g = nullptr;
+        if ((e = get_graph(s, draw, 0, G, &g)) != cudaSuccess) return poison(s, e, "graph capture");
+        while (remaining >= G) {
+            if ((e = cudaGraphLaunch(g, s->stream)) != cudaSuccess) return poison(s, e, "graph launch");
+            remaining -= G;
+        }
+    }
+    if (remaining > 0) {
+        cudaGraphExec_t g1 = nullptr;
+        if ((e = get_graph(s, draw, 1, 1, &g1)) != cudaSuccess) return poison(s, e, "graph capture");
+        for (; remaining > 0; --remaining)
+            if ((e = cudaGraphLaunch(g1, s->stream)) != cudaSuccess) return poison(s, e, "graph launch");
+    }
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_hyper_update(gmrf_sampler *s)
+{
+    g_last_error.clear();
+    if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
+    if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "hyper_update on the plain sweep");
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < s->kmax && e == cudaSuccess; ++c)
+        e = launch_colour_step(s->precision, s->V, step_args(s, c, 0), s->stream);
+    if (e == cudaSuccess) e = launch_hyper(s->precision, hyper_args(s, 1, 0), s->stream);
+    if (e != cudaSuccess) return poison(s, e, "hyper update launch");
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_fetch_samples(gmrf_sampler *s, int32_t field, int32_t chain, double *x_last, double *x_mean,
+                               double *x_var, int64_t trace_cap, double *tau_trace, double *sigma2_trace,
+                               int64_t *n_trace, double *tau_now, double *sigma2_now)
+{
+    g_last_error.clear();
+    if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
+    if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (field < 0 || field >= s->nfields || chain < 0 || chain >= s->C)
+        return fail(GMRF_E_INVALID, "field or chain out of range");
+    if (trace_cap < 0) return fail(GMRF_E_INVALID, "trace_cap must be >= 0");
+    const HostField &h = s->hf[field];
+    const int64_t n = h.n;
+    try {
+        SweepCtl c{};
+        CK(cudaMemcpyAsync(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        const bool plain = s->algorithm == GMRF_ALGO_PLAIN;
+        const int64_t k = plain ? 0 : c.acc_count;
+        auto fetch = [&](const void *src, const void *m2, double scale, double *dst) {
+            if (plain) {
+                CK(cudaMemcpyAsync(dst, s->plain.x + chain * n, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+                return;
+            }
+            CK(launch_unpack(s->precision, s->fields_dev, s->fd[field], field, s->Cp, chain, src, m2, scale, s->perm_inv,
+                             s->staging, s->stream));
+            CK(cudaMemcpyAsync(dst, s->staging, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+        };
+        if (x_last) fetch(s->x, nullptr, 1.0, x_last);
+        if (x_mean) {
+            if (plain || k < 1) std::fill(x_mean, x_mean + n, plain ? NAN : 0.0);
+            else fetch(s->mean, nullptr, 1.0, x_mean);
+        }
+        if (x_var) {
+            if (plain || k < 2) std::fill(x_var, x_var + n, NAN);
+            else fetch(nullptr, s->m2, 1.0 / static_cast<double>(k - 1), x_var);
+        }
+        const int64_t cap = s->opts.trace_capacity;
+        const int64_t avail = std::min<int64_t>(c.sweep - s->opts.start_sweep, cap);
+        if (n_trace) *n_trace = avail;
+        const int64_t hc = plain ? chain : static_cast<int64_t>(field) * s->Cp + chain;
+        if ((tau_trace || sigma2_trace) && trace_cap > 0 && avail > 0) {
+            std::vector<double> rt(static_cast<size_t>(cap)), rs(static_cast<size_t>(cap));
+            CK(cudaMemcpyAsync(rt.data(), s->trace_tau + hc * cap, sizeof(double) * cap, cudaMemcpyDeviceToHost, s->stream));
+            CK(cudaMemcpyAsync(rs.data(), s->trace_sig + hc * cap, sizeof(double) * cap, cudaMemcpyDeviceToHost, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+            const int64_t m = std::min(trace_cap, avail);
+            for (int64_t q = 0; q < m; ++q) {
+                const int64_t sw = c.sweep - m + q;
+                if (tau_trace) tau_trace[q] = rt[sw % cap];
+                if (sigma2_trace) sigma2_trace[q] = rs[sw % cap];
+            }
+        }
+        if (tau_now) CK(cudaMemcpyAsync(tau_now, s->tau + hc, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        if (sigma2_now) CK(cudaMemcpyAsync(sigma2_now, s->sig2 + hc, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    } catch (const CudaFail &f) {
+        s->poisoned = true;
+        return cuda_status(f);
+    }
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_sampler_reset(gmrf_sampler *s)
+{
+    g_last_error.clear();
+    if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
+    if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    try {
+        const bool plain = s->algorithm == GMRF_ALGO_PLAIN;
+        void *x = plain ? static_cast<void *>(s->plain.x) : s->x;
+        CK(cudaMemcpyAsync(x, s->x_init, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
+        CK(cudaMemcpyAsync(s->tau, s->tau_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+        CK(cudaMemcpyAsync(s->sig2, s->sig2_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+        if (!plain) {
+            CK(cudaMemcpyAsync(s->hyp, s->hyp_init, s->hyp_bytes, cudaMemcpyDeviceToDevice, s->stream));
+            CK(cudaMemsetAsync(s->mean, 0, s->x_bytes, s->stream));
+            CK(cudaMemsetAsync(s->m2, 0, s->x_bytes, s->stream));
+        }
+        CK(launch_ctl_reset(s->ctl, s->opts.start_sweep, s->stream));
+    } catch (const CudaFail &f) {
+        s->poisoned = true;
+        return cuda_status(f);
+    }
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_launch_colour_step(gmrf_sampler *s, int32_t colour, int32_t accumulate)
+{
+    g_last_error.clear();
+    if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
+    if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "colour steps of the plain sweep");
+    if (colour < 0 || colour >= s->kmax) return fail(GMRF_E_INVALID, "colour out of range");
+    cudaError_t e = launch_colour_step(s->precision, s->V, step_args(s, colour, 1, accumulate ? 1 : 0), s->stream);
+    if (e != cudaSuccess) return poison(s, e, "colour step launch");
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_field_colors(gmrf_sampler *s, int32_t field, int32_t *colors, int32_t *num_colors)
+{
+    g_last_error.clear();
+    if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
+    if (field < 0 || field >= s->nfields) return fail(GMRF_E_INVALID, "field out of range");
+    const HostField &h = s->hf[field];
+    if (colors) {
+        if (h.kind == GMRF_CSR) std::copy(h.colors.begin(), h.colors.end(), colors);
+        else
+            for (int64_t i = 0; i < h.n; ++i) colors[i] = lattice_colour_host(h.kind, h.dims, i);
+    }
+    if (num_colors) *num_colors = h.ncolors;
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_sampler_info(gmrf_sampler *s, gmrf_info *out)
+{
+    g_last_error.clear();
+    if (!s || !out) return fail(GMRF_E_INVALID, "sampler and out are required");
+    if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    SweepCtl c{};
+    cudaError_t e = cudaMemcpyAsync(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return poison(s, e, "info");
+    out->nfields = s->nfields;
+    out->chains = s->C;
+    out->precision = s->precision;
+    out->max_colors = s->kmax;
+    out->sweeps_done = c.sweep;
+    out->accumulated = c.acc_count;
+    out->hyper_fallbacks = c.fallbacks;
+    out->device_bytes = s->bytes;
+    out->launches_per_sweep = s->launches_per_sweep;
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, int64_t count, uint32_t *out,
+                              void *cuda_stream)
+{
+    g_last_error.clear();
+    if (count < 0 || (count > 0 && !out)) return fail(GMRF_E_INVALID, "count >= 0 and a device output are required");
+    if (count > (int64_t(1) << 32)) return fail(GMRF_E_INVALID, "count must be <= 2^32");
+    cudaError_t e = launch_philox_words(seed, c1, c2, c3, count, out, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_status(CudaFail{e, "philox_words"});
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream, uint32_t chain, int32_t precision,
+                              int64_t count, void *out, void *cuda_stream)
+{
+    g_last_error.clear();
+    if (count < 0 || (count > 0 && !out)) return fail(GMRF_E_INVALID, "count >= 0 and a device output are required");
+    if (count > (int64_t(1) << 32)) return fail(GMRF_E_INVALID, "count must be <= 2^32");
+    if (precision != GMRF_FP32 && precision != GMRF_FP64) return fail(GMRF_E_INVALID, "precision");
+    cudaError_t e = launch_site_normals(seed, sweep, stream, chain, precision, count, out,
+                                        static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_status(CudaFail{e, "site_normals"});
+    return GMRF_OK;
+}
+
+}  // extern "C"

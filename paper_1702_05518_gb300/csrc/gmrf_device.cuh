@@ -1,0 +1,245 @@
+// gmrf_device.cuh -- device-side building blocks of libgmrf: the counter-based generators
+// (Philox4x32-10, Box-Muller normals, Marsaglia-Tsang Gamma variates), the field/tile
+// descriptors shared by host and device code, and small vector load/store helpers.
+//
+// The generators follow their published definitions (Salmon et al., SC'11 for Philox;
+// Box-Muller; Marsaglia & Tsang, ACM TOMS 2000 for Gamma) with the counter assignment stated
+// in include/gmrf.h, so every draw is a pure function of (seed, counter).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gmrf {
+
+constexpr uint32_t kTagX = 0, kTagTau = 1, kTagSig = 2, kTagPrio = 3, kTagTauExtra = 5,
+                   kTagSigExtra = 6;
+constexpr int kMaxChains = 64;
+constexpr int kBlock = 256;            // threads per block of the colour-step kernels
+constexpr int kMaxGammaAttempts = 64;  // bounded rejection loop
+
+enum FieldKind : int32_t { kLat2D4 = 0, kLat2D8 = 1, kLat3D6 = 2, kCsr = 3 };
+
+// Per-field descriptor, device-resident.  "Slots" index the colour-split layout: a lattice of
+// colour count k keeps k sub-arrays of rows x cols slots each (padded; invalid slots are never
+// read); a CSR field keeps its n sites permuted so each colour class is contiguous.
+struct FieldDev {
+    int32_t kind;
+    int32_t ncolors;
+    int32_t n;          // sites
+    int32_t rows;       // lattice: sub-array rows; CSR: 0
+    int32_t cols;       // lattice: sub-array columns (padded); CSR: 0
+    int32_t dims[3];    // 2-D: H, W; 3-D: L, H, W; CSR: n
+    uint32_t stream;    // Philox counter word 2
+    int32_t rank;       // n - components (intrinsic prior) or n (proper prior)
+    int64_t slot0;      // first slot of this field in the concatenated state arrays
+    int64_t nslots;     // slots of this field
+    int64_t csr0;       // CSR: first index into the per-site CSR arrays (perm, deg)
+    int64_t rp0;        // CSR: first index into the row-pointer array (n + 1 entries)
+    int64_t nnz0;       // CSR: first index into col_idx / weights
+    int64_t coff0;      // CSR: first index into the colour-offset array (ncolors + 1 entries)
+    int32_t part0;      // first partial-sum slot (tiles of all colours of this field)
+    int32_t nparts;     // partial-sum slots of this field
+};
+
+// A unit of work of one colour step: a range of sub-array rows (lattice) or of permuted
+// positions (CSR) of one field's colour class.
+struct Tile {
+    int32_t field;
+    int32_t colour;
+    int32_t start;
+    int32_t count;
+    int32_t part;       // partial-sum slot
+    int32_t pad[3];
+};
+
+// Device-resident sweep control, read by every kernel of a sweep and advanced by the last.
+struct SweepCtl {
+    long long sweep;       // number of the sweep in progress
+    long long extra;       // gmrf_hyper_update calls so far
+    long long fallbacks;   // Gamma draws that hit the attempt limit
+    long long acc_count;   // sweeps accumulated into the running mean / M2
+    unsigned long long ticket;  // blocks of the current hyper launch that have finished
+    long long pad[3];
+};
+
+// Whether sweep number `sweep` is accumulated (burn-in, then every thin-th sweep).
+__host__ __device__ __forceinline__ bool sweep_accumulated(long long sweep, long long burn_in, int thin)
+{
+    return sweep >= burn_in && (sweep - burn_in) % thin == 0;
+}
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds, multipliers 0xD2511F53 and
+// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__host__ __device__ __forceinline__ uint2 philox_key(uint64_t seed)
+{
+    return make_uint2(static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32));
+}
+
+// ------------------------------------------------------------------------------------------
+// Uniforms u = (w + 1/2) 2^-32 and Box-Muller normals (r = sqrt(-2 ln u_a), angle 2 pi u_b).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double u01_f64(uint32_t w) { return (static_cast<double>(w) + 0.5) * 0x1p-32; }
+
+__device__ __forceinline__ float u01_f32(uint32_t w)
+{
+    return fmaf(static_cast<float>(w), 0x1p-32f, 0x1p-33f);
+}
+
+// -2 ln u in single precision with small relative error for every word: the lower half of the
+// range takes the logarithm of u itself, the upper half log1p(-(1 - u)) with 1 - u formed
+// exactly from the complemented word, so radii near zero keep their precision.
+__device__ __forceinline__ float neg2log_u_f32(uint32_t w)
+{
+    if (w < 0x80000000u)
+        return -2.0f * __logf(u01_f32(w));
+    return -2.0f * log1pf(-u01_f32(~w));
+}
+
+__device__ __forceinline__ void box_muller_f32(uint32_t wa, uint32_t wb, float &zc, float &zs)
+{
+    const float r = sqrtf(neg2log_u_f32(wa));
+    float s, c;
+    sincospif(2.0f * u01_f32(wb), &s, &c);
+    zc = r * c;
+    zs = r * s;
+}
+
+__device__ __forceinline__ void box_muller_f64(uint32_t wa, uint32_t wb, double &zc, double &zs)
+{
+    const double r = sqrt(-2.0 * log(u01_f64(wa)));
+    double s, c;
+    sincospi(2.0 * u01_f64(wb), &s, &c);
+    zc = r * c;
+    zs = r * s;
+}
+
+template <typename T> struct Prec;
+template <> struct Prec<float> {
+    __device__ __forceinline__ static void bm(uint32_t a, uint32_t b, float &c, float &s) { box_muller_f32(a, b, c, s); }
+};
+template <> struct Prec<double> {
+    __device__ __forceinline__ static void bm(uint32_t a, uint32_t b, double &c, double &s) { box_muller_f64(a, b, c, s); }
+};
+
+// The V normals that update chains chain0 .. chain0+V-1 of `site` at `sweep` (chain0 a multiple
+// of V, V in {1, 2, 4}).  Block counter (site, sweep, stream, chain0 / 4); chain c takes normal
+// c mod 4 of the block (cos/sin of (w0,w1), then cos/sin of (w2,w3)).
+template <typename T, int V>
+__device__ __forceinline__ void site_normals(uint2 key, uint32_t site, uint32_t sweep, uint32_t stream,
+                                             uint32_t chain0, T (&z)[V])
+{
+    const uint4 w = philox4x32_10(make_uint4(site, sweep, stream, (kTagX << 24) | (chain0 >> 2)), key);
+    if constexpr (V == 4) {
+        Prec<T>::bm(w.x, w.y, z[0], z[1]);
+        Prec<T>::bm(w.z, w.w, z[2], z[3]);
+    } else if constexpr (V == 2) {
+        if ((chain0 & 2u) == 0) Prec<T>::bm(w.x, w.y, z[0], z[1]);
+        else Prec<T>::bm(w.z, w.w, z[0], z[1]);
+    } else {
+        T c, s;
+        if ((chain0 & 2u) == 0) Prec<T>::bm(w.x, w.y, c, s);
+        else Prec<T>::bm(w.z, w.w, c, s);
+        z[0] = (chain0 & 1u) ? s : c;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Gamma(shape, rate) by Marsaglia & Tsang (2000), FP64.  Attempt k uses the block at counter
+// (k, word1, stream, tag_chain): z = Box-Muller cos of (w0, w1), acceptance uniform w2, boost
+// uniform w3 (shape < 1: Gamma(a) = Gamma(a + 1) U^(1/a)).  At most kMaxGammaAttempts
+// attempts; if all reject (probability < 1e-100 here) the draw is d / rate and *fell_back = 1.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double gamma_mt(double shape, double rate, uint2 key, uint32_t word1,
+                                           uint32_t stream, uint32_t tag_chain, int &fell_back)
+{
+    const bool boost = shape < 1.0;
+    const double a = boost ? shape + 1.0 : shape;
+    const double d = a - 1.0 / 3.0;
+    const double c = 1.0 / sqrt(9.0 * d);
+    fell_back = 0;
+    for (uint32_t k = 0; k < static_cast<uint32_t>(kMaxGammaAttempts); ++k) {
+        const uint4 w = philox4x32_10(make_uint4(k, word1, stream, tag_chain), key);
+        double z, unused;
+        box_muller_f64(w.x, w.y, z, unused);
+        double v = 1.0 + c * z;
+        if (v <= 0.0)
+            continue;
+        v = v * v * v;
+        const double u = u01_f64(w.z);
+        if (log(u) < 0.5 * z * z + d - d * v + d * log(v)) {
+            double g = d * v;
+            if (boost)
+                g *= pow(u01_f64(w.w), 1.0 / shape);
+            return g / rate;
+        }
+    }
+    fell_back = 1;
+    return d / rate;
+}
+
+// ------------------------------------------------------------------------------------------
+// Vector loads/stores of V consecutive chain values.
+// ------------------------------------------------------------------------------------------
+template <typename T, int V> struct Vec;
+template <> struct Vec<float, 1> {
+    __device__ __forceinline__ static void ld(const float *p, float (&v)[1]) { v[0] = *p; }
+    __device__ __forceinline__ static void st(float *p, const float (&v)[1]) { *p = v[0]; }
+};
+template <> struct Vec<float, 2> {
+    __device__ __forceinline__ static void ld(const float *p, float (&v)[2]) { float2 t = *reinterpret_cast<const float2 *>(p); v[0] = t.x; v[1] = t.y; }
+    __device__ __forceinline__ static void st(float *p, const float (&v)[2]) { *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]); }
+};
+template <> struct Vec<float, 4> {
+    __device__ __forceinline__ static void ld(const float *p, float (&v)[4]) { float4 t = *reinterpret_cast<const float4 *>(p); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+    __device__ __forceinline__ static void st(float *p, const float (&v)[4]) { *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]); }
+};
+template <> struct Vec<double, 1> {
+    __device__ __forceinline__ static void ld(const double *p, double (&v)[1]) { v[0] = *p; }
+    __device__ __forceinline__ static void st(double *p, const double (&v)[1]) { *p = v[0]; }
+};
+template <> struct Vec<double, 2> {
+    __device__ __forceinline__ static void ld(const double *p, double (&v)[2]) { double2 t = *reinterpret_cast<const double2 *>(p); v[0] = t.x; v[1] = t.y; }
+    __device__ __forceinline__ static void st(double *p, const double (&v)[2]) { *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]); }
+};
+
+// Natural site index <-> slot of the colour-split lattice layouts.
+//   2-D 4-neighbour and 3-D 6-neighbour: colour c = parity of the coordinate sum; sub-array
+//   row = (l*H + i), column h = j / 2 (the colour-c sites of a row are j = 2h + ((c+l+i) & 1)).
+//   2-D 8-neighbour: colour c = 2 (i & 1) + (j & 1); sub-array (i / 2, j / 2).
+__device__ __forceinline__ int64_t lattice_slot_of_site(const FieldDev &f, int64_t site)
+{
+    if (f.kind == kLat2D8) {
+        const int64_t W = f.dims[1];
+        const int64_t i = site / W, j = site - i * W;
+        const int64_t c = 2 * (i & 1) + (j & 1);
+        return (c * f.rows + (i >> 1)) * f.cols + (j >> 1);
+    }
+    const int64_t W = (f.kind == kLat3D6) ? f.dims[2] : f.dims[1];
+    const int64_t r = site / W, j = site - r * W;  // r = l*H + i
+    int64_t par = r + j;
+    if (f.kind == kLat3D6) {
+        const int64_t H = f.dims[1];
+        const int64_t l = r / H, i = r - l * H;
+        par = l + i + j;
+    }
+    const int64_t c = par & 1;
+    return (c * f.rows + r) * f.cols + (j >> 1);
+}
+
+}  // namespace gmrf

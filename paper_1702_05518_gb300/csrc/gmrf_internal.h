@@ -1,0 +1,125 @@
+// gmrf_internal.h -- declarations shared by the translation units of libgmrf (host side).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gmrf_device.cuh"
+
+namespace gmrf {
+
+// Arguments of one colour-step launch (one colour class of every field, or a reduce-only pass
+// over the current state when `update` is 0).
+struct StepArgs {
+    const FieldDev *fields;
+    const Tile *tiles;
+    int32_t ntiles;
+    int32_t colour;
+    void *x;             // [slots][Cp]  state, colour-split layout, chains innermost
+    const void *y;       // [slots]      observations
+    void *mean;          // [slots][Cp]  Welford mean
+    void *m2;            // [slots][Cp]  Welford sum of squared deviations
+    const int32_t *rp;   // CSR: local row pointers of the permuted graph (n + 1 per field)
+    const int32_t *ci;   // CSR: local permuted column indices
+    const void *w;       // CSR: edge weights (precision T) or nullptr
+    const void *deg;     // CSR: degrees d_i (precision T), permuted order
+    const int32_t *perm; // CSR: slot -> natural site
+    const int32_t *coff; // CSR: colour offsets (ncolors + 1 per field)
+    const void *hyp;     // [F * Cp][2]: tau, 1/sigma^2 in precision T
+    double2 *partials;   // [parts][Cp]: (x'(D - rho W)x, ||y - x||^2) per tile and chain
+    const SweepCtl *ctl;
+    uint2 key;
+    int32_t Cp;          // chains in the layout (power of two >= chains)
+    double rho;
+    long long burn_in;
+    int32_t thin;
+    int32_t acc_enabled;
+    int32_t update;      // 1: draw the colour class; 0: only recompute the partial sums
+};
+
+struct HyperArgs {
+    const FieldDev *fields;
+    int32_t nfields;
+    int32_t Cp;
+    const double2 *partials;
+    double *tau;          // [F * Cp]
+    double *sig2;         // [F * Cp]
+    void *hyp;            // [F * Cp][2] copies in precision T
+    double *trace_tau;    // [F * Cp][cap]
+    double *trace_sig;
+    int32_t trace_cap;
+    SweepCtl *ctl;
+    uint2 key;
+    double a_tau, b_tau, a_sig, b_sig;
+    int32_t draw;         // 0: keep tau, sigma^2
+    int32_t end_of_sweep; // 1: sweep counter, traces; 0: extra draw (tags 5 and 6)
+    long long burn_in;    // accumulation schedule (to advance the accumulation count)
+    int32_t thin;
+    int32_t acc_enabled;
+};
+
+// Launchers (each enqueues on `stream` and returns the launch status).
+cudaError_t launch_colour_step(int precision, int V, const StepArgs &a, cudaStream_t stream);
+cudaError_t launch_hyper(int precision, const HyperArgs &a, cudaStream_t stream);
+cudaError_t launch_pack(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx,
+                        int32_t C, int32_t Cp, const double *y_nat, const double *x0_nat,
+                        const int32_t *perm_inv, void *x, void *y, cudaStream_t stream);
+cudaError_t launch_unpack(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx,
+                          int32_t Cp, int32_t chain, const void *src, const void *m2, double inv_km1,
+                          const int32_t *perm_inv, double *out, cudaStream_t stream);
+cudaError_t launch_ctl_reset(SweepCtl *ctl, long long start_sweep, cudaStream_t stream);
+cudaError_t launch_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, int64_t count,
+                                uint32_t *out, cudaStream_t stream);
+cudaError_t launch_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream_id, uint32_t chain,
+                                int precision, int64_t count, void *out, cudaStream_t stream);
+
+// Jones-Plassmann colouring and colour-permuted CSR layout (csr_build.cu).
+struct CsrBuild {
+    int32_t n;
+    const int32_t *rp;     // device, natural order
+    const int32_t *ci;
+    const double *w;       // device or nullptr
+    int32_t *colors;       // device [n] (in: given colours, or out: JP colours)
+};
+// JP colouring on the device; priorities: device [n] or nullptr for Philox(seed).
+// Scratch (`scratch_bytes` from jp_scratch_bytes) is caller-provided device memory.
+size_t jp_scratch_bytes(int32_t n);
+cudaError_t jp_color(int32_t n, const int32_t *rp, const int32_t *ci, const uint32_t *prio,
+                     uint64_t seed, int32_t *colors, void *scratch, int32_t *num_colors_host,
+                     cudaStream_t stream);
+// Stable counting sort of the sites by colour and the permuted CSR (cols remapped, row order
+// kept), degrees and weights in precision T.  Outputs are device arrays of the field's block.
+size_t layout_scratch_bytes(int32_t n, int32_t ncolors);
+cudaError_t csr_layout(int precision, int32_t n, int32_t ncolors, const int32_t *rp, const int32_t *ci,
+                       const double *w, const int32_t *colors, void *scratch, int32_t *perm,
+                       int32_t *perm_inv, int32_t *coff, int32_t *rp_out, int32_t *ci_out,
+                       void *w_out, void *deg_out, cudaStream_t stream);
+
+// Plain FP64 baseline sweep (plain.cu): natural layout, one pass per colour over all sites.
+struct PlainArgs {
+    int32_t n;
+    int32_t kind;
+    int32_t dims[3];
+    const int32_t *rp;     // CSR graphs (natural order) or nullptr for lattices
+    const int32_t *ci;
+    const double *w;
+    const int32_t *colors; // natural order
+    int32_t ncolors;
+    double *x;             // [C][n] natural order
+    const double *y;
+    double *tau, *sig2;    // [C]
+    double *trace_tau, *trace_sig;
+    int32_t trace_cap;
+    double *red;           // [C][2] scratch sums
+    SweepCtl *ctl;
+    uint2 key;
+    uint32_t stream_id;
+    int32_t C;
+    int32_t rank;
+    double rho;
+    double a_tau, b_tau, a_sig, b_sig;
+    int32_t draw;
+};
+cudaError_t launch_plain_sweep(const PlainArgs &a, cudaStream_t stream, int64_t *launches);
+
+}  // namespace gmrf
