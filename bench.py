@@ -75,10 +75,11 @@ def site_updates_per_step(spec):
     return sum(f["n"] for f in spec["fields"]) * spec["chains"] * spec["sweeps"]
 
 
-def colour_classes(field):
-    """Sites per colour class of a field (lattice closed forms; CSR via the oracle-free count
-    of the GPU's own colouring is not needed for lattices)."""
+def colour_classes(field, colors=None):
+    """Sites per colour class of a field (closed forms for lattices; CSR from its colouring)."""
     k = field["kind"]
+    if k == wl.CSR:
+        return np.bincount(colors).tolist()
     if k == wl.LATTICE2D_8:
         H, W = field["dims"][:2]
         return [((H - a + 1) // 2) * ((W - b + 1) // 2) for a in (0, 1) for b in (0, 1)]
@@ -91,21 +92,44 @@ def colour_classes(field):
     return [even, H * W - even]
 
 
-def algorithmic_bytes_per_colour_step(spec, colour, state_bytes=4):
-    """Bytes a colour step must move at least: every neighbour value of the class read once
-    (for lattices: all sites of the other colours adjacent to the class), the class's y read
-    once, its new state written once (C chains), no accumulation."""
+def stage_algorithmic_bytes(spec, stage_name, colour, colourings, S=4):
+    """Least bytes a launch of the stage must move (accumulation off), summed over its fields.
+
+    fused 2-D sweep: every site's state read once and written once (C chains), y read once:
+        n (2 C S + S);
+    lattice colour step c: the other colours' states read once, y and the new state of class c:
+        (n - n_c) C S + n_c S + n_c C S;
+    CSR colour step c: for the sites of class c, row pointers, degrees, permutation, y, the
+    column indices of their edges, the states of the distinct neighbours, and the new states.
+    """
     C = spec["chains"]
     total = 0
-    for f in spec["fields"]:
-        if f["kind"] == wl.CSR:
-            raise ValueError("CSR roofline bytes need the colouring")
-        cls = colour_classes(f)
+    for fi, f in enumerate(spec["fields"]):
+        kind = f["kind"]
+        if "fused" in stage_name:
+            if ("8-neighbour" in stage_name) != (kind == wl.LATTICE2D_8) or kind not in (wl.LATTICE2D_4, wl.LATTICE2D_8):
+                continue
+            total += f["n"] * (2 * C * S + S)
+            continue
+        if "colour step" not in stage_name:
+            continue
+        if ("CSR" in stage_name) != (kind == wl.CSR):
+            continue
+        if kind != wl.CSR and ("3-D" in stage_name) != (kind == wl.LATTICE3D_6):
+            continue
+        cls = colour_classes(f, colourings.get(fi))
         if colour >= len(cls):
             continue
         n_c = cls[colour]
-        others = sum(cls) - n_c  # every other-colour site neighbours the class
-        total += others * C * state_bytes + n_c * state_bytes + n_c * C * state_bytes
+        if kind == wl.CSR:
+            col = colourings[fi]
+            rp, ci = f["row_ptr"], f["col_idx"]
+            members = np.flatnonzero(col == colour)
+            deg = np.diff(rp)[members]
+            nbrs = np.unique(np.concatenate([ci[rp[i]:rp[i + 1]] for i in members])) if len(members) else []
+            total += n_c * (4 + S + 4 + S) + 4 * int(deg.sum()) + len(nbrs) * C * S + n_c * C * S
+        else:
+            total += (sum(cls) - n_c) * C * S + n_c * S + n_c * C * S
     return total
 
 
@@ -325,25 +349,29 @@ def run_ours(args):
     dev_s_max = max_over_ranks(dev_s, world, device="cuda")
     value = world * units * args.steps / dev_s_max
 
-    # Colour-step kernel alone: back-to-back launches of each colour class, CUDA events on the
-    # launching stream (accumulation off); average duration per launch.
-    k_colours = info["max_colors"]
+    # Each stage of a sweep alone: back-to-back launches, CUDA events on the launching stream
+    # (accumulation off); the dominant stage is the one with the longest launch.
     reps = 50
+    colourings = {fi: s.colors(fi)[0] for fi, f in enumerate(spec["fields"]) if f["kind"] == wl.CSR}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for c in range(k_colours):
-        s.launch_colour_step(c)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(reps):
-        for c in range(k_colours):
-            s.launch_colour_step(c)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    kernel_us = ev0.elapsed_time(ev1) * 1e3 / (reps * k_colours)
-    try:
-        algo_bytes = np.mean([algorithmic_bytes_per_colour_step(spec, c) for c in range(k_colours)])
-    except ValueError:
-        algo_bytes = None
+    stages = []
+    colour_of_stage = {}
+    seen = {}
+    for st in range(info["launches_per_sweep"]):
+        name = s.launch_stage(st)
+        key = name
+        colour_of_stage[st] = seen.get(key, 0)
+        seen[key] = colour_of_stage[st] + 1
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            s.launch_stage(st)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        stages.append((st, name, ev0.elapsed_time(ev1) * 1e3 / reps))
+    dom = max(stages, key=lambda x: x[2])
+    kernel_us = dom[2]
+    algo_bytes = stage_algorithmic_bytes(spec, dom[1], colour_of_stage[dom[0]], colourings)
     s.close()
 
     # End to end through the C ABI with host buffers: create (H2D copy of y), all sweeps, fetch
@@ -372,13 +400,11 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs")
     peak_note = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    roofline = None
-    if algo_bytes is not None:
-        achieved = algo_bytes / (kernel_us * 1e-6) / 1e9
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": None, "peak_source": peak_note,
-                    "kernel": "colour_step_kernel<float,1>", "algorithmic_bytes_per_launch": algo_bytes,
-                    "avg_launch_us": kernel_us}
+    achieved = algo_bytes / (kernel_us * 1e-6) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": peak_note,
+                "kernel": dom[1], "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": kernel_us,
+                "stages_us": {f"{st}:{name}": round(us, 3) for st, name, us in stages}}
 
     if rank != 0:
         if world > 1:

@@ -119,7 +119,12 @@ typedef struct {
     int32_t trace_capacity;   /* tau/sigma^2 trace ring length per chain (>= 1)             */
     int32_t algorithm;        /* gmrf_algorithm                                             */
     int32_t graph_sweeps;     /* sweeps captured per CUDA graph; 0 = launch kernels directly */
+    int32_t flags;            /* GMRF_FLAG_* bits; 0 for the defaults                        */
 } gmrf_opts;
+
+/* gmrf_opts.flags: GMRF_FLAG_PER_COLOUR makes 2-D lattice fields use one launch per colour
+ * class instead of the fused one-launch-per-sweep kernel (same results up to rounding). */
+#define GMRF_FLAG_PER_COLOUR 1
 
 typedef struct {
     int32_t nfields;
@@ -206,14 +211,16 @@ gmrf_status gmrf_fetch_samples(gmrf_sampler *s, int32_t field, int32_t chain, do
 gmrf_status gmrf_sampler_reset(gmrf_sampler *s);
 
 /*
- * Diagnostic: enqueue exactly one colour step (the kernel and arguments a sweep uses for
- * colour class `colour` of every field) on the sampler's stream, without the hyperparameter
- * draw and without advancing the sweep counter; `accumulate` = 0 skips the running-mean update.
- * For timing the colour-step kernel in isolation; the state moves on as in a sweep.
- * Errors: GMRF_E_INVALID (colour out of range), GMRF_E_UNSUPPORTED (plain algorithm),
+ * Diagnostic: enqueue exactly one launch of stage `stage` of a sweep on the sampler's stream.
+ * A sweep is gmrf_info.launches_per_sweep stages in order: the fused 2-D lattice sweeps (one
+ * per lattice kind present), the colour steps of the other fields (one per colour and field
+ * kind), then the hyperparameter draw (the last stage, which also advances the sweep counter).
+ * `accumulate` = 0 skips the running-mean update.  For timing one kernel in isolation; the state
+ * moves on as in a sweep.  *name (may be NULL) receives a static description of the stage.
+ * Errors: GMRF_E_INVALID (stage out of range), GMRF_E_UNSUPPORTED (plain algorithm),
  * GMRF_E_STATE, GMRF_E_CUDA.
  */
-gmrf_status gmrf_launch_colour_step(gmrf_sampler *s, int32_t colour, int32_t accumulate);
+gmrf_status gmrf_launch_stage(gmrf_sampler *s, int32_t stage, int32_t accumulate, const char **name);
 
 /* The colouring a field is sampled with (natural order) and its number of colours. */
 gmrf_status gmrf_field_colors(gmrf_sampler *s, int32_t field, int32_t *colors,

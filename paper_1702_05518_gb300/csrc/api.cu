@@ -39,6 +39,7 @@ struct HostField {
     int32_t n = 0;
     int32_t ncolors = 0;
     int32_t components = 1;
+    bool fused = false;           // sampled by the fused 2-D lattice sweep (ping-pong state)
     std::vector<int32_t> colors;  // CSR: natural-order colouring used
 };
 
@@ -59,10 +60,22 @@ struct gmrf_sampler {
     int64_t max_n = 0;
     std::vector<HostField> hf;
     std::vector<FieldDev> fd;
-    std::vector<int32_t> tile_off, tile_cnt;  // per colour
+    std::vector<int32_t> tile_off, tile_cnt;  // per (colour, kind): index colour * 4 + kind
+    // Stages of one sweep, in launch order.
+    struct Stage {
+        int type;    // 0: colour step, 1: fused 2-D lattice sweep, 2: hyperparameter draw
+        int kind;
+        int colour;
+    };
+    std::vector<Stage> stages;
+    TileXY *ftiles_dev = nullptr;
+    int32_t ftile_off[4] = {0, 0, 0, 0}, ftile_cnt[4] = {0, 0, 0, 0};
+    int32_t fTR[4] = {0, 0, 0, 0}, fTC[4] = {0, 0, 0, 0};
+    size_t fsmem[4] = {0, 0, 0, 0};
     FieldDev *fields_dev = nullptr;
     Tile *tiles_dev = nullptr;
     void *x = nullptr, *y = nullptr, *mean = nullptr, *m2 = nullptr;
+    void *x_alt = nullptr;  // second state buffer of fused fields (state of odd sweeps)
     int32_t *rp = nullptr, *ci = nullptr, *perm = nullptr, *perm_inv = nullptr, *coff = nullptr;
     void *w = nullptr, *deg = nullptr;
     double *tau = nullptr, *sig2 = nullptr;
@@ -333,12 +346,13 @@ void free_tmp(std::vector<void *> &tmp)
 // ---------------------------------------------------------------------------------------------
 // Sweep launches
 // ---------------------------------------------------------------------------------------------
-StepArgs step_args(gmrf_sampler *s, int colour, int update, int accumulate = 1)
+StepArgs step_args(gmrf_sampler *s, int colour, int kind, int update, int accumulate = 1)
 {
     StepArgs a{};
+    const size_t slot = static_cast<size_t>(colour) * 4 + kind;
     a.fields = s->fields_dev;
-    a.tiles = s->tiles_dev + s->tile_off[colour];
-    a.ntiles = s->tile_cnt[colour];
+    a.tiles = s->tiles_dev + s->tile_off[slot];
+    a.ntiles = s->tile_cnt[slot];
     a.colour = colour;
     a.x = s->x;
     a.y = s->y;
@@ -390,6 +404,49 @@ HyperArgs hyper_args(gmrf_sampler *s, int draw, int end_of_sweep)
     return h;
 }
 
+FusedArgs fused_args(gmrf_sampler *s, int kind, int update, int accumulate)
+{
+    FusedArgs a{};
+    a.fields = s->fields_dev;
+    a.tiles = s->ftiles_dev + s->ftile_off[kind];
+    a.ntiles = s->ftile_cnt[kind];
+    a.TR = s->fTR[kind];
+    a.TC = s->fTC[kind];
+    const int K = kind == GMRF_LATTICE2D_8 ? 4 : 2;
+    fast_div_magic(static_cast<uint32_t>(a.TC + 2 * K), a.rc_m, a.rc_s);
+    fast_div_magic(static_cast<uint32_t>(a.TC > 0 ? a.TC : 1), a.tc_m, a.tc_s);
+    a.x = s->x;
+    a.x_alt = s->x_alt;
+    a.y = s->y;
+    a.mean = s->mean;
+    a.m2 = s->m2;
+    a.hyp = s->hyp;
+    a.partials = s->partials;
+    a.ctl = s->ctl;
+    a.key = philox_key(s->opts.seed);
+    a.Cp = s->Cp;
+    a.rho = s->model.prior == GMRF_PRIOR_PCAR ? s->model.rho : 1.0;
+    a.burn_in = s->opts.burn_in;
+    a.thin = s->opts.thin;
+    a.acc_enabled = accumulate;
+    a.update = update;
+    return a;
+}
+
+// One stage of a sweep (see gmrf_launch_stage); `draw` and `end_of_sweep` only matter for the
+// hyperparameter stage.
+cudaError_t enqueue_stage(gmrf_sampler *s, size_t k, int update, int accumulate, int draw, int end_of_sweep,
+                          cudaStream_t st)
+{
+    const gmrf_sampler::Stage &g = s->stages[k];
+    if (g.type == 1)
+        return launch_lattice_fused(s->precision, s->V, g.kind, fused_args(s, g.kind, update, accumulate),
+                                    s->fsmem[g.kind], st);
+    if (g.type == 0)
+        return launch_colour_step(s->precision, s->V, g.kind, step_args(s, g.colour, g.kind, update, accumulate), st);
+    return launch_hyper(s->precision, hyper_args(s, draw, end_of_sweep), st);
+}
+
 cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int draw, cudaStream_t st)
 {
     cudaError_t e = cudaSuccess;
@@ -401,9 +458,8 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int draw, cudaStream_t 
             e = launch_plain_sweep(a, st, &l);
             continue;
         }
-        for (int c = 0; c < s->kmax && e == cudaSuccess; ++c)
-            e = launch_colour_step(s->precision, s->V, step_args(s, c, 1), st);
-        if (e == cudaSuccess) e = launch_hyper(s->precision, hyper_args(s, draw, 1), st);
+        for (size_t k = 0; k < s->stages.size() && e == cudaSuccess; ++k)
+            e = enqueue_stage(s, k, 1, 1, draw, 1, st);
     }
     return e;
 }
@@ -567,9 +623,13 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
             }
             d.ncolors = h.ncolors;
             d.nslots = static_cast<int64_t>(h.ncolors) * d.rows * d.cols;
+            fast_div_magic(static_cast<uint32_t>(d.cols), d.cols_m, d.cols_s);
+            fast_div_magic(static_cast<uint32_t>(h.kind == GMRF_LATTICE3D_6 ? h.dims[1] : 1), d.h_m, d.h_s);
         }
         slots += d.nslots;
         s->max_n = std::max<int64_t>(s->max_n, h.n);
+        if (d.nslots * s->Cp >= (int64_t(1) << 31))
+            return fail(GMRF_E_INVALID, "field " + std::to_string(fi) + ": sites x chains must be < 2^31");
     }
     if (csr_nnz >= (int64_t(1) << 31)) return fail(GMRF_E_INVALID, "total CSR entries must be < 2^31");
     s->slots = slots;
@@ -649,17 +709,56 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
         }
     }
 
-    // Tiles: per colour, each field's colour class cut into tiles of about 2048 (site, chain
-    // vector) elements; partial-sum slots are contiguous per field.
+    // Tiles: per colour, each field's colour class cut into tiles of `target` (site, chain
+    // vector) elements, sized so a colour step has several blocks per SM (at least 512 and at
+    // most 16384 elements per tile); partial-sum slots are contiguous per field.
     const int CV = s->Cp / s->V;
-    const int64_t target = 2048;
+    // 2-D lattice fields take the fused sweep when a tile of at least 16 x 16 sites with its
+    // halo fits the 48 KiB shared-memory budget (4 blocks per SM) and it is not switched off.
+    bool fused_kind[4] = {false, false, false, false};
+    const bool allow_fused = (s->opts.flags & GMRF_FLAG_PER_COLOUR) == 0;
+    for (int kind : {static_cast<int>(GMRF_LATTICE2D_4), static_cast<int>(GMRF_LATTICE2D_8)}) {
+        const int K = kind == GMRF_LATTICE2D_8 ? 4 : 2;
+        const double per_site = static_cast<double>(T) * (s->Cp + 1);
+        int side = static_cast<int>(std::floor(std::sqrt(48.0 * 1024.0 / per_site))) - 2 * K;
+        side = std::min(64, side - side % 8);
+        if (!allow_fused || side < 16) continue;
+        for (auto &h : s->hf)
+            if (h.kind == kind) fused_kind[kind] = true;
+        if (fused_kind[kind]) {
+            s->fTR[kind] = side;
+            s->fTC[kind] = side;
+            s->fsmem[kind] = lattice_fused_smem(s->precision, kind, s->Cp, side, side);
+            CK(prepare_lattice_fused(s->precision, s->V, kind, s->fsmem[kind]));
+        }
+    }
+    int64_t total_elems = 0;
+    for (int fi = 0; fi < s->nfields; ++fi)
+        if (!fused_kind[s->hf[fi].kind]) total_elems += static_cast<int64_t>(s->hf[fi].n) * CV;
+    const int64_t per_colour = total_elems / 2;
+    const int64_t target = std::min<int64_t>(16384, std::max<int64_t>(512, per_colour / (152 * 4)));
     s->kmax = 0;
     for (auto &h : s->hf) s->kmax = std::max(s->kmax, h.ncolors);
     std::vector<std::vector<Tile>> by_colour(s->kmax);
+    std::vector<TileXY> fz[4];
     int part = 0;
     for (int fi = 0; fi < s->nfields; ++fi) {
         FieldDev &d = s->fd[fi];
         d.part0 = part;
+        if (fused_kind[d.kind]) {
+            s->hf[fi].fused = true;
+            for (int i0 = 0; i0 < d.dims[0]; i0 += s->fTR[d.kind])
+                for (int j0 = 0; j0 < d.dims[1]; j0 += s->fTC[d.kind]) {
+                    TileXY t{};
+                    t.field = fi;
+                    t.i0 = i0;
+                    t.j0 = j0;
+                    t.part = part++;
+                    fz[d.kind].push_back(t);
+                }
+            d.nparts = part - d.part0;
+            continue;
+        }
         for (int c = 0; c < d.ncolors; ++c) {
             if (d.kind == GMRF_CSR) {
                 const int32_t lo = coff_host[fi][c], hi = coff_host[fi][c + 1];
@@ -689,17 +788,38 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
         d.nparts = part - d.part0;
     }
     s->nparts = part;
-    std::vector<Tile> all;
-    s->tile_off.assign(s->kmax, 0);
-    s->tile_cnt.assign(s->kmax, 0);
-    for (int c = 0; c < s->kmax; ++c) {
-        s->tile_off[c] = static_cast<int32_t>(all.size());
-        s->tile_cnt[c] = static_cast<int32_t>(by_colour[c].size());
-        all.insert(all.end(), by_colour[c].begin(), by_colour[c].end());
+    // Stages: fused lattice sweeps first (their fields do not interact with the others within a
+    // sweep), then colour steps in colour order, one launch per field kind, then the draw.
+    s->stages.clear();
+    std::vector<TileXY> fall;
+    for (int kind = 0; kind < 4; ++kind) {
+        s->ftile_off[kind] = static_cast<int32_t>(fall.size());
+        s->ftile_cnt[kind] = static_cast<int32_t>(fz[kind].size());
+        fall.insert(fall.end(), fz[kind].begin(), fz[kind].end());
+        if (!fz[kind].empty()) s->stages.push_back({1, kind, -1});
     }
+    std::vector<Tile> all;
+    s->tile_off.assign(static_cast<size_t>(s->kmax) * 4, 0);
+    s->tile_cnt.assign(static_cast<size_t>(s->kmax) * 4, 0);
+    for (int c = 0; c < s->kmax; ++c)
+        for (int kind = 0; kind < 4; ++kind) {
+            const size_t slot = static_cast<size_t>(c) * 4 + kind;
+            s->tile_off[slot] = static_cast<int32_t>(all.size());
+            for (const Tile &t : by_colour[c])
+                if (s->fd[t.field].kind == kind) all.push_back(t);
+            s->tile_cnt[slot] = static_cast<int32_t>(all.size()) - s->tile_off[slot];
+            if (s->tile_cnt[slot] > 0) s->stages.push_back({0, kind, c});
+        }
+    s->stages.push_back({2, -1, -1});
+    s->launches_per_sweep = static_cast<int64_t>(s->stages.size());
     CK(s->alloc_t(&s->tiles_dev, std::max<size_t>(all.size(), 1), sizeof(Tile)));
     if (!all.empty())
         CK(cudaMemcpyAsync(s->tiles_dev, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice, s->stream));
+    if (!fall.empty()) CK(s->alloc(&s->x_alt, static_cast<size_t>(slots) * Cp * T));
+    CK(s->alloc_t(&s->ftiles_dev, std::max<size_t>(fall.size(), 1), sizeof(TileXY)));
+    if (!fall.empty())
+        CK(cudaMemcpyAsync(s->ftiles_dev, fall.data(), sizeof(TileXY) * fall.size(), cudaMemcpyHostToDevice,
+                           s->stream));
     CK(s->alloc_t(&s->partials, static_cast<size_t>(std::max(part, 1)) * Cp, sizeof(double2)));
     CK(cudaMemsetAsync(s->partials, 0, static_cast<size_t>(std::max(part, 1)) * Cp * sizeof(double2), s->stream));
     CK(cudaMemcpyAsync(s->fields_dev, s->fd.data(), sizeof(FieldDev) * s->nfields, cudaMemcpyHostToDevice, s->stream));
@@ -746,13 +866,13 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     s->hyp_bytes = nh * 2 * T;
     CK(s->alloc(&s->x_init, s->x_bytes));
     CK(cudaMemcpyAsync(s->x_init, s->x, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
+    if (s->x_alt) CK(cudaMemcpyAsync(s->x_alt, s->x, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
     CK(s->alloc_t(&s->tau_init, nh, sizeof(double)));
     CK(s->alloc_t(&s->sig2_init, nh, sizeof(double)));
     CK(s->alloc(&s->hyp_init, s->hyp_bytes));
     CK(cudaMemcpyAsync(s->tau_init, s->tau, nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->sig2_init, s->sig2, nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->hyp_init, s->hyp, s->hyp_bytes, cudaMemcpyDeviceToDevice, s->stream));
-    s->launches_per_sweep = s->kmax + 1;
     CK(cudaStreamSynchronize(s->stream));
     return GMRF_OK;
 }
@@ -911,8 +1031,8 @@ gmrf_status gmrf_hyper_update(gmrf_sampler *s)
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
     if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "hyper_update on the plain sweep");
     cudaError_t e = cudaSuccess;
-    for (int c = 0; c < s->kmax && e == cudaSuccess; ++c)
-        e = launch_colour_step(s->precision, s->V, step_args(s, c, 0), s->stream);
+    for (size_t k = 0; k + 1 < s->stages.size() && e == cudaSuccess; ++k)
+        e = enqueue_stage(s, k, 0, 0, 0, 0, s->stream);
     if (e == cudaSuccess) e = launch_hyper(s->precision, hyper_args(s, 1, 0), s->stream);
     if (e != cudaSuccess) return poison(s, e, "hyper update launch");
     return GMRF_OK;
@@ -946,7 +1066,9 @@ gmrf_status gmrf_fetch_samples(gmrf_sampler *s, int32_t field, int32_t chain, do
             CK(cudaMemcpyAsync(dst, s->staging, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
             CK(cudaStreamSynchronize(s->stream));
         };
-        if (x_last) fetch(s->x, nullptr, 1.0, x_last);
+        // Fused fields keep the state at the start of sweep t in buffer t & 1.
+        void *xcur = (h.fused && (c.sweep & 1)) ? s->x_alt : s->x;
+        if (x_last) fetch(xcur, nullptr, 1.0, x_last);
         if (x_mean) {
             if (plain || k < 1) std::fill(x_mean, x_mean + n, plain ? NAN : 0.0);
             else fetch(s->mean, nullptr, 1.0, x_mean);
@@ -990,6 +1112,7 @@ gmrf_status gmrf_sampler_reset(gmrf_sampler *s)
         const bool plain = s->algorithm == GMRF_ALGO_PLAIN;
         void *x = plain ? static_cast<void *>(s->plain.x) : s->x;
         CK(cudaMemcpyAsync(x, s->x_init, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
+        if (s->x_alt) CK(cudaMemcpyAsync(s->x_alt, s->x_init, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
         CK(cudaMemcpyAsync(s->tau, s->tau_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
         CK(cudaMemcpyAsync(s->sig2, s->sig2_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
         if (!plain) {
@@ -1005,15 +1128,23 @@ gmrf_status gmrf_sampler_reset(gmrf_sampler *s)
     return GMRF_OK;
 }
 
-gmrf_status gmrf_launch_colour_step(gmrf_sampler *s, int32_t colour, int32_t accumulate)
+gmrf_status gmrf_launch_stage(gmrf_sampler *s, int32_t stage, int32_t accumulate, const char **name)
 {
     g_last_error.clear();
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
-    if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "colour steps of the plain sweep");
-    if (colour < 0 || colour >= s->kmax) return fail(GMRF_E_INVALID, "colour out of range");
-    cudaError_t e = launch_colour_step(s->precision, s->V, step_args(s, colour, 1, accumulate ? 1 : 0), s->stream);
-    if (e != cudaSuccess) return poison(s, e, "colour step launch");
+    if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "stages of the plain sweep");
+    if (stage < 0 || stage >= static_cast<int32_t>(s->stages.size())) return fail(GMRF_E_INVALID, "stage out of range");
+    static const char *kNames[3][4] = {
+        {"colour step, 2-D 4-neighbour lattice", "colour step, 2-D 8-neighbour lattice",
+         "colour step, 3-D 6-neighbour lattice", "colour step, CSR graph"},
+        {"fused sweep, 2-D 4-neighbour lattice", "fused sweep, 2-D 8-neighbour lattice", "", ""},
+        {"hyperparameter draw", "hyperparameter draw", "hyperparameter draw", "hyperparameter draw"}};
+    const gmrf_sampler::Stage &g = s->stages[stage];
+    if (name) *name = kNames[g.type][g.kind < 0 ? 0 : g.kind];
+    const int draw = s->model.fix_hyper ? 0 : 1;
+    cudaError_t e = enqueue_stage(s, static_cast<size_t>(stage), 1, accumulate ? 1 : 0, draw, 1, s->stream);
+    if (e != cudaSuccess) return poison(s, e, "stage launch");
     return GMRF_OK;
 }
 

@@ -40,7 +40,24 @@ struct FieldDev {
     int64_t coff0;      // CSR: first index into the colour-offset array (ncolors + 1 entries)
     int32_t part0;      // first partial-sum slot (tiles of all colours of this field)
     int32_t nparts;     // partial-sum slots of this field
+    uint32_t cols_m;    // lattice: invariant-divisor multiplier and shift of cols (fast_div)
+    int32_t cols_s;
+    uint32_t h_m;       // 3-D lattice: the same for H
+    int32_t h_s;
 };
+
+// Division by an invariant divisor d >= 1 for 0 <= n < 2^31 (Granlund & Montgomery, PLDI'94,
+// round-up variant): s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1, q = (mulhi(n, m) + n) >> s.
+__host__ __device__ __forceinline__ void fast_div_magic(uint32_t d, uint32_t &m, int32_t &s)
+{
+    s = 0;
+    while ((uint64_t(1) << s) < d) ++s;
+    m = static_cast<uint32_t>((uint64_t(1) << 32) * ((uint64_t(1) << s) - d) / d + 1);
+}
+__device__ __forceinline__ int fast_div(int n, uint32_t m, int s)
+{
+    return static_cast<int>((__umulhi(static_cast<uint32_t>(n), m) + static_cast<uint32_t>(n)) >> s);
+}
 
 // A unit of work of one colour step: a range of sub-array rows (lattice) or of permuted
 // positions (CSR) of one field's colour class.

@@ -37,6 +37,38 @@ struct StepArgs {
     int32_t update;      // 1: draw the colour class; 0: only recompute the partial sums
 };
 
+// A tile of the fused 2-D lattice sweep: natural coordinates of its first site.
+struct TileXY {
+    int32_t field;
+    int32_t i0, j0;
+    int32_t part;       // partial-sum slot
+};
+
+// Arguments of one fused-sweep launch (every tile of the fields of one 2-D lattice kind).
+struct FusedArgs {
+    const FieldDev *fields;
+    const TileXY *tiles;
+    int32_t ntiles;
+    int32_t TR, TC;      // tile rows and columns (natural sites)
+    uint32_t rc_m, tc_m; // invariant-divisor constants of the staged row length and of TC
+    int32_t rc_s, tc_s;
+    void *x;             // state buffer 0 (the state at the start of even sweeps)
+    void *x_alt;         // state buffer 1 (the state at the start of odd sweeps)
+    const void *y;
+    void *mean;
+    void *m2;
+    const void *hyp;
+    double2 *partials;
+    const SweepCtl *ctl;
+    uint2 key;
+    int32_t Cp;
+    double rho;
+    long long burn_in;
+    int32_t thin;
+    int32_t acc_enabled;
+    int32_t update;      // 1: run the colour steps; 0: only recompute the partial sums
+};
+
 struct HyperArgs {
     const FieldDev *fields;
     int32_t nfields;
@@ -59,7 +91,8 @@ struct HyperArgs {
 };
 
 // Launchers (each enqueues on `stream` and returns the launch status).
-cudaError_t launch_colour_step(int precision, int V, const StepArgs &a, cudaStream_t stream);
+// One colour step of the tiles in `a` (all of field kind `kind`).
+cudaError_t launch_colour_step(int precision, int V, int kind, const StepArgs &a, cudaStream_t stream);
 cudaError_t launch_hyper(int precision, const HyperArgs &a, cudaStream_t stream);
 cudaError_t launch_pack(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx,
                         int32_t C, int32_t Cp, const double *y_nat, const double *x0_nat,
@@ -72,6 +105,12 @@ cudaError_t launch_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_
                                 uint32_t *out, cudaStream_t stream);
 cudaError_t launch_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream_id, uint32_t chain,
                                 int precision, int64_t count, void *out, cudaStream_t stream);
+
+// Fused 2-D lattice sweep (lattice_fused.cu).
+size_t lattice_fused_smem(int precision, int kind, int Cp, int TR, int TC);
+cudaError_t prepare_lattice_fused(int precision, int V, int kind, size_t smem);
+cudaError_t launch_lattice_fused(int precision, int V, int kind, const FusedArgs &a, size_t smem,
+                                 cudaStream_t stream);
 
 // Jones-Plassmann colouring and colour-permuted CSR layout (csr_build.cu).
 struct CsrBuild {

@@ -12,8 +12,9 @@
 //     (1 - rho) d_i x_i^2 + rho sum_{j lower colour} w_ij (x_i - x_j)^2,   (y_i - x_i)^2,
 // so that after the last colour every undirected edge has been counted once, at its endpoint
 // of higher colour, with both endpoints final: summed over sites this is x'(D - rho W)x.
-// Thread partial sums are in the state precision; warps and blocks reduce in FP64 in a fixed
-// order, so results are reproducible run to run.  When the sweep is accumulated, the Welford
+// Thread, warp and block partial sums are in the state precision (a tile holds at most a few
+// thousand terms); the sums over tiles are FP64; every sum is taken in a fixed order, so
+// results are reproducible run to run.  When the sweep is accumulated, the Welford
 // running mean and M2 of the site are updated in the same pass.
 #include <cuda_runtime.h>
 
@@ -23,7 +24,16 @@
 namespace gmrf {
 namespace {
 
-template <typename T> struct AccOf { using type = T; };
+template <typename T> struct Arith;
+template <> struct Arith<float> {
+    // 1/P and 1/sqrt(P) within 2 ulp: well inside the FP32 parity budget.
+    __device__ __forceinline__ static float rcp(float x) { return __frcp_rn(x); }
+    __device__ __forceinline__ static float rsq(float x) { return rsqrtf(x); }
+};
+template <> struct Arith<double> {
+    __device__ __forceinline__ static double rcp(double x) { return 1.0 / x; }
+    __device__ __forceinline__ static double rsq(double x) { return 1.0 / sqrt(x); }
+};
 
 template <typename T, int V>
 struct SiteCtx {
@@ -33,13 +43,14 @@ struct SiteCtx {
     bool acc;
 };
 
-// Draw (or, in reduce-only mode, read) the V chain values of one site given the neighbour
-// values nb[0..nnb), and fold the site's terms into the partial sums.
+// Draw (or, in reduce-only mode, read) the V chain values of one site given its neighbour sum s
+// and the neighbour values nb[k] of the neighbours flagged in `lower_mask` (those of lower
+// colour), and fold the site's terms into the partial sums.
 template <typename T, int V, int NB>
 __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx, T *xp, T *meanp, T *m2p,
                                             T yv, T d, uint32_t site, uint32_t sweep, uint32_t stream,
                                             uint32_t chain0, const T (&s)[V], const T (&nb)[NB][V],
-                                            uint32_t lower_mask, const T (&wnb)[NB], int nnb)
+                                            uint32_t lower_mask, const T (&wnb)[NB])
 {
     const T rho = static_cast<T>(a.rho);
     T xn[V];
@@ -49,8 +60,8 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const T P = cx.tau[v] * d + cx.isig[v];
-            const T m = (cx.tau[v] * rho * s[v] + yv * cx.isig[v]) / P;
-            xn[v] = m + z[v] / sqrt(P);
+            const T m = (cx.tau[v] * rho * s[v] + yv * cx.isig[v]) * Arith<T>::rcp(P);
+            xn[v] = m + z[v] * Arith<T>::rsq(P);
         }
         Vec<T, V>::st(xp, xn);
     } else {
@@ -58,16 +69,15 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
     }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        T q = (static_cast<T>(1) - rho) * d * xn[v] * xn[v];
         T e = 0;
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
-            if (k < nnb && ((lower_mask >> k) & 1u)) {
+            if ((lower_mask >> k) & 1u) {
                 const T df = xn[v] - nb[k][v];
                 e += wnb[k] * df * df;
             }
         }
-        cx.accS[v] += q + rho * e;
+        cx.accS[v] += (static_cast<T>(1) - rho) * d * xn[v] * xn[v] + rho * e;
         const T r = yv - xn[v];
         cx.accR[v] += r * r;
     }
@@ -89,45 +99,57 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
 // Lattices with parity colourings: 2-D 4-neighbour and 3-D 6-neighbour.  Site of colour c in
 // sub-array row r = l*H + i, column h sits at j = 2h + p, p = (c + l + i) & 1; its in-row
 // neighbours are columns h - 1 + p and h + p of the other colour's row r, the others column h
-// of rows r -+ 1 (i -+ 1) and r -+ H (l -+ 1).
+// of rows r -+ 1 (i -+ 1) and r -+ H (l -+ 1).  Neighbour k has a fixed position in nb[k];
+// missing ones (outside the lattice) are masked.
 template <typename T, int V, bool THREE_D>
 __device__ void lattice_parity_tile(const StepArgs &a, const FieldDev &f, const Tile &t, SiteCtx<T, V> &cx,
-                                    int CV, uint32_t sweep)
+                                    int CV, int cv_shift, uint32_t sweep)
 {
     constexpr int NB = THREE_D ? 6 : 4;
     const int L = THREE_D ? f.dims[0] : 1;
     const int H = THREE_D ? f.dims[1] : f.dims[0];
     const int W = THREE_D ? f.dims[2] : f.dims[1];
     const int c = t.colour;
+    const int cols = f.cols;
     T *X = static_cast<T *>(a.x);
     const T *Y = static_cast<const T *>(a.y);
     T *MEAN = static_cast<T *>(a.mean);
     T *M2 = static_cast<T *>(a.m2);
-    const int64_t Cp = a.Cp;
-    const int64_t self_base = f.slot0 + static_cast<int64_t>(c) * f.rows * f.cols;
-    const int64_t oth_base = f.slot0 + static_cast<int64_t>(1 - c) * f.rows * f.cols;
-    const bool lower = (c == 1);  // all neighbours have the other colour
-    const int64_t nelem = static_cast<int64_t>(t.count) * f.cols * CV;
-    for (int64_t e = threadIdx.x; e < nelem; e += kBlock) {
-        const int cv = static_cast<int>(e % CV);
-        const int64_t sr = e / CV;
-        const int r = t.start + static_cast<int>(sr / f.cols);
-        const int h = static_cast<int>(sr % f.cols);
-        const int l = THREE_D ? r / H : 0;
+    const int Cp = a.Cp;
+    const int cvo = (threadIdx.x & (CV - 1)) * V;  // chain offset of this thread (fixed)
+    const int64_t self_base = f.slot0 + static_cast<int64_t>(c) * f.rows * cols;
+    const int64_t oth_base = f.slot0 + static_cast<int64_t>(1 - c) * f.rows * cols;
+    const T *XO = X + oth_base * Cp + cvo;
+    T *XS = X + self_base * Cp + cvo;
+    T *MS = MEAN + self_base * Cp + cvo;
+    T *QS = M2 + self_base * Cp + cvo;
+    const T *YS = Y + self_base;
+    const uint32_t lower_all = (c == 1) ? 0xffu : 0u;  // all neighbours have the other colour
+    const int plane = H * cols;
+    const int nelem = t.count * cols * CV;
+    for (int e = threadIdx.x; e < nelem; e += kBlock) {
+        const int cv = e & (CV - 1);
+        const int sr = e >> cv_shift;
+        const int rr = fast_div(sr, f.cols_m, f.cols_s);
+        const int h = sr - rr * cols;
+        const int r = t.start + rr;
+        const int l = THREE_D ? fast_div(r, f.h_m, f.h_s) : 0;
         const int i = THREE_D ? r - l * H : r;
         const int p = (c + l + i) & 1;
         const int j = 2 * h + p;
         if (j >= W)
             continue;
-        int64_t ns[NB];
-        int nnb = 0;
-        if (j > 0) ns[nnb++] = static_cast<int64_t>(r) * f.cols + (h - 1 + p);
-        if (j + 1 < W) ns[nnb++] = static_cast<int64_t>(r) * f.cols + (h + p);
-        if (i > 0) ns[nnb++] = static_cast<int64_t>(r - 1) * f.cols + h;
-        if (i + 1 < H) ns[nnb++] = static_cast<int64_t>(r + 1) * f.cols + h;
+        uint32_t valid = (j > 0 ? 1u : 0u) | (j + 1 < W ? 2u : 0u) | (i > 0 ? 4u : 0u) | (i + 1 < H ? 8u : 0u);
+        if (THREE_D) valid |= (l > 0 ? 16u : 0u) | (l + 1 < L ? 32u : 0u);
+        const int rb = r * cols + h;
+        int ns[NB];
+        ns[0] = rb - 1 + p;
+        ns[1] = rb + p;
+        ns[2] = rb - cols;
+        ns[3] = rb + cols;
         if (THREE_D) {
-            if (l > 0) ns[nnb++] = static_cast<int64_t>(r - H) * f.cols + h;
-            if (l + 1 < L) ns[nnb++] = static_cast<int64_t>(r + H) * f.cols + h;
+            ns[4] = rb - plane;
+            ns[5] = rb + plane;
         }
         T nb[NB][V], wnb[NB], s[V];
 #pragma unroll
@@ -135,78 +157,97 @@ __device__ void lattice_parity_tile(const StepArgs &a, const FieldDev &f, const 
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             wnb[k] = 1;
-            if (k < nnb) {
-                Vec<T, V>::ld(X + (oth_base + ns[k]) * Cp + cv * V, nb[k]);
+            if ((valid >> k) & 1u) {
+                Vec<T, V>::ld(XO + ns[k] * Cp, nb[k]);
+            } else {
 #pragma unroll
-                for (int v = 0; v < V; ++v) s[v] += nb[k][v];
+                for (int v = 0; v < V; ++v) nb[k][v] = 0;
             }
+#pragma unroll
+            for (int v = 0; v < V; ++v) s[v] += nb[k][v];
         }
-        const int64_t self = self_base + static_cast<int64_t>(r) * f.cols + h;
-        const uint32_t site = static_cast<uint32_t>(static_cast<int64_t>(r) * W + j);
-        finish_site<T, V, NB>(a, cx, X + self * Cp + cv * V, MEAN + self * Cp + cv * V, M2 + self * Cp + cv * V,
-                              Y[self], static_cast<T>(nnb), site, sweep, f.stream, static_cast<uint32_t>(cv * V),
-                              s, nb, lower ? 0xffu : 0u, wnb, nnb);
+        const uint32_t site = static_cast<uint32_t>(r * W + j);
+        finish_site<T, V, NB>(a, cx, XS + rb * Cp, MS + rb * Cp, QS + rb * Cp, YS[rb], static_cast<T>(__popc(valid)),
+                              site, sweep, f.stream, static_cast<uint32_t>(cv * V), s, nb, lower_all & valid, wnb);
     }
 }
 
 // 2-D 8-neighbour lattice with the 2x2 colouring c = 2 (i & 1) + (j & 1): the site of colour
 // c = 2a + b at sub-array (u, v) is (2u + a, 2v + b); neighbour (i + di, j + dj) lives in
-// colour 2((i + di) & 1) + ((j + dj) & 1) at ((i + di) >> 1, (j + dj) >> 1).
+// colour 2((a + di) & 1) + ((b + dj) & 1) at sub-array (u + ((a + di) >> 1), v + ((b + dj) >> 1)).
 template <typename T, int V>
 __device__ void lattice8_tile(const StepArgs &a, const FieldDev &f, const Tile &t, SiteCtx<T, V> &cx, int CV,
-                              uint32_t sweep)
+                              int cv_shift, uint32_t sweep)
 {
     constexpr int NB = 8;
     const int H = f.dims[0], W = f.dims[1];
     const int c = t.colour;
     const int ca = c >> 1, cb = c & 1;
+    const int cols = f.cols;
     T *X = static_cast<T *>(a.x);
     const T *Y = static_cast<const T *>(a.y);
     T *MEAN = static_cast<T *>(a.mean);
     T *M2 = static_cast<T *>(a.m2);
-    const int64_t Cp = a.Cp;
-    const int64_t sub = static_cast<int64_t>(f.rows) * f.cols;
-    const int64_t nelem = static_cast<int64_t>(t.count) * f.cols * CV;
-    for (int64_t e = threadIdx.x; e < nelem; e += kBlock) {
-        const int cv = static_cast<int>(e % CV);
-        const int64_t sr = e / CV;
-        const int u = t.start + static_cast<int>(sr / f.cols);
-        const int vv = static_cast<int>(sr % f.cols);
+    const int Cp = a.Cp;
+    const int cvo = (threadIdx.x & (CV - 1)) * V;  // chain offset of this thread (fixed)
+    const int sub = f.rows * cols;
+    const T *XF = X + f.slot0 * Cp + cvo;
+    T *XS = X + (f.slot0 + static_cast<int64_t>(c) * sub) * Cp + cvo;
+    T *MS = MEAN + (f.slot0 + static_cast<int64_t>(c) * sub) * Cp + cvo;
+    T *QS = M2 + (f.slot0 + static_cast<int64_t>(c) * sub) * Cp + cvo;
+    const T *YS = Y + f.slot0 + static_cast<int64_t>(c) * sub;
+    // Per direction (block-uniform): offset of the neighbour's slot relative to (u, v) in its
+    // colour's sub-array, and whether that colour is lower than c.
+    int doff[NB];
+    uint32_t lower = 0;
+#pragma unroll
+    for (int k = 0, q = 0; q < 9; ++q) {
+        const int di = q / 3 - 1, dj = q % 3 - 1;
+        if (di == 0 && dj == 0) continue;
+        const int cc = 2 * ((ca + di) & 1) + ((cb + dj) & 1);
+        doff[k] = cc * sub + ((ca + di) >> 1) * cols + ((cb + dj) >> 1);
+        if (cc < c) lower |= 1u << k;
+        ++k;
+    }
+    const int nelem = t.count * cols * CV;
+    for (int e = threadIdx.x; e < nelem; e += kBlock) {
+        const int cv = e & (CV - 1);
+        const int sr = e >> cv_shift;
+        const int rr = fast_div(sr, f.cols_m, f.cols_s);
+        const int vv = sr - rr * cols;
+        const int u = t.start + rr;
         const int i = 2 * u + ca, j = 2 * vv + cb;
         if (i >= H || j >= W)
             continue;
-        int64_t ns[NB];
-        uint32_t lower = 0;
-        int nnb = 0;
+        const int base = u * cols + vv;
+        uint32_t valid = 0;
 #pragma unroll
-        for (int di = -1; di <= 1; ++di)
-#pragma unroll
-            for (int dj = -1; dj <= 1; ++dj) {
-                if (di == 0 && dj == 0) continue;
-                const int ii = i + di, jj = j + dj;
-                if (ii < 0 || ii >= H || jj < 0 || jj >= W) continue;
-                const int cc = 2 * (ii & 1) + (jj & 1);
-                ns[nnb] = f.slot0 + cc * sub + static_cast<int64_t>(ii >> 1) * f.cols + (jj >> 1);
-                if (cc < c) lower |= 1u << nnb;
-                ++nnb;
-            }
+        for (int k = 0, q = 0; q < 9; ++q) {
+            const int di = q / 3 - 1, dj = q % 3 - 1;
+            if (di == 0 && dj == 0) continue;
+            const bool ok = (i + di >= 0) && (i + di < H) && (j + dj >= 0) && (j + dj < W);
+            valid |= ok ? (1u << k) : 0u;
+            ++k;
+        }
         T nb[NB][V], wnb[NB], s[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) s[v] = 0;
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             wnb[k] = 1;
-            if (k < nnb) {
-                Vec<T, V>::ld(X + ns[k] * Cp + cv * V, nb[k]);
+            if ((valid >> k) & 1u) {
+                Vec<T, V>::ld(XF + (doff[k] + base) * Cp, nb[k]);
+            } else {
 #pragma unroll
-                for (int v = 0; v < V; ++v) s[v] += nb[k][v];
+                for (int v = 0; v < V; ++v) nb[k][v] = 0;
             }
+#pragma unroll
+            for (int v = 0; v < V; ++v) s[v] += nb[k][v];
         }
-        const int64_t self = f.slot0 + c * sub + static_cast<int64_t>(u) * f.cols + vv;
-        const uint32_t site = static_cast<uint32_t>(static_cast<int64_t>(i) * W + j);
-        finish_site<T, V, NB>(a, cx, X + self * Cp + cv * V, MEAN + self * Cp + cv * V, M2 + self * Cp + cv * V,
-                              Y[self], static_cast<T>(nnb), site, sweep, f.stream, static_cast<uint32_t>(cv * V),
-                              s, nb, lower, wnb, nnb);
+        const uint32_t site = static_cast<uint32_t>(i * W + j);
+        finish_site<T, V, NB>(a, cx, XS + base * Cp, MS + base * Cp, QS + base * Cp, YS[base],
+                              static_cast<T>(__popc(valid)), site, sweep, f.stream, static_cast<uint32_t>(cv * V),
+                              s, nb, lower & valid, wnb);
     }
 }
 
@@ -215,7 +256,7 @@ __device__ void lattice8_tile(const StepArgs &a, const FieldDev &f, const Tile &
 // first position.  The lower-colour terms of the reduction take a second pass over the row.
 template <typename T, int V>
 __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, SiteCtx<T, V> &cx, int CV,
-                         uint32_t sweep)
+                         int cv_shift, uint32_t sweep)
 {
     T *X = static_cast<T *>(a.x);
     const T *Y = static_cast<const T *>(a.y);
@@ -229,10 +270,10 @@ __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, Si
     const T *wr = Wt ? Wt + f.nnz0 : nullptr;
     const int32_t lo = a.coff[f.coff0 + t.colour];
     const T rho = static_cast<T>(a.rho);
-    const int64_t nelem = static_cast<int64_t>(t.count) * CV;
-    for (int64_t e = threadIdx.x; e < nelem; e += kBlock) {
-        const int cv = static_cast<int>(e % CV);
-        const int pos = t.start + static_cast<int>(e / CV);
+    const int nelem = t.count * CV;
+    for (int e = threadIdx.x; e < nelem; e += kBlock) {
+        const int cv = e & (CV - 1);
+        const int pos = t.start + (e >> cv_shift);
         const int rb = rp[pos], re = rp[pos + 1];
         T s[V];
 #pragma unroll
@@ -251,7 +292,7 @@ __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, Si
         T nb0[1][V];
         T w0[1] = {0};
         finish_site<T, V, 1>(a, cx, X + self * Cp + cv * V, MEAN + self * Cp + cv * V, M2 + self * Cp + cv * V, yv,
-                             d, site, sweep, f.stream, static_cast<uint32_t>(cv * V), s, nb0, 0u, w0, 0);
+                             d, site, sweep, f.stream, static_cast<uint32_t>(cv * V), s, nb0, 0u, w0);
         // finish_site added (1 - rho) d x^2 and the likelihood term; add the lower-colour edges.
         T xn[V];
         Vec<T, V>::ld(X + self * Cp + cv * V, xn);
@@ -275,7 +316,7 @@ __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, Si
     }
 }
 
-template <typename T, int V>
+template <typename T, int V, int KIND>
 __global__ void __launch_bounds__(kBlock) colour_step_kernel(const StepArgs a)
 {
     const Tile t = a.tiles[blockIdx.x];
@@ -302,19 +343,21 @@ __global__ void __launch_bounds__(kBlock) colour_step_kernel(const StepArgs a)
         cx.inv_k = static_cast<T>(1) / static_cast<T>(a.ctl->acc_count + 1);
     }
 
-    if (f.kind == kLat2D4) lattice_parity_tile<T, V, false>(a, f, t, cx, CV, sweep);
-    else if (f.kind == kLat3D6) lattice_parity_tile<T, V, true>(a, f, t, cx, CV, sweep);
-    else if (f.kind == kLat2D8) lattice8_tile<T, V>(a, f, t, cx, CV, sweep);
-    else csr_tile<T, V>(a, f, t, cx, CV, sweep);
+    const int cv_shift = __ffs(CV) - 1;
+    if constexpr (KIND == kLat2D4) lattice_parity_tile<T, V, false>(a, f, t, cx, CV, cv_shift, sweep);
+    else if constexpr (KIND == kLat3D6) lattice_parity_tile<T, V, true>(a, f, t, cx, CV, cv_shift, sweep);
+    else if constexpr (KIND == kLat2D8) lattice8_tile<T, V>(a, f, t, cx, CV, cv_shift, sweep);
+    else csr_tile<T, V>(a, f, t, cx, CV, cv_shift, sweep);
 
-    // Deterministic block reduction of the 2 V partial sums of each chain: FP64 shuffle tree
-    // over the lanes that share a chain vector (lanes equal mod CV), then warps in order.
-    __shared__ double red[kBlock / 32][kMaxChains][2];
+    // Deterministic block reduction of the 2 V partial sums of each chain in the state precision:
+    // a shuffle tree over the lanes that share a chain vector (lanes equal mod CV), then the
+    // warps' sums in order; the tile's sum is stored in FP64 and summed over tiles in FP64.
+    __shared__ T red[kBlock / 32][kMaxChains][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        double sS = static_cast<double>(cx.accS[v]);
-        double sR = static_cast<double>(cx.accR[v]);
+        T sS = cx.accS[v];
+        T sR = cx.accR[v];
         for (int off = 16; off >= CV; off >>= 1) {
             sS += __shfl_xor_sync(0xffffffffu, sS, off);
             sR += __shfl_xor_sync(0xffffffffu, sR, off);
@@ -327,77 +370,67 @@ __global__ void __launch_bounds__(kBlock) colour_step_kernel(const StepArgs a)
     __syncthreads();
     for (int q = threadIdx.x; q < a.Cp * 2; q += kBlock) {
         const int chain = q >> 1, k = q & 1;
-        double acc = 0.0;
+        T acc = 0;
         for (int w = 0; w < kBlock / 32; ++w) acc += red[w][chain][k];
         double *dst = reinterpret_cast<double *>(a.partials + static_cast<int64_t>(t.part) * a.Cp + chain);
-        dst[k] = acc;
+        dst[k] = static_cast<double>(acc);
     }
 }
 
-// One block per (field, chain): the block sums the field's tile partials in a fixed order (thread
-// strides, then a shuffle tree, then warps in order) and thread 0 draws tau and 1/sigma^2 from
-// their Gamma full conditionals (Sec. 3.1), refreshes the precision-T copies the colour kernels
-// read, and records the traces.  The last block to finish (ticket counter; no block waits for
-// another) advances the sweep counter, the accumulation count, or the extra-draw counter.
+// Two blocks per (field, chain): block 2p draws tau of pair p, block 2p + 1 draws 1/sigma^2 (the
+// two are conditionally independent given x, Sec. 3.1).  Each sums its sum (x'(D - rho W)x or
+// ||y - x||^2) over the field's tile partials in a fixed order (thread strides, shuffle tree,
+// warps in order), then thread 0 draws from the Gamma full conditional, refreshes the
+// precision-T copy the colour kernels read, and records the trace.  FP64 arithmetic has a long
+// dependent-operation latency on this GPU, so the two draws run in parallel.  The last block to
+// finish (ticket counter; no block waits for another) advances the sweep counter, the
+// accumulation count, or the extra-draw counter.
 template <typename T>
 __global__ void __launch_bounds__(256) hyper_kernel(const HyperArgs a)
 {
-    __shared__ double red[8][2];
+    __shared__ double red[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long sweep = a.ctl->sweep;
     const long long extra = a.ctl->extra;
-    const int pidx = blockIdx.x;
+    const int pidx = blockIdx.x >> 1, which = blockIdx.x & 1;  // which: 0 tau, 1 sigma^2
     const int fi = pidx / a.Cp, chain = pidx - fi * a.Cp;
     const FieldDev f = a.fields[fi];
-    double S = 0.0, R = 0.0;
+    double S = 0.0;
     if (a.draw) {
         for (int k = threadIdx.x; k < f.nparts; k += blockDim.x) {
             const double2 p = a.partials[static_cast<int64_t>(f.part0 + k) * a.Cp + chain];
-            S += p.x;
-            R += p.y;
+            S += which ? p.y : p.x;
         }
-        for (int off = 16; off >= 1; off >>= 1) {
-            S += __shfl_xor_sync(0xffffffffu, S, off);
-            R += __shfl_xor_sync(0xffffffffu, R, off);
-        }
-        if (lane == 0) {
-            red[warp][0] = S;
-            red[warp][1] = R;
-        }
+        for (int off = 16; off >= 1; off >>= 1) S += __shfl_xor_sync(0xffffffffu, S, off);
+        if (lane == 0) red[warp] = S;
         __syncthreads();
-        S = 0.0;
-        R = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            S += red[w][0];
-            R += red[w][1];
-        }
+        S = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
     }
     if (threadIdx.x == 0) {
         const int64_t hc = static_cast<int64_t>(fi) * a.Cp + chain;
-        double tau = a.tau[hc], sig2 = a.sig2[hc];
+        double val = which ? a.sig2[hc] : a.tau[hc];
         if (a.draw) {
             const uint32_t word1 = static_cast<uint32_t>(a.end_of_sweep ? sweep : extra);
-            const uint32_t ttag = (a.end_of_sweep ? kTagTau : kTagTauExtra) << 24;
-            const uint32_t stag = (a.end_of_sweep ? kTagSig : kTagSigExtra) << 24;
-            int fb1 = 0, fb2 = 0;
-            tau = gamma_mt(a.a_tau + 0.5 * f.rank, a.b_tau + 0.5 * S, a.key, word1, f.stream,
-                           ttag | static_cast<uint32_t>(chain), fb1);
-            const double prec = gamma_mt(a.a_sig + 0.5 * f.n, a.b_sig + 0.5 * R, a.key, word1, f.stream,
-                                         stag | static_cast<uint32_t>(chain), fb2);
-            sig2 = 1.0 / prec;
-            if (fb1 + fb2)
-                atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks),
-                          static_cast<unsigned long long>(fb1 + fb2));
-            a.tau[hc] = tau;
-            a.sig2[hc] = sig2;
+            const uint32_t tag = which ? (a.end_of_sweep ? kTagSig : kTagSigExtra) : (a.end_of_sweep ? kTagTau : kTagTauExtra);
+            int fb = 0;
+            const double shape = which ? a.a_sig + 0.5 * f.n : a.a_tau + 0.5 * f.rank;
+            const double rate = which ? a.b_sig + 0.5 * S : a.b_tau + 0.5 * S;
+            const double g = gamma_mt(shape, rate, a.key, word1, f.stream, (tag << 24) | static_cast<uint32_t>(chain), fb);
+            if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), 1ull);
             T *hyp = static_cast<T *>(a.hyp);
-            hyp[hc * 2] = static_cast<T>(tau);
-            hyp[hc * 2 + 1] = static_cast<T>(prec);
+            if (which) {
+                val = 1.0 / g;
+                a.sig2[hc] = val;
+                hyp[hc * 2 + 1] = static_cast<T>(g);
+            } else {
+                val = g;
+                a.tau[hc] = val;
+                hyp[hc * 2] = static_cast<T>(g);
+            }
         }
         if (a.end_of_sweep && a.trace_cap > 0) {
             const int64_t slot = hc * a.trace_cap + (sweep % a.trace_cap);
-            a.trace_tau[slot] = tau;
-            a.trace_sig[slot] = sig2;
+            (which ? a.trace_sig : a.trace_tau)[slot] = val;
         }
         __threadfence();
         const unsigned long long done = atomicAdd(&a.ctl->ticket, 1ull);
@@ -479,24 +512,35 @@ int grid_for(int64_t n, int block)
 
 }  // namespace
 
-cudaError_t launch_colour_step(int precision, int V, const StepArgs &a, cudaStream_t stream)
+template <int KIND>
+void launch_kind(int precision, int V, const StepArgs &a, cudaStream_t stream)
 {
-    if (a.ntiles <= 0) return cudaSuccess;
     const dim3 grid(a.ntiles), block(kBlock);
     if (precision == 0) {
-        if (V == 4) colour_step_kernel<float, 4><<<grid, block, 0, stream>>>(a);
-        else if (V == 2) colour_step_kernel<float, 2><<<grid, block, 0, stream>>>(a);
-        else colour_step_kernel<float, 1><<<grid, block, 0, stream>>>(a);
+        if (V == 4) colour_step_kernel<float, 4, KIND><<<grid, block, 0, stream>>>(a);
+        else if (V == 2) colour_step_kernel<float, 2, KIND><<<grid, block, 0, stream>>>(a);
+        else colour_step_kernel<float, 1, KIND><<<grid, block, 0, stream>>>(a);
     } else {
-        if (V == 2) colour_step_kernel<double, 2><<<grid, block, 0, stream>>>(a);
-        else colour_step_kernel<double, 1><<<grid, block, 0, stream>>>(a);
+        if (V == 2) colour_step_kernel<double, 2, KIND><<<grid, block, 0, stream>>>(a);
+        else colour_step_kernel<double, 1, KIND><<<grid, block, 0, stream>>>(a);
+    }
+}
+
+cudaError_t launch_colour_step(int precision, int V, int kind, const StepArgs &a, cudaStream_t stream)
+{
+    if (a.ntiles <= 0) return cudaSuccess;
+    switch (kind) {
+    case kLat2D4: launch_kind<kLat2D4>(precision, V, a, stream); break;
+    case kLat2D8: launch_kind<kLat2D8>(precision, V, a, stream); break;
+    case kLat3D6: launch_kind<kLat3D6>(precision, V, a, stream); break;
+    default: launch_kind<kCsr>(precision, V, a, stream); break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_hyper(int precision, const HyperArgs &a, cudaStream_t stream)
 {
-    const int grid = a.nfields * a.Cp;
+    const int grid = a.nfields * a.Cp * 2;
     if (precision == 0) hyper_kernel<float><<<grid, 256, 0, stream>>>(a);
     else hyper_kernel<double><<<grid, 256, 0, stream>>>(a);
     return cudaGetLastError();

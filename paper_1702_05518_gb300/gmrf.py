@@ -20,10 +20,11 @@ LATTICE2D_4, LATTICE2D_8, LATTICE3D_6, CSR = range(4)
 PRIOR_ICAR, PRIOR_PCAR = 0, 1
 FP32, FP64 = 0, 1
 ALGO_CHROMATIC, ALGO_PLAIN = 0, 1
+FLAG_PER_COLOUR = 1
 
 EXPORTED = ["gmrf_color_graph", "gmrf_sampler_create", "gmrf_sampler_destroy", "gmrf_sweep",
             "gmrf_hyper_update", "gmrf_fetch_samples", "gmrf_field_colors", "gmrf_sampler_info",
-            "gmrf_sampler_reset", "gmrf_launch_colour_step",
+            "gmrf_sampler_reset", "gmrf_launch_stage",
             "gmrf_validate_csr", "gmrf_philox_words", "gmrf_site_normals", "gmrf_last_error",
             "gmrf_version"]
 
@@ -57,7 +58,7 @@ class Opts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("start_sweep", ctypes.c_int64),
                 ("burn_in", ctypes.c_int64), ("thin", ctypes.c_int32),
                 ("trace_capacity", ctypes.c_int32), ("algorithm", ctypes.c_int32),
-                ("graph_sweeps", ctypes.c_int32)]
+                ("graph_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -96,8 +97,8 @@ def lib() -> ctypes.CDLL:
             L.gmrf_sweep.restype = st
             L.gmrf_sampler_reset.argtypes = [vp]
             L.gmrf_sampler_reset.restype = st
-            L.gmrf_launch_colour_step.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
-            L.gmrf_launch_colour_step.restype = st
+            L.gmrf_launch_stage.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_char_p)]
+            L.gmrf_launch_stage.restype = st
             L.gmrf_hyper_update.argtypes = [vp]
             L.gmrf_hyper_update.restype = st
             L.gmrf_fetch_samples.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, f64p, f64p, f64p,
@@ -208,7 +209,7 @@ class Sampler:
     def __init__(self, fields, *, precision=FP32, chains=1, seed=0, prior=PRIOR_ICAR, rho=1.0,
                  a_tau=1.0, b_tau=0.01, a_sigma=1.0, b_sigma=0.01, fix_hyper=False, tau0=1.0,
                  sigma2_0=1.0, start_sweep=0, burn_in=0, thin=1, trace_capacity=4096,
-                 algorithm=ALGO_CHROMATIC, graph_sweeps=0, stream=None):
+                 algorithm=ALGO_CHROMATIC, graph_sweeps=0, flags=0, stream=None):
         L = lib()
         self._h = ctypes.c_void_p()
         self.chains = int(chains)
@@ -251,7 +252,7 @@ class Sampler:
         model = Model(int(prior), float(rho), float(a_tau), float(b_tau), float(a_sigma),
                       float(b_sigma), 1 if fix_hyper else 0, float(tau0), float(sigma2_0))
         opts = Opts(int(precision), self.chains, int(seed), int(start_sweep), int(burn_in),
-                    int(thin), int(trace_capacity), int(algorithm), int(graph_sweeps))
+                    int(thin), int(trace_capacity), int(algorithm), int(graph_sweeps), int(flags))
         self.stream = current_stream() if stream is None else stream
         _check(L.gmrf_sampler_create(ctypes.byref(self._h), descs, len(fields), ctypes.byref(model),
                                      ctypes.byref(opts), self.stream))
@@ -280,8 +281,11 @@ class Sampler:
     def reset(self):
         _check(lib().gmrf_sampler_reset(self._h))
 
-    def launch_colour_step(self, colour, accumulate=False):
-        _check(lib().gmrf_launch_colour_step(self._h, int(colour), 1 if accumulate else 0))
+    def launch_stage(self, stage, accumulate=False):
+        """Launch stage `stage` of a sweep once (diagnostic); returns the stage's description."""
+        name = ctypes.c_char_p()
+        _check(lib().gmrf_launch_stage(self._h, int(stage), 1 if accumulate else 0, ctypes.byref(name)))
+        return name.value.decode()
 
     def hyper_update(self):
         _check(lib().gmrf_hyper_update(self._h))

@@ -288,3 +288,53 @@ def test_field_colours_reported():
     want0 = oracle_colors(f)
     assert np.array_equal(c0, want0) and k0 == want0.max() + 1
     assert np.array_equal(c1, oracle.lattice_colors(oracle.LAT2D_8, (6, 7))[0]) and k1 == 4
+
+
+# --------------------------------------------------------------------------------------------
+# Fused one-launch-per-sweep 2-D lattice kernel vs the per-colour launches vs the oracle
+# --------------------------------------------------------------------------------------------
+FUSED = [("2d4_150x133", wl.LATTICE2D_4, (150, 133)), ("2d8_131x140", wl.LATTICE2D_8, (131, 140)),
+         ("2d8_17x200", wl.LATTICE2D_8, (17, 200)), ("2d4_3x300", wl.LATTICE2D_4, (3, 300)),
+         ("2d8_65x64", wl.LATTICE2D_8, (65, 64))]
+
+
+@pytest.mark.parametrize("name,kind,dims", FUSED, ids=[c[0] for c in FUSED])
+@pytest.mark.parametrize("chains", [1, 3, 8])
+@pytest.mark.parametrize("flags", [0, g.FLAG_PER_COLOUR], ids=["fused", "per_colour"])
+def test_lattice_paths_one_sweep(name, kind, dims, chains, flags):
+    f = wl.small_lattice(kind, dims, 21)
+    res, info = gpu_run([f], chains, 1, g.FP32, seed=73, flags=flags)
+    compare(f, res[0], chains, 1, 73, 0, TOL_FP32_1)
+    k = 4 if kind == wl.LATTICE2D_8 else 2
+    assert info["launches_per_sweep"] == (2 if flags == 0 else k + 1)
+
+
+@pytest.mark.parametrize("precision,T,tol", [(g.FP32, 300, TOL_FP32_1000), (g.FP64, 100, TOL_FP64)])
+@pytest.mark.parametrize("kind,dims", [(wl.LATTICE2D_8, (130, 97)), (wl.LATTICE2D_4, (99, 140))])
+def test_fused_long_run(precision, T, tol, kind, dims):
+    f = wl.small_lattice(kind, dims, 22)
+    res, _ = gpu_run([f], 2, T, precision, seed=79, graph_sweeps=10, burn_in=T // 3)
+    st, _ = compare(f, res[0], 2, T, 79, 0, tol, burn_in=T // 3)
+    for c in range(2):
+        assert relerr(res[0][c]["mean"], st.mean[c]) <= tol
+
+
+def test_fused_and_per_colour_agree_to_rounding():
+    f = wl.small_lattice(wl.LATTICE2D_8, (140, 150), 23)
+    a, _ = gpu_run([f], 2, 50, g.FP64, seed=83)
+    b, _ = gpu_run([f], 2, 50, g.FP64, seed=83, flags=g.FLAG_PER_COLOUR)
+    for c in range(2):
+        assert relerr(a[0][c]["x"], b[0][c]["x"]) <= TOL_FP64
+        assert trace_relerr(a[0][c]["tau_trace"], b[0][c]["tau_trace"]) <= TOL_FP64
+
+
+def test_stage_launch_diagnostic():
+    fields = [wl.small_lattice(wl.LATTICE2D_8, (40, 40), 1), _delaunay(300, 2)]
+    with g.Sampler(fields, chains=1, seed=3) as s:
+        info = s.info()
+        names = [s.launch_stage(k) for k in range(info["launches_per_sweep"])]
+        with pytest.raises(g.GmrfError):
+            s.launch_stage(info["launches_per_sweep"])
+    assert names[0].startswith("fused sweep, 2-D 8-neighbour")
+    assert names[-1] == "hyperparameter draw"
+    assert all(n.startswith("colour step, CSR") for n in names[1:-1])
