@@ -419,7 +419,10 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{spec['cpu_sweeps']} sweeps of the full workload ({u} site-updates, {dt:.1f} s); "
                          f"CPU: {cpu_model()}"}
-    launches = args.steps * spec["sweeps"] * info["launches_per_sweep"] + args.steps  # + reset kernel
+    # per step: every stage of every sweep, one Gamma-variate batch per 64 (or graph_sweeps)
+    # sweeps, and the restart kernel
+    batch = max(64, spec["graph_sweeps"])
+    launches = args.steps * (spec["sweeps"] * info["launches_per_sweep"] + -(-spec["sweeps"] // batch) + 1)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

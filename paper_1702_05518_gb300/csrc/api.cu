@@ -4,6 +4,7 @@
 // csr_build.cu and plain.cu; this file only validates, allocates, launches and copies.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <numeric>
@@ -83,6 +84,8 @@ struct gmrf_sampler {
     double2 *partials = nullptr;
     double *trace_tau = nullptr, *trace_sig = nullptr;
     SweepCtl *ctl = nullptr;
+    double *gpre = nullptr;     // [gpre_batch][F * Cp][2] unit-rate Gamma variates of a batch
+    int32_t gpre_batch = 0;     // sweeps per batch of precomputed variates
     double *staging = nullptr;  // [max_n] doubles for fetch
     void *x_init = nullptr;     // state at creation (for gmrf_sampler_reset)
     double *tau_init = nullptr, *sig2_init = nullptr;
@@ -401,7 +404,23 @@ HyperArgs hyper_args(gmrf_sampler *s, int draw, int end_of_sweep)
     h.burn_in = s->opts.burn_in;
     h.thin = s->opts.thin;
     h.acc_enabled = 1;
+    h.gpre = s->gpre;
     return h;
+}
+
+cudaError_t launch_pre(gmrf_sampler *s, int count, cudaStream_t st)
+{
+    GammaPreArgs g{};
+    g.fields = s->fields_dev;
+    g.nfields = s->nfields;
+    g.Cp = s->Cp;
+    g.ctl = s->ctl;
+    g.key = philox_key(s->opts.seed);
+    g.a_tau = s->model.a_tau;
+    g.a_sig = s->model.a_sigma;
+    g.count = count;
+    g.gpre = s->gpre;
+    return launch_gamma_pre(g, st);
 }
 
 FusedArgs fused_args(gmrf_sampler *s, int kind, int update, int accumulate)
@@ -451,6 +470,10 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int draw, cudaStream_t 
 {
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < nsweeps && e == cudaSuccess; ++k) {
+        // A batch of sweeps starts with the parallel draw of its unit-rate Gamma variates.
+        if (draw && s->gpre && k % s->gpre_batch == 0)
+            e = launch_pre(s, std::min(s->gpre_batch, nsweeps - k), st);
+        if (e != cudaSuccess) break;
         if (s->algorithm == GMRF_ALGO_PLAIN) {
             PlainArgs a = s->plain;
             a.draw = draw;
@@ -714,21 +737,32 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     // most 16384 elements per tile); partial-sum slots are contiguous per field.
     const int CV = s->Cp / s->V;
     // 2-D lattice fields take the fused sweep when a tile of at least 16 x 16 sites with its
-    // halo fits the 48 KiB shared-memory budget (4 blocks per SM) and it is not switched off.
+    // halo (state, normals and y) fits the 72 KiB shared-memory budget (3 blocks per SM) and it
+    // is not switched off.
     bool fused_kind[4] = {false, false, false, false};
     const bool allow_fused = (s->opts.flags & GMRF_FLAG_PER_COLOUR) == 0;
     for (int kind : {static_cast<int>(GMRF_LATTICE2D_4), static_cast<int>(GMRF_LATTICE2D_8)}) {
         const int K = kind == GMRF_LATTICE2D_8 ? 4 : 2;
-        const double per_site = static_cast<double>(T) * (s->Cp + 1);
-        int side = static_cast<int>(std::floor(std::sqrt(48.0 * 1024.0 / per_site))) - 2 * K;
+        const double per_site = static_cast<double>(T) * (2 * s->Cp + 1);
+        int side = static_cast<int>(std::floor(std::sqrt(72.0 * 1024.0 / per_site))) - 2 * K;
         side = std::min(64, side - side % 8);
         if (!allow_fused || side < 16) continue;
         for (auto &h : s->hf)
             if (h.kind == kind) fused_kind[kind] = true;
         if (fused_kind[kind]) {
-            s->fTR[kind] = side;
-            s->fTC[kind] = side;
-            s->fsmem[kind] = lattice_fused_smem(s->precision, kind, s->Cp, side, side);
+            int tr = side, tc = side;
+            // Tuning override: GMRF_FUSED_TILE="<rows>x<cols>" (each 8..256, within the budget).
+            if (const char *env = std::getenv("GMRF_FUSED_TILE")) {
+                int r = 0, c = 0;
+                if (std::sscanf(env, "%dx%d", &r, &c) == 2 && r >= 8 && c >= 8 && r <= 256 && c <= 256 &&
+                    lattice_fused_smem(s->precision, kind, s->Cp, r, c) <= 160 * 1024) {
+                    tr = r;
+                    tc = c;
+                }
+            }
+            s->fTR[kind] = tr;
+            s->fTC[kind] = tc;
+            s->fsmem[kind] = lattice_fused_smem(s->precision, kind, s->Cp, tr, tc);
             CK(prepare_lattice_fused(s->precision, s->V, kind, s->fsmem[kind]));
         }
     }
@@ -854,6 +888,8 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
         }
     CK(s->alloc_t(&s->tau, nh, sizeof(double)));
     CK(s->alloc_t(&s->sig2, nh, sizeof(double)));
+    s->gpre_batch = std::max(64, s->opts.graph_sweeps);
+    CK(s->alloc_t(&s->gpre, static_cast<size_t>(s->gpre_batch) * nh * 2, sizeof(double)));
     CK(s->alloc(&s->hyp, nh * 2 * T));
     CK(cudaMemcpyAsync(s->tau, t0.data(), nh * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(s->sig2, s0.data(), nh * sizeof(double), cudaMemcpyHostToDevice, s->stream));

@@ -77,7 +77,9 @@ struct SweepCtl {
     long long fallbacks;   // Gamma draws that hit the attempt limit
     long long acc_count;   // sweeps accumulated into the running mean / M2
     unsigned long long ticket;  // blocks of the current hyper launch that have finished
-    long long pad[3];
+    long long batch_base;  // first sweep of the current batch of precomputed Gamma variates
+    long long batch_count; // sweeps in that batch
+    long long pad;
 };
 
 // Whether sweep number `sweep` is accumulated (burn-in, then every thin-th sweep).
@@ -118,19 +120,27 @@ __device__ __forceinline__ float u01_f32(uint32_t w)
     return fmaf(static_cast<float>(w), 0x1p-32f, 0x1p-33f);
 }
 
-// -2 ln u in single precision with small relative error for every word: the lower half of the
-// range takes the logarithm of u itself, the upper half log1p(-(1 - u)) with 1 - u formed
-// exactly from the complemented word, so radii near zero keep their precision.
+// -2 ln u in single precision with small relative error for every word, without branches:
+// for u < 3/4 the logarithm of u itself (|ln u| > 0.28, so the absolute error of the fast log
+// is a relative error below 1.3e-6); for u >= 3/4, with v = 1 - u formed exactly from the
+// complemented word, ln(1 - v) = -2 atanh(t), t = v / (2 - v) <= 1/7, by the atanh series
+// t (1 + t^2/3 + t^4/5 + t^6/7 + t^8/9) (truncation below 4e-10 relative), so radii near zero
+// keep their precision.
 __device__ __forceinline__ float neg2log_u_f32(uint32_t w)
 {
-    if (w < 0x80000000u)
-        return -2.0f * __logf(u01_f32(w));
-    return -2.0f * log1pf(-u01_f32(~w));
+    const float l1 = __logf(u01_f32(w));
+    const float v = u01_f32(~w);
+    const float t = v * __frcp_rn(2.0f - v);
+    const float t2 = t * t;
+    const float p = fmaf(fmaf(fmaf(fmaf(1.0f / 9.0f, t2, 1.0f / 7.0f), t2, 1.0f / 5.0f), t2, 1.0f / 3.0f), t2, 1.0f);
+    const float l2 = -2.0f * t * p;
+    return -2.0f * (w >= 0xC0000000u ? l2 : l1);
 }
 
 __device__ __forceinline__ void box_muller_f32(uint32_t wa, uint32_t wb, float &zc, float &zs)
 {
-    const float r = sqrtf(neg2log_u_f32(wa));
+    const float q = neg2log_u_f32(wa);  // > 0 for every word
+    const float r = q * rsqrtf(q);
     float s, c;
     sincospif(2.0f * u01_f32(wb), &s, &c);
     zc = r * c;
@@ -177,7 +187,9 @@ __device__ __forceinline__ void site_normals(uint2 key, uint32_t site, uint32_t 
 }
 
 // ------------------------------------------------------------------------------------------
-// Gamma(shape, rate) by Marsaglia & Tsang (2000), FP64.  Attempt k uses the block at counter
+// Gamma(shape, rate) by Marsaglia & Tsang (2000), FP64.  The accept/reject loop depends on the
+// shape only; the rate divides the accepted variate at the end, so gamma_mt(a, rate) ==
+// gamma_mt(a, 1) / rate exactly (same operations in the same order).  Attempt k uses the block at counter
 // (k, word1, stream, tag_chain): z = Box-Muller cos of (w0, w1), acceptance uniform w2, boost
 // uniform w3 (shape < 1: Gamma(a) = Gamma(a + 1) U^(1/a)).  At most kMaxGammaAttempts
 // attempts; if all reject (probability < 1e-100 here) the draw is d / rate and *fell_back = 1.

@@ -88,7 +88,22 @@ struct HyperArgs {
     long long burn_in;    // accumulation schedule (to advance the accumulation count)
     int32_t thin;
     int32_t acc_enabled;
+    const double *gpre;   // [batch][F * Cp][2] unit-rate Gamma variates of the batch's sweeps
 };
+
+// Unit-rate Gamma variates (tau and 1/sigma^2 of every field and chain) for sweeps
+// ctl->sweep .. ctl->sweep + count - 1, one thread each; records the batch in ctl.
+struct GammaPreArgs {
+    const FieldDev *fields;
+    int32_t nfields;
+    int32_t Cp;
+    SweepCtl *ctl;
+    uint2 key;
+    double a_tau, a_sig;
+    int32_t count;
+    double *gpre;
+};
+cudaError_t launch_gamma_pre(const GammaPreArgs &a, cudaStream_t stream);
 
 // Launchers (each enqueues on `stream` and returns the launch status).
 // One colour step of the tiles in `a` (all of field kind `kind`).

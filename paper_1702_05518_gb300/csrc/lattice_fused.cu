@@ -3,8 +3,9 @@
 //
 // A block owns a TR x TC tile of natural sites.  It stages the tile plus a halo of width k
 // (k = 2 colours for the 4-neighbour lattice, 4 for the 8-neighbour one) from the colour-split
-// state into shared memory, then performs colour steps c = 0..k-1 in place: step c draws the
-// colour-c sites of the tile grown by k-1-c rings.  Each step reads only values the previous
+// state into shared memory, draws the normals of every site it will update (phase A, no
+// barriers), then performs colour steps c = 0..k-1 in place: step c draws the colour-c sites
+// of the tile grown by k-1-c rings.  Each step reads only values the previous
 // steps made final, so after the last step the owned sites hold exactly the sweep's result
 // (Sec. 2.3: the sites of one colour are conditionally independent given the others).  Sites
 // of the halo are drawn by every block that overlaps them; the counter-based generator makes
@@ -63,8 +64,10 @@ __device__ __forceinline__ void device_magic(uint32_t d, uint32_t &m, int &s)
                               ((static_cast<unsigned long long>(1) << s) - d) / d + 1);
 }
 
+constexpr int kFusedBlock = 512;
+
 template <typename T, int V, int KIND>
-__global__ void __launch_bounds__(kBlock) lattice_fused_kernel(const FusedArgs a)
+__global__ void __launch_bounds__(kFusedBlock) lattice_fused_kernel(const FusedArgs a)
 {
     using D = Dirs<KIND>;
     constexpr int K = (KIND == kLat2D8) ? 4 : 2;  // colours = halo width
@@ -75,8 +78,9 @@ __global__ void __launch_bounds__(kBlock) lattice_fused_kernel(const FusedArgs a
     const int TR = a.TR, TC = a.TC, RR = TR + 2 * K, RC = TC + 2 * K;
     const int Cp = a.Cp, CV = Cp / V, cv_shift = __ffs(CV) - 1;
     const int cvo = (threadIdx.x & (CV - 1)) * V;  // chain offset of this thread (fixed)
-    T *xs = reinterpret_cast<T *>(smem_raw);       // [RR * RC][Cp]
-    T *ys = xs + RR * RC * Cp;                     // [RR * RC]
+    T *xs = reinterpret_cast<T *>(smem_raw);       // [RR * RC][Cp] state
+    T *zs = xs + RR * RC * Cp;                     // [RR * RC][Cp] this sweep's normals
+    T *ys = zs + RR * RC * Cp;                     // [RR * RC] observations
     const int gi0 = t.i0 - K, gj0 = t.j0 - K;
     // Ping-pong state: sweep t reads buffer t & 1 and writes the other, so no block can see a
     // neighbour's new values while staging its halo.
@@ -99,7 +103,7 @@ __global__ void __launch_bounds__(kBlock) lattice_fused_kernel(const FusedArgs a
     }
 
     // Stage x (all chains) and y of the tile and its halo.
-    for (int q = threadIdx.x; q < RR * RC * CV; q += kBlock) {
+    for (int q = threadIdx.x; q < RR * RC * CV; q += kFusedBlock) {
         const int p = q >> cv_shift;
         const int ri = fast_div(p, a.rc_m, a.rc_s), rj = p - ri * RC;
         const int gi = gi0 + ri, gj = gj0 + rj;
@@ -114,6 +118,24 @@ __global__ void __launch_bounds__(kBlock) lattice_fused_kernel(const FusedArgs a
             if (cvo == 0) ys[p] = 0;
         }
         Vec<T, V>::st(xs + p * Cp + cvo, v);
+    }
+
+    // Phase A: the normals of every site this block draws in this sweep (colour c within
+    // k - 1 - c rings of the tile).  They depend on (site, sweep, chain) only, so this phase has
+    // no barriers and carries most of the arithmetic.
+    if (a.update) {
+        for (int q = threadIdx.x; q < RR * RC * CV; q += kFusedBlock) {
+            const int p = q >> cv_shift;
+            const int ri = fast_div(p, a.rc_m, a.rc_s), rj = p - ri * RC;
+            const int i = gi0 + ri, j = gj0 + rj;
+            if (i < 0 || i >= Hl || j < 0 || j >= Wl) continue;
+            const int c = D::colour(i, j);
+            const int e = K - 1 - c;
+            if (i < t.i0 - e || i >= t.i0 + TR + e || j < t.j0 - e || j >= t.j0 + TC + e) continue;
+            T z[V];
+            site_normals<T, V>(a.key, static_cast<uint32_t>(i * Wl + j), sweep, f.stream, static_cast<uint32_t>(cvo), z);
+            Vec<T, V>::st(zs + p * Cp + cvo, z);
+        }
     }
     __syncthreads();
 
@@ -138,7 +160,7 @@ __global__ void __launch_bounds__(kBlock) lattice_fused_kernel(const FusedArgs a
         uint32_t nc_m;
         int nc_s;
         device_magic(static_cast<uint32_t>(ncols > 0 ? ncols : 1), nc_m, nc_s);
-        for (int q = threadIdx.x; q < nq; q += kBlock) {
+        for (int q = threadIdx.x; q < nq; q += kFusedBlock) {
             const int p = q >> cv_shift;
             const int u = fast_div(p, nc_m, nc_s), w = p - u * ncols;
             int i, j;
@@ -152,23 +174,23 @@ __global__ void __launch_bounds__(kBlock) lattice_fused_kernel(const FusedArgs a
             }
             const int ri = i - gi0, rj = j - gj0;
             const T *xc = xs + (ri * RC + rj) * Cp + cvo;
+            // Staged positions outside the lattice hold zeros, so the neighbour sum needs no
+            // bounds tests; the degree follows from how many of the rows i-1..i+1 and columns
+            // j-1..j+1 exist.
             T s[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) s[v] = 0;
-            int deg = 0;
 #pragma unroll
             for (int k = 0; k < D::N; ++k) {
-                const int ii = i + D::di(k), jj = j + D::dj(k);
-                if (ii >= 0 && ii < Hl && jj >= 0 && jj < Wl) {
-                    T nb[V];
-                    Vec<T, V>::ld(xc + (D::di(k) * RC + D::dj(k)) * Cp, nb);
+                T nb[V];
+                Vec<T, V>::ld(xc + (D::di(k) * RC + D::dj(k)) * Cp, nb);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) s[v] += nb[v];
-                    ++deg;
-                }
+                for (int v = 0; v < V; ++v) s[v] += nb[v];
             }
+            const int vr = (i > 0) + (i + 1 < Hl), vc = (j > 0) + (j + 1 < Wl);
+            const int deg = (KIND == kLat2D8) ? (vr + 1) * (vc + 1) - 1 : vr + vc;
             T z[V];
-            site_normals<T, V>(a.key, static_cast<uint32_t>(i * Wl + j), sweep, f.stream, static_cast<uint32_t>(cvo), z);
+            Vec<T, V>::ld(zs + (ri * RC + rj) * Cp + cvo, z);
             const T yv = ys[ri * RC + rj];
             const T d = static_cast<T>(deg);
             T xn[V];
@@ -197,7 +219,7 @@ __global__ void __launch_bounds__(kBlock) lattice_fused_kernel(const FusedArgs a
         accR[v] = 0;
     }
     const int oq = TR * TC * CV;
-    for (int q = threadIdx.x; q < oq; q += kBlock) {
+    for (int q = threadIdx.x; q < oq; q += kFusedBlock) {
         const int p = q >> cv_shift;
         const int oi = fast_div(p, a.tc_m, a.tc_s), oj = p - oi * TC;
         const int i = t.i0 + oi, j = t.j0 + oj;
@@ -207,26 +229,26 @@ __global__ void __launch_bounds__(kBlock) lattice_fused_kernel(const FusedArgs a
         T xn[V];
         Vec<T, V>::ld(xc, xn);
         const int c = D::colour(i, j);
+        const bool up = i > 0, down = i + 1 < Hl, left = j > 0, right = j + 1 < Wl;
         T e[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) e[v] = 0;
-        int deg = 0;
 #pragma unroll
         for (int k = 0; k < D::N; ++k) {
-            const int ii = i + D::di(k), jj = j + D::dj(k);
-            if (ii >= 0 && ii < Hl && jj >= 0 && jj < Wl) {
-                ++deg;
-                if (D::colour(ii, jj) < c) {
-                    T nb[V];
-                    Vec<T, V>::ld(xc + (D::di(k) * RC + D::dj(k)) * Cp, nb);
+            const int di = D::di(k), dj = D::dj(k);
+            const bool ok = (di < 0 ? up : (di > 0 ? down : true)) && (dj < 0 ? left : (dj > 0 ? right : true));
+            if (ok && D::colour(i + di, j + dj) < c) {
+                T nb[V];
+                Vec<T, V>::ld(xc + (di * RC + dj) * Cp, nb);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const T df = xn[v] - nb[v];
-                        e[v] += df * df;
-                    }
+                for (int v = 0; v < V; ++v) {
+                    const T df = xn[v] - nb[v];
+                    e[v] += df * df;
                 }
             }
         }
+        const int vr = up + down, vc = left + right;
+        const int deg = (KIND == kLat2D8) ? (vr + 1) * (vc + 1) - 1 : vr + vc;
         const T yv = ys[ri * RC + rj];
         const T d = static_cast<T>(deg);
 #pragma unroll
@@ -255,7 +277,7 @@ __global__ void __launch_bounds__(kBlock) lattice_fused_kernel(const FusedArgs a
     // Deterministic block reduction in precision T (shuffle tree over lanes sharing a chain
     // vector, then warps in order) into the tile's FP64 partial-sum slot; a tile holds at most a
     // few thousand terms, the sum over tiles is FP64.
-    __shared__ T red[kBlock / 32][kMaxChains][2];
+    __shared__ T red[kFusedBlock / 32][kMaxChains][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -270,10 +292,10 @@ __global__ void __launch_bounds__(kBlock) lattice_fused_kernel(const FusedArgs a
         }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < Cp * 2; q += kBlock) {
+    for (int q = threadIdx.x; q < Cp * 2; q += kFusedBlock) {
         const int chain = q >> 1, k = q & 1;
         T sum = 0;
-        for (int w = 0; w < kBlock / 32; ++w) sum += red[w][chain][k];
+        for (int w = 0; w < kFusedBlock / 32; ++w) sum += red[w][chain][k];
         reinterpret_cast<double *>(a.partials + static_cast<int64_t>(t.part) * Cp + chain)[k] = static_cast<double>(sum);
     }
 }
@@ -281,7 +303,7 @@ __global__ void __launch_bounds__(kBlock) lattice_fused_kernel(const FusedArgs a
 template <typename T, int V, int KIND>
 cudaError_t launch_t(const FusedArgs &a, size_t smem, cudaStream_t stream)
 {
-    lattice_fused_kernel<T, V, KIND><<<a.ntiles, kBlock, smem, stream>>>(a);
+    lattice_fused_kernel<T, V, KIND><<<a.ntiles, kFusedBlock, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -310,7 +332,7 @@ size_t lattice_fused_smem(int precision, int kind, int Cp, int TR, int TC)
 {
     const int K = (kind == kLat2D8) ? 4 : 2;
     const size_t S = precision == 0 ? sizeof(float) : sizeof(double);
-    return static_cast<size_t>(TR + 2 * K) * (TC + 2 * K) * (Cp + 1) * S;
+    return static_cast<size_t>(TR + 2 * K) * (TC + 2 * K) * (2 * Cp + 1) * S;
 }
 
 cudaError_t prepare_lattice_fused(int precision, int V, int kind, size_t smem)

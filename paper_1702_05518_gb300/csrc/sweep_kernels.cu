@@ -415,13 +415,22 @@ __global__ void __launch_bounds__(256) hyper_kernel(const HyperArgs a)
             int fb = 0;
             const double shape = which ? a.a_sig + 0.5 * f.n : a.a_tau + 0.5 * f.rank;
             const double rate = which ? a.b_sig + 0.5 * S : a.b_tau + 0.5 * S;
-            const double g = gamma_mt(shape, rate, a.key, word1, f.stream, (tag << 24) | static_cast<uint32_t>(chain), fb);
-            if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), 1ull);
+            const long long kb = sweep - a.ctl->batch_base;
+            double g;
+            if (a.end_of_sweep && a.gpre && kb >= 0 && kb < a.ctl->batch_count) {
+                // Precomputed unit-rate variate of this sweep: the draw is g = G / rate.
+                g = a.gpre[(kb * a.nfields * a.Cp + pidx) * 2 + which] / rate;
+            } else {
+                g = gamma_mt(shape, rate, a.key, word1, f.stream, (tag << 24) | static_cast<uint32_t>(chain), fb);
+                if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), 1ull);
+            }
             T *hyp = static_cast<T *>(a.hyp);
             if (which) {
+                // The sweep kernels use 1/sigma^2 recomputed from sigma^2, as the oracle does, so
+                // a run resumed from a fetched sigma^2 continues bit for bit.
                 val = 1.0 / g;
                 a.sig2[hc] = val;
-                hyp[hc * 2 + 1] = static_cast<T>(g);
+                hyp[hc * 2 + 1] = static_cast<T>(1.0 / val);
             } else {
                 val = g;
                 a.tau[hc] = val;
@@ -492,6 +501,31 @@ __global__ void site_normals_kernel(uint2 key, uint32_t sweep, uint32_t stream, 
         T z[1];
         site_normals<T, 1>(key, static_cast<uint32_t>(i), sweep, stream, chain, z);
         out[i] = z[0];
+    }
+}
+
+// One thread per (sweep of the batch, field, chain, tau or sigma^2): the unit-rate Marsaglia-Tsang
+// variate with the counters of that sweep's draw.  The draws are independent of the state, so a
+// whole batch runs in parallel and the per-sweep draw reduces to a division by the rate.
+__global__ void gamma_pre_kernel(const GammaPreArgs a)
+{
+    const long long base = a.ctl->sweep;
+    const int npairs = a.nfields * a.Cp;
+    const int total = a.count * npairs * 2;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const int which = q & 1, pidx = (q >> 1) % npairs, k = (q >> 1) / npairs;
+        const int fi = pidx / a.Cp, chain = pidx - fi * a.Cp;
+        const FieldDev &f = a.fields[fi];
+        const double shape = which ? a.a_sig + 0.5 * f.n : a.a_tau + 0.5 * f.rank;
+        const uint32_t tag = which ? kTagSig : kTagTau;
+        int fb = 0;
+        a.gpre[q] = gamma_mt(shape, 1.0, a.key, static_cast<uint32_t>(base + k), f.stream,
+                             (tag << 24) | static_cast<uint32_t>(chain), fb);
+        if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), 1ull);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->batch_base = base;
+        a.ctl->batch_count = a.count;
     }
 }
 
@@ -571,6 +605,14 @@ cudaError_t launch_unpack(int precision, const FieldDev *fields_dev, const Field
     else
         unpack_kernel<double><<<grid, 256, 0, stream>>>(fields_dev, fidx, Cp, chain, static_cast<const double *>(src),
                                                         static_cast<const double *>(m2), inv_km1, perm_inv, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gamma_pre(const GammaPreArgs &a, cudaStream_t stream)
+{
+    const int total = a.count * a.nfields * a.Cp * 2;
+    if (total <= 0) return cudaSuccess;
+    gamma_pre_kernel<<<(total + 127) / 128, 128, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
