@@ -23,9 +23,11 @@
  * Random numbers are Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seed, with
  * counters that name the draw, so results do not depend on launch shapes or on the order of
  * sites within a colour class:
- *     site update      counter (site, sweep, stream, (0 << 24) | chain/4), normal chain mod 4
- *                      of the block: Box-Muller of (w0,w1) gives normals 0 (cos), 1 (sin),
- *                      (w2,w3) gives 2 and 3; u = (w + 1/2) 2^-32.
+ *     site update      a block gives normals n0, n1 (cos, sin of Box-Muller(w0, w1)) and n2, n3
+ *                      (of (w2, w3)), u = (w + 1/2) 2^-32; with lanes = min(4, chains
+ *                      rounded up to a power of two) and G = 4 / lanes it serves G consecutive
+ *                      sites: counter (site / G, sweep, stream, (0 << 24) | chain/4), normal
+ *                      n[(site mod G) * lanes + chain mod lanes].
  *     tau draw         counter (attempt, sweep, stream, (1 << 24) | chain)   [Marsaglia-Tsang]
  *     1/sigma^2 draw   counter (attempt, sweep, stream, (2 << 24) | chain)
  *     JP priority      word 0 of counter (vertex, 0, 0, 3 << 24)
@@ -242,14 +244,16 @@ gmrf_status gmrf_validate_csr(int32_t n, const int32_t *row_ptr, const int32_t *
  * gmrf_philox_words: out[4i..4i+3] = Philox4x32-10 of counter (i, c1, c2, c3) under the key
  *   (seed lo, seed hi), i = 0..count-1.  `out` is a DEVICE pointer of 4*count words.
  * gmrf_site_normals: out[i] = the normal that updates (site i, chain) at `sweep` of a field
- *   with stream id `stream`, in the given precision; `out` is a DEVICE pointer of `count`
- *   floats (GMRF_FP32) or doubles (GMRF_FP64).
+ *   with stream id `stream` in a sampler whose Philox blocks serve `lanes` chains (1, 2 or 4:
+ *   min(4, chains rounded up to a power of two); see the layout above), in the given precision;
+ *   `out` is a DEVICE pointer of `count` floats (GMRF_FP32) or doubles (GMRF_FP64).
  * Both enqueue on `cuda_stream` and return without synchronising.
  */
 gmrf_status gmrf_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3,
                               int64_t count, uint32_t *out, void *cuda_stream);
 gmrf_status gmrf_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream, uint32_t chain,
-                              int32_t precision, int64_t count, void *out, void *cuda_stream);
+                              int32_t lanes, int32_t precision, int64_t count, void *out,
+                              void *cuda_stream);
 
 /* Description of the last failure on the calling thread ("" if none). */
 const char *gmrf_last_error(void);

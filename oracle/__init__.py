@@ -73,11 +73,13 @@ def _load():
             lib.ora_uniform.argtypes = [ctypes.c_uint32]
             lib.ora_uniform.restype = ctypes.c_double
             lib.ora_normals4.argtypes = [u32p, f64p]
+            lib.ora_lanes_for.argtypes = [ctypes.c_int32]
+            lib.ora_lanes_for.restype = ctypes.c_int32
             lib.ora_site_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
-                                            ctypes.c_uint32, ctypes.c_uint32]
+                                            ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32]
             lib.ora_site_normal.restype = ctypes.c_double
             lib.ora_site_normals.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_uint32,
-                                             ctypes.c_uint32, ctypes.c_uint32, f64p]
+                                             ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32, f64p]
             lib.ora_gamma_draw.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                            ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                            ctypes.c_uint32, i32p]
@@ -147,14 +149,20 @@ def normals4(words):
     return z
 
 
-def site_normal(seed, site, sweep, stream, chain):
-    return _load().ora_site_normal(seed, site, sweep, stream, chain)
+def lanes_for(chains):
+    """Normals per site of one Philox block for a sampler with `chains` chains: 1, 2 or 4."""
+    return _load().ora_lanes_for(int(chains))
 
 
-def site_normals(seed, n, sweep, stream, chain):
-    """Normals z_i used to update sites 0..n-1 of `chain` at `sweep` (natural site order)."""
+def site_normal(seed, site, sweep, stream, chain, lanes):
+    return _load().ora_site_normal(seed, site, sweep, stream, chain, lanes)
+
+
+def site_normals(seed, n, sweep, stream, chain, lanes):
+    """Normals z_i used to update sites 0..n-1 of `chain` at `sweep` (natural site order) in a
+    sampler whose Philox blocks serve `lanes` chains (see lanes_for)."""
     out = np.zeros(int(n), np.float64)
-    _load().ora_site_normals(seed, int(n), sweep, stream, chain, _ptr(out, ctypes.c_double))
+    _load().ora_site_normals(seed, int(n), sweep, stream, chain, int(lanes), _ptr(out, ctypes.c_double))
     return out
 
 

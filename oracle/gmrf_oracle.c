@@ -30,7 +30,8 @@
  *   - Running posterior mean and sum of squared deviations (Welford) of x after burn-in.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), uniforms
- * u = (w + 1/2) 2^-32, normals by Box-Muller, Gamma variates by Marsaglia & Tsang (2000).
+ * u = (w + 1/2) 2^-32, normals by Box-Muller (four per Philox block, shared by consecutive sites
+ * when there are fewer than four chains), Gamma variates by Marsaglia & Tsang (2000).
  * The counter assignment (which counter feeds which draw) is part of the parity contract with
  * the CUDA path and is stated in the comments of each generator below.
  *
@@ -117,25 +118,40 @@ void ora_normals4(const uint32_t w[4], double z[4])
     ora_box_muller(w[2], w[3], &z[2], &z[3]);
 }
 
-/* The normal that updates (site, chain) at a given sweep of the field with stream id `stream`:
- * counter (site, sweep, stream, (TAG_X << 24) | chain/4), component chain mod 4. */
-double ora_site_normal(uint64_t seed, uint32_t site, uint32_t sweep, uint32_t stream, uint32_t chain)
+/* Normals per site of one Philox block: `lanes` = min(4, C rounded up to a power of two) for a
+ * sampler with C chains (1, 2 or 4). */
+int32_t ora_lanes_for(int32_t chains)
+{
+    int32_t p = 1;
+    while (p < chains) p <<= 1;
+    return p < 4 ? p : 4;
+}
+
+/* The normal that updates (site, chain) at a given sweep of the field with stream id `stream`.
+ * Each Philox block gives four normals n0, n1 (cos, sin of Box-Muller(w0, w1)) and n2, n3 (of
+ * (w2, w3)); it serves G = 4 / lanes consecutive sites and `lanes` chains: block counter
+ * (site / G, sweep, stream, (TAG_X << 24) | chain / 4), normal n[(site mod G) * lanes + chain mod
+ * lanes].  With four or more chains this is one block per site and chain quadruple; with one
+ * chain one block per four consecutive sites. */
+double ora_site_normal(uint64_t seed, uint32_t site, uint32_t sweep, uint32_t stream, uint32_t chain,
+                       int32_t lanes)
 {
     uint32_t key[2], w[4];
     ora_key_of_seed(seed, key);
-    uint32_t ctr[4] = {site, sweep, stream, ((uint32_t)ORA_TAG_X << 24) | (chain >> 2)};
+    uint32_t G = 4u / (uint32_t)lanes;
+    uint32_t ctr[4] = {site / G, sweep, stream, ((uint32_t)ORA_TAG_X << 24) | (chain >> 2)};
     ora_philox4x32_10(ctr, key, w);
     double z[4];
     ora_normals4(w, z);
-    return z[chain & 3u];
+    return z[(site % G) * (uint32_t)lanes + chain % (uint32_t)lanes];
 }
 
 /* The update normals of sites 0..n-1 of one chain at one sweep (natural order). */
 void ora_site_normals(uint64_t seed, int32_t n, uint32_t sweep, uint32_t stream, uint32_t chain,
-                      double *out)
+                      int32_t lanes, double *out)
 {
     for (int32_t i = 0; i < n; ++i)
-        out[i] = ora_site_normal(seed, (uint32_t)i, sweep, stream, chain);
+        out[i] = ora_site_normal(seed, (uint32_t)i, sweep, stream, chain, lanes);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -382,6 +398,7 @@ int32_t ora_run(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const
         deg[i] = d;
     }
     int32_t rank = model->prior_proper ? n : n - ora_components(n, row_ptr, col_idx);
+    int32_t lanes = ora_lanes_for(C);
     int32_t fallbacks = 0;
     for (int32_t t = 0; t < opts->nsweeps; ++t) {
         uint32_t sweep = opts->start_sweep + (uint32_t)t;
@@ -398,7 +415,7 @@ int32_t ora_run(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const
                         s += (weights ? weights[e] : 1.0) * xc[col_idx[e]];
                     double P = tau[c] * deg[i] + prec_noise;
                     double m = (tau[c] * rho * s + y[i] * prec_noise) / P;
-                    double z = ora_site_normal(opts->seed, (uint32_t)i, sweep, opts->stream, (uint32_t)c);
+                    double z = ora_site_normal(opts->seed, (uint32_t)i, sweep, opts->stream, (uint32_t)c, lanes);
                     xc[i] = m + z / sqrt(P);
                 }
             if (!model->fix_hyper) {

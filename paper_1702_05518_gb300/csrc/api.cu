@@ -71,7 +71,7 @@ struct gmrf_sampler {
     std::vector<Stage> stages;
     TileXY *ftiles_dev = nullptr;
     int32_t ftile_off[4] = {0, 0, 0, 0}, ftile_cnt[4] = {0, 0, 0, 0};
-    int32_t fTR[4] = {0, 0, 0, 0}, fTC[4] = {0, 0, 0, 0};
+    int32_t fTR[4] = {0, 0, 0, 0}, fTC[4] = {0, 0, 0, 0}, fNT[4] = {512, 512, 512, 512};
     size_t fsmem[4] = {0, 0, 0, 0};
     FieldDev *fields_dev = nullptr;
     Tile *tiles_dev = nullptr;
@@ -372,6 +372,7 @@ StepArgs step_args(gmrf_sampler *s, int colour, int kind, int update, int accumu
     a.ctl = s->ctl;
     a.key = philox_key(s->opts.seed);
     a.Cp = s->Cp;
+    a.lanes = std::min(s->Cp, 4);
     a.rho = s->model.prior == GMRF_PRIOR_PCAR ? s->model.rho : 1.0;
     a.burn_in = s->opts.burn_in;
     a.thin = s->opts.thin;
@@ -431,9 +432,13 @@ FusedArgs fused_args(gmrf_sampler *s, int kind, int update, int accumulate)
     a.ntiles = s->ftile_cnt[kind];
     a.TR = s->fTR[kind];
     a.TC = s->fTC[kind];
+    a.threads = s->fNT[kind];
     const int K = kind == GMRF_LATTICE2D_8 ? 4 : 2;
     fast_div_magic(static_cast<uint32_t>(a.TC + 2 * K), a.rc_m, a.rc_s);
     fast_div_magic(static_cast<uint32_t>(a.TC > 0 ? a.TC : 1), a.tc_m, a.tc_s);
+    a.lanes = std::min(s->Cp, 4);
+    const int gs = a.lanes == 4 ? 0 : (a.lanes == 2 ? 1 : 2);
+    fast_div_magic(static_cast<uint32_t>(((a.TC + 2 * K) >> gs) + 2), a.ng_m, a.ng_s);
     a.x = s->x;
     a.x_alt = s->x_alt;
     a.y = s->y;
@@ -525,6 +530,7 @@ gmrf_status build_plain(gmrf_sampler *s, const gmrf_field_desc &f, std::vector<v
     a.kind = h.kind;
     for (int d = 0; d < 3; ++d) a.dims[d] = h.dims[d];
     a.C = s->C;
+    a.lanes = std::min(pow2_at_least(s->C), 4);
     a.rho = s->model.prior == GMRF_PRIOR_PCAR ? s->model.rho : 1.0;
     a.rank = s->model.prior == GMRF_PRIOR_PCAR ? h.n : h.n - h.components;
     a.a_tau = s->model.a_tau;
@@ -751,15 +757,50 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
             if (h.kind == kind) fused_kind[kind] = true;
         if (fused_kind[kind]) {
             int tr = side, tc = side;
-            // Tuning override: GMRF_FUSED_TILE="<rows>x<cols>" (each 8..256, within the budget).
+            // Cost model over tile shapes and block sizes: waves of blocks (152 SMs, one block of
+            // 1024 or two of 512 threads per SM) times the sites a wave computes per SM, halo
+            // recomputation included.  Deterministic, so a sampler's tiling (and with it the
+            // rounding of the tile partial sums) does not change from run to run.
+            double best = 1e300;
+            for (int nt : {512, 1024}) {
+                const int bps = nt == 1024 ? 1 : 2;
+                for (int cr = 16; cr <= 160; cr += 2)
+                    for (int cc = 16; cc <= 128; cc += 2) {
+                        const size_t sm = lattice_fused_smem(s->precision, kind, s->Cp, cr, cc);
+                        if (sm * bps > 200 * 1024 || static_cast<int64_t>(cr + 2 * K) * (cc + 2 * K) * s->Cp >= 65536)
+                            continue;
+                        int64_t tiles = 0;
+                        for (auto &h : s->hf)
+                            if (h.kind == kind)
+                                tiles += static_cast<int64_t>((h.dims[0] + cr - 1) / cr) * ((h.dims[1] + cc - 1) / cc);
+                        double work = 0;  // sites computed per tile over the K colour steps
+                        for (int e = 0; e < K; ++e) work += static_cast<double>(cr + 2 * e) * (cc + 2 * e) / K;
+                        const double waves = std::ceil(static_cast<double>(tiles) / (152.0 * bps));
+                        const double cost = waves * bps * work;
+                        if (cost < best * 0.999) {
+                            best = cost;
+                            tr = cr;
+                            tc = cc;
+                            s->fNT[kind] = nt;
+                        }
+                    }
+            }
+            // Tuning override: GMRF_FUSED_TILE="<rows>x<cols>[x<threads>]" (extents 8..256, made
+            // even so every staged region is aligned to the colour pattern; threads 512 or 1024).
             if (const char *env = std::getenv("GMRF_FUSED_TILE")) {
-                int r = 0, c = 0;
-                if (std::sscanf(env, "%dx%d", &r, &c) == 2 && r >= 8 && c >= 8 && r <= 256 && c <= 256 &&
-                    lattice_fused_smem(s->precision, kind, s->Cp, r, c) <= 160 * 1024) {
+                int r = 0, c = 0, nt = 512;
+                const int got = std::sscanf(env, "%dx%dx%d", &r, &c, &nt);
+                r &= ~1;
+                c &= ~1;
+                if (got >= 2 && r >= 8 && c >= 8 && r <= 256 && c <= 256 && (nt == 512 || nt == 1024) &&
+                    lattice_fused_smem(s->precision, kind, s->Cp, r, c) <= 200 * 1024) {
                     tr = r;
                     tc = c;
+                    s->fNT[kind] = nt;
                 }
             }
+            // The kernel's flattened loops divide indices below 2^16 by one float multiply.
+            while (static_cast<int64_t>(tr + 2 * K) * (tc + 2 * K) * (s->Cp / s->V) >= 65536 && tr > 8) tr -= 8;
             s->fTR[kind] = tr;
             s->fTC[kind] = tc;
             s->fsmem[kind] = lattice_fused_smem(s->precision, kind, s->Cp, tr, tc);
@@ -1231,14 +1272,16 @@ gmrf_status gmrf_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t 
     return GMRF_OK;
 }
 
-gmrf_status gmrf_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream, uint32_t chain, int32_t precision,
-                              int64_t count, void *out, void *cuda_stream)
+gmrf_status gmrf_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream, uint32_t chain, int32_t lanes,
+                              int32_t precision, int64_t count, void *out, void *cuda_stream)
 {
     g_last_error.clear();
     if (count < 0 || (count > 0 && !out)) return fail(GMRF_E_INVALID, "count >= 0 and a device output are required");
     if (count > (int64_t(1) << 32)) return fail(GMRF_E_INVALID, "count must be <= 2^32");
     if (precision != GMRF_FP32 && precision != GMRF_FP64) return fail(GMRF_E_INVALID, "precision");
-    cudaError_t e = launch_site_normals(seed, sweep, stream, chain, precision, count, out,
+    if (lanes != 1 && lanes != 2 && lanes != 4) return fail(GMRF_E_INVALID, "lanes must be 1, 2 or 4");
+    if (lanes < 4 && chain >= static_cast<uint32_t>(lanes)) return fail(GMRF_E_INVALID, "chain must be < lanes");
+    cudaError_t e = launch_site_normals(seed, sweep, stream, chain, lanes, precision, count, out,
                                         static_cast<cudaStream_t>(cuda_stream));
     if (e != cudaSuccess) return cuda_status(CudaFail{e, "site_normals"});
     return GMRF_OK;

@@ -164,26 +164,44 @@ template <> struct Prec<double> {
     __device__ __forceinline__ static void bm(uint32_t a, uint32_t b, double &c, double &s) { box_muller_f64(a, b, c, s); }
 };
 
+// Normal layout: a Philox block gives four normals n0, n1 (cos, sin of Box-Muller(w0, w1)) and
+// n2, n3 (of (w2, w3)).  With `lanes` = min(4, chains rounded up to a power of two) it serves
+// G = 4 / lanes consecutive sites and `lanes` chains: block counter (site / G, sweep, stream,
+// (kTagX << 24) | chain / 4), normal n[(site mod G) * lanes + chain mod lanes].
+__device__ __forceinline__ int lanes_shift(int lanes) { return lanes == 4 ? 0 : (lanes == 2 ? 1 : 2); }
+
 // The V normals that update chains chain0 .. chain0+V-1 of `site` at `sweep` (chain0 a multiple
-// of V, V in {1, 2, 4}).  Block counter (site, sweep, stream, chain0 / 4); chain c takes normal
-// c mod 4 of the block (cos/sin of (w0,w1), then cos/sin of (w2,w3)).
+// of V; V = 4 implies lanes = 4, V = 1 any lanes, V = 2 lanes 2 or 4).
 template <typename T, int V>
 __device__ __forceinline__ void site_normals(uint2 key, uint32_t site, uint32_t sweep, uint32_t stream,
-                                             uint32_t chain0, T (&z)[V])
+                                             uint32_t chain0, int lanes, T (&z)[V])
 {
-    const uint4 w = philox4x32_10(make_uint4(site, sweep, stream, (kTagX << 24) | (chain0 >> 2)), key);
+    const int gs = lanes_shift(lanes);
+    const uint32_t first = ((site & ((1u << gs) - 1u)) * static_cast<uint32_t>(lanes)) +
+                           (chain0 & static_cast<uint32_t>(lanes - 1));
+    const uint4 w = philox4x32_10(make_uint4(site >> gs, sweep, stream, (kTagX << 24) | (chain0 >> 2)), key);
     if constexpr (V == 4) {
         Prec<T>::bm(w.x, w.y, z[0], z[1]);
         Prec<T>::bm(w.z, w.w, z[2], z[3]);
     } else if constexpr (V == 2) {
-        if ((chain0 & 2u) == 0) Prec<T>::bm(w.x, w.y, z[0], z[1]);
+        if ((first & 2u) == 0) Prec<T>::bm(w.x, w.y, z[0], z[1]);
         else Prec<T>::bm(w.z, w.w, z[0], z[1]);
     } else {
         T c, s;
-        if ((chain0 & 2u) == 0) Prec<T>::bm(w.x, w.y, c, s);
+        if ((first & 2u) == 0) Prec<T>::bm(w.x, w.y, c, s);
         else Prec<T>::bm(w.z, w.w, c, s);
-        z[0] = (chain0 & 1u) ? s : c;
+        z[0] = (first & 1u) ? s : c;
     }
+}
+
+// All four normals of block `grp` (chains 0 .. 3 of the quadruple chain_quad).
+template <typename T>
+__device__ __forceinline__ void block_normals(uint2 key, uint32_t grp, uint32_t sweep, uint32_t stream,
+                                              uint32_t chain_quad, T (&n)[4])
+{
+    const uint4 w = philox4x32_10(make_uint4(grp, sweep, stream, (kTagX << 24) | chain_quad), key);
+    Prec<T>::bm(w.x, w.y, n[0], n[1]);
+    Prec<T>::bm(w.z, w.w, n[2], n[3]);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -30,6 +30,7 @@ struct StepArgs {
     const SweepCtl *ctl;
     uint2 key;
     int32_t Cp;          // chains in the layout (power of two >= chains)
+    int32_t lanes;       // normals per site of one Philox block: min(4, Cp)
     double rho;
     long long burn_in;
     int32_t thin;
@@ -50,8 +51,11 @@ struct FusedArgs {
     const TileXY *tiles;
     int32_t ntiles;
     int32_t TR, TC;      // tile rows and columns (natural sites)
-    uint32_t rc_m, tc_m; // invariant-divisor constants of the staged row length and of TC
-    int32_t rc_s, tc_s;
+    int32_t threads;     // threads per block: 512 or 1024
+    uint32_t rc_m, tc_m; // invariant-divisor constants of the staged row length, of TC and of
+    int32_t rc_s, tc_s;  // the Philox-group slots per staged row
+    uint32_t ng_m;
+    int32_t ng_s;
     void *x;             // state buffer 0 (the state at the start of even sweeps)
     void *x_alt;         // state buffer 1 (the state at the start of odd sweeps)
     const void *y;
@@ -62,6 +66,7 @@ struct FusedArgs {
     const SweepCtl *ctl;
     uint2 key;
     int32_t Cp;
+    int32_t lanes;       // normals per site of one Philox block: min(4, Cp)
     double rho;
     long long burn_in;
     int32_t thin;
@@ -118,7 +123,7 @@ cudaError_t launch_unpack(int precision, const FieldDev *fields_dev, const Field
 cudaError_t launch_ctl_reset(SweepCtl *ctl, long long start_sweep, cudaStream_t stream);
 cudaError_t launch_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, int64_t count,
                                 uint32_t *out, cudaStream_t stream);
-cudaError_t launch_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream_id, uint32_t chain,
+cudaError_t launch_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream_id, uint32_t chain, int lanes,
                                 int precision, int64_t count, void *out, cudaStream_t stream);
 
 // Fused 2-D lattice sweep (lattice_fused.cu).
@@ -169,6 +174,7 @@ struct PlainArgs {
     uint2 key;
     uint32_t stream_id;
     int32_t C;
+    int32_t lanes;         // normals per site of one Philox block: min(4, chains rounded up)
     int32_t rank;
     double rho;
     double a_tau, b_tau, a_sig, b_sig;

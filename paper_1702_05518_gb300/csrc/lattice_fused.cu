@@ -48,51 +48,64 @@ template <> struct Dirs<kLat2D4> {
     __device__ __forceinline__ static int colour(int i, int j) { return (i + j) & 1; }
 };
 
-// Slot of site (i, j) relative to the field's first slot (32-bit: fields hold < 2^31 slots).
+// Shared memory holds the staged region (natural rows gi0 .. gi0+RR-1, columns gj0 .. gj0+RC-1,
+// gi0 and gj0 even) in the same colour-split layout as the state in global memory:
+//   8-neighbour lattice: sub-array s = 2 (i & 1) + (j & 1), row (i - gi0) / 2, column (j - gj0) / 2;
+//   4-neighbour lattice: sub-array s = (i + j) & 1,           row  i - gi0,     column (j - gj0) / 2;
+// each sub-array SR x SC sites with Cp chains innermost.  A colour class is one sub-array, so a
+// warp walking a class reads consecutive addresses, and staging and write-back copy rows of
+// the global sub-arrays.
 template <int KIND>
-__device__ __forceinline__ int slot_rel(const FieldDev &f, int i, int j)
+__device__ __forceinline__ int sm_index(int i, int j, int gi0, int gj0, int SR, int SC)
 {
-    if (KIND == kLat2D8) return ((2 * (i & 1) + (j & 1)) * f.rows + (i >> 1)) * f.cols + (j >> 1);
-    return (((i + j) & 1) * f.rows + i) * f.cols + (j >> 1);
+    if (KIND == kLat2D8) return ((2 * (i & 1) + (j & 1)) * SR + ((i - gi0) >> 1)) * SC + ((j - gj0) >> 1);
+    return (((i + j) & 1) * SR + (i - gi0)) * SC + ((j - gj0) >> 1);
 }
 
-// Invariant-divisor constants for a divisor known only on the device (computed once per loop).
-__device__ __forceinline__ void device_magic(uint32_t d, uint32_t &m, int &s)
+
+// q / d for 0 <= q < 2^16 and d >= 1 by one single-precision multiply: (q + 1/2) / d is at least
+// 1/(2d) away from an integer and the two roundings err by less than 2^-7 / d, so the floor is
+// exact.
+__device__ __forceinline__ int div_small(int q, float rcp_d)
 {
-    s = (d <= 1) ? 0 : 32 - __clz(d - 1);
-    m = static_cast<uint32_t>((static_cast<unsigned long long>(1) << 32) *
-                              ((static_cast<unsigned long long>(1) << s) - d) / d + 1);
+    return static_cast<int>((static_cast<float>(q) + 0.5f) * rcp_d);
 }
 
-constexpr int kFusedBlock = 512;
-
-template <typename T, int V, int KIND>
-__global__ void __launch_bounds__(kFusedBlock) lattice_fused_kernel(const FusedArgs a)
+template <typename T, int V, int KIND, int kFusedBlock>
+__global__ void __launch_bounds__(kFusedBlock, (kFusedBlock == 512 && sizeof(T) == 4 && V <= 2) ? 2 : 1)
+    lattice_fused_kernel(const FusedArgs a)
 {
     using D = Dirs<KIND>;
-    constexpr int K = (KIND == kLat2D8) ? 4 : 2;  // colours = halo width
+    constexpr bool E8 = (KIND == kLat2D8);
+    constexpr int K = E8 ? 4 : 2;   // colours = halo width
+    constexpr int NS = E8 ? 4 : 2;  // sub-arrays
+    constexpr int NW = kFusedBlock / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const TileXY t = a.tiles[blockIdx.x];
     const FieldDev f = a.fields[t.field];
     const int Hl = f.dims[0], Wl = f.dims[1];
     const int TR = a.TR, TC = a.TC, RR = TR + 2 * K, RC = TC + 2 * K;
+    const int SR = E8 ? (RR >> 1) : RR, SC = RC >> 1, SUB = SR * SC;
     const int Cp = a.Cp, CV = Cp / V, cv_shift = __ffs(CV) - 1;
-    const int cvo = (threadIdx.x & (CV - 1)) * V;  // chain offset of this thread (fixed)
-    T *xs = reinterpret_cast<T *>(smem_raw);       // [RR * RC][Cp] state
-    T *zs = xs + RR * RC * Cp;                     // [RR * RC][Cp] this sweep's normals
-    T *ys = zs + RR * RC * Cp;                     // [RR * RC] observations
+    const int tx = threadIdx.x & 31;
+    const int cvo = (tx & (CV - 1)) * V;  // chain offset of this thread (fixed: 32 % CV == 0)
+    T *xs = reinterpret_cast<T *>(smem_raw);  // [NS][SR][SC][Cp] state
+    T *zs = xs + NS * SUB * Cp;               // [NS][SR][SC][Cp] normals of this sweep
+    T *ys = zs + NS * SUB * Cp;               // [NS][SR][SC] observations
     const int gi0 = t.i0 - K, gj0 = t.j0 - K;
+    const int gu0 = E8 ? (gi0 >> 1) : gi0, gv0 = gj0 >> 1;  // staged origin in the global sub-arrays
+    const bool interior = gi0 >= 0 && gj0 >= 0 && gi0 + RR <= Hl && gj0 + RC <= Wl;
     // Ping-pong state: sweep t reads buffer t & 1 and writes the other, so no block can see a
     // neighbour's new values while staging its halo.
     const long long sweep_ll = a.ctl->sweep;
     const void *xsrc = (sweep_ll & 1) ? a.x_alt : a.x;
     void *xdst = (sweep_ll & 1) ? a.x : a.x_alt;
+    const int64_t gsub = static_cast<int64_t>(f.rows) * f.cols;  // sites per global sub-array
     const T *X = static_cast<const T *>(xsrc) + f.slot0 * Cp + cvo;
     const T *Y = static_cast<const T *>(a.y) + f.slot0;
     const uint32_t sweep = static_cast<uint32_t>(sweep_ll);
     const T rho = static_cast<T>(a.rho);
 
-    // Chain parameters of this thread's chain vector.
     T tau[V], isig[V];
     const T *hyp = static_cast<const T *>(a.hyp);
 #pragma unroll
@@ -102,96 +115,190 @@ __global__ void __launch_bounds__(kFusedBlock) lattice_fused_kernel(const FusedA
         isig[v] = hyp[hc + 1];
     }
 
-    // Stage x (all chains) and y of the tile and its halo.
-    for (int q = threadIdx.x; q < RR * RC * CV; q += kFusedBlock) {
-        const int p = q >> cv_shift;
-        const int ri = fast_div(p, a.rc_m, a.rc_s), rj = p - ri * RC;
-        const int gi = gi0 + ri, gj = gj0 + rj;
-        T v[V];
-        if (gi >= 0 && gi < Hl && gj >= 0 && gj < Wl) {
-            const int slot = slot_rel<KIND>(f, gi, gj);
-            Vec<T, V>::ld(X + slot * Cp, v);
-            if (cvo == 0) ys[p] = Y[slot];
-        } else {
+    // Stage: rows of the NS sub-arrays; slots outside a global sub-array read as zero, and the
+    // global padding slots (sites beyond an odd extent) hold zero, so every position outside
+    // the lattice is zero.
+    {
+        const int rowu = SC << cv_shift;  // work units per staged row
+        const float rcp_rowu = __frcp_rn(static_cast<float>(rowu)), rcp_sr = __frcp_rn(static_cast<float>(SR));
+        // Four loads per thread in flight before their stores (the loads come from L2 or HBM).
+        constexpr int UNR = 4;
+        const int total = NS * SR * rowu;
+        for (int q0 = threadIdx.x; q0 < total; q0 += UNR * kFusedBlock) {
+            T val[UNR][V], yv[UNR];
+            int si[UNR];
 #pragma unroll
-            for (int k = 0; k < V; ++k) v[k] = 0;
-            if (cvo == 0) ys[p] = 0;
+            for (int k = 0; k < UNR; ++k) {
+                const int q = q0 + k * kFusedBlock;
+                si[k] = -1;
+                if (q >= total) continue;
+                const int rr = div_small(q, rcp_rowu), u = q - rr * rowu;
+                const int sa = div_small(rr, rcp_sr), r = rr - sa * SR;
+                const int v = u >> cv_shift, gu = gu0 + r, gv = gv0 + v;
+                const bool ok = interior || (gu >= 0 && gu < f.rows && gv >= 0 && gv < f.cols);
+                const int64_t go = sa * gsub + static_cast<int64_t>(gu) * f.cols + gv;
+                si[k] = rr * SC + v;
+                if (ok) {
+                    Vec<T, V>::ld(X + go * Cp, val[k]);
+                    yv[k] = Y[go];
+                } else {
+#pragma unroll
+                    for (int w = 0; w < V; ++w) val[k][w] = 0;
+                    yv[k] = 0;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                if (si[k] < 0) continue;
+                Vec<T, V>::st(xs + si[k] * Cp + cvo, val[k]);
+                if (cvo == 0) ys[si[k]] = yv[k];
+            }
         }
-        Vec<T, V>::st(xs + p * Cp + cvo, v);
     }
 
-    // Phase A: the normals of every site this block draws in this sweep (colour c within
-    // k - 1 - c rings of the tile).  They depend on (site, sweep, chain) only, so this phase has
-    // no barriers and carries most of the arithmetic.
-    if (a.update) {
-        for (int q = threadIdx.x; q < RR * RC * CV; q += kFusedBlock) {
-            const int p = q >> cv_shift;
-            const int ri = fast_div(p, a.rc_m, a.rc_s), rj = p - ri * RC;
-            const int i = gi0 + ri, j = gj0 + rj;
-            if (i < 0 || i >= Hl || j < 0 || j >= Wl) continue;
-            const int c = D::colour(i, j);
-            const int e = K - 1 - c;
-            if (i < t.i0 - e || i >= t.i0 + TR + e || j < t.j0 - e || j >= t.j0 + TC + e) continue;
-            T z[V];
-            site_normals<T, V>(a.key, static_cast<uint32_t>(i * Wl + j), sweep, f.stream, static_cast<uint32_t>(cvo), z);
-            Vec<T, V>::st(zs + p * Cp + cvo, z);
+    // Region of the colour-c sites drawn by this block: the tile grown by K - 1 - c rings,
+    // clipped to the lattice.  Calls fn(i, j, idx) with idx the site's shared-memory index.
+    auto for_region = [&](int c, auto &&fn) {
+        const int e = K - 1 - c;
+        const int lo_i = max(0, t.i0 - e), hi_i = min(Hl, t.i0 + TR + e);
+        const int lo_j = max(0, t.j0 - e), hi_j = min(Wl, t.j0 + TC + e);
+        if (E8) {
+            const int ca = c >> 1, cb = c & 1;
+            const int u_lo = (lo_i - gi0 - ca + 1) >> 1, u_hi = (hi_i - gi0 - ca + 1) >> 1;
+            const int v_lo = (lo_j - gj0 - cb + 1) >> 1, v_hi = (hi_j - gj0 - cb + 1) >> 1;
+            const int nu = (v_hi - v_lo) << cv_shift;
+            if (u_hi <= u_lo || nu <= 0) return;
+            const float rcp = __frcp_rn(static_cast<float>(nu));
+            for (int q = threadIdx.x; q < (u_hi - u_lo) * nu; q += kFusedBlock) {
+                const int ru = div_small(q, rcp), w = q - ru * nu;
+                const int u = u_lo + ru, v = v_lo + (w >> cv_shift);
+                fn(gi0 + 2 * u + ca, gj0 + 2 * v + cb, (c * SR + u) * SC + v);
+            }
+        } else {
+            // Colour-c sites of row i sit at columns of parity (c + i) & 1: at most nv per row.
+            const int nv = (hi_j - lo_j + 1) >> 1, nu = nv << cv_shift;
+            if (hi_i <= lo_i || nu <= 0) return;
+            const float rcp = __frcp_rn(static_cast<float>(nu));
+            for (int q = threadIdx.x; q < (hi_i - lo_i) * nu; q += kFusedBlock) {
+                const int ri = div_small(q, rcp), w = q - ri * nu;
+                const int i = lo_i + ri, p = (c + i) & 1;
+                const int v = ((lo_j - gj0 - p + 1) >> 1) + (w >> cv_shift);
+                const int j = gj0 + 2 * v + p;
+                if (j >= hi_j) continue;
+                fn(i, j, (c * SR + (i - gi0)) * SC + v);
+            }
+        }
+    };
+
+    // Phase A: the normals of every site this block draws in this sweep.  They depend on
+    // (site, sweep, chain) only, so this phase has no barriers and carries most of the
+    // arithmetic.
+    if (a.update && a.lanes == 4) {
+        // One Philox block per (site, chain quadruple).
+        for (int c = 0; c < K; ++c)
+            for_region(c, [&](int i, int j, int idx) {
+                T z[V];
+                site_normals<T, V>(a.key, static_cast<uint32_t>(i * Wl + j), sweep, f.stream,
+                                   static_cast<uint32_t>(cvo), 4, z);
+                Vec<T, V>::st(zs + idx * Cp + cvo, z);
+            });
+    } else if (a.update) {
+        // One Philox block per group of G = 4 / lanes consecutive natural sites (one or two
+        // chains, so every thread holds all chains): its four normals go to the group's sites
+        // in this row that some colour step of this block draws.
+        const int gs = lanes_shift(a.lanes), G = 1 << gs, L = a.lanes;
+        const int ngmax = (RC >> gs) + 2;
+        const int jl = max(0, gj0), jh = min(Wl, gj0 + RC);
+        for (int q = threadIdx.x; q < RR * ngmax; q += kFusedBlock) {
+            const int ri = fast_div(q, a.ng_m, a.ng_s), k = q - ri * ngmax;
+            const int i = gi0 + ri;
+            if (i < 0 || i >= Hl || jl >= jh) continue;
+            const int s0 = i * Wl + jl, s1 = i * Wl + jh;
+            const int g = (s0 >> gs) + k;
+            if ((g << gs) >= s1) continue;
+            T n4[4];
+            block_normals<T>(a.key, static_cast<uint32_t>(g), sweep, f.stream, 0u, n4);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (r >= G) break;
+                const int st = (g << gs) + r;
+                if (st < s0 || st >= s1) continue;
+                const int j = st - i * Wl;
+                const int e = K - 1 - D::colour(i, j);
+                if (i < t.i0 - e || i >= t.i0 + TR + e || j < t.j0 - e || j >= t.j0 + TC + e) continue;
+                T *zp = zs + sm_index<KIND>(i, j, gi0, gj0, SR, SC) * Cp;
+                for (int ch = 0; ch < L; ++ch) zp[ch] = n4[r * L + ch];
+            }
         }
     }
     __syncthreads();
 
-    // Colour steps in shared memory (skipped in reduce-only mode).
+    // Phase B: colour steps in shared memory.  Neighbour k of a colour-c site sits at a fixed
+    // offset from the site (block-uniform per step; for the 4-neighbour lattice the in-row
+    // offsets depend on the row's parity); positions outside the lattice hold zeros, so the
+    // sum needs no bounds tests.  The owned sites also fold their terms of the two sums of the
+    // hyperparameter conditionals here, while their neighbours are in registers: (1 - rho) d x^2
+    // + rho sum over lower-colour neighbours of (x - x_j)^2, and (y - x)^2.
+    T accS[V], accR[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        accS[v] = 0;
+        accR[v] = 0;
+    }
 #pragma unroll 1
     for (int c = 0; c < (a.update ? K : 0); ++c) {
-        const int e = K - 1 - c;
-        const int lo_i = max(0, t.i0 - e), hi_i = min(Hl, t.i0 + TR + e);
-        const int lo_j = max(0, t.j0 - e), hi_j = min(Wl, t.j0 + TC + e);
-        int fi, ni, ncols;
-        if (KIND == kLat2D8) {
-            fi = lo_i + (((c >> 1) - lo_i) & 1);
-            ni = hi_i > fi ? (hi_i - fi + 1) >> 1 : 0;
-            const int fj = lo_j + (((c & 1) - lo_j) & 1);
-            ncols = hi_j > fj ? (hi_j - fj + 1) >> 1 : 0;
-        } else {
-            fi = lo_i;
-            ni = hi_i - lo_i;
-            ncols = (hi_j - lo_j + 1) >> 1;
-        }
-        const int nq = ni * ncols * CV;
-        uint32_t nc_m;
-        int nc_s;
-        device_magic(static_cast<uint32_t>(ncols > 0 ? ncols : 1), nc_m, nc_s);
-        for (int q = threadIdx.x; q < nq; q += kFusedBlock) {
-            const int p = q >> cv_shift;
-            const int u = fast_div(p, nc_m, nc_s), w = p - u * ncols;
-            int i, j;
-            if (KIND == kLat2D8) {
-                i = fi + 2 * u;
-                j = lo_j + (((c & 1) - lo_j) & 1) + 2 * w;
-            } else {
-                i = fi + u;
-                j = lo_j + ((c + i - lo_j) & 1) + 2 * w;
-                if (j >= hi_j) continue;
+        int off8[8];
+        uint32_t lower = 0;
+        if (E8) {
+            const int ca = c >> 1, cb = c & 1;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int ai = ca + D::di(k), bj = cb + D::dj(k);
+                const int cc = 2 * (ai & 1) + (bj & 1);
+                off8[k] = ((cc - c) * SR + (ai >> 1)) * SC + (bj >> 1);
+                if (cc < c) lower |= 1u << k;
             }
-            const int ri = i - gi0, rj = j - gj0;
-            const T *xc = xs + (ri * RC + rj) * Cp + cvo;
-            // Staged positions outside the lattice hold zeros, so the neighbour sum needs no
-            // bounds tests; the degree follows from how many of the rows i-1..i+1 and columns
-            // j-1..j+1 exist.
-            T s[V];
+        } else if (c == 1) {
+            lower = 0xfu;
+        }
+        for_region(c, [&, off8](int i, int j, int idx) {
+            int off[D::N];
+            if (E8) {
+#pragma unroll
+                for (int k = 0; k < D::N; ++k) off[k] = off8[k];
+            } else {
+                const int p = (c + i) & 1, o = (1 - 2 * c) * SR * SC;  // other colour's sub-array
+                off[0] = o - SC;         // (i - 1, j)
+                off[1] = o - 1 + p;      // (i, j - 1)
+                off[2] = o + p;          // (i, j + 1)
+                off[3] = o + SC;         // (i + 1, j)
+            }
+            const T *xc = xs + idx * Cp + cvo;
+            T nb[D::N][V], s[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) s[v] = 0;
 #pragma unroll
             for (int k = 0; k < D::N; ++k) {
-                T nb[V];
-                Vec<T, V>::ld(xc + (D::di(k) * RC + D::dj(k)) * Cp, nb);
+                Vec<T, V>::ld(xc + off[k] * Cp, nb[k]);
 #pragma unroll
-                for (int v = 0; v < V; ++v) s[v] += nb[v];
+                for (int v = 0; v < V; ++v) s[v] += nb[k][v];
             }
-            const int vr = (i > 0) + (i + 1 < Hl), vc = (j > 0) + (j + 1 < Wl);
-            const int deg = (KIND == kLat2D8) ? (vr + 1) * (vc + 1) - 1 : vr + vc;
+            int deg = D::N;
+            uint32_t valid = (1u << D::N) - 1u;
+            if (!interior) {
+                const bool up = i > 0, down = i + 1 < Hl, left = j > 0, right = j + 1 < Wl;
+                valid = 0;
+#pragma unroll
+                for (int k = 0; k < D::N; ++k) {
+                    const int di = D::di(k), dj = D::dj(k);
+                    const bool ok = (di < 0 ? up : (di > 0 ? down : true)) && (dj < 0 ? left : (dj > 0 ? right : true));
+                    valid |= ok ? (1u << k) : 0u;
+                }
+                deg = __popc(valid);
+            }
             T z[V];
-            Vec<T, V>::ld(zs + (ri * RC + rj) * Cp + cvo, z);
-            const T yv = ys[ri * RC + rj];
+            Vec<T, V>::ld(zs + idx * Cp + cvo, z);
+            const T yv = ys[idx];
             const T d = static_cast<T>(deg);
             T xn[V];
 #pragma unroll
@@ -200,84 +307,112 @@ __global__ void __launch_bounds__(kFusedBlock) lattice_fused_kernel(const FusedA
                 const T m = (tau[v] * rho * s[v] + yv * isig[v]) * FArith<T>::rcp(P);
                 xn[v] = m + z[v] * FArith<T>::rsq(P);
             }
-            Vec<T, V>::st(xs + (ri * RC + rj) * Cp + cvo, xn);
-        }
+            Vec<T, V>::st(xs + idx * Cp + cvo, xn);
+            if (i >= t.i0 && i < t.i0 + TR && j >= t.j0 && j < t.j0 + TC) {
+                const uint32_t lv = lower & valid;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    T e = 0;
+#pragma unroll
+                    for (int k = 0; k < D::N; ++k)
+                        if ((lv >> k) & 1u) {
+                            const T df = xn[v] - nb[k][v];
+                            e += df * df;
+                        }
+                    accS[v] += (static_cast<T>(1) - rho) * d * xn[v] * xn[v] + rho * e;
+                    const T r = yv - xn[v];
+                    accR[v] += r * r;
+                }
+            }
+        });
         __syncthreads();
     }
 
-    // Owned sites: write back, reduce, accumulate.
-    const bool acc = a.update && a.acc_enabled && sweep_accumulated(sweep_ll, a.burn_in, a.thin);
-    T inv_k = 0;
-    if (acc) inv_k = static_cast<T>(1) / static_cast<T>(a.ctl->acc_count + 1);
-    T *XW = static_cast<T *>(xdst) + f.slot0 * Cp + cvo;
-    T *MEAN = static_cast<T *>(a.mean) + f.slot0 * Cp + cvo;
-    T *M2 = static_cast<T *>(a.m2) + f.slot0 * Cp + cvo;
-    T accS[V], accR[V];
+    // Reduce-only mode (no colour steps): fold the owned sites' terms from the staged state.
+    if (!a.update) {
+        for (int c = 0; c < K; ++c) {
+            for_region(c, [&](int i, int j, int idx) {
+                if (i < t.i0 || i >= t.i0 + TR || j < t.j0 || j >= t.j0 + TC) return;
+                T xn[V];
+                Vec<T, V>::ld(xs + idx * Cp + cvo, xn);
+                int deg = 0;
+                T e[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        accS[v] = 0;
-        accR[v] = 0;
-    }
-    const int oq = TR * TC * CV;
-    for (int q = threadIdx.x; q < oq; q += kFusedBlock) {
-        const int p = q >> cv_shift;
-        const int oi = fast_div(p, a.tc_m, a.tc_s), oj = p - oi * TC;
-        const int i = t.i0 + oi, j = t.j0 + oj;
-        if (i >= Hl || j >= Wl) continue;
-        const int ri = oi + K, rj = oj + K;
-        const T *xc = xs + (ri * RC + rj) * Cp + cvo;
-        T xn[V];
-        Vec<T, V>::ld(xc, xn);
-        const int c = D::colour(i, j);
-        const bool up = i > 0, down = i + 1 < Hl, left = j > 0, right = j + 1 < Wl;
-        T e[V];
+                for (int v = 0; v < V; ++v) e[v] = 0;
 #pragma unroll
-        for (int v = 0; v < V; ++v) e[v] = 0;
+                for (int k = 0; k < D::N; ++k) {
+                    const int ii = i + D::di(k), jj = j + D::dj(k);
+                    if (ii < 0 || ii >= Hl || jj < 0 || jj >= Wl) continue;
+                    ++deg;
+                    if (D::colour(ii, jj) >= c) continue;
+                    T nbv[V];
+                    Vec<T, V>::ld(xs + sm_index<KIND>(ii, jj, gi0, gj0, SR, SC) * Cp + cvo, nbv);
 #pragma unroll
-        for (int k = 0; k < D::N; ++k) {
-            const int di = D::di(k), dj = D::dj(k);
-            const bool ok = (di < 0 ? up : (di > 0 ? down : true)) && (dj < 0 ? left : (dj > 0 ? right : true));
-            if (ok && D::colour(i + di, j + dj) < c) {
-                T nb[V];
-                Vec<T, V>::ld(xc + (di * RC + dj) * Cp, nb);
+                    for (int v = 0; v < V; ++v) {
+                        const T df = xn[v] - nbv[v];
+                        e[v] += df * df;
+                    }
+                }
+                const T yv = ys[idx];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    const T df = xn[v] - nb[v];
-                    e[v] += df * df;
+                    accS[v] += (static_cast<T>(1) - rho) * static_cast<T>(deg) * xn[v] * xn[v] + rho * e[v];
+                    const T r = yv - xn[v];
+                    accR[v] += r * r;
+                }
+            });
+        }
+    }
+
+    // Write-back of the owned sites (rows of the sub-arrays) and the running mean / M2.
+    const bool acc = a.update && a.acc_enabled && sweep_accumulated(sweep_ll, a.burn_in, a.thin);
+    if (a.update) {
+        T inv_k = 0;
+        if (acc) inv_k = static_cast<T>(1) / static_cast<T>(a.ctl->acc_count + 1);
+        T *XW = static_cast<T *>(xdst) + f.slot0 * Cp + cvo;
+        T *MEAN = static_cast<T *>(a.mean) + f.slot0 * Cp + cvo;
+        T *M2 = static_cast<T *>(a.m2) + f.slot0 * Cp + cvo;
+        const int orow = E8 ? (TR >> 1) : TR;          // owned rows per sub-array
+        const int r0 = E8 ? (K >> 1) : K, v0 = K >> 1;  // first owned row / column in a sub-array
+        const int rowu = (TC >> 1) << cv_shift;
+        const float rcp_rowu = __frcp_rn(static_cast<float>(rowu)), rcp_orow = __frcp_rn(static_cast<float>(orow));
+        for (int q = threadIdx.x; q < NS * orow * rowu; q += kFusedBlock) {
+            const int rr = div_small(q, rcp_rowu), w = q - rr * rowu;
+            const int sa = div_small(rr, rcp_orow), r = rr - sa * orow;
+            const int sr = r0 + r, gu = gu0 + sr;
+            const int i = E8 ? gi0 + 2 * sr + (sa >> 1) : gi0 + sr;
+            if (i >= Hl) continue;
+            {
+                const int v = v0 + (w >> cv_shift);
+                const int pj = E8 ? (sa & 1) : ((sa + i) & 1);
+                const int j = gj0 + 2 * v + pj;
+                if (j >= Wl) continue;
+                const int64_t go = (sa * gsub + static_cast<int64_t>(gu) * f.cols + gv0 + v) * Cp;
+                T xn[V];
+                Vec<T, V>::ld(xs + ((sa * SR + sr) * SC + v) * Cp + cvo, xn);
+                Vec<T, V>::st(XW + go, xn);
+                if (acc) {
+                    T mu[V], mm[V];
+                    Vec<T, V>::ld(MEAN + go, mu);
+                    Vec<T, V>::ld(M2 + go, mm);
+#pragma unroll
+                    for (int q = 0; q < V; ++q) {
+                        const T delta = xn[q] - mu[q];
+                        mu[q] += delta * inv_k;
+                        mm[q] += delta * (xn[q] - mu[q]);
+                    }
+                    Vec<T, V>::st(MEAN + go, mu);
+                    Vec<T, V>::st(M2 + go, mm);
                 }
             }
-        }
-        const int vr = up + down, vc = left + right;
-        const int deg = (KIND == kLat2D8) ? (vr + 1) * (vc + 1) - 1 : vr + vc;
-        const T yv = ys[ri * RC + rj];
-        const T d = static_cast<T>(deg);
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            accS[v] += (static_cast<T>(1) - rho) * d * xn[v] * xn[v] + rho * e[v];
-            const T r = yv - xn[v];
-            accR[v] += r * r;
-        }
-        const int so = slot_rel<KIND>(f, i, j) * Cp;
-        if (a.update) Vec<T, V>::st(XW + so, xn);
-        if (acc) {
-            T mu[V], mm[V];
-            Vec<T, V>::ld(MEAN + so, mu);
-            Vec<T, V>::ld(M2 + so, mm);
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const T delta = xn[v] - mu[v];
-                mu[v] += delta * inv_k;
-                mm[v] += delta * (xn[v] - mu[v]);
-            }
-            Vec<T, V>::st(MEAN + so, mu);
-            Vec<T, V>::st(M2 + so, mm);
         }
     }
 
     // Deterministic block reduction in precision T (shuffle tree over lanes sharing a chain
     // vector, then warps in order) into the tile's FP64 partial-sum slot; a tile holds at most a
     // few thousand terms, the sum over tiles is FP64.
-    __shared__ T red[kFusedBlock / 32][kMaxChains][2];
+    // Reduction scratch [NW][Cp][2] reuses the normals' space (dead after phase B).
+    T *red = zs;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -287,31 +422,350 @@ __global__ void __launch_bounds__(kFusedBlock) lattice_fused_kernel(const FusedA
             sR += __shfl_xor_sync(0xffffffffu, sR, off);
         }
         if (lane < CV) {
-            red[warp][lane * V + v][0] = sS;
-            red[warp][lane * V + v][1] = sR;
+            red[(warp * Cp + lane * V + v) * 2] = sS;
+            red[(warp * Cp + lane * V + v) * 2 + 1] = sR;
         }
     }
     __syncthreads();
     for (int q = threadIdx.x; q < Cp * 2; q += kFusedBlock) {
         const int chain = q >> 1, k = q & 1;
         T sum = 0;
-        for (int w = 0; w < kFusedBlock / 32; ++w) sum += red[w][chain][k];
+        for (int w = 0; w < NW; ++w) sum += red[(w * Cp + chain) * 2 + k];
         reinterpret_cast<double *>(a.partials + static_cast<int64_t>(t.part) * Cp + chain)[k] = static_cast<double>(sum);
+    }
+}
+
+// Fast path: every thread holds all CP chains of a site (CP = 1, 2 or 4, the chain count of the
+// layout), so chain strides are compile-time constants; only colour steps (update mode).  Same
+// phases and results as lattice_fused_kernel, with the per-site index work cut down:
+// field-relative 32-bit offsets, staging indices equal to the shared-memory index, normals
+// drawn for every staged site (no per-site region tests), neighbour offsets fixed per colour
+// step, lower-colour terms as 0/1 weights, and bounds tests only for sites on the lattice edge.
+template <typename T, int KIND, int NT, int CP>
+__global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4) ? 2 : 1) lattice_fused_fast(const FusedArgs a)
+{
+    using D = Dirs<KIND>;
+    constexpr bool E8 = (KIND == kLat2D8);
+    constexpr int K = E8 ? 4 : 2;
+    constexpr int NS = E8 ? 4 : 2;
+    constexpr int NW = NT / 32;
+    constexpr int ND = D::N;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileXY t = a.tiles[blockIdx.x];
+    const FieldDev f = a.fields[t.field];
+    const int Hl = f.dims[0], Wl = f.dims[1];
+    const int TR = a.TR, TC = a.TC, RR = TR + 2 * K, RC = TC + 2 * K;
+    const int SR = E8 ? (RR >> 1) : RR, SC = RC >> 1, SUB = SR * SC;
+    T *xs = reinterpret_cast<T *>(smem_raw);  // [NS * SUB][CP]
+    T *zs = xs + NS * SUB * CP;               // [NS * SUB][CP]
+    T *ys = zs + NS * SUB * CP;               // [NS * SUB]
+    const int gi0 = t.i0 - K, gj0 = t.j0 - K;
+    const int gu0 = E8 ? (gi0 >> 1) : gi0, gv0 = gj0 >> 1;
+    const bool interior = gi0 >= 0 && gj0 >= 0 && gi0 + RR <= Hl && gj0 + RC <= Wl;
+    const long long sweep_ll = a.ctl->sweep;
+    const uint32_t sweep = static_cast<uint32_t>(sweep_ll);
+    const T *X = static_cast<const T *>((sweep_ll & 1) ? a.x_alt : a.x) + f.slot0 * CP;
+    T *XW = static_cast<T *>((sweep_ll & 1) ? a.x : a.x_alt) + f.slot0 * CP;
+    const T *Y = static_cast<const T *>(a.y) + f.slot0;
+    const int gsub = f.rows * f.cols, gcols = f.cols, grows = f.rows;
+    const T rho = static_cast<T>(a.rho);
+    T tau[CP], isig[CP];
+    {
+        const T *hyp = static_cast<const T *>(a.hyp) + static_cast<int64_t>(t.field) * CP * 2;
+#pragma unroll
+        for (int v = 0; v < CP; ++v) {
+            tau[v] = hyp[2 * v];
+            isig[v] = hyp[2 * v + 1];
+        }
+    }
+    const float rcp_sc = __frcp_rn(static_cast<float>(SC)), rcp_sr = __frcp_rn(static_cast<float>(SR));
+
+    // Stage (four loads in flight per thread).  The staged index q is the shared-memory index.
+    {
+        constexpr int UNR = 4;
+        const int total = NS * SUB;
+        for (int q0 = threadIdx.x; q0 < total; q0 += UNR * NT) {
+            T val[UNR][CP], yv[UNR];
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const int q = q0 + k * NT;
+                if (q >= total) continue;
+                const int rr = div_small(q, rcp_sc), v = q - rr * SC;
+                const int sa = div_small(rr, rcp_sr), r = rr - sa * SR;
+                const int gu = gu0 + r, gv = gv0 + v;
+                const bool ok = interior || (gu >= 0 && gu < grows && gv >= 0 && gv < gcols);
+                const int go = sa * gsub + gu * gcols + gv;
+                if (ok) {
+                    Vec<T, CP>::ld(X + go * CP, val[k]);
+                    yv[k] = Y[go];
+                } else {
+#pragma unroll
+                    for (int w = 0; w < CP; ++w) val[k][w] = 0;
+                    yv[k] = 0;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const int q = q0 + k * NT;
+                if (q >= total) continue;
+                Vec<T, CP>::st(xs + q * CP, val[k]);
+                ys[q] = yv[k];
+            }
+        }
+    }
+
+    // Phase A: normals of every staged site (those outside the drawn regions are unused).
+    if (CP == 4) {
+        for (int q = threadIdx.x; q < NS * SUB; q += NT) {
+            const int rr = div_small(q, rcp_sc), v = q - rr * SC;
+            const int sa = div_small(rr, rcp_sr), r = rr - sa * SR;
+            const int i = E8 ? gi0 + 2 * r + (sa >> 1) : gi0 + r;
+            const int j = E8 ? gj0 + 2 * v + (sa & 1) : gj0 + 2 * v + ((sa + i) & 1);
+            if (!interior && (i < 0 || i >= Hl || j < 0 || j >= Wl)) continue;
+            T z[CP];
+            site_normals<T, CP>(a.key, static_cast<uint32_t>(i * Wl + j), sweep, f.stream, 0u, 4, z);
+            Vec<T, CP>::st(zs + q * CP, z);
+        }
+    } else {
+        // Groups of G = 4 / CP consecutive natural sites share a Philox block.
+        constexpr int GS = (CP == 2) ? 1 : 2, G = 1 << GS;
+        const int NG = (RC >> GS) + 2;
+        const float rcp_ng = __frcp_rn(static_cast<float>(NG));
+        const int jl = max(0, gj0), jh = min(Wl, gj0 + RC);
+        for (int q = threadIdx.x; q < RR * NG; q += NT) {
+            const int ri = div_small(q, rcp_ng), k = q - ri * NG;
+            const int i = gi0 + ri;
+            if (i < 0 || i >= Hl || jl >= jh) continue;
+            const int s0 = i * Wl + jl, s1 = i * Wl + jh;
+            const int g = (s0 >> GS) + k;
+            if ((g << GS) >= s1) continue;
+            T n4[4];
+            block_normals<T>(a.key, static_cast<uint32_t>(g), sweep, f.stream, 0u, n4);
+#pragma unroll
+            for (int r = 0; r < G; ++r) {
+                const int st = (g << GS) + r;
+                if (st < s0 || st >= s1) continue;
+                const int j = st - i * Wl;
+                T *zp = zs + sm_index<KIND>(i, j, gi0, gj0, SR, SC) * CP;
+#pragma unroll
+                for (int ch = 0; ch < CP; ++ch) zp[ch] = n4[r * CP + ch];
+            }
+        }
+    }
+    __syncthreads();
+
+    // Phase B: colour steps; owned sites fold their terms of the hyperparameter sums.
+    T accS[CP], accR[CP];
+#pragma unroll
+    for (int v = 0; v < CP; ++v) {
+        accS[v] = 0;
+        accR[v] = 0;
+    }
+#pragma unroll 1
+    for (int c = 0; c < K; ++c) {
+        const int e = K - 1 - c;
+        const int lo_i = max(0, t.i0 - e), hi_i = min(Hl, t.i0 + TR + e);
+        const int lo_j = max(0, t.j0 - e), hi_j = min(Wl, t.j0 + TC + e);
+        // Fixed neighbour offsets (shared-memory index units) and 0/1 weights of the
+        // lower-colour directions for this colour.
+        int off[ND];
+        T wl[ND];
+        if (E8) {
+            const int ca = c >> 1, cb = c & 1;
+#pragma unroll
+            for (int k = 0; k < ND; ++k) {
+                const int ai = ca + D::di(k), bj = cb + D::dj(k);
+                const int cc = 2 * (ai & 1) + (bj & 1);
+                off[k] = ((cc - c) * SR + (ai >> 1)) * SC + (bj >> 1);
+                wl[k] = cc < c ? static_cast<T>(1) : static_cast<T>(0);
+            }
+        } else {
+            const int o = (1 - 2 * c) * SR * SC;
+            off[0] = o - SC;
+            off[1] = o - 1;  // + p, added per row
+            off[2] = o;      // + p
+            off[3] = o + SC;
+#pragma unroll
+            for (int k = 0; k < ND; ++k) wl[k] = static_cast<T>(c);
+        }
+        int n_rows, n_cols, first_u = 0, first_v = 0;
+        if (E8) {
+            const int ca = c >> 1, cb = c & 1;
+            first_u = (lo_i - gi0 - ca + 1) >> 1;
+            first_v = (lo_j - gj0 - cb + 1) >> 1;
+            n_rows = ((hi_i - gi0 - ca + 1) >> 1) - first_u;
+            n_cols = ((hi_j - gj0 - cb + 1) >> 1) - first_v;
+        } else {
+            n_rows = hi_i - lo_i;
+            n_cols = (hi_j - lo_j + 1) >> 1;
+        }
+        if (n_rows > 0 && n_cols > 0) {
+            const float rcp_nc = __frcp_rn(static_cast<float>(n_cols));
+            for (int q = threadIdx.x; q < n_rows * n_cols; q += NT) {
+                const int ru = div_small(q, rcp_nc), w = q - ru * n_cols;
+                int i, j, idx, dp = 0;
+                if (E8) {
+                    const int u = first_u + ru, v = first_v + w;
+                    i = gi0 + 2 * u + (c >> 1);
+                    j = gj0 + 2 * v + (c & 1);
+                    idx = (c * SR + u) * SC + v;
+                } else {
+                    i = lo_i + ru;
+                    const int p = (c + i) & 1;
+                    const int v = ((lo_j - gj0 - p + 1) >> 1) + w;
+                    j = gj0 + 2 * v + p;
+                    if (j >= hi_j) continue;
+                    idx = (c * SR + (i - gi0)) * SC + v;
+                    dp = p;
+                }
+                T nb[ND][CP], s[CP];
+#pragma unroll
+                for (int v = 0; v < CP; ++v) s[v] = 0;
+#pragma unroll
+                for (int k = 0; k < ND; ++k) {
+                    const int o = off[k] + ((!E8 && (k == 1 || k == 2)) ? dp : 0);
+                    Vec<T, CP>::ld(xs + (idx + o) * CP, nb[k]);
+#pragma unroll
+                    for (int v = 0; v < CP; ++v) s[v] += nb[k][v];
+                }
+                T d = static_cast<T>(ND);
+                T wv[ND];
+#pragma unroll
+                for (int k = 0; k < ND; ++k) wv[k] = wl[k];
+                if (!interior && (i == 0 || j == 0 || i == Hl - 1 || j == Wl - 1)) {
+                    // Edge site: missing neighbours hold zero (the sum is right) but must not
+                    // count in the degree or the prior sum.
+                    int deg = 0;
+#pragma unroll
+                    for (int k = 0; k < ND; ++k) {
+                        const int ii = i + D::di(k), jj = j + D::dj(k);
+                        const bool ok = ii >= 0 && ii < Hl && jj >= 0 && jj < Wl;
+                        deg += ok;
+                        if (!ok) wv[k] = 0;
+                    }
+                    d = static_cast<T>(deg);
+                }
+                T z[CP];
+                Vec<T, CP>::ld(zs + idx * CP, z);
+                const T yv = ys[idx];
+                T xn[CP];
+#pragma unroll
+                for (int v = 0; v < CP; ++v) {
+                    const T P = tau[v] * d + isig[v];
+                    const T m = (tau[v] * rho * s[v] + yv * isig[v]) * FArith<T>::rcp(P);
+                    xn[v] = m + z[v] * FArith<T>::rsq(P);
+                }
+                Vec<T, CP>::st(xs + idx * CP, xn);
+                if (i >= t.i0 && i < t.i0 + TR && j >= t.j0 && j < t.j0 + TC) {
+#pragma unroll
+                    for (int v = 0; v < CP; ++v) {
+                        T e2 = 0;
+#pragma unroll
+                        for (int k = 0; k < ND; ++k) {
+                            const T df = xn[v] - nb[k][v];
+                            e2 += wv[k] * df * df;
+                        }
+                        accS[v] += (static_cast<T>(1) - rho) * d * xn[v] * xn[v] + rho * e2;
+                        const T r = yv - xn[v];
+                        accR[v] += r * r;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // Write-back of the owned sites and the running mean / M2.
+    {
+        const bool acc = a.acc_enabled && sweep_accumulated(sweep_ll, a.burn_in, a.thin);
+        T inv_k = 0;
+        if (acc) inv_k = static_cast<T>(1) / static_cast<T>(a.ctl->acc_count + 1);
+        T *MEAN = static_cast<T *>(a.mean) + f.slot0 * CP;
+        T *M2 = static_cast<T *>(a.m2) + f.slot0 * CP;
+        const int orow = E8 ? (TR >> 1) : TR, tc2 = TC >> 1;
+        const int r0 = E8 ? (K >> 1) : K, v0 = K >> 1;
+        const bool tile_full = t.i0 + TR <= Hl && t.j0 + TC <= Wl;
+        const float rcp_tc2 = __frcp_rn(static_cast<float>(tc2)), rcp_orow = __frcp_rn(static_cast<float>(orow));
+        for (int q = threadIdx.x; q < NS * orow * tc2; q += NT) {
+            const int rr = div_small(q, rcp_tc2), w = q - rr * tc2;
+            const int sa = div_small(rr, rcp_orow), r = rr - sa * orow;
+            const int sr = r0 + r, v = v0 + w;
+            if (!tile_full) {
+                const int i = E8 ? gi0 + 2 * sr + (sa >> 1) : gi0 + sr;
+                const int j = gj0 + 2 * v + (E8 ? (sa & 1) : ((sa + i) & 1));
+                if (i >= Hl || j >= Wl) continue;
+            }
+            const int go = (sa * gsub + (gu0 + sr) * gcols + gv0 + v) * CP;
+            T xn[CP];
+            Vec<T, CP>::ld(xs + ((sa * SR + sr) * SC + v) * CP, xn);
+            Vec<T, CP>::st(XW + go, xn);
+            if (acc) {
+                T mu[CP], mm[CP];
+                Vec<T, CP>::ld(MEAN + go, mu);
+                Vec<T, CP>::ld(M2 + go, mm);
+#pragma unroll
+                for (int v2 = 0; v2 < CP; ++v2) {
+                    const T delta = xn[v2] - mu[v2];
+                    mu[v2] += delta * inv_k;
+                    mm[v2] += delta * (xn[v2] - mu[v2]);
+                }
+                Vec<T, CP>::st(MEAN + go, mu);
+                Vec<T, CP>::st(M2 + go, mm);
+            }
+        }
+    }
+
+    // Block reduction (all lanes hold the same chains): warp shuffle tree, then warps in order.
+    T *red = zs;  // [NW][CP][2], the normals are dead
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < CP; ++v) {
+        T sS = accS[v], sR = accR[v];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            sS += __shfl_xor_sync(0xffffffffu, sS, o);
+            sR += __shfl_xor_sync(0xffffffffu, sR, o);
+        }
+        if (lane == 0) {
+            red[(warp * CP + v) * 2] = sS;
+            red[(warp * CP + v) * 2 + 1] = sR;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < CP * 2) {
+        const int chain = threadIdx.x >> 1, k = threadIdx.x & 1;
+        T sum = 0;
+        for (int w = 0; w < NW; ++w) sum += red[(w * CP + chain) * 2 + k];
+        reinterpret_cast<double *>(a.partials + static_cast<int64_t>(t.part) * CP + chain)[k] = static_cast<double>(sum);
     }
 }
 
 template <typename T, int V, int KIND>
 cudaError_t launch_t(const FusedArgs &a, size_t smem, cudaStream_t stream)
 {
-    lattice_fused_kernel<T, V, KIND><<<a.ntiles, kFusedBlock, smem, stream>>>(a);
+    const bool fast = a.update && a.Cp == V;  // every thread holds all chains
+    if (a.threads == 1024) {
+        if (fast) lattice_fused_fast<T, KIND, 1024, V><<<a.ntiles, 1024, smem, stream>>>(a);
+        else lattice_fused_kernel<T, V, KIND, 1024><<<a.ntiles, 1024, smem, stream>>>(a);
+    } else {
+        if (fast) lattice_fused_fast<T, KIND, 512, V><<<a.ntiles, 512, smem, stream>>>(a);
+        else lattice_fused_kernel<T, V, KIND, 512><<<a.ntiles, 512, smem, stream>>>(a);
+    }
     return cudaGetLastError();
 }
 
 template <typename T, int V, int KIND>
 cudaError_t prepare_t(size_t smem)
 {
-    return cudaFuncSetAttribute(lattice_fused_kernel<T, V, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem));
+    const int b = static_cast<int>(smem);
+    cudaError_t e = cudaFuncSetAttribute(lattice_fused_kernel<T, V, KIND, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(lattice_fused_kernel<T, V, KIND, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(lattice_fused_fast<T, KIND, 512, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(lattice_fused_fast<T, KIND, 1024, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return e;
 }
 
 template <int KIND>

@@ -81,7 +81,7 @@ __global__ void plain_colour_kernel(const PlainArgs a, int colour)
         const double m = (tau * a.rho * s + a.y[i] * isig) / P;
         double z[1];
         site_normals<double, 1>(a.key, static_cast<uint32_t>(i), static_cast<uint32_t>(sweep), a.stream_id,
-                                static_cast<uint32_t>(chain), z);
+                                static_cast<uint32_t>(chain), a.lanes, z);
         a.x[static_cast<int64_t>(chain) * a.n + i] = m + z[0] / sqrt(P);
     }
 }

@@ -56,7 +56,7 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
     T xn[V];
     if (a.update) {
         T z[V];
-        site_normals<T, V>(a.key, site, sweep, stream, chain0, z);
+        site_normals<T, V>(a.key, site, sweep, stream, chain0, a.lanes, z);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const T P = cx.tau[v] * d + cx.isig[v];
@@ -494,12 +494,13 @@ __global__ void philox_words_kernel(uint2 key, uint32_t c1, uint32_t c2, uint32_
 }
 
 template <typename T>
-__global__ void site_normals_kernel(uint2 key, uint32_t sweep, uint32_t stream, uint32_t chain, int64_t count, T *out)
+__global__ void site_normals_kernel(uint2 key, uint32_t sweep, uint32_t stream, uint32_t chain, int lanes,
+                                    int64_t count, T *out)
 {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         T z[1];
-        site_normals<T, 1>(key, static_cast<uint32_t>(i), sweep, stream, chain, z);
+        site_normals<T, 1>(key, static_cast<uint32_t>(i), sweep, stream, chain, lanes, z);
         out[i] = z[0];
     }
 }
@@ -631,16 +632,16 @@ cudaError_t launch_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream_id, uint32_t chain, int precision,
-                                int64_t count, void *out, cudaStream_t stream)
+cudaError_t launch_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream_id, uint32_t chain, int lanes,
+                                int precision, int64_t count, void *out, cudaStream_t stream)
 {
     if (count <= 0) return cudaSuccess;
     if (precision == 0)
         site_normals_kernel<float><<<grid_for(count, 256), 256, 0, stream>>>(philox_key(seed), sweep, stream_id, chain,
-                                                                            count, static_cast<float *>(out));
+                                                                            lanes, count, static_cast<float *>(out));
     else
         site_normals_kernel<double><<<grid_for(count, 256), 256, 0, stream>>>(philox_key(seed), sweep, stream_id, chain,
-                                                                             count, static_cast<double *>(out));
+                                                                             lanes, count, static_cast<double *>(out));
     return cudaGetLastError();
 }
 

@@ -114,7 +114,8 @@ def lib() -> ctypes.CDLL:
                                             ctypes.c_uint32, ctypes.c_int64, vp, vp]
             L.gmrf_philox_words.restype = st
             L.gmrf_site_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
-                                            ctypes.c_uint32, ctypes.c_int32, ctypes.c_int64, vp, vp]
+                                            ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int64, vp, vp]
             L.gmrf_site_normals.restype = st
             L.gmrf_last_error.argtypes = []
             L.gmrf_last_error.restype = ctypes.c_char_p
@@ -186,13 +187,14 @@ def philox_words(seed, c1, c2, c3, count):
     return out.cpu().numpy().view(np.uint32).reshape(-1, 4)
 
 
-def site_normals(seed, sweep, stream, chain, count, precision=FP64):
-    """The GPU's update normals of sites 0..count-1 (one chain, one sweep)."""
+def site_normals(seed, sweep, stream, chain, count, precision=FP64, lanes=4):
+    """The GPU's update normals of sites 0..count-1 (one chain, one sweep) for a sampler whose
+    Philox blocks serve `lanes` chains."""
     import torch
 
     dt = torch.float32 if precision == FP32 else torch.float64
     out = torch.empty(int(count), dtype=dt, device="cuda")
-    _check(lib().gmrf_site_normals(int(seed), sweep, stream, chain, precision, int(count),
+    _check(lib().gmrf_site_normals(int(seed), sweep, stream, chain, int(lanes), precision, int(count),
                                    ctypes.c_void_p(out.data_ptr()), current_stream()))
     torch.cuda.synchronize()
     return out.cpu().numpy()

@@ -274,7 +274,7 @@ def test_fixed_hyper_and_tau_zero():
     f = wl.small_lattice(wl.LATTICE2D_8, (20, 21), 9)
     res, _ = gpu_run([f], 2, 5, g.FP64, seed=71, fix_hyper=True, tau0=0.0, sigma2_0=0.49)
     st, out = compare(f, res[0], 2, 5, 71, 0, TOL_FP64, fix_hyper=True, tau0=0.0, sigma2_0=0.49)
-    z = oracle.site_normals(71, f["n"], 4, 0, 1)
+    z = oracle.site_normals(71, f["n"], 4, 0, 1, oracle.lanes_for(2))
     np.testing.assert_allclose(res[0][1]["x"], f["y"] + 0.7 * z, rtol=1e-12, atol=1e-12)
     assert np.all(res[0][0]["tau_trace"] == 0.0)
 

@@ -38,19 +38,22 @@ def test_philox_words_known_answer():
     assert [hex(v) for v in got] == ["0x6627e8d5", "0xe169c58d", "0xbc57ac4c", "0x9b00dbd8"]
 
 
-@pytest.mark.parametrize("chain", [0, 1, 2, 3, 4, 7, 13])
-def test_site_normals_fp64(chain):
+LANE_CHAINS = [(4, 0), (4, 1), (4, 2), (4, 3), (4, 4), (4, 7), (4, 13), (2, 0), (2, 1), (1, 0)]
+
+
+@pytest.mark.parametrize("lanes,chain", LANE_CHAINS)
+def test_site_normals_fp64(lanes, chain):
     n = 1 << 17
-    got = g.site_normals(99, 5, 3, chain, n, g.FP64)
-    want = oracle.site_normals(99, n, 5, 3, chain)
+    got = g.site_normals(99, 5, 3, chain, n, g.FP64, lanes=lanes)
+    want = oracle.site_normals(99, n, 5, 3, chain, lanes)
     assert np.max(np.abs(got - want) / np.maximum(np.abs(want), 1.0)) < 1e-14
 
 
-@pytest.mark.parametrize("chain", [0, 1, 2, 3, 5])
-def test_site_normals_fp32(chain):
+@pytest.mark.parametrize("lanes,chain", LANE_CHAINS[:5] + LANE_CHAINS[-3:])
+def test_site_normals_fp32(lanes, chain):
     n = 1 << 20
-    got = g.site_normals(7, 11, 0, chain, n, g.FP32).astype(np.float64)
-    want = oracle.site_normals(7, n, 11, 0, chain)
+    got = g.site_normals(7, 11, 0, chain, n, g.FP32, lanes=lanes).astype(np.float64)
+    want = oracle.site_normals(7, n, 11, 0, chain, lanes)
     # radius and angle each carry a few single-precision ulps; no tail loses relative precision
     assert np.max(np.abs(got - want) / np.maximum(np.abs(want), 1.0)) < 3e-6
 

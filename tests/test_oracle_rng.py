@@ -78,8 +78,9 @@ def test_box_muller_definition_one_block():
     np.testing.assert_allclose(oracle.normals4(w), want, rtol=1e-14, atol=1e-15)
 
 
-def test_site_normals_distribution():
-    z = oracle.site_normals(seed=5, n=400_000, sweep=3, stream=1, chain=0)
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_site_normals_distribution(lanes):
+    z = oracle.site_normals(seed=5, n=400_000, sweep=3, stream=1, chain=0, lanes=lanes)
     assert abs(z.mean()) < 5 / np.sqrt(len(z))
     assert abs(z.var() - 1.0) < 5 * np.sqrt(2.0 / len(z))
     assert abs(stats.kurtosis(z)) < 0.05
@@ -90,7 +91,7 @@ def test_site_normals_chains_independent():
     # Chains 0..3 share one Philox block (cos/sin of two Box-Muller pairs): check they are
     # uncorrelated and each standard normal; chain 4 starts a new block.
     n = 200_000
-    zs = np.stack([oracle.site_normals(9, n, 0, 2, c) for c in range(5)])
+    zs = np.stack([oracle.site_normals(9, n, 0, 2, c, 4) for c in range(5)])
     cc = np.corrcoef(zs)
     assert np.max(np.abs(cc - np.eye(5))) < 5 / np.sqrt(n)
     for c in range(5):
@@ -120,3 +121,26 @@ def test_gamma_counters_and_attempts():
     # the rate only rescales: same counters, rate 4 -> a / 4 exactly
     a4, _ = oracle.gamma_draw(5.0, 4.0, 1, 0, 0, 1, 0)
     assert a4 == pytest.approx(a / 4.0, rel=1e-15)
+
+
+def test_lanes_for_chain_counts():
+    assert [oracle.lanes_for(c) for c in (1, 2, 3, 4, 5, 8, 64)] == [1, 2, 4, 4, 4, 4, 4]
+
+
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_site_normals_grouped_layout(lanes):
+    # With fewer than four chains one Philox block serves G = 4 / lanes consecutive sites:
+    # block (site // G, sweep, stream, chain // 4), normal (site % G) * lanes + chain % lanes.
+    G = 4 // lanes
+    n = 4000
+    for chain in range(lanes):
+        z = oracle.site_normals(21, n, 7, 5, chain, lanes)
+        blk = oracle.philox_fill(21, 7, 5, 0, n // G)
+        want = np.array([oracle.normals4(blk[i // G])[(i % G) * lanes + chain] for i in range(n)])
+        assert np.array_equal(z, want)
+    # every normal of a block is used exactly once, so the draws are independent standard normals
+    zs = np.stack([oracle.site_normals(3, 200_000, 0, 0, c, lanes) for c in range(lanes)])
+    for c in range(lanes):
+        assert stats.kstest(zs[c], "norm").pvalue > 1e-4
+        a, b = zs[c][0::2], zs[c][1::2]
+        assert abs(np.corrcoef(a, b)[0, 1]) < 5 / np.sqrt(len(a))

@@ -71,7 +71,7 @@ def test_one_sweep_equals_dense_conditionals(name, make, prior, rho, weighted):
             new = {}
             for i in idx:
                 cond_mean = (b[i] - (Qp[i] @ x - Qp[i, i] * x[i])) / Qp[i, i]
-                z = oracle.site_normal(seed, int(i), sweep, stream, c)
+                z = oracle.site_normal(seed, int(i), sweep, stream, c, oracle.lanes_for(2))
                 new[i] = cond_mean + z / math.sqrt(Qp[i, i])
             for i, v in new.items():
                 x[i] = v
@@ -87,7 +87,7 @@ def test_tau_zero_gives_independent_normals():
     st = oracle.initial_state(y, 3, tau0=0.0, sigma2_0=[0.25, 1.0, 4.0])
     oracle.run((rp, ci), colors, y, st, seed=8, nsweeps=1, start_sweep=2, fix_hyper=True)
     for c in range(3):
-        z = oracle.site_normals(8, n, 2, 0, c)
+        z = oracle.site_normals(8, n, 2, 0, c, oracle.lanes_for(3))
         np.testing.assert_allclose(st.x[c], y + math.sqrt(st.sigma2[c]) * z, rtol=1e-14, atol=1e-14)
 
 
@@ -126,15 +126,18 @@ def _philox_py(ctr, key):
     return c
 
 
-def _normal_py(seed, site, sweep, stream, chain):
-    w = _philox_py([site, sweep, stream, chain >> 2], [seed & 0xFFFFFFFF, seed >> 32])
-    pair = (w[0], w[1]) if (chain & 3) < 2 else (w[2], w[3])
+def _normal_py(seed, site, sweep, stream, chain, lanes):
+    G = 4 // lanes
+    w = _philox_py([site // G, sweep, stream, chain >> 2], [seed & 0xFFFFFFFF, seed >> 32])
+    idx = (site % G) * lanes + chain % lanes
+    pair = (w[0], w[1]) if idx < 2 else (w[2], w[3])
     ua, ub = [(v + 0.5) / 2**32 for v in pair]
     r = math.sqrt(-2 * math.log(ua))
-    return r * (math.cos(2 * math.pi * ub) if (chain & 1) == 0 else math.sin(2 * math.pi * ub))
+    return r * (math.cos(2 * math.pi * ub) if (idx & 1) == 0 else math.sin(2 * math.pi * ub))
 
 
-def test_single_site_sampler_in_colour_order_matches():
+@pytest.mark.parametrize("chains", [1, 2, 5])
+def test_single_site_sampler_in_colour_order_matches(chains):
     # The paper's single-site sampler (Sec. 3.1, variance form with tau^2 = 1/tau):
     #   mu_i = s2_i (y_i / sigma^2 + sum_j w_ij x_j / tau^2),  s2_i = tau^2 sigma^2 / (sigma^2 D_ii + tau^2),
     # visiting sites colour class by colour class, equals the chromatic sweep (Sec. 2.3, "single-site
@@ -144,20 +147,22 @@ def test_single_site_sampler_in_colour_order_matches():
     g = wl.rng(9)
     y = g.normal(0, 1, n)
     colors, k = oracle.color_graph(rp, ci, 21)
-    st = oracle.initial_state(y, 5, tau0=np.linspace(0.5, 3, 5), sigma2_0=np.linspace(0.2, 2, 5))
+    st = oracle.initial_state(y, chains, tau0=np.linspace(0.5, 3, 5)[:chains],
+                              sigma2_0=np.linspace(0.2, 2, 5)[:chains])
     x = st.x.copy()
     seed, T = 12345678901, 6
     oracle.run((rp, ci), colors, y, st, seed=seed, nsweeps=T, stream=4, fix_hyper=True,
                accumulate=False)
     deg = np.diff(rp)
-    for c in range(5):
+    lanes = 1 if chains == 1 else (2 if chains == 2 else 4)
+    for c in range(chains):
         tau2, sig2 = 1.0 / np.linspace(0.5, 3, 5)[c], np.linspace(0.2, 2, 5)[c]
         for t in range(T):
             for col in range(k):
                 for i in np.flatnonzero(colors == col):
                     s2i = tau2 * sig2 / (sig2 * deg[i] + tau2)
                     mu = s2i * (y[i] / sig2 + x[c, ci[rp[i]:rp[i + 1]]].sum() / tau2)
-                    x[c, i] = mu + math.sqrt(s2i) * _normal_py(seed, int(i), t, 4, c)
+                    x[c, i] = mu + math.sqrt(s2i) * _normal_py(seed, int(i), t, 4, c, lanes)
     np.testing.assert_allclose(st.x, x, rtol=1e-12, atol=1e-12)
 
 
