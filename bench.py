@@ -133,6 +133,37 @@ def stage_algorithmic_bytes(spec, stage_name, colour, colourings, S=4):
     return total
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel of
+# a workload, from one ncu capture (cold L2: ncu flushes caches before the launch), with the
+# SHA-256 of the kernel's sources at capture time.  Reported only while the sources are unchanged.
+MEASURED_TRAFFIC = {
+    "image1024": dict(kernel="lattice_fused_fast<float, 1, 1024, 1>", bytes=8_423_680,
+                      sources={"lattice_fused.cu": "b6111251199cbb41ea739f5c7090a09820f357d19c462fb06c5d1b7ab966e84f",
+                               "gmrf_device.cuh": "cc325fbeac4dd2dba381352aa93b6e47b62b3124fa03fd20bb1a0876904aefdc"}),
+    "volume256": dict(kernel="colour_step_kernel<float, 4, 2>", bytes=313_337_088 + 234_184_448,
+                      sources={"sweep_kernels.cu": "565e05f93e74b79094a34aa8c3fb8d8122291d3bcfb201348b83ee20246286a1",
+                               "gmrf_device.cuh": "cc325fbeac4dd2dba381352aa93b6e47b62b3124fa03fd20bb1a0876904aefdc"}),
+}
+
+
+def measured_traffic(workload: str):
+    """DRAM bytes per launch of the workload's dominant kernel, or None if not captured for the
+    current kernel sources."""
+    import hashlib
+
+    rec = MEASURED_TRAFFIC.get(workload)
+    if rec is None:
+        return None
+    for name, digest in rec["sources"].items():
+        path = os.path.join(ROOT, "paper_1702_05518_gb300", "csrc", name)
+        try:
+            if hashlib.sha256(open(path, "rb").read()).hexdigest() != digest:
+                return None
+        except OSError:
+            return None
+    return rec["bytes"]
+
+
 # ----------------------------------------------------------------------------------------------
 # Clocks
 # ----------------------------------------------------------------------------------------------
@@ -296,6 +327,28 @@ def run_reference(args):
     return 0
 
 
+def run_profile_case(args):
+    """A fixed launch sequence for a profiler: create, S sweeps launched stage by stage, fetch."""
+    import torch
+
+    from paper_1702_05518_gb300 import build as libbuild
+    from paper_1702_05518_gb300 import gmrf as g
+
+    torch.cuda.set_device(0)
+    if not os.path.exists(g.LIB_PATH):
+        libbuild.build()
+    spec = workload_spec(args.workload)
+    prior = g.PRIOR_PCAR if spec["prior"] == "pcar" else g.PRIOR_ICAR
+    with g.Sampler(spec["fields"], precision=g.FP32, chains=spec["chains"], seed=spec["seed"], prior=prior,
+                   rho=spec["rho"], burn_in=spec["burn_in"], graph_sweeps=0) as s:
+        s.sweep(args.profile_sweeps)
+        x = s.fetch_x(0, 0)
+        info = s.info()
+    print(json.dumps({"profile_case": spec["name"], "sweeps": args.profile_sweeps,
+                      "launches_per_sweep": info["launches_per_sweep"], "finite": bool(np.isfinite(x).all())}))
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -402,7 +455,7 @@ def run_ours(args):
     hbm = hbm or 6800.0
     achieved = algo_bytes / (kernel_us * 1e-6) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_source": peak_note,
+                "frac": achieved / hbm, "traffic": measured_traffic(args.workload), "peak_source": peak_note,
                 "kernel": dom[1], "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": kernel_us,
                 "stages_us": {f"{st}:{name}": round(us, 3) for st, name, us in stages}}
 
@@ -453,9 +506,14 @@ def main(argv=None):
     ap.add_argument("--workload", default="image1024",
                     choices=["image1024", "image64", "volume256", "delaunay16k", "batched"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--profile-sweeps", type=int, default=0, metavar="S",
+                    help="untimed: run S sweeps of the workload with one launch per stage (no graphs) "
+                         "and exit; a short, fixed launch sequence for a profiler to capture")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_sweeps > 0:
+        return run_profile_case(args)
     return run_ours(args)
 
 
