@@ -158,6 +158,36 @@ gmrf_status gmrf_color_graph(int32_t n, const int32_t *row_ptr, const int32_t *c
                              const uint32_t *priorities, uint64_t seed, int32_t *colors,
                              int32_t *num_colors);
 
+/* Vertex capacity of the static scratch of gmrf_color_graph_noalloc (5 MiB of device memory). */
+#define GMRF_NOALLOC_MAX_VERTICES 1048576
+
+/*
+ * The colouring of gmrf_color_graph (same rounds, same result) for a CSR graph already on the
+ * device, allocating no memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot let a library allocate device memory -- a process whose device memory
+ * is held by its own caching allocator (a cudaMalloc inside the call could fail although the
+ * pool has room) or a serving loop that must not take the device-wide synchronisation that
+ * cudaFree implies.
+ *   n: vertices, 1 <= n <= GMRF_NOALLOC_MAX_VERTICES (larger n: GMRF_E_INVALID, nothing runs).
+ *   nnz: entries of col_idx.  row_ptr[n+1], col_idx[nnz]: device, caller-owned, read only.
+ *   priorities: device [n] or NULL for Philox priorities of `seed`.
+ *   colors: device out [n], 0-based, caller-owned; num_colors: host out.
+ *   cuda_stream: a cudaStream_t (NULL: legacy default stream); the call synchronises it.
+ * Scratch: one fixed file-scope device array (priorities, round flags, counters; 5 MiB).  The
+ * first call on each device, with that device current, looks up the array's address
+ * (cudaGetSymbolAddress) and keeps it; make that first call before any stream capture.  Each
+ * call clears the counters and the check flag it needs at its start.  Concurrent or
+ * overlapping calls on one device share the array and race: serialise them.
+ * The structure (row_ptr[0] == 0, non-decreasing, row_ptr[n] == nnz, columns in [0, n), no
+ * self-loops) is checked on the device before colouring: GMRF_E_INVALID if it fails.  Symmetry
+ * is the caller's duty (not checked; a non-symmetric graph still terminates in bounds).
+ * Errors: GMRF_E_INVALID, GMRF_E_UNSUPPORTED (device ordinal > 63), GMRF_E_CUDA.
+ */
+gmrf_status gmrf_color_graph_noalloc(int32_t n, int64_t nnz, const int32_t *row_ptr,
+                                     const int32_t *col_idx, const uint32_t *priorities,
+                                     uint64_t seed, int32_t *colors, int32_t *num_colors,
+                                     void *cuda_stream);
+
 /*
  * Create a sampler over `nfields` independent fields (each with `opts.chains` chains and its
  * own tau, sigma^2 per chain), copy y / x0 / graphs to the device in the colour-split layout

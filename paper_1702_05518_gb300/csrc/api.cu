@@ -46,6 +46,12 @@ struct HostField {
 
 }  // namespace
 
+int gmrf::record_error(int st, const char *msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
 struct gmrf_sampler {
     int device = 0;
     cudaStream_t stream = nullptr;

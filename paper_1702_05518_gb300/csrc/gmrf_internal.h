@@ -132,6 +132,9 @@ cudaError_t prepare_lattice_fused(int precision, int V, int kind, size_t smem);
 cudaError_t launch_lattice_fused(int precision, int V, int kind, const FusedArgs &a, size_t smem,
                                  cudaStream_t stream);
 
+// Records msg as the calling thread's gmrf_last_error() text and returns st (api.cu).
+int record_error(int st, const char *msg);
+
 // Jones-Plassmann colouring and colour-permuted CSR layout (csr_build.cu).
 struct CsrBuild {
     int32_t n;

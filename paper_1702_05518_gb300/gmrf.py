@@ -22,7 +22,7 @@ FP32, FP64 = 0, 1
 ALGO_CHROMATIC, ALGO_PLAIN = 0, 1
 FLAG_PER_COLOUR = 1
 
-EXPORTED = ["gmrf_color_graph", "gmrf_sampler_create", "gmrf_sampler_destroy", "gmrf_sweep",
+EXPORTED = ["gmrf_color_graph", "gmrf_color_graph_noalloc", "gmrf_sampler_create", "gmrf_sampler_destroy", "gmrf_sweep",
             "gmrf_hyper_update", "gmrf_fetch_samples", "gmrf_field_colors", "gmrf_sampler_info",
             "gmrf_sampler_reset", "gmrf_launch_stage",
             "gmrf_validate_csr", "gmrf_philox_words", "gmrf_site_normals", "gmrf_last_error",
@@ -89,6 +89,9 @@ def lib() -> ctypes.CDLL:
             vp = ctypes.c_void_p
             L.gmrf_color_graph.argtypes = [ctypes.c_int32, i32p, i32p, u32p, ctypes.c_uint64, i32p, i32p]
             L.gmrf_color_graph.restype = st
+            L.gmrf_color_graph_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int64, vp, vp, vp, ctypes.c_uint64,
+                                                   vp, i32p, vp]
+            L.gmrf_color_graph_noalloc.restype = st
             L.gmrf_sampler_create.argtypes = [P(vp), P(FieldDesc), ctypes.c_int32, P(Model), P(Opts), vp]
             L.gmrf_sampler_create.restype = st
             L.gmrf_sampler_destroy.argtypes = [vp]
@@ -174,6 +177,19 @@ def color_graph(row_ptr, col_idx, seed=0, priorities=None):
                                   _p(pr, ctypes.c_uint32), int(seed), _p(colors, ctypes.c_int32),
                                   ctypes.byref(k)))
     return colors, k.value
+
+
+def color_graph_noalloc(row_ptr, col_idx, colors, priorities=None, seed=0):
+    """gmrf_color_graph_noalloc on device tensors (int32 row_ptr [n+1], col_idx [nnz], colors
+    [n] out; optional int32/uint32 priorities [n]) on the current stream -> number of colours."""
+    n = int(row_ptr.numel()) - 1
+    k = ctypes.c_int32(0)
+    pr = None if priorities is None else ctypes.c_void_p(priorities.data_ptr())
+    _check(lib().gmrf_color_graph_noalloc(n, int(col_idx.numel()), ctypes.c_void_p(row_ptr.data_ptr()),
+                                          ctypes.c_void_p(col_idx.data_ptr()), pr, int(seed),
+                                          ctypes.c_void_p(colors.data_ptr()), ctypes.byref(k),
+                                          current_stream()))
+    return k.value
 
 
 def philox_words(seed, c1, c2, c3, count):
