@@ -120,31 +120,79 @@ __device__ __forceinline__ float u01_f32(uint32_t w)
     return fmaf(static_cast<float>(w), 0x1p-32f, 0x1p-33f);
 }
 
+// Hardware approximations (PTX .approx, flush-to-zero): reciprocal and reciprocal square root
+// within 1 ulp, base-2 logarithm within 2^-22 absolute.  Every argument here is a normal float.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // -2 ln u in single precision with small relative error for every word, without branches:
-// for u < 3/4 the logarithm of u itself (|ln u| > 0.28, so the absolute error of the fast log
-// is a relative error below 1.3e-6); for u >= 3/4, with v = 1 - u formed exactly from the
-// complemented word, ln(1 - v) = -2 atanh(t), t = v / (2 - v) <= 1/7, by the atanh series
+// for u < 3/4 from the base-2 logarithm of u itself (|ln u| > 0.28, so its absolute error is a
+// relative error below 1e-6); for u >= 3/4, with v = 1 - u formed from the complemented word,
+// ln(1 - v) = -2 atanh(t), t = v / (2 - v) <= 1/7, by the atanh series
 // t (1 + t^2/3 + t^4/5 + t^6/7 + t^8/9) (truncation below 4e-10 relative), so radii near zero
 // keep their precision.
 __device__ __forceinline__ float neg2log_u_f32(uint32_t w)
 {
-    const float l1 = __logf(u01_f32(w));
+    const float l1 = lg2_approx(u01_f32(w)) * -1.3862943611198906f;  // -2 ln 2 log2(u)
     const float v = u01_f32(~w);
-    const float t = v * __frcp_rn(2.0f - v);
+    const float t = v * rcp_approx(2.0f - v);
     const float t2 = t * t;
     const float p = fmaf(fmaf(fmaf(fmaf(1.0f / 9.0f, t2, 1.0f / 7.0f), t2, 1.0f / 5.0f), t2, 1.0f / 3.0f), t2, 1.0f);
-    const float l2 = -2.0f * t * p;
-    return -2.0f * (w >= 0xC0000000u ? l2 : l1);
+    const float l2 = 4.0f * t * p;
+    return w >= 0xC0000000u ? l2 : l1;
 }
 
+// sin and cos of the angle pi d / 2, |d| <= 1/2 (a quarter turn centred at 0), by their Taylor
+// series in d: coefficients (-1)^j (pi/2)^k / k!, to d^9 for the sine and d^8 for the cosine;
+// the truncation error is below 3e-8 on the interval.
+__device__ __forceinline__ void sincos_quarter_turn(float d, float &s, float &c)
+{
+    const float d2 = d * d;
+    const float ps = fmaf(fmaf(fmaf(fmaf(1.6044118478735982e-4f, d2, -4.6817541353186881e-3f), d2,
+                                    7.9692626246167046e-2f), d2, -6.4596409750624625e-1f), d2, 1.5707963267948966f);
+    s = d * ps;
+    c = fmaf(fmaf(fmaf(fmaf(9.1926027483942659e-4f, d2, -2.0863480763352961e-2f), d2, 2.5366950790104802e-1f), d2,
+                   -1.2337005501361697f), d2, 1.0f);
+}
+
+// Box-Muller pair in single precision: r = sqrt(-2 ln u_a), angle 2 pi u_b.  The angle is reduced
+// exactly on the word: adding 2^29 shifts u_b by 1/8 turn, the top two bits of the sum give the
+// quadrant q and the next 23 bits (bucket midpoint, error below 1e-7 rad) the offset d in
+// [-1/2, 1/2), so that 2 pi u_b = q pi/2 + pi d/2; (cos, sin) of pi d/2 is then turned by q
+// quarter turns.
 __device__ __forceinline__ void box_muller_f32(uint32_t wa, uint32_t wb, float &zc, float &zs)
 {
-    const float q = neg2log_u_f32(wa);  // > 0 for every word
-    const float r = q * rsqrtf(q);
+    const float q2 = neg2log_u_f32(wa);  // > 0 for every word
+    const float r = q2 * rsqrt_approx(q2);
+    const uint32_t ws = wb + 0x20000000u;
+    const uint32_t quad = ws >> 30;
+    const float d = __uint_as_float(0x3F800000u | ((ws >> 7) & 0x7FFFFFu)) - 1.5f + 0x1p-24f;
     float s, c;
-    sincospif(2.0f * u01_f32(wb), &s, &c);
-    zc = r * c;
-    zs = r * s;
+    sincos_quarter_turn(d, s, c);
+    float cq = (quad & 1u) ? -s : c;
+    float sq = (quad & 1u) ? c : s;
+    if (quad & 2u) {
+        cq = -cq;
+        sq = -sq;
+    }
+    zc = r * cq;
+    zs = r * sq;
 }
 
 __device__ __forceinline__ void box_muller_f64(uint32_t wa, uint32_t wb, double &zc, double &zs)

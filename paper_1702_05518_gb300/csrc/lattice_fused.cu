@@ -24,8 +24,9 @@ namespace {
 
 template <typename T> struct FArith;
 template <> struct FArith<float> {
-    __device__ __forceinline__ static float rcp(float x) { return __frcp_rn(x); }
-    __device__ __forceinline__ static float rsq(float x) { return rsqrtf(x); }
+    // 1/P and 1/sqrt(P) within 1 ulp (P is a normal float): well inside the FP32 parity budget.
+    __device__ __forceinline__ static float rcp(float x) { return rcp_approx(x); }
+    __device__ __forceinline__ static float rsq(float x) { return rsqrt_approx(x); }
 };
 template <> struct FArith<double> {
     __device__ __forceinline__ static double rcp(double x) { return 1.0 / x; }

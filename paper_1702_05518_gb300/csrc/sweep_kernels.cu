@@ -26,9 +26,9 @@ namespace {
 
 template <typename T> struct Arith;
 template <> struct Arith<float> {
-    // 1/P and 1/sqrt(P) within 2 ulp: well inside the FP32 parity budget.
-    __device__ __forceinline__ static float rcp(float x) { return __frcp_rn(x); }
-    __device__ __forceinline__ static float rsq(float x) { return rsqrtf(x); }
+    // 1/P and 1/sqrt(P) within 1 ulp (P is a normal float): well inside the FP32 parity budget.
+    __device__ __forceinline__ static float rcp(float x) { return rcp_approx(x); }
+    __device__ __forceinline__ static float rsq(float x) { return rsqrt_approx(x); }
 };
 template <> struct Arith<double> {
     __device__ __forceinline__ static double rcp(double x) { return 1.0 / x; }
@@ -317,7 +317,7 @@ __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, Si
 }
 
 template <typename T, int V, int KIND>
-__global__ void __launch_bounds__(kBlock) colour_step_kernel(const StepArgs a)
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_kernel(const StepArgs a)
 {
     const Tile t = a.tiles[blockIdx.x];
     const FieldDev f = a.fields[t.field];
