@@ -31,7 +31,7 @@ _lock = threading.Lock()
 _lib = None
 
 LAT2D_4, LAT2D_8, LAT3D_6 = 0, 1, 2
-TAG_X, TAG_TAU, TAG_SIG, TAG_PRIO = 0, 1, 2, 3
+TAG_X, TAG_TAU, TAG_SIG, TAG_PRIO, TAG_BETA = 0, 1, 2, 3, 7
 
 
 def build(force: bool = False) -> str:
@@ -50,7 +50,7 @@ class _Model(ctypes.Structure):
     _fields_ = [("prior_proper", ctypes.c_int32), ("rho", ctypes.c_double),
                 ("a_tau", ctypes.c_double), ("b_tau", ctypes.c_double),
                 ("a_sig", ctypes.c_double), ("b_sig", ctypes.c_double),
-                ("fix_hyper", ctypes.c_int32)]
+                ("fix_hyper", ctypes.c_int32), ("intercept", ctypes.c_int32)]
 
 
 class _RunOpts(ctypes.Structure):
@@ -97,8 +97,11 @@ def _load():
             lib.ora_quadform.restype = ctypes.c_double
             lib.ora_run.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p, ctypes.c_int32, f64p,
                                     ctypes.c_int32, P(_Model), P(_RunOpts), f64p, f64p, f64p,
-                                    f64p, f64p, f64p, f64p, i64p, f64p]
+                                    f64p, f64p, f64p, f64p, f64p, f64p, i64p, f64p]
             lib.ora_run.restype = ctypes.c_int32
+            lib.ora_beta_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                            ctypes.c_uint32, ctypes.c_uint32]
+            lib.ora_beta_normal.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -175,6 +178,12 @@ def gamma_draw(shape, rate, seed, sweep, stream, tag, chain):
     return g, att.value
 
 
+def beta_normal(seed, sweep, stream, chain, tag=TAG_BETA):
+    """Standard normal of the intercept draw: Box-Muller cosine of words (w0, w1) of the Philox
+    block at counter (0, sweep, stream, (tag << 24) | chain)."""
+    return _load().ora_beta_normal(seed, sweep, stream, tag, chain)
+
+
 # --------------------------------------------------------------------------------------------
 # Graphs and colourings
 # --------------------------------------------------------------------------------------------
@@ -246,28 +255,32 @@ def quadform(row_ptr, col_idx, x, rho=1.0, weights=None):
 # The sampler
 # --------------------------------------------------------------------------------------------
 class State:
-    """Chain state of one field: x [C, n], tau [C], sigma2 [C] and the Welford accumulators."""
+    """Chain state of one field: x [C, n], tau [C], sigma2 [C], the intercept beta0 [C] and the
+    Welford accumulators."""
 
-    def __init__(self, x, tau, sigma2, mean=None, m2=None, count=0):
+    def __init__(self, x, tau, sigma2, mean=None, m2=None, count=0, beta0=None):
         self.x = np.array(x, dtype=np.float64, order="C")
         C, n = self.x.shape
         self.tau = np.array(tau, dtype=np.float64).reshape(C).copy()
         self.sigma2 = np.array(sigma2, dtype=np.float64).reshape(C).copy()
+        self.beta0 = np.zeros(C) if beta0 is None else np.array(beta0, dtype=np.float64).reshape(C).copy()
         self.mean = np.zeros((C, n)) if mean is None else np.array(mean, dtype=np.float64)
         self.m2 = np.zeros((C, n)) if m2 is None else np.array(m2, dtype=np.float64)
         self.count = int(count)
 
     def copy(self):
-        return State(self.x, self.tau, self.sigma2, self.mean, self.m2, self.count)
+        return State(self.x, self.tau, self.sigma2, self.mean, self.m2, self.count, self.beta0)
 
 
 def run(graph, colors, y, state, *, seed, nsweeps, stream=0, start_sweep=0, prior="icar",
         rho=1.0, a_tau=1.0, b_tau=0.01, a_sig=1.0, b_sig=0.01, fix_hyper=False, burn_in=0,
-        thin=1, accumulate=True, record_x=False, weights=None):
-    """Run `nsweeps` chromatic Gibbs sweeps (Algorithm 1 + conjugate tau, sigma^2 draws) of
-    every chain in `state` (modified in place).  graph = (row_ptr, col_idx) in natural order.
+        thin=1, accumulate=True, record_x=False, weights=None, intercept=False):
+    """Run `nsweeps` chromatic Gibbs sweeps (Algorithm 1 + conjugate tau, sigma^2 draws, and with
+    `intercept` the flat-prior beta0 draw of Sec. 3.1) of every chain in `state` (modified in
+    place).  graph = (row_ptr, col_idx) in natural order.
 
-    Returns dict(tau_trace [C, T], sigma2_trace [C, T], fallbacks, xtrace [T, C, n] or None).
+    Returns dict(tau_trace [C, T], sigma2_trace [C, T], beta0_trace [C, T], fallbacks,
+    xtrace [T, C, n] or None).
     """
     lib = _load()
     rp, ci = _i32(graph[0]), _i32(graph[1])
@@ -279,31 +292,33 @@ def run(graph, colors, y, state, *, seed, nsweeps, stream=0, start_sweep=0, prio
     assert state.x.shape == (C, n) and yy.shape == (n,)
     w = None if weights is None else _f64(weights)
     model = _Model(1 if prior == "pcar" else 0, float(rho), float(a_tau), float(b_tau),
-                   float(a_sig), float(b_sig), 1 if fix_hyper else 0)
+                   float(a_sig), float(b_sig), 1 if fix_hyper else 0, 1 if intercept else 0)
     opts = _RunOpts(int(seed), int(stream), int(start_sweep), int(nsweeps), int(burn_in),
                     int(thin))
     tt = np.zeros((C, max(nsweeps, 1)))
     st = np.zeros((C, max(nsweeps, 1)))
+    bt = np.zeros((C, max(nsweeps, 1)))
     xt = np.zeros((max(nsweeps, 1), C, n)) if record_x else None
     cnt = ctypes.c_int64(state.count)
     fb = lib.ora_run(n, _ptr(rp, ctypes.c_int32), _ptr(ci, ctypes.c_int32),
                      _ptr(w, ctypes.c_double), _ptr(col, ctypes.c_int32), k,
                      _ptr(yy, ctypes.c_double), C, ctypes.byref(model), ctypes.byref(opts),
                      _ptr(state.x, ctypes.c_double), _ptr(state.tau, ctypes.c_double),
-                     _ptr(state.sigma2, ctypes.c_double), _ptr(tt, ctypes.c_double),
-                     _ptr(st, ctypes.c_double),
+                     _ptr(state.sigma2, ctypes.c_double), _ptr(state.beta0, ctypes.c_double),
+                     _ptr(tt, ctypes.c_double), _ptr(st, ctypes.c_double), _ptr(bt, ctypes.c_double),
                      _ptr(state.mean, ctypes.c_double) if accumulate else None,
                      _ptr(state.m2, ctypes.c_double) if accumulate else None,
                      ctypes.byref(cnt) if accumulate else None,
                      _ptr(xt, ctypes.c_double))
     if accumulate:
         state.count = cnt.value
-    return {"tau_trace": tt[:, :nsweeps], "sigma2_trace": st[:, :nsweeps], "fallbacks": fb,
+    return {"tau_trace": tt[:, :nsweeps], "sigma2_trace": st[:, :nsweeps],
+            "beta0_trace": bt[:, :nsweeps], "fallbacks": fb,
             "xtrace": xt[:nsweeps] if record_x else None}
 
 
-def initial_state(y, chains, tau0=1.0, sigma2_0=1.0, x0=None):
-    """x0 = y for every chain unless given ([C, n] or [n]); tau0, sigma2_0 scalars or [C]."""
+def initial_state(y, chains, tau0=1.0, sigma2_0=1.0, x0=None, beta0=0.0):
+    """x0 = y for every chain unless given ([C, n] or [n]); tau0, sigma2_0, beta0 scalars or [C]."""
     y = _f64(y)
     if x0 is None:
         x = np.tile(y, (chains, 1))
@@ -312,4 +327,5 @@ def initial_state(y, chains, tau0=1.0, sigma2_0=1.0, x0=None):
         x = np.tile(x0, (chains, 1)) if x0.ndim == 1 else x0.copy()
     tau = np.broadcast_to(np.asarray(tau0, dtype=np.float64), (chains,)).copy()
     sig = np.broadcast_to(np.asarray(sigma2_0, dtype=np.float64), (chains,)).copy()
-    return State(x, tau, sig)
+    b0 = np.broadcast_to(np.asarray(beta0, dtype=np.float64), (chains,)).copy()
+    return State(x, tau, sig, beta0=b0)

@@ -55,7 +55,8 @@ enum {
     ORA_TAG_X = 0,     /* field-site update normals          */
     ORA_TAG_TAU = 1,   /* Gamma draw of tau                  */
     ORA_TAG_SIG = 2,   /* Gamma draw of 1/sigma^2            */
-    ORA_TAG_PRIO = 3   /* colouring priorities               */
+    ORA_TAG_PRIO = 3,  /* colouring priorities               */
+    ORA_TAG_BETA = 7   /* normal of the intercept draw       */
 };
 
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
@@ -196,6 +197,19 @@ double ora_gamma_draw(double shape, double rate, uint64_t seed, uint32_t sweep, 
     if (attempts_out)
         *attempts_out = -1;
     return d / rate;
+}
+
+/* Standard normal of the intercept draw after sweep `sweep`: the cosine normal of Box-Muller on
+ * words (w0, w1) of the Philox block at counter (0, sweep, stream, (tag << 24) | chain). */
+double ora_beta_normal(uint64_t seed, uint32_t sweep, uint32_t stream, uint32_t tag, uint32_t chain)
+{
+    uint32_t ctr[4] = {0u, sweep, stream, (tag << 24) | chain};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t w[4];
+    double z[4];
+    ora_philox4x32_10(ctr, key, w);
+    ora_normals4(w, z);
+    return z[0];
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -363,6 +377,7 @@ typedef struct {
     double a_tau, b_tau;   /* tau ~ Gamma(a_tau, rate b_tau)                             */
     double a_sig, b_sig;   /* 1/sigma^2 ~ Gamma(a_sig, rate b_sig)                       */
     int32_t fix_hyper;     /* 1: tau and sigma^2 stay at their initial values             */
+    int32_t intercept;     /* 1: y = beta0 1 + x + noise, flat prior on beta0 (Sec. 3.1)  */
 } ora_model;
 
 typedef struct {
@@ -378,7 +393,9 @@ typedef struct {
  * Run `nsweeps` sweeps of C independent chains on one field.
  *   x[c*n + i]             in: state before the call, out: state after it (natural order)
  *   tau[c], sig2[c]        in/out: current tau (precision) and sigma^2 of chain c
- *   tau_trace/sig2_trace   out: [c*nsweeps + t], value after sweep t of this call (may be NULL)
+ *   beta0[c]               in/out: intercept of chain c (read only when model->intercept)
+ *   tau_trace/sig2_trace/beta0_trace
+ *                          out: [c*nsweeps + t], value after sweep t of this call (may be NULL)
  *   mean, m2, acc_count    in/out Welford accumulators [c*n + i] and the count of accumulated
  *                          sweeps (shared by all chains); NULL disables accumulation
  *   xtrace                 out: [(t*C + c)*n + i] state after every sweep (may be NULL)
@@ -387,8 +404,8 @@ typedef struct {
 int32_t ora_run(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const double *weights,
                 const int32_t *colors, int32_t ncolors, const double *y, int32_t C,
                 const ora_model *model, const ora_run_opts *opts, double *x, double *tau,
-                double *sig2, double *tau_trace, double *sig2_trace, double *mean, double *m2,
-                int64_t *acc_count, double *xtrace)
+                double *sig2, double *beta0, double *tau_trace, double *sig2_trace,
+                double *beta0_trace, double *mean, double *m2, int64_t *acc_count, double *xtrace)
 {
     double rho = model->prior_proper ? model->rho : 1.0;
     double *deg = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -405,8 +422,10 @@ int32_t ora_run(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const
         for (int32_t c = 0; c < C; ++c) {
             double *xc = x + (int64_t)c * n;
             double prec_noise = 1.0 / sig2[c];
+            double b0 = model->intercept ? beta0[c] : 0.0;
             /* Algorithm 1: colour classes in order, every site of the class from its local
-             * characteristics given the newest values of the other classes. */
+             * characteristics given the newest values of the other classes (Sec. 3.1: the
+             * observations enter through b = (y - beta0 1) / sigma^2). */
             for (int32_t col = 0; col < ncolors; ++col)
                 for (int32_t i = 0; i < n; ++i) {
                     if (colors[i] != col) continue;
@@ -414,14 +433,23 @@ int32_t ora_run(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const
                     for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
                         s += (weights ? weights[e] : 1.0) * xc[col_idx[e]];
                     double P = tau[c] * deg[i] + prec_noise;
-                    double m = (tau[c] * rho * s + y[i] * prec_noise) / P;
+                    double m = (tau[c] * rho * s + (y[i] - b0) * prec_noise) / P;
                     double z = ora_site_normal(opts->seed, (uint32_t)i, sweep, opts->stream, (uint32_t)c, lanes);
                     xc[i] = m + z / sqrt(P);
                 }
+            /* Intercept (Sec. 3.1, flat prior): beta0 | y, x, sigma^2 ~ N(1'(y - x) / n, sigma^2 / n),
+             * drawn before sigma^2, whose conditional then uses the new beta0. */
+            if (model->intercept) {
+                double A = 0.0;
+                for (int32_t i = 0; i < n; ++i) A += y[i] - xc[i];
+                double zb = ora_beta_normal(opts->seed, sweep, opts->stream, ORA_TAG_BETA, (uint32_t)c);
+                b0 = A / n + sqrt(sig2[c] / n) * zb;
+                beta0[c] = b0;
+            }
             if (!model->fix_hyper) {
                 double S = ora_quadform(n, row_ptr, col_idx, weights, rho, xc);
                 double R = 0.0;
-                for (int32_t i = 0; i < n; ++i) R += (y[i] - xc[i]) * (y[i] - xc[i]);
+                for (int32_t i = 0; i < n; ++i) R += (y[i] - b0 - xc[i]) * (y[i] - b0 - xc[i]);
                 int32_t att;
                 tau[c] = ora_gamma_draw(model->a_tau + 0.5 * rank, model->b_tau + 0.5 * S,
                                         opts->seed, sweep, opts->stream, ORA_TAG_TAU, (uint32_t)c, &att);
@@ -433,6 +461,7 @@ int32_t ora_run(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const
             }
             if (tau_trace) tau_trace[(int64_t)c * opts->nsweeps + t] = tau[c];
             if (sig2_trace) sig2_trace[(int64_t)c * opts->nsweeps + t] = sig2[c];
+            if (beta0_trace) beta0_trace[(int64_t)c * opts->nsweeps + t] = b0;
             if (xtrace) memcpy(xtrace + ((int64_t)t * C + c) * n, xc, sizeof(double) * (size_t)n);
         }
         if (mean && m2 && acc_count && (int64_t)sweep >= opts->burn_in &&

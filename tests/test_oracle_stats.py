@@ -105,3 +105,105 @@ def test_hyper_posterior_matches_block_gibbs(name, make, prior, rho):
         qc, qb = np.quantile(chrom, q, axis=0), np.quantile(block, q, axis=0)
         spread = chrom.std(0)
         assert np.all(np.abs(qc - qb) < 0.06 * spread + 5 * se), (q, qc, qb)
+
+
+# --------------------------------------------------------------------------------------------
+# Intercept (Sec. 3.1: y = beta0 1 + x + noise, flat prior on beta0)
+# --------------------------------------------------------------------------------------------
+def _joint_with_intercept(rp, ci, y, tau, sig2, rho):
+    """Precision and mean of (x, beta0) given tau, sigma^2: the likelihood adds
+    (x + beta0 1)'(x + beta0 1) / sigma^2 and the linear term y'(x + beta0 1) / sigma^2."""
+    n = len(rp) - 1
+    Wm, D = _dense(rp, ci)
+    Q = np.zeros((n + 1, n + 1))
+    Q[:n, :n] = tau * (D - rho * Wm) + np.eye(n) / sig2
+    Q[:n, n] = Q[n, :n] = 1.0 / sig2
+    Q[n, n] = n / sig2
+    h = np.concatenate([y / sig2, [y.sum() / sig2]])
+    cov = np.linalg.inv(Q)
+    return cov @ h, cov
+
+
+@pytest.mark.parametrize("name,make", [("path6", lambda: wl.path_graph(6)), ("grid3x4", lambda: wl.grid_graph(3, 4)),
+                                       ("k4e", wl.k4_minus_edge)])
+def test_intercept_fixed_hyper_stationary_law(name, make):
+    # Proper CAR, so the joint law of (x, beta0) is a proper Gaussian.
+    rp, ci = make()
+    n = len(rp) - 1
+    y = wl.rng(23).normal(2.0, 1.5, n)
+    tau, sig2, rho = 1.3, 0.7, 0.85
+    colors, _ = oracle.color_graph(rp, ci, 4)
+    st = oracle.initial_state(y, 1, tau0=tau, sigma2_0=sig2)
+    T = 120_000
+    out = oracle.run((rp, ci), colors, y, st, seed=37, nsweeps=T, prior="pcar", rho=rho, fix_hyper=True,
+                     accumulate=False, record_x=True, intercept=True)
+    z = np.concatenate([out["xtrace"][1000:, 0, :], out["beta0_trace"][0, 1000:, None]], 1)
+    mu, cov = _joint_with_intercept(rp, ci, y, tau, sig2, rho)
+    se = _batch_se(z)
+    assert np.all(np.abs(z.mean(0) - mu) < 5 * se + 1e-12), (z.mean(0), mu)
+    dev = z - mu
+    outer = dev[:, :, None] * dev[:, None, :]
+    assert np.all(np.abs(outer.mean(0) - cov) < 5 * _batch_se(outer) + 1e-12)
+
+
+def test_intercept_zero_data_shift_equivariance():
+    # Adding a constant c to y shifts the intercept chain by exactly c in law; with the same
+    # random numbers the chain of x is unchanged and beta0 moves by c up to rounding.
+    rp, ci = wl.grid_graph(4, 5, eight=True)
+    n = len(rp) - 1
+    y = wl.rng(3).normal(0, 1, n)
+    colors, _ = oracle.color_graph(rp, ci, 2)
+    runs = []
+    for c in (0.0, 7.5):
+        st = oracle.initial_state(y + c, 2, beta0=c, x0=y)
+        out = oracle.run((rp, ci), colors, y + c, st, seed=5, nsweeps=50, intercept=True, accumulate=False)
+        runs.append((st, out))
+    (s0, o0), (s1, o1) = runs
+    np.testing.assert_allclose(s1.x, s0.x, atol=1e-9)
+    np.testing.assert_allclose(o1["beta0_trace"] - 7.5, o0["beta0_trace"], atol=1e-9)
+    np.testing.assert_allclose(o1["sigma2_trace"], o0["sigma2_trace"], rtol=1e-9)
+    np.testing.assert_allclose(o1["tau_trace"], o0["tau_trace"], rtol=1e-9)
+
+
+def _block_gibbs_intercept(rp, ci, y, prior, rho, a_tau, b_tau, a_sig, b_sig, T, seed):
+    """Block Gibbs of Sec. 3.1 with the intercept: x | beta0, tau, sigma^2 by Cholesky of Q_p with
+    b = (y - beta0 1) / sigma^2, then beta0 | x, sigma^2 ~ N(mean(y - x), sigma^2 / n), then
+    tau^2 and sigma^2 from their inverse-gamma conditionals."""
+    n = len(rp) - 1
+    Wm, D = _dense(rp, ci)
+    R = D - rho * Wm
+    r = n - oracle.components(rp, ci) if prior == "icar" else n
+    g = np.random.default_rng(seed)
+    tau, sig2, b0 = 1.0, 1.0, 0.0
+    out = np.zeros((T, 3))
+    for t in range(T):
+        L = np.linalg.cholesky(tau * R + np.eye(n) / sig2)
+        x = np.linalg.solve(L.T, np.linalg.solve(L, (y - b0) / sig2) + g.standard_normal(n))
+        b0 = np.mean(y - x) + np.sqrt(sig2 / n) * g.standard_normal()
+        tau = g.gamma(a_tau + r / 2, 1.0 / (b_tau + x @ R @ x / 2))
+        sig2 = 1.0 / g.gamma(a_sig + n / 2, 1.0 / (b_sig + np.sum((y - b0 - x) ** 2) / 2))
+        out[t] = tau, sig2, b0 + (np.mean(x) if prior == "icar" else 0.0)
+    return out
+
+
+@pytest.mark.parametrize("prior,rho", [("icar", 1.0), ("pcar", 0.8)])
+def test_intercept_posterior_matches_block_gibbs(prior, rho):
+    # Under the intrinsic prior only beta0 + mean(x) is identified; it is what is compared.
+    rp, ci = wl.grid_graph(3, 4)
+    n = len(rp) - 1
+    y = wl.rng(8).normal(1.5, 1.0, n)
+    hp = dict(a_tau=3.0, b_tau=2.0, a_sig=3.0, b_sig=1.0)
+    T = 60_000
+    colors, _ = oracle.color_graph(rp, ci, 1)
+    st = oracle.initial_state(y, 1)
+    out = oracle.run((rp, ci), colors, y, st, seed=4, nsweeps=T, prior=prior, rho=rho, accumulate=False,
+                     record_x=True, intercept=True, **hp)
+    loc = out["beta0_trace"][0] + (out["xtrace"][:, 0, :].mean(1) if prior == "icar" else 0.0)
+    chrom = np.stack([out["tau_trace"][0], out["sigma2_trace"][0], loc], 1)[2000:]
+    block = _block_gibbs_intercept(rp, ci, y, prior, rho, hp["a_tau"], hp["b_tau"], hp["a_sig"], hp["b_sig"],
+                                   30_000, 9)[1000:]
+    se = np.sqrt(_batch_se(chrom) ** 2 + _batch_se(block) ** 2)
+    assert np.all(np.abs(chrom.mean(0) - block.mean(0)) < 5 * se), (chrom.mean(0), block.mean(0), se)
+    for q in (0.1, 0.5, 0.9):
+        qc, qb = np.quantile(chrom, q, axis=0), np.quantile(block, q, axis=0)
+        assert np.all(np.abs(qc - qb) < 0.06 * chrom.std(0) + 5 * se), (q, qc, qb)
