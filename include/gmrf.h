@@ -31,8 +31,9 @@
  *     tau draw         counter (attempt, sweep, stream, (1 << 24) | chain)   [Marsaglia-Tsang]
  *     1/sigma^2 draw   counter (attempt, sweep, stream, (2 << 24) | chain)
  *     JP priority      word 0 of counter (vertex, 0, 0, 3 << 24)
- *     extra hyper draw counter (attempt, k, stream, ((5|6) << 24) | chain), k-th call of
- *                      gmrf_hyper_update
+ *     beta0 draw       Box-Muller cosine of (w0, w1) at counter (0, sweep, stream, (7 << 24) | chain)
+ *     extra hyper draw counter (attempt, k, stream, ((5|6) << 24) | chain) and, for beta0,
+ *                      (0, k, stream, (8 << 24) | chain), k-th call of gmrf_hyper_update
  * "site" is the natural (row-major for lattices) index, "stream" the field's stream id.
  *
  * Conventions.  Every call returns a gmrf_status and never aborts or prints.  Host pointers
@@ -100,6 +101,7 @@ typedef struct {
     const double *tau0;       /* [chains] initial tau or NULL: model.tau0                   */
     const double *sigma2_0;   /* [chains] initial sigma^2 or NULL: model.sigma2_0           */
     uint32_t stream_id;       /* Philox counter word 2 of this field's draws                */
+    const double *beta0;      /* [chains] initial intercept or NULL: model.beta0_0           */
 } gmrf_field_desc;
 
 typedef struct {
@@ -109,6 +111,10 @@ typedef struct {
     double a_sigma, b_sigma;  /* 1/sigma^2 ~ Gamma(a_sigma, rate b_sigma)                   */
     int32_t fix_hyper;        /* nonzero: tau, sigma^2 stay at their initial values         */
     double tau0, sigma2_0;    /* default initial values (tau0 >= 0, sigma2_0 > 0)            */
+    int32_t intercept;        /* 1: y = beta0 1 + x + noise with a flat prior on beta0 and  */
+                              /* beta0 | x, sigma^2 ~ N(1'(y - x)/n, sigma^2/n) drawn before */
+                              /* sigma^2 (Sec. 3.1); 0: no intercept                         */
+    double beta0_0;           /* default initial intercept (used when intercept = 1)        */
 } gmrf_model;
 
 typedef struct {
@@ -205,17 +211,17 @@ gmrf_status gmrf_sampler_create(gmrf_sampler **out, const gmrf_field_desc *field
 void gmrf_sampler_destroy(gmrf_sampler *s);
 
 /*
- * Enqueue `nsweeps` sweeps (Algorithm 1 over all colours of all fields, then the conjugate
- * tau, sigma^2 draws unless with_hyper == 0 or model.fix_hyper, then trace and accumulator
- * updates) on the sampler's stream.  Asynchronous: returns before the work finishes.
+ * Enqueue `nsweeps` sweeps (Algorithm 1 over all colours of all fields, then -- unless
+ * with_hyper == 0 -- the intercept draw (model.intercept) and the conjugate tau, sigma^2 draws
+ * (unless model.fix_hyper), then trace and accumulator updates) on the sampler's stream.  Asynchronous: returns before the work finishes.
  * Errors: GMRF_E_INVALID (nsweeps < 0), GMRF_E_STATE, GMRF_E_CUDA.
  */
 gmrf_status gmrf_sweep(gmrf_sampler *s, int32_t nsweeps, int32_t with_hyper);
 
 /*
- * One extra draw of tau and sigma^2 from their full conditionals (Sec. 3.1) given the current
- * x of every field and chain, without a sweep (counters: tags 5 and 6, k = number of earlier
- * calls).  Asynchronous.  Errors: GMRF_E_STATE, GMRF_E_CUDA.
+ * One extra draw of tau and sigma^2 (and beta0 first, with the intercept) from their full
+ * conditionals (Sec. 3.1) given the current x of every field and chain, without a sweep
+ * (counters: tags 5, 6 and 8, k = number of earlier calls).  Asynchronous.  Errors: GMRF_E_STATE, GMRF_E_CUDA.
  */
 gmrf_status gmrf_hyper_update(gmrf_sampler *s);
 
@@ -235,7 +241,17 @@ gmrf_status gmrf_fetch_samples(gmrf_sampler *s, int32_t field, int32_t chain, do
                                double *tau_now, double *sigma2_now);
 
 /*
- * Restart the run: state, tau and sigma^2 back to their values at creation, sweep counter back
+ * The intercept of one (field, chain) (model.intercept = 1): the current beta0 and the last
+ * min(trace_cap, available) values of its trace (the value after each sweep, oldest first),
+ * like the tau/sigma^2 traces of gmrf_fetch_samples.  Synchronises the stream.  Any output
+ * pointer may be NULL.  Errors: GMRF_E_INVALID (no intercept, bad indices), GMRF_E_STATE,
+ * GMRF_E_CUDA.
+ */
+gmrf_status gmrf_fetch_intercept(gmrf_sampler *s, int32_t field, int32_t chain, int64_t trace_cap,
+                                 double *beta0_trace, int64_t *n_trace, double *beta0_now);
+
+/*
+ * Restart the run: state, tau, sigma^2 and beta0 back to their values at creation, sweep counter back
  * to opts.start_sweep, accumulators cleared.  Asynchronous (device copies on the sampler's
  * stream); lets one sampler run many independent MCMC runs of the same data without re-upload.
  * Errors: GMRF_E_STATE, GMRF_E_CUDA.

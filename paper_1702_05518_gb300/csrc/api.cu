@@ -85,16 +85,16 @@ struct gmrf_sampler {
     void *x_alt = nullptr;  // second state buffer of fused fields (state of odd sweeps)
     int32_t *rp = nullptr, *ci = nullptr, *perm = nullptr, *perm_inv = nullptr, *coff = nullptr;
     void *w = nullptr, *deg = nullptr;
-    double *tau = nullptr, *sig2 = nullptr;
-    void *hyp = nullptr;
-    double2 *partials = nullptr;
-    double *trace_tau = nullptr, *trace_sig = nullptr;
+    double *tau = nullptr, *sig2 = nullptr, *beta = nullptr;
+    void *hyp = nullptr;        // [F * Cp][kHypStride] copies in precision T
+    Part3 *partials = nullptr;
+    double *trace_tau = nullptr, *trace_sig = nullptr, *trace_beta = nullptr;
     SweepCtl *ctl = nullptr;
-    double *gpre = nullptr;     // [gpre_batch][F * Cp][2] unit-rate Gamma variates of a batch
+    double *gpre = nullptr;     // [gpre_batch][F * Cp][4] precomputed variates of a batch
     int32_t gpre_batch = 0;     // sweeps per batch of precomputed variates
     double *staging = nullptr;  // [max_n] doubles for fetch
     void *x_init = nullptr;     // state at creation (for gmrf_sampler_reset)
-    double *tau_init = nullptr, *sig2_init = nullptr;
+    double *tau_init = nullptr, *sig2_init = nullptr, *beta_init = nullptr;
     void *hyp_init = nullptr;
     size_t x_bytes = 0, hyp_bytes = 0, nh = 0;
     // plain path
@@ -244,6 +244,8 @@ gmrf_status check_model(const gmrf_model *m)
         return fail(GMRF_E_INVALID, "model: Gamma rates b_tau, b_sigma must be > 0");
     if (!(finite(m->tau0) && m->tau0 >= 0) || !(finite(m->sigma2_0) && m->sigma2_0 > 0))
         return fail(GMRF_E_INVALID, "model: tau0 >= 0 and sigma2_0 > 0 required");
+    if (m->intercept != 0 && m->intercept != 1) return fail(GMRF_E_INVALID, "model.intercept must be 0 or 1");
+    if (!finite(m->beta0_0)) return fail(GMRF_E_INVALID, "model.beta0_0 must be finite");
     return GMRF_OK;
 }
 
@@ -305,6 +307,9 @@ gmrf_status check_field(const gmrf_field_desc &f, int idx, int chains, HostField
         for (int c = 0; c < chains; ++c)
             if (!(finite(f.sigma2_0[c]) && f.sigma2_0[c] > 0))
                 return fail(GMRF_E_INVALID, at + "sigma2_0 must be > 0");
+    if (f.beta0)
+        for (int c = 0; c < chains; ++c)
+            if (!finite(f.beta0[c])) return fail(GMRF_E_INVALID, at + "beta0 must be finite");
     return GMRF_OK;
 }
 
@@ -387,7 +392,7 @@ StepArgs step_args(gmrf_sampler *s, int colour, int kind, int update, int accumu
     return a;
 }
 
-HyperArgs hyper_args(gmrf_sampler *s, int draw, int end_of_sweep)
+HyperArgs hyper_args(gmrf_sampler *s, int draw, int draw_beta, int end_of_sweep)
 {
     HyperArgs h{};
     h.fields = s->fields_dev;
@@ -396,9 +401,11 @@ HyperArgs hyper_args(gmrf_sampler *s, int draw, int end_of_sweep)
     h.partials = s->partials;
     h.tau = s->tau;
     h.sig2 = s->sig2;
+    h.beta = s->beta;
     h.hyp = s->hyp;
     h.trace_tau = s->trace_tau;
     h.trace_sig = s->trace_sig;
+    h.trace_beta = s->model.intercept ? s->trace_beta : nullptr;
     h.trace_cap = s->opts.trace_capacity;
     h.ctl = s->ctl;
     h.key = philox_key(s->opts.seed);
@@ -407,6 +414,7 @@ HyperArgs hyper_args(gmrf_sampler *s, int draw, int end_of_sweep)
     h.a_sig = s->model.a_sigma;
     h.b_sig = s->model.b_sigma;
     h.draw = draw;
+    h.draw_beta = s->model.intercept ? draw_beta : 0;
     h.end_of_sweep = end_of_sweep;
     h.burn_in = s->opts.burn_in;
     h.thin = s->opts.thin;
@@ -426,6 +434,7 @@ cudaError_t launch_pre(gmrf_sampler *s, int count, cudaStream_t st)
     g.a_tau = s->model.a_tau;
     g.a_sig = s->model.a_sigma;
     g.count = count;
+    g.intercept = s->model.intercept ? 1 : 0;
     g.gpre = s->gpre;
     return launch_gamma_pre(g, st);
 }
@@ -463,10 +472,10 @@ FusedArgs fused_args(gmrf_sampler *s, int kind, int update, int accumulate)
     return a;
 }
 
-// One stage of a sweep (see gmrf_launch_stage); `draw` and `end_of_sweep` only matter for the
-// hyperparameter stage.
-cudaError_t enqueue_stage(gmrf_sampler *s, size_t k, int update, int accumulate, int draw, int end_of_sweep,
-                          cudaStream_t st)
+// One stage of a sweep (see gmrf_launch_stage); `draw`, `draw_beta` and `end_of_sweep` only
+// matter for the hyperparameter stage.
+cudaError_t enqueue_stage(gmrf_sampler *s, size_t k, int update, int accumulate, int draw, int draw_beta,
+                          int end_of_sweep, cudaStream_t st)
 {
     const gmrf_sampler::Stage &g = s->stages[k];
     if (g.type == 1)
@@ -474,15 +483,19 @@ cudaError_t enqueue_stage(gmrf_sampler *s, size_t k, int update, int accumulate,
                                     s->fsmem[g.kind], st);
     if (g.type == 0)
         return launch_colour_step(s->precision, s->V, g.kind, step_args(s, g.colour, g.kind, update, accumulate), st);
-    return launch_hyper(s->precision, hyper_args(s, draw, end_of_sweep), st);
+    return launch_hyper(s->precision, hyper_args(s, draw, draw_beta, end_of_sweep), st);
 }
 
-cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int draw, cudaStream_t st)
+// Sweeps with (with_hyper = 1) or without the draws of tau, sigma^2 (unless fixed) and beta0
+// (with the intercept).
+cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int with_hyper, cudaStream_t st)
 {
     cudaError_t e = cudaSuccess;
+    const int draw = (with_hyper && !s->model.fix_hyper) ? 1 : 0;
+    const int draw_beta = (with_hyper && s->model.intercept) ? 1 : 0;
     for (int k = 0; k < nsweeps && e == cudaSuccess; ++k) {
         // A batch of sweeps starts with the parallel draw of its unit-rate Gamma variates.
-        if (draw && s->gpre && k % s->gpre_batch == 0)
+        if ((draw || draw_beta) && s->gpre && k % s->gpre_batch == 0)
             e = launch_pre(s, std::min(s->gpre_batch, nsweeps - k), st);
         if (e != cudaSuccess) break;
         if (s->algorithm == GMRF_ALGO_PLAIN) {
@@ -493,20 +506,20 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int draw, cudaStream_t 
             continue;
         }
         for (size_t k = 0; k < s->stages.size() && e == cudaSuccess; ++k)
-            e = enqueue_stage(s, k, 1, 1, draw, 1, st);
+            e = enqueue_stage(s, k, 1, 1, draw, draw_beta, 1, st);
     }
     return e;
 }
 
-cudaError_t get_graph(gmrf_sampler *s, int draw, int which, int nsweeps, cudaGraphExec_t *out)
+cudaError_t get_graph(gmrf_sampler *s, int with_hyper, int which, int nsweeps, cudaGraphExec_t *out)
 {
-    if (s->exec[draw][which]) {
-        *out = s->exec[draw][which];
+    if (s->exec[with_hyper][which]) {
+        *out = s->exec[with_hyper][which];
         return cudaSuccess;
     }
     cudaError_t e = cudaStreamBeginCapture(s->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    cudaError_t le = enqueue_sweeps(s, nsweeps, draw, s->capture_stream);
+    cudaError_t le = enqueue_sweeps(s, nsweeps, with_hyper, s->capture_stream);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s->capture_stream, &g);
     if (le != cudaSuccess) {
@@ -514,10 +527,10 @@ cudaError_t get_graph(gmrf_sampler *s, int draw, int which, int nsweeps, cudaGra
         return le;
     }
     if (e != cudaSuccess) return e;
-    e = cudaGraphInstantiate(&s->exec[draw][which], g, 0);
+    e = cudaGraphInstantiate(&s->exec[with_hyper][which], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return e;
-    *out = s->exec[draw][which];
+    *out = s->exec[with_hyper][which];
     return cudaSuccess;
 }
 
@@ -901,8 +914,8 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     if (!fall.empty())
         CK(cudaMemcpyAsync(s->ftiles_dev, fall.data(), sizeof(TileXY) * fall.size(), cudaMemcpyHostToDevice,
                            s->stream));
-    CK(s->alloc_t(&s->partials, static_cast<size_t>(std::max(part, 1)) * Cp, sizeof(double2)));
-    CK(cudaMemsetAsync(s->partials, 0, static_cast<size_t>(std::max(part, 1)) * Cp * sizeof(double2), s->stream));
+    CK(s->alloc_t(&s->partials, static_cast<size_t>(std::max(part, 1)) * Cp, sizeof(Part3)));
+    CK(cudaMemsetAsync(s->partials, 0, static_cast<size_t>(std::max(part, 1)) * Cp * sizeof(Part3), s->stream));
     CK(cudaMemcpyAsync(s->fields_dev, s->fd.data(), sizeof(FieldDev) * s->nfields, cudaMemcpyHostToDevice, s->stream));
 
     // y and x0 into the colour-split layout.
@@ -917,44 +930,48 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
 
     // Hyperparameters and their precision-T copies.
     const size_t nh = static_cast<size_t>(s->nfields) * Cp;
-    std::vector<double> t0(nh), s0(nh);
-    std::vector<char> hypT(nh * 2 * T);
+    std::vector<double> t0(nh), s0(nh), b0(nh);
+    std::vector<char> hypT(nh * kHypStride * T, 0);
     for (int fi = 0; fi < s->nfields; ++fi)
         for (int c = 0; c < s->Cp; ++c) {
             const size_t k = static_cast<size_t>(fi) * Cp + c;
             const gmrf_field_desc &f = fields[fi];
             t0[k] = (f.tau0 && c < s->C) ? f.tau0[c] : s->model.tau0;
             s0[k] = (f.sigma2_0 && c < s->C) ? f.sigma2_0[c] : s->model.sigma2_0;
-            if (s->precision == GMRF_FP32) {
-                reinterpret_cast<float *>(hypT.data())[2 * k] = static_cast<float>(t0[k]);
-                reinterpret_cast<float *>(hypT.data())[2 * k + 1] = static_cast<float>(1.0 / s0[k]);
-            } else {
-                reinterpret_cast<double *>(hypT.data())[2 * k] = t0[k];
-                reinterpret_cast<double *>(hypT.data())[2 * k + 1] = 1.0 / s0[k];
+            b0[k] = !s->model.intercept ? 0.0 : ((f.beta0 && c < s->C) ? f.beta0[c] : s->model.beta0_0);
+            const double v[3] = {t0[k], 1.0 / s0[k], b0[k]};
+            for (int q = 0; q < 3; ++q) {
+                if (s->precision == GMRF_FP32) reinterpret_cast<float *>(hypT.data())[kHypStride * k + q] = static_cast<float>(v[q]);
+                else reinterpret_cast<double *>(hypT.data())[kHypStride * k + q] = v[q];
             }
         }
     CK(s->alloc_t(&s->tau, nh, sizeof(double)));
     CK(s->alloc_t(&s->sig2, nh, sizeof(double)));
+    CK(s->alloc_t(&s->beta, nh, sizeof(double)));
     s->gpre_batch = std::max(64, s->opts.graph_sweeps);
-    CK(s->alloc_t(&s->gpre, static_cast<size_t>(s->gpre_batch) * nh * 2, sizeof(double)));
-    CK(s->alloc(&s->hyp, nh * 2 * T));
+    CK(s->alloc_t(&s->gpre, static_cast<size_t>(s->gpre_batch) * nh * 4, sizeof(double)));
+    CK(s->alloc(&s->hyp, nh * kHypStride * T));
     CK(cudaMemcpyAsync(s->tau, t0.data(), nh * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(s->sig2, s0.data(), nh * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->beta, b0.data(), nh * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(s->hyp, hypT.data(), hypT.size(), cudaMemcpyHostToDevice, s->stream));
     CK(s->alloc_t(&s->trace_tau, nh * s->opts.trace_capacity, sizeof(double)));
     CK(s->alloc_t(&s->trace_sig, nh * s->opts.trace_capacity, sizeof(double)));
+    if (s->model.intercept) CK(s->alloc_t(&s->trace_beta, nh * s->opts.trace_capacity, sizeof(double)));
     // Initial state kept for gmrf_sampler_reset.
     s->nh = nh;
     s->x_bytes = static_cast<size_t>(slots) * Cp * T;
-    s->hyp_bytes = nh * 2 * T;
+    s->hyp_bytes = nh * kHypStride * T;
     CK(s->alloc(&s->x_init, s->x_bytes));
     CK(cudaMemcpyAsync(s->x_init, s->x, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
     if (s->x_alt) CK(cudaMemcpyAsync(s->x_alt, s->x, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
     CK(s->alloc_t(&s->tau_init, nh, sizeof(double)));
     CK(s->alloc_t(&s->sig2_init, nh, sizeof(double)));
+    CK(s->alloc_t(&s->beta_init, nh, sizeof(double)));
     CK(s->alloc(&s->hyp_init, s->hyp_bytes));
     CK(cudaMemcpyAsync(s->tau_init, s->tau, nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->sig2_init, s->sig2, nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->beta_init, s->beta, nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->hyp_init, s->hyp, s->hyp_bytes, cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return GMRF_OK;
@@ -1023,6 +1040,8 @@ gmrf_status gmrf_sampler_create(gmrf_sampler **out, const gmrf_field_desc *field
         if ((st = check_field(fields[i], i, opts->chains, hf[i])) != GMRF_OK) return st;
     if (opts->algorithm == GMRF_ALGO_PLAIN && (nfields != 1 || opts->precision != GMRF_FP64))
         return fail(GMRF_E_UNSUPPORTED, "the plain sweep takes exactly one field in FP64");
+    if (opts->algorithm == GMRF_ALGO_PLAIN && model->intercept)
+        return fail(GMRF_E_UNSUPPORTED, "the plain sweep has no intercept");
 
     gmrf_sampler *s = new gmrf_sampler();
     s->model = *model;
@@ -1081,18 +1100,18 @@ gmrf_status gmrf_sweep(gmrf_sampler *s, int32_t nsweeps, int32_t with_hyper)
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
     if (nsweeps < 0) return fail(GMRF_E_INVALID, "nsweeps must be >= 0");
-    const int draw = (with_hyper && !s->model.fix_hyper) ? 1 : 0;
+    const int wh = with_hyper ? 1 : 0;
     cudaError_t e = cudaSuccess;
     const int G = s->opts.graph_sweeps;
     if (G <= 0) {
-        e = enqueue_sweeps(s, nsweeps, draw, s->stream);
+        e = enqueue_sweeps(s, nsweeps, wh, s->stream);
         if (e != cudaSuccess) return poison(s, e, "sweep launch");
         return GMRF_OK;
     }
     int remaining = nsweeps;
     if (remaining >= G) {
         cudaGraphExec_t g = nullptr;
-        if ((e = get_graph(s, draw, 0, G, &g)) != cudaSuccess) return poison(s, e, "graph capture");
+        if ((e = get_graph(s, wh, 0, G, &g)) != cudaSuccess) return poison(s, e, "graph capture");
         while (remaining >= G) {
             if ((e = cudaGraphLaunch(g, s->stream)) != cudaSuccess) return poison(s, e, "graph launch");
             remaining -= G;
@@ -1100,7 +1119,7 @@ gmrf_status gmrf_sweep(gmrf_sampler *s, int32_t nsweeps, int32_t with_hyper)
     }
     if (remaining > 0) {
         cudaGraphExec_t g1 = nullptr;
-        if ((e = get_graph(s, draw, 1, 1, &g1)) != cudaSuccess) return poison(s, e, "graph capture");
+        if ((e = get_graph(s, wh, 1, 1, &g1)) != cudaSuccess) return poison(s, e, "graph capture");
         for (; remaining > 0; --remaining)
             if ((e = cudaGraphLaunch(g1, s->stream)) != cudaSuccess) return poison(s, e, "graph launch");
     }
@@ -1115,8 +1134,8 @@ gmrf_status gmrf_hyper_update(gmrf_sampler *s)
     if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "hyper_update on the plain sweep");
     cudaError_t e = cudaSuccess;
     for (size_t k = 0; k + 1 < s->stages.size() && e == cudaSuccess; ++k)
-        e = enqueue_stage(s, k, 0, 0, 0, 0, s->stream);
-    if (e == cudaSuccess) e = launch_hyper(s->precision, hyper_args(s, 1, 0), s->stream);
+        e = enqueue_stage(s, k, 0, 0, 0, 0, 0, s->stream);
+    if (e == cudaSuccess) e = launch_hyper(s->precision, hyper_args(s, 1, 1, 0), s->stream);
     if (e != cudaSuccess) return poison(s, e, "hyper update launch");
     return GMRF_OK;
 }
@@ -1186,6 +1205,40 @@ gmrf_status gmrf_fetch_samples(gmrf_sampler *s, int32_t field, int32_t chain, do
     return GMRF_OK;
 }
 
+gmrf_status gmrf_fetch_intercept(gmrf_sampler *s, int32_t field, int32_t chain, int64_t trace_cap, double *beta0_trace,
+                                 int64_t *n_trace, double *beta0_now)
+{
+    g_last_error.clear();
+    if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
+    if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (!s->model.intercept) return fail(GMRF_E_INVALID, "the model has no intercept");
+    if (field < 0 || field >= s->nfields || chain < 0 || chain >= s->C)
+        return fail(GMRF_E_INVALID, "field or chain out of range");
+    if (trace_cap < 0) return fail(GMRF_E_INVALID, "trace_cap must be >= 0");
+    try {
+        SweepCtl c{};
+        CK(cudaMemcpyAsync(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        const int64_t cap = s->opts.trace_capacity;
+        const int64_t avail = std::min<int64_t>(c.sweep - s->opts.start_sweep, cap);
+        if (n_trace) *n_trace = avail;
+        const int64_t hc = static_cast<int64_t>(field) * s->Cp + chain;
+        if (beta0_trace && trace_cap > 0 && avail > 0) {
+            std::vector<double> rb(static_cast<size_t>(cap));
+            CK(cudaMemcpyAsync(rb.data(), s->trace_beta + hc * cap, sizeof(double) * cap, cudaMemcpyDeviceToHost, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+            const int64_t m = std::min(trace_cap, avail);
+            for (int64_t q = 0; q < m; ++q) beta0_trace[q] = rb[(c.sweep - m + q) % cap];
+        }
+        if (beta0_now) CK(cudaMemcpyAsync(beta0_now, s->beta + hc, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    } catch (const CudaFail &f) {
+        s->poisoned = true;
+        return cuda_status(f);
+    }
+    return GMRF_OK;
+}
+
 gmrf_status gmrf_sampler_reset(gmrf_sampler *s)
 {
     g_last_error.clear();
@@ -1199,6 +1252,7 @@ gmrf_status gmrf_sampler_reset(gmrf_sampler *s)
         CK(cudaMemcpyAsync(s->tau, s->tau_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
         CK(cudaMemcpyAsync(s->sig2, s->sig2_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
         if (!plain) {
+            CK(cudaMemcpyAsync(s->beta, s->beta_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
             CK(cudaMemcpyAsync(s->hyp, s->hyp_init, s->hyp_bytes, cudaMemcpyDeviceToDevice, s->stream));
             CK(cudaMemsetAsync(s->mean, 0, s->x_bytes, s->stream));
             CK(cudaMemsetAsync(s->m2, 0, s->x_bytes, s->stream));
@@ -1226,7 +1280,7 @@ gmrf_status gmrf_launch_stage(gmrf_sampler *s, int32_t stage, int32_t accumulate
     const gmrf_sampler::Stage &g = s->stages[stage];
     if (name) *name = kNames[g.type][g.kind < 0 ? 0 : g.kind];
     const int draw = s->model.fix_hyper ? 0 : 1;
-    cudaError_t e = enqueue_stage(s, static_cast<size_t>(stage), 1, accumulate ? 1 : 0, draw, 1, s->stream);
+    cudaError_t e = enqueue_stage(s, static_cast<size_t>(stage), 1, accumulate ? 1 : 0, draw, 1, 1, s->stream);
     if (e != cudaSuccess) return poison(s, e, "stage launch");
     return GMRF_OK;
 }

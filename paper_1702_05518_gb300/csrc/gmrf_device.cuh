@@ -13,7 +13,10 @@
 namespace gmrf {
 
 constexpr uint32_t kTagX = 0, kTagTau = 1, kTagSig = 2, kTagPrio = 3, kTagTauExtra = 5,
-                   kTagSigExtra = 6;
+                   kTagSigExtra = 6, kTagBeta = 7, kTagBetaExtra = 8;
+// Per (field, chain) parameter copies read by the sweep kernels, in the state precision:
+// tau, 1/sigma^2, beta0 (0 without the intercept), and one pad.
+constexpr int kHypStride = 4;
 constexpr int kMaxChains = 64;
 constexpr int kBlock = 256;            // threads per block of the colour-step kernels
 constexpr int kMaxGammaAttempts = 64;  // bounded rejection loop
@@ -71,6 +74,13 @@ struct Tile {
 };
 
 // Device-resident sweep control, read by every kernel of a sweep and advanced by the last.
+// Per tile and chain: the sums behind the conjugate draws, FP64.
+//   S = the tile's part of x'(D - rho W)x,  R = sum (y - beta0 - x)^2,  A = sum (y - beta0 - x)
+// (beta0 = 0 without the intercept).
+struct alignas(16) Part3 {
+    double S, R, A, pad;
+};
+
 struct SweepCtl {
     long long sweep;       // number of the sweep in progress
     long long extra;       // gmrf_hyper_update calls so far

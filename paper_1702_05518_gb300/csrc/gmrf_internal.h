@@ -25,8 +25,8 @@ struct StepArgs {
     const void *deg;     // CSR: degrees d_i (precision T), permuted order
     const int32_t *perm; // CSR: slot -> natural site
     const int32_t *coff; // CSR: colour offsets (ncolors + 1 per field)
-    const void *hyp;     // [F * Cp][2]: tau, 1/sigma^2 in precision T
-    double2 *partials;   // [parts][Cp]: (x'(D - rho W)x, ||y - x||^2) per tile and chain
+    const void *hyp;     // [F * Cp][kHypStride]: tau, 1/sigma^2, beta0 in precision T
+    Part3 *partials;     // [parts][Cp]: per tile and chain sums (S, R, A)
     const SweepCtl *ctl;
     uint2 key;
     int32_t Cp;          // chains in the layout (power of two >= chains)
@@ -61,8 +61,8 @@ struct FusedArgs {
     const void *y;
     void *mean;
     void *m2;
-    const void *hyp;
-    double2 *partials;
+    const void *hyp;     // [F * Cp][kHypStride]
+    Part3 *partials;
     const SweepCtl *ctl;
     uint2 key;
     int32_t Cp;
@@ -78,22 +78,26 @@ struct HyperArgs {
     const FieldDev *fields;
     int32_t nfields;
     int32_t Cp;
-    const double2 *partials;
+    const Part3 *partials;
     double *tau;          // [F * Cp]
     double *sig2;         // [F * Cp]
-    void *hyp;            // [F * Cp][2] copies in precision T
+    double *beta;         // [F * Cp] intercepts (read and drawn only when draw_beta)
+    void *hyp;            // [F * Cp][kHypStride] copies in precision T
     double *trace_tau;    // [F * Cp][cap]
     double *trace_sig;
+    double *trace_beta;
     int32_t trace_cap;
     SweepCtl *ctl;
     uint2 key;
     double a_tau, b_tau, a_sig, b_sig;
     int32_t draw;         // 0: keep tau, sigma^2
+    int32_t draw_beta;    // 1: draw the intercept beta0 (before sigma^2)
     int32_t end_of_sweep; // 1: sweep counter, traces; 0: extra draw (tags 5 and 6)
     long long burn_in;    // accumulation schedule (to advance the accumulation count)
     int32_t thin;
     int32_t acc_enabled;
-    const double *gpre;   // [batch][F * Cp][2] unit-rate Gamma variates of the batch's sweeps
+    const double *gpre;   // [batch][F * Cp][4]: unit-rate Gamma variates of tau and 1/sigma^2 and
+                          // the intercept's standard normal, for the batch's sweeps
 };
 
 // Unit-rate Gamma variates (tau and 1/sigma^2 of every field and chain) for sweeps
@@ -106,6 +110,7 @@ struct GammaPreArgs {
     uint2 key;
     double a_tau, a_sig;
     int32_t count;
+    int32_t intercept;   // 1: also the standard normals of the intercept draws
     double *gpre;
 };
 cudaError_t launch_gamma_pre(const GammaPreArgs &a, cudaStream_t stream);

@@ -107,13 +107,14 @@ __global__ void __launch_bounds__(kFusedBlock, (kFusedBlock == 512 && sizeof(T) 
     const uint32_t sweep = static_cast<uint32_t>(sweep_ll);
     const T rho = static_cast<T>(a.rho);
 
-    T tau[V], isig[V];
+    T tau[V], isig[V], beta[V];
     const T *hyp = static_cast<const T *>(a.hyp);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const int64_t hc = (static_cast<int64_t>(t.field) * Cp + cvo + v) * 2;
+        const int64_t hc = (static_cast<int64_t>(t.field) * Cp + cvo + v) * kHypStride;
         tau[v] = hyp[hc];
         isig[v] = hyp[hc + 1];
+        beta[v] = hyp[hc + 2];
     }
 
     // Stage: rows of the NS sub-arrays; slots outside a global sub-array read as zero, and the
@@ -239,12 +240,13 @@ __global__ void __launch_bounds__(kFusedBlock, (kFusedBlock == 512 && sizeof(T) 
     // offsets depend on the row's parity); positions outside the lattice hold zeros, so the
     // sum needs no bounds tests.  The owned sites also fold their terms of the two sums of the
     // hyperparameter conditionals here, while their neighbours are in registers: (1 - rho) d x^2
-    // + rho sum over lower-colour neighbours of (x - x_j)^2, and (y - x)^2.
-    T accS[V], accR[V];
+    // + rho sum over lower-colour neighbours of (x - x_j)^2, and e^2 and e, e = y - beta0 - x.
+    T accS[V], accR[V], accA[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         accS[v] = 0;
         accR[v] = 0;
+        accA[v] = 0;
     }
 #pragma unroll 1
     for (int c = 0; c < (a.update ? K : 0); ++c) {
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(kFusedBlock, (kFusedBlock == 512 && sizeof(T) 
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const T P = tau[v] * d + isig[v];
-                const T m = (tau[v] * rho * s[v] + yv * isig[v]) * FArith<T>::rcp(P);
+                const T m = (tau[v] * rho * s[v] + (yv - beta[v]) * isig[v]) * FArith<T>::rcp(P);
                 xn[v] = m + z[v] * FArith<T>::rsq(P);
             }
             Vec<T, V>::st(xs + idx * Cp + cvo, xn);
@@ -321,8 +323,9 @@ __global__ void __launch_bounds__(kFusedBlock, (kFusedBlock == 512 && sizeof(T) 
                             e += df * df;
                         }
                     accS[v] += (static_cast<T>(1) - rho) * d * xn[v] * xn[v] + rho * e;
-                    const T r = yv - xn[v];
+                    const T r = (yv - beta[v]) - xn[v];
                     accR[v] += r * r;
+                    accA[v] += r;
                 }
             }
         });
@@ -358,8 +361,9 @@ __global__ void __launch_bounds__(kFusedBlock, (kFusedBlock == 512 && sizeof(T) 
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     accS[v] += (static_cast<T>(1) - rho) * static_cast<T>(deg) * xn[v] * xn[v] + rho * e[v];
-                    const T r = yv - xn[v];
+                    const T r = (yv - beta[v]) - xn[v];
                     accR[v] += r * r;
+                    accA[v] += r;
                 }
             });
         }
@@ -412,26 +416,28 @@ __global__ void __launch_bounds__(kFusedBlock, (kFusedBlock == 512 && sizeof(T) 
     // Deterministic block reduction in precision T (shuffle tree over lanes sharing a chain
     // vector, then warps in order) into the tile's FP64 partial-sum slot; a tile holds at most a
     // few thousand terms, the sum over tiles is FP64.
-    // Reduction scratch [NW][Cp][2] reuses the normals' space (dead after phase B).
+    // Reduction scratch [NW][Cp][3] reuses the normals' space (dead after phase B).
     T *red = zs;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        T sS = accS[v], sR = accR[v];
+        T sS = accS[v], sR = accR[v], sA = accA[v];
         for (int off = 16; off >= CV; off >>= 1) {
             sS += __shfl_xor_sync(0xffffffffu, sS, off);
             sR += __shfl_xor_sync(0xffffffffu, sR, off);
+            sA += __shfl_xor_sync(0xffffffffu, sA, off);
         }
         if (lane < CV) {
-            red[(warp * Cp + lane * V + v) * 2] = sS;
-            red[(warp * Cp + lane * V + v) * 2 + 1] = sR;
+            red[(warp * Cp + lane * V + v) * 3] = sS;
+            red[(warp * Cp + lane * V + v) * 3 + 1] = sR;
+            red[(warp * Cp + lane * V + v) * 3 + 2] = sA;
         }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < Cp * 2; q += kFusedBlock) {
-        const int chain = q >> 1, k = q & 1;
+    for (int q = threadIdx.x; q < Cp * 3; q += kFusedBlock) {
+        const int chain = q / 3, k = q - 3 * chain;
         T sum = 0;
-        for (int w = 0; w < NW; ++w) sum += red[(w * Cp + chain) * 2 + k];
+        for (int w = 0; w < NW; ++w) sum += red[(w * Cp + chain) * 3 + k];
         reinterpret_cast<double *>(a.partials + static_cast<int64_t>(t.part) * Cp + chain)[k] = static_cast<double>(sum);
     }
 }
@@ -470,13 +476,14 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4) ? 2 : 1) lat
     const T *Y = static_cast<const T *>(a.y) + f.slot0;
     const int gsub = f.rows * f.cols, gcols = f.cols, grows = f.rows;
     const T rho = static_cast<T>(a.rho);
-    T tau[CP], isig[CP];
+    T tau[CP], isig[CP], beta[CP];
     {
-        const T *hyp = static_cast<const T *>(a.hyp) + static_cast<int64_t>(t.field) * CP * 2;
+        const T *hyp = static_cast<const T *>(a.hyp) + static_cast<int64_t>(t.field) * CP * kHypStride;
 #pragma unroll
         for (int v = 0; v < CP; ++v) {
-            tau[v] = hyp[2 * v];
-            isig[v] = hyp[2 * v + 1];
+            tau[v] = hyp[kHypStride * v];
+            isig[v] = hyp[kHypStride * v + 1];
+            beta[v] = hyp[kHypStride * v + 2];
         }
     }
     const float rcp_sc = __frcp_rn(static_cast<float>(SC)), rcp_sr = __frcp_rn(static_cast<float>(SR));
@@ -556,11 +563,12 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4) ? 2 : 1) lat
     __syncthreads();
 
     // Phase B: colour steps; owned sites fold their terms of the hyperparameter sums.
-    T accS[CP], accR[CP];
+    T accS[CP], accR[CP], accA[CP];
 #pragma unroll
     for (int v = 0; v < CP; ++v) {
         accS[v] = 0;
         accR[v] = 0;
+        accA[v] = 0;
     }
 #pragma unroll 1
     for (int c = 0; c < K; ++c) {
@@ -653,7 +661,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4) ? 2 : 1) lat
 #pragma unroll
                 for (int v = 0; v < CP; ++v) {
                     const T P = tau[v] * d + isig[v];
-                    const T m = (tau[v] * rho * s[v] + yv * isig[v]) * FArith<T>::rcp(P);
+                    const T m = (tau[v] * rho * s[v] + (yv - beta[v]) * isig[v]) * FArith<T>::rcp(P);
                     xn[v] = m + z[v] * FArith<T>::rsq(P);
                 }
                 Vec<T, CP>::st(xs + idx * CP, xn);
@@ -667,8 +675,9 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4) ? 2 : 1) lat
                             e2 += wv[k] * df * df;
                         }
                         accS[v] += (static_cast<T>(1) - rho) * d * xn[v] * xn[v] + rho * e2;
-                        const T r = yv - xn[v];
+                        const T r = (yv - beta[v]) - xn[v];
                         accR[v] += r * r;
+                        accA[v] += r;
                     }
                 }
             }
@@ -717,26 +726,28 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4) ? 2 : 1) lat
     }
 
     // Block reduction (all lanes hold the same chains): warp shuffle tree, then warps in order.
-    T *red = zs;  // [NW][CP][2], the normals are dead
+    T *red = zs;  // [NW][CP][3], the normals are dead
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < CP; ++v) {
-        T sS = accS[v], sR = accR[v];
+        T sS = accS[v], sR = accR[v], sA = accA[v];
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
             sS += __shfl_xor_sync(0xffffffffu, sS, o);
             sR += __shfl_xor_sync(0xffffffffu, sR, o);
+            sA += __shfl_xor_sync(0xffffffffu, sA, o);
         }
         if (lane == 0) {
-            red[(warp * CP + v) * 2] = sS;
-            red[(warp * CP + v) * 2 + 1] = sR;
+            red[(warp * CP + v) * 3] = sS;
+            red[(warp * CP + v) * 3 + 1] = sR;
+            red[(warp * CP + v) * 3 + 2] = sA;
         }
     }
     __syncthreads();
-    if (threadIdx.x < CP * 2) {
-        const int chain = threadIdx.x >> 1, k = threadIdx.x & 1;
+    if (threadIdx.x < CP * 3) {
+        const int chain = threadIdx.x / 3, k = threadIdx.x - 3 * chain;
         T sum = 0;
-        for (int w = 0; w < NW; ++w) sum += red[(w * CP + chain) * 2 + k];
+        for (int w = 0; w < NW; ++w) sum += red[(w * CP + chain) * 3 + k];
         reinterpret_cast<double *>(a.partials + static_cast<int64_t>(t.part) * CP + chain)[k] = static_cast<double>(sum);
     }
 }

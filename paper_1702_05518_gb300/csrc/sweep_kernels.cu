@@ -8,8 +8,10 @@
 //     s_i = sum_j w_ij x_j                         (neighbours all have other colours)
 //     P_i = tau d_i + 1/sigma^2,  m_i = (tau rho s_i + y_i/sigma^2) / P_i
 //     x_i = m_i + z_i / sqrt(P_i),                 z_i Philox/Box-Muller normal of (site, sweep)
-// and accumulates, per chain, the two sums the conjugate draws need:
-//     (1 - rho) d_i x_i^2 + rho sum_{j lower colour} w_ij (x_i - x_j)^2,   (y_i - x_i)^2,
+// (with the intercept of Sec. 3.1, y_i - beta0 in place of y_i) and accumulates, per chain, the
+// sums the conjugate draws need:
+//     (1 - rho) d_i x_i^2 + rho sum_{j lower colour} w_ij (x_i - x_j)^2,
+//     (y_i - beta0 - x_i)^2  and  y_i - beta0 - x_i,
 // so that after the last colour every undirected edge has been counted once, at its endpoint
 // of higher colour, with both endpoints final: summed over sites this is x'(D - rho W)x.
 // Thread, warp and block partial sums are in the state precision (a tile holds at most a few
@@ -37,8 +39,8 @@ template <> struct Arith<double> {
 
 template <typename T, int V>
 struct SiteCtx {
-    T tau[V], isig[V];   // per chain of this thread
-    T accS[V], accR[V];  // thread partial sums
+    T tau[V], isig[V], beta[V];  // per chain of this thread
+    T accS[V], accR[V], accA[V]; // thread partial sums
     T inv_k;             // 1 / (accumulated count) when accumulating
     bool acc;
 };
@@ -60,7 +62,7 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const T P = cx.tau[v] * d + cx.isig[v];
-            const T m = (cx.tau[v] * rho * s[v] + yv * cx.isig[v]) * Arith<T>::rcp(P);
+            const T m = (cx.tau[v] * rho * s[v] + (yv - cx.beta[v]) * cx.isig[v]) * Arith<T>::rcp(P);
             xn[v] = m + z[v] * Arith<T>::rsq(P);
         }
         Vec<T, V>::st(xp, xn);
@@ -78,8 +80,9 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
             }
         }
         cx.accS[v] += (static_cast<T>(1) - rho) * d * xn[v] * xn[v] + rho * e;
-        const T r = yv - xn[v];
+        const T r = (yv - cx.beta[v]) - xn[v];
         cx.accR[v] += r * r;
+        cx.accA[v] += r;
     }
     if (cx.acc) {
         T mu[V], mm[V];
@@ -330,11 +333,13 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_ke
     const T *hyp = static_cast<const T *>(a.hyp);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const int64_t hc = (static_cast<int64_t>(t.field) * a.Cp + cv * V + v) * 2;
+        const int64_t hc = (static_cast<int64_t>(t.field) * a.Cp + cv * V + v) * kHypStride;
         cx.tau[v] = hyp[hc];
         cx.isig[v] = hyp[hc + 1];
+        cx.beta[v] = hyp[hc + 2];
         cx.accS[v] = 0;
         cx.accR[v] = 0;
+        cx.accA[v] = 0;
     }
     cx.acc = false;
     cx.inv_k = 0;
@@ -349,27 +354,30 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_ke
     else if constexpr (KIND == kLat2D8) lattice8_tile<T, V>(a, f, t, cx, CV, cv_shift, sweep);
     else csr_tile<T, V>(a, f, t, cx, CV, cv_shift, sweep);
 
-    // Deterministic block reduction of the 2 V partial sums of each chain in the state precision:
+    // Deterministic block reduction of the 3 V partial sums of each chain in the state precision:
     // a shuffle tree over the lanes that share a chain vector (lanes equal mod CV), then the
     // warps' sums in order; the tile's sum is stored in FP64 and summed over tiles in FP64.
-    __shared__ T red[kBlock / 32][kMaxChains][2];
+    __shared__ T red[kBlock / 32][kMaxChains][3];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         T sS = cx.accS[v];
         T sR = cx.accR[v];
+        T sA = cx.accA[v];
         for (int off = 16; off >= CV; off >>= 1) {
             sS += __shfl_xor_sync(0xffffffffu, sS, off);
             sR += __shfl_xor_sync(0xffffffffu, sR, off);
+            sA += __shfl_xor_sync(0xffffffffu, sA, off);
         }
         if (lane < CV) {
             red[warp][lane * V + v][0] = sS;
             red[warp][lane * V + v][1] = sR;
+            red[warp][lane * V + v][2] = sA;
         }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < a.Cp * 2; q += kBlock) {
-        const int chain = q >> 1, k = q & 1;
+    for (int q = threadIdx.x; q < a.Cp * 3; q += kBlock) {
+        const int chain = q / 3, k = q - 3 * chain;
         T acc = 0;
         for (int w = 0; w < kBlock / 32; ++w) acc += red[w][chain][k];
         double *dst = reinterpret_cast<double *>(a.partials + static_cast<int64_t>(t.part) * a.Cp + chain);
@@ -377,69 +385,108 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_ke
     }
 }
 
-// Two blocks per (field, chain): block 2p draws tau of pair p, block 2p + 1 draws 1/sigma^2 (the
-// two are conditionally independent given x, Sec. 3.1).  Each sums its sum (x'(D - rho W)x or
-// ||y - x||^2) over the field's tile partials in a fixed order (thread strides, shuffle tree,
-// warps in order), then thread 0 draws from the Gamma full conditional, refreshes the
-// precision-T copy the colour kernels read, and records the trace.  FP64 arithmetic has a long
-// dependent-operation latency on this GPU, so the two draws run in parallel.  The last block to
-// finish (ticket counter; no block waits for another) advances the sweep counter, the
-// accumulation count, or the extra-draw counter.
+// Two blocks per (field, chain): block 2p draws tau of pair p, block 2p + 1 draws the intercept
+// (when present) and then 1/sigma^2 of pair p (given x, tau is conditionally independent of
+// beta0 and sigma^2, Sec. 3.1).  Each sums what it needs over the field's tile partials in a
+// fixed order (thread strides, shuffle tree, warps in order), then thread 0 draws from the full
+// conditionals, refreshes the precision-T copies the colour kernels read, and records the
+// traces.  FP64 arithmetic has a long dependent-operation latency on this GPU, so the two blocks
+// run in parallel.  The last block to finish (ticket counter; no block waits for another)
+// advances the sweep counter, the accumulation count, or the extra-draw counter.
+//
+// Intercept: the partials hold R = sum e_i^2 and A = sum e_i with e_i = y_i - b - x_i, b the
+// copy of beta0 the sweep used.  beta0 | x, sigma^2 ~ N(1'(y - x)/n, sigma^2/n) is drawn as
+// b + delta, delta = A/n + sqrt(sigma^2/n) z, and the sigma^2 draw takes
+// sum (e_i - delta)^2 = R - 2 delta A + n delta^2 (exact algebra; delta is small next to e).
 template <typename T>
 __global__ void __launch_bounds__(256) hyper_kernel(const HyperArgs a)
 {
-    __shared__ double red[8];
+    __shared__ double red[2][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long sweep = a.ctl->sweep;
     const long long extra = a.ctl->extra;
-    const int pidx = blockIdx.x >> 1, which = blockIdx.x & 1;  // which: 0 tau, 1 sigma^2
+    const int pidx = blockIdx.x >> 1, which = blockIdx.x & 1;  // which: 0 tau, 1 beta0 and sigma^2
     const int fi = pidx / a.Cp, chain = pidx - fi * a.Cp;
     const FieldDev f = a.fields[fi];
-    double S = 0.0;
-    if (a.draw) {
+    const bool need_sum = which ? (a.draw || a.draw_beta) : a.draw;
+    const bool need_a = which && a.draw_beta;
+    double S = 0.0, A = 0.0;
+    if (need_sum) {
         for (int k = threadIdx.x; k < f.nparts; k += blockDim.x) {
-            const double2 p = a.partials[static_cast<int64_t>(f.part0 + k) * a.Cp + chain];
-            S += which ? p.y : p.x;
+            const Part3 p = a.partials[static_cast<int64_t>(f.part0 + k) * a.Cp + chain];
+            S += which ? p.R : p.S;
+            if (need_a) A += p.A;
         }
         for (int off = 16; off >= 1; off >>= 1) S += __shfl_xor_sync(0xffffffffu, S, off);
-        if (lane == 0) red[warp] = S;
+        if (need_a)
+            for (int off = 16; off >= 1; off >>= 1) A += __shfl_xor_sync(0xffffffffu, A, off);
+        if (lane == 0) {
+            red[0][warp] = S;
+            red[1][warp] = A;
+        }
         __syncthreads();
-        S = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
+        S = ((red[0][0] + red[0][1]) + (red[0][2] + red[0][3])) + ((red[0][4] + red[0][5]) + (red[0][6] + red[0][7]));
+        A = ((red[1][0] + red[1][1]) + (red[1][2] + red[1][3])) + ((red[1][4] + red[1][5]) + (red[1][6] + red[1][7]));
     }
     if (threadIdx.x == 0) {
         const int64_t hc = static_cast<int64_t>(fi) * a.Cp + chain;
+        T *hyp = static_cast<T *>(a.hyp);
+        const long long kb = sweep - a.ctl->batch_base;
+        const bool pre = a.end_of_sweep && a.gpre && kb >= 0 && kb < a.ctl->batch_count;
+        const double *gp = pre ? a.gpre + (kb * a.nfields * a.Cp + pidx) * 4 : nullptr;
+        const uint32_t word1 = static_cast<uint32_t>(a.end_of_sweep ? sweep : extra);
         double val = which ? a.sig2[hc] : a.tau[hc];
+        double bval = 0.0;
+        if (which && a.draw_beta) {
+            // The sweep's residuals used b = the precision-T copy of beta0.
+            const double b = static_cast<double>(hyp[hc * kHypStride + 2]);
+            double zb;
+            if (pre) {
+                zb = gp[2];
+            } else {
+                const uint32_t tag = a.end_of_sweep ? kTagBeta : kTagBetaExtra;
+                const uint4 w = philox4x32_10(make_uint4(0u, word1, f.stream, (tag << 24) | static_cast<uint32_t>(chain)),
+                                              a.key);
+                double unused;
+                box_muller_f64(w.x, w.y, zb, unused);
+            }
+            const double delta = A / f.n + sqrt(a.sig2[hc] / f.n) * zb;
+            bval = b + delta;
+            a.beta[hc] = bval;
+            hyp[hc * kHypStride + 2] = static_cast<T>(bval);
+            S = S - 2.0 * delta * A + f.n * (delta * delta);
+        } else if (which && a.trace_beta) {
+            bval = a.beta[hc];
+        }
         if (a.draw) {
-            const uint32_t word1 = static_cast<uint32_t>(a.end_of_sweep ? sweep : extra);
             const uint32_t tag = which ? (a.end_of_sweep ? kTagSig : kTagSigExtra) : (a.end_of_sweep ? kTagTau : kTagTauExtra);
             int fb = 0;
             const double shape = which ? a.a_sig + 0.5 * f.n : a.a_tau + 0.5 * f.rank;
             const double rate = which ? a.b_sig + 0.5 * S : a.b_tau + 0.5 * S;
-            const long long kb = sweep - a.ctl->batch_base;
             double g;
-            if (a.end_of_sweep && a.gpre && kb >= 0 && kb < a.ctl->batch_count) {
+            if (pre) {
                 // Precomputed unit-rate variate of this sweep: the draw is g = G / rate.
-                g = a.gpre[(kb * a.nfields * a.Cp + pidx) * 2 + which] / rate;
+                g = gp[which] / rate;
             } else {
                 g = gamma_mt(shape, rate, a.key, word1, f.stream, (tag << 24) | static_cast<uint32_t>(chain), fb);
                 if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), 1ull);
             }
-            T *hyp = static_cast<T *>(a.hyp);
             if (which) {
                 // The sweep kernels use 1/sigma^2 recomputed from sigma^2, as the oracle does, so
                 // a run resumed from a fetched sigma^2 continues bit for bit.
                 val = 1.0 / g;
                 a.sig2[hc] = val;
-                hyp[hc * 2 + 1] = static_cast<T>(1.0 / val);
+                hyp[hc * kHypStride + 1] = static_cast<T>(1.0 / val);
             } else {
                 val = g;
                 a.tau[hc] = val;
-                hyp[hc * 2] = static_cast<T>(g);
+                hyp[hc * kHypStride] = static_cast<T>(g);
             }
         }
         if (a.end_of_sweep && a.trace_cap > 0) {
             const int64_t slot = hc * a.trace_cap + (sweep % a.trace_cap);
             (which ? a.trace_sig : a.trace_tau)[slot] = val;
+            if (which && a.trace_beta) a.trace_beta[slot] = bval;
         }
         __threadfence();
         const unsigned long long done = atomicAdd(&a.ctl->ticket, 1ull);
@@ -505,23 +552,35 @@ __global__ void site_normals_kernel(uint2 key, uint32_t sweep, uint32_t stream, 
     }
 }
 
-// One thread per (sweep of the batch, field, chain, tau or sigma^2): the unit-rate Marsaglia-Tsang
-// variate with the counters of that sweep's draw.  The draws are independent of the state, so a
-// whole batch runs in parallel and the per-sweep draw reduces to a division by the rate.
+// One thread per (sweep of the batch, field, chain, variate): the unit-rate Marsaglia-Tsang
+// variates of tau and 1/sigma^2 and the intercept's standard normal, with the counters of that
+// sweep's draws.  They are independent of the state, so a whole batch runs in parallel and the
+// per-sweep draw reduces to a division by the rate (and a shift for the intercept).
 __global__ void gamma_pre_kernel(const GammaPreArgs a)
 {
     const long long base = a.ctl->sweep;
     const int npairs = a.nfields * a.Cp;
-    const int total = a.count * npairs * 2;
+    const int total = a.count * npairs * 4;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-        const int which = q & 1, pidx = (q >> 1) % npairs, k = (q >> 1) / npairs;
+        const int which = q & 3, pidx = (q >> 2) % npairs, k = (q >> 2) / npairs;
         const int fi = pidx / a.Cp, chain = pidx - fi * a.Cp;
         const FieldDev &f = a.fields[fi];
+        const uint32_t word1 = static_cast<uint32_t>(base + k);
+        if (which == 3) continue;
+        if (which == 2) {
+            double zb = 0.0, unused;
+            if (a.intercept) {
+                const uint4 w = philox4x32_10(
+                    make_uint4(0u, word1, f.stream, (kTagBeta << 24) | static_cast<uint32_t>(chain)), a.key);
+                box_muller_f64(w.x, w.y, zb, unused);
+            }
+            a.gpre[q] = zb;
+            continue;
+        }
         const double shape = which ? a.a_sig + 0.5 * f.n : a.a_tau + 0.5 * f.rank;
         const uint32_t tag = which ? kTagSig : kTagTau;
         int fb = 0;
-        a.gpre[q] = gamma_mt(shape, 1.0, a.key, static_cast<uint32_t>(base + k), f.stream,
-                             (tag << 24) | static_cast<uint32_t>(chain), fb);
+        a.gpre[q] = gamma_mt(shape, 1.0, a.key, word1, f.stream, (tag << 24) | static_cast<uint32_t>(chain), fb);
         if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), 1ull);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -611,7 +670,7 @@ cudaError_t launch_unpack(int precision, const FieldDev *fields_dev, const Field
 
 cudaError_t launch_gamma_pre(const GammaPreArgs &a, cudaStream_t stream)
 {
-    const int total = a.count * a.nfields * a.Cp * 2;
+    const int total = a.count * a.nfields * a.Cp * 4;
     if (total <= 0) return cudaSuccess;
     gamma_pre_kernel<<<(total + 127) / 128, 128, 0, stream>>>(a);
     return cudaGetLastError();

@@ -24,7 +24,7 @@ FLAG_PER_COLOUR = 1
 
 EXPORTED = ["gmrf_color_graph", "gmrf_color_graph_noalloc", "gmrf_sampler_create", "gmrf_sampler_destroy", "gmrf_sweep",
             "gmrf_hyper_update", "gmrf_fetch_samples", "gmrf_field_colors", "gmrf_sampler_info",
-            "gmrf_sampler_reset", "gmrf_launch_stage",
+            "gmrf_sampler_reset", "gmrf_launch_stage", "gmrf_fetch_intercept",
             "gmrf_validate_csr", "gmrf_philox_words", "gmrf_site_normals", "gmrf_last_error",
             "gmrf_version"]
 
@@ -43,14 +43,16 @@ class FieldDesc(ctypes.Structure):
                 ("colors", ctypes.POINTER(ctypes.c_int32)), ("color_seed", ctypes.c_uint64),
                 ("y", ctypes.POINTER(ctypes.c_double)), ("x0", ctypes.POINTER(ctypes.c_double)),
                 ("tau0", ctypes.POINTER(ctypes.c_double)),
-                ("sigma2_0", ctypes.POINTER(ctypes.c_double)), ("stream_id", ctypes.c_uint32)]
+                ("sigma2_0", ctypes.POINTER(ctypes.c_double)), ("stream_id", ctypes.c_uint32),
+                ("beta0", ctypes.POINTER(ctypes.c_double))]
 
 
 class Model(ctypes.Structure):
     _fields_ = [("prior", ctypes.c_int32), ("rho", ctypes.c_double), ("a_tau", ctypes.c_double),
                 ("b_tau", ctypes.c_double), ("a_sigma", ctypes.c_double),
                 ("b_sigma", ctypes.c_double), ("fix_hyper", ctypes.c_int32),
-                ("tau0", ctypes.c_double), ("sigma2_0", ctypes.c_double)]
+                ("tau0", ctypes.c_double), ("sigma2_0", ctypes.c_double),
+                ("intercept", ctypes.c_int32), ("beta0_0", ctypes.c_double)]
 
 
 class Opts(ctypes.Structure):
@@ -107,6 +109,9 @@ def lib() -> ctypes.CDLL:
             L.gmrf_fetch_samples.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, f64p, f64p, f64p,
                                              ctypes.c_int64, f64p, f64p, i64p, f64p, f64p]
             L.gmrf_fetch_samples.restype = st
+            L.gmrf_fetch_intercept.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, f64p, i64p,
+                                               f64p]
+            L.gmrf_fetch_intercept.restype = st
             L.gmrf_field_colors.argtypes = [vp, ctypes.c_int32, i32p, i32p]
             L.gmrf_field_colors.restype = st
             L.gmrf_sampler_info.argtypes = [vp, P(Info)]
@@ -220,14 +225,16 @@ class Sampler:
     """A chromatic Gibbs sampler over one or more fields (see include/gmrf.h).
 
     fields: list of dicts with keys kind, dims, n, y and, for CSR fields, row_ptr, col_idx and
-    optionally weights, colors, color_seed; optional per field: x0 ([chains, n]), tau0 and
-    sigma2_0 ([chains]), stream_id (default: the field's index).
+    optionally weights, colors, color_seed; optional per field: x0 ([chains, n]), tau0,
+    sigma2_0 and beta0 ([chains]), stream_id (default: the field's index).  intercept=True adds
+    the flat-prior intercept beta0 of Sec. 3.1 (initial value beta0_0).
     """
 
     def __init__(self, fields, *, precision=FP32, chains=1, seed=0, prior=PRIOR_ICAR, rho=1.0,
                  a_tau=1.0, b_tau=0.01, a_sigma=1.0, b_sigma=0.01, fix_hyper=False, tau0=1.0,
                  sigma2_0=1.0, start_sweep=0, burn_in=0, thin=1, trace_capacity=4096,
-                 algorithm=ALGO_CHROMATIC, graph_sweeps=0, flags=0, stream=None):
+                 algorithm=ALGO_CHROMATIC, graph_sweeps=0, flags=0, stream=None, intercept=False,
+                 beta0_0=0.0):
         L = lib()
         self._h = ctypes.c_void_p()
         self.chains = int(chains)
@@ -246,7 +253,7 @@ class Sampler:
             if f.get("x0") is not None:
                 arrs["x0"] = _f64(np.broadcast_to(np.asarray(f["x0"], np.float64),
                                                   (self.chains, d.n)))
-            for key in ("tau0", "sigma2_0"):
+            for key in ("tau0", "sigma2_0", "beta0"):
                 if f.get(key) is not None:
                     arrs[key] = _f64(np.broadcast_to(np.asarray(f[key], np.float64), (self.chains,)))
             if d.kind == CSR:
@@ -261,6 +268,7 @@ class Sampler:
             d.x0 = _p(arrs.get("x0"), ctypes.c_double)
             d.tau0 = _p(arrs.get("tau0"), ctypes.c_double)
             d.sigma2_0 = _p(arrs.get("sigma2_0"), ctypes.c_double)
+            d.beta0 = _p(arrs.get("beta0"), ctypes.c_double)
             d.row_ptr = _p(arrs.get("row_ptr"), ctypes.c_int32)
             d.col_idx = _p(arrs.get("col_idx"), ctypes.c_int32)
             d.weights = _p(arrs.get("weights"), ctypes.c_double)
@@ -268,7 +276,8 @@ class Sampler:
             d.stream_id = int(f.get("stream_id", i))
             keep.append(arrs)
         model = Model(int(prior), float(rho), float(a_tau), float(b_tau), float(a_sigma),
-                      float(b_sigma), 1 if fix_hyper else 0, float(tau0), float(sigma2_0))
+                      float(b_sigma), 1 if fix_hyper else 0, float(tau0), float(sigma2_0),
+                      1 if intercept else 0, float(beta0_0))
         opts = Opts(int(precision), self.chains, int(seed), int(start_sweep), int(burn_in),
                     int(thin), int(trace_capacity), int(algorithm), int(graph_sweeps), int(flags))
         self.stream = current_stream() if stream is None else stream
@@ -325,6 +334,16 @@ class Sampler:
         m = min(int(trace), nt.value)
         return {"x": x, "mean": mean, "var": var, "tau_trace": tt[:m], "sigma2_trace": ts[:m],
                 "n_trace": nt.value, "tau": tau.value, "sigma2": sig.value}
+
+    def fetch_intercept(self, field=0, chain=0, trace=0):
+        """Current beta0 and its last `trace` values (oldest first) of one (field, chain)."""
+        tb = np.zeros(max(int(trace), 1))
+        nt = ctypes.c_int64(0)
+        b = ctypes.c_double(0)
+        _check(lib().gmrf_fetch_intercept(self._h, field, chain, int(trace), _p(tb, ctypes.c_double),
+                                          ctypes.byref(nt), ctypes.byref(b)))
+        m = min(int(trace), nt.value)
+        return {"beta0": b.value, "beta0_trace": tb[:m], "n_trace": nt.value}
 
     def fetch_x(self, field=0, chain=0):
         n = int(self.fields[field]["n"])

@@ -31,13 +31,15 @@ def oracle_colors(field):
 
 def run_oracle(field, chains, nsweeps, *, seed, stream, prior="icar", rho=1.0, start_sweep=0,
                fix_hyper=False, burn_in=0, thin=1, tau0=1.0, sigma2_0=1.0, a_tau=1.0, b_tau=0.01,
-               a_sig=1.0, b_sig=0.01, record_x=False):
+               a_sig=1.0, b_sig=0.01, record_x=False, intercept=False, beta0=0.0):
     st = oracle.initial_state(field["y"], chains, tau0=field.get("tau0", tau0),
-                              sigma2_0=field.get("sigma2_0", sigma2_0), x0=field.get("x0"))
+                              sigma2_0=field.get("sigma2_0", sigma2_0), x0=field.get("x0"),
+                              beta0=field.get("beta0", beta0))
     out = oracle.run(oracle_graph(field), oracle_colors(field), field["y"], st, seed=seed,
                      nsweeps=nsweeps, stream=stream, start_sweep=start_sweep, prior=prior, rho=rho,
                      fix_hyper=fix_hyper, burn_in=burn_in, thin=thin, a_tau=a_tau, b_tau=b_tau,
-                     a_sig=a_sig, b_sig=b_sig, weights=field.get("weights"), record_x=record_x)
+                     a_sig=a_sig, b_sig=b_sig, weights=field.get("weights"), record_x=record_x,
+                     intercept=intercept)
     return st, out
 
 
