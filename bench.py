@@ -68,6 +68,17 @@ def workload_spec(name: str):
         return dict(name="224 lattices (sides log-U[32,512]) + 32 Delaunay graphs (n log-U[1k,50k])",
                     fields=fields, chains=1, sweeps=1000, burn_in=500, prior="icar", rho=1.0,
                     seed=4, graph_sweeps=25, cpu_sweeps=3)
+    if name in ("paper50", "paper512"):
+        # Sec. 3.1 simulation: p x p image, 5 exp(-|v|^2/2)/pi on [-3, 3]^2, 8-neighbour intrinsic
+        # prior, flat intercept, InvGam(0.001, 0.001) on tau^2 and sigma^2, three chains, 10,000
+        # iterations with 8,000 burn-in; N(0, 1) noise at p = 50 and N(0, 50^2) at p = 512.
+        p, noise = (50, 1.0) if name == "paper50" else (512, 50.0)
+        y = (wl.paper_image(p) + wl.rng(6).normal(0.0, noise, (p, p))).ravel()
+        f = {"kind": wl.LATTICE2D_8, "dims": (p, p), "n": p * p, "y": y}
+        return dict(name=f"{p}x{p} image of Sec. 3.1 (noise sd {noise:g}), 8-neighbour ICAR + intercept, "
+                         "InvGam(0.001, 0.001), 3 chains", fields=[f], chains=3, sweeps=10_000, burn_in=8000,
+                    prior="icar", rho=1.0, seed=6, graph_sweeps=100, cpu_sweeps=2000 if p == 50 else 20,
+                    intercept=True, hyper=dict(a_tau=0.001, b_tau=0.001, a_sigma=0.001, b_sigma=0.001))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -244,7 +255,10 @@ def oracle_rate(spec, sweeps):
     updates = 0
     for graph, colors, y, i in prepared:
         st = oracle.initial_state(y, spec["chains"])
+        hp = spec.get("hyper", {})
+        hp = {("a_sig" if k == "a_sigma" else "b_sig" if k == "b_sigma" else k): v for k, v in hp.items()}
         oracle.run(graph, colors, y, st, seed=spec["seed"], nsweeps=sweeps, stream=i, prior=spec["prior"],
+                   intercept=spec.get("intercept", False), **hp,
                    rho=spec["rho"], burn_in=0, accumulate=True)
         updates += len(y) * spec["chains"] * sweeps
     dt = time.perf_counter() - t0
@@ -327,6 +341,16 @@ def run_reference(args):
     return 0
 
 
+def sampler_kwargs(spec, g, seed, **over):
+    """Sampler arguments of a workload: FP32 state, its prior, chains, intercept and priors."""
+    kw = dict(precision=g.FP32, chains=spec["chains"], seed=seed,
+              prior=g.PRIOR_PCAR if spec["prior"] == "pcar" else g.PRIOR_ICAR, rho=spec["rho"],
+              burn_in=spec["burn_in"], graph_sweeps=spec["graph_sweeps"], trace_capacity=spec["sweeps"],
+              intercept=spec.get("intercept", False), **spec.get("hyper", {}))
+    kw.update(over)
+    return kw
+
+
 def run_profile_case(args):
     """A fixed launch sequence for a profiler: create, S sweeps launched stage by stage, fetch."""
     import torch
@@ -338,9 +362,7 @@ def run_profile_case(args):
     if not os.path.exists(g.LIB_PATH):
         libbuild.build()
     spec = workload_spec(args.workload)
-    prior = g.PRIOR_PCAR if spec["prior"] == "pcar" else g.PRIOR_ICAR
-    with g.Sampler(spec["fields"], precision=g.FP32, chains=spec["chains"], seed=spec["seed"], prior=prior,
-                   rho=spec["rho"], burn_in=spec["burn_in"], graph_sweeps=0) as s:
+    with g.Sampler(spec["fields"], **sampler_kwargs(spec, g, spec["seed"], graph_sweeps=0)) as s:
         s.sweep(args.profile_sweeps)
         x = s.fetch_x(0, 0)
         info = s.info()
@@ -367,9 +389,7 @@ def run_ours(args):
         libbuild.build()
     spec = workload_spec(args.workload)
     seed = replica_seed(spec["seed"], rank)
-    prior = g.PRIOR_PCAR if spec["prior"] == "pcar" else g.PRIOR_ICAR
-    kw = dict(precision=g.FP32, chains=spec["chains"], seed=seed, prior=prior, rho=spec["rho"],
-              burn_in=spec["burn_in"], graph_sweeps=spec["graph_sweeps"], trace_capacity=spec["sweeps"])
+    kw = sampler_kwargs(spec, g, seed)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     units = site_updates_per_step(spec)
@@ -426,6 +446,23 @@ def run_ours(args):
     kernel_us = dom[2]
     algo_bytes = stage_algorithmic_bytes(spec, dom[1], colour_of_stage[dom[0]], colourings)
     s.close()
+
+    # The plain single-field FP64 sweep (natural layout, one unfused pass per colour) on the same
+    # workload and chains, a bounded number of sweeps: the speed-up of the path is value / its rate.
+    plain = None
+    if len(spec["fields"]) == 1 and not spec.get("intercept", False):
+        ps = min(spec["sweeps"], 200)
+        with g.Sampler(spec["fields"], **sampler_kwargs(spec, g, seed, precision=g.FP64, algorithm=g.ALGO_PLAIN,
+                                                       graph_sweeps=min(spec["graph_sweeps"], ps))) as sp:
+            sp.sweep(ps)
+            torch.cuda.synchronize()
+            sp.reset()
+            ev0.record(stream)
+            sp.sweep(ps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            prate = spec["fields"][0]["n"] * spec["chains"] * ps / (ev0.elapsed_time(ev1) * 1e-3)
+        plain = {"value": prate, "unit": UNIT, "dtype": "f64", "sweeps": ps, "speedup": None}
 
     # End to end through the C ABI with host buffers: create (H2D copy of y), all sweeps, fetch
     # of the posterior mean (D2H), destroy.
@@ -488,7 +525,10 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "roofline": roofline,
-            "cpu_baseline": cpu}
+            "cpu_baseline": cpu,
+            "plain_fp64": plain}
+    if plain:
+        plain["speedup"] = value / plain["value"]
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -504,7 +544,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="image1024",
-                    choices=["image1024", "image64", "volume256", "delaunay16k", "batched"])
+                    choices=["image1024", "image64", "volume256", "delaunay16k", "batched", "paper50",
+                             "paper512"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--profile-sweeps", type=int, default=0, metavar="S",
                     help="untimed: run S sweeps of the workload with one launch per stage (no graphs) "

@@ -102,6 +102,12 @@ def _load():
             lib.ora_beta_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.c_uint32, ctypes.c_uint32]
             lib.ora_beta_normal.restype = ctypes.c_double
+            lib.ora_iat.argtypes = [f64p, ctypes.c_int64]
+            lib.ora_iat.restype = ctypes.c_double
+            lib.ora_psrf.argtypes = [f64p, ctypes.c_int32, ctypes.c_int64]
+            lib.ora_psrf.restype = ctypes.c_double
+            lib.ora_psrf_moments.argtypes = [f64p, f64p, ctypes.c_int32, ctypes.c_int64]
+            lib.ora_psrf_moments.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -329,3 +335,31 @@ def initial_state(y, chains, tau0=1.0, sigma2_0=1.0, x0=None, beta0=0.0):
     sig = np.broadcast_to(np.asarray(sigma2_0, dtype=np.float64), (chains,)).copy()
     b0 = np.broadcast_to(np.asarray(beta0, dtype=np.float64), (chains,)).copy()
     return State(x, tau, sig, beta0=b0)
+
+
+# --------------------------------------------------------------------------------------------
+# Chain diagnostics
+# --------------------------------------------------------------------------------------------
+def iat(x):
+    """Integrated autocorrelation time by Geyer's initial monotone sequence (NaN if undefined)."""
+    xx = _f64(x)
+    return _load().ora_iat(_ptr(xx, ctypes.c_double), len(xx))
+
+
+def ess(x):
+    """Effective sample size N / IAT."""
+    return len(x) / iat(x)
+
+
+def psrf(chains):
+    """Potential scale reduction factor of chains [m, N] (Brooks-Gelman form)."""
+    xx = np.ascontiguousarray(chains, dtype=np.float64)
+    m, N = xx.shape
+    return _load().ora_psrf(_ptr(xx, ctypes.c_double), m, N)
+
+
+def psrf_moments(means, variances, N):
+    """PSRF from per-chain means and variances (divisor N - 1) of N values each."""
+    mu, var = _f64(means), _f64(variances)
+    return _load().ora_psrf_moments(_ptr(mu, ctypes.c_double), _ptr(var, ctypes.c_double), len(mu), int(N))
+

@@ -477,3 +477,89 @@ int32_t ora_run(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const
     free(deg);
     return fallbacks;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Diagnostics of the chains (Sec. 3.1 reports ESS, IAT and CES = IAT T / N of the tau^2 chain, */
+/* and Gelman plots)                                                                            */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Integrated autocorrelation time kappa of x[0..N-1] by Geyer's initial monotone sequence
+ * estimator (Geyer 1992, Statistical Science 7, Sec. 3.3):
+ *   gamma(k) = (1/N) sum_{t=0}^{N-1-k} (x_t - mean)(x_{t+k} - mean),
+ *   Gamma_m = gamma(2m) + gamma(2m+1) for 2m+1 <= N-1,
+ *   M = the largest m with Gamma_0, ..., Gamma_m all > 0 (M = 0 when Gamma_0 <= 0),
+ *   Gamma~_m = min(Gamma_0, ..., Gamma_m),
+ *   kappa = (-gamma(0) + 2 sum_{m=0}^{M} Gamma~_m) / gamma(0),
+ * floored at 1 / log10(N) (an effective sample size of at most N log10 N).  NaN when N < 4 or
+ * the chain is constant. */
+double ora_iat(const double *x, int64_t N)
+{
+    if (N < 4) return NAN;
+    double mean = 0.0;
+    for (int64_t t = 0; t < N; ++t) mean += x[t];
+    mean /= (double)N;
+    double g0 = 0.0;
+    for (int64_t t = 0; t < N; ++t) g0 += (x[t] - mean) * (x[t] - mean);
+    g0 /= (double)N;
+    if (!(g0 > 0.0)) return NAN;
+    double sum = 0.0, run_min = INFINITY;
+    for (int64_t m = 0; 2 * m + 1 <= N - 1; ++m) {
+        double G = 0.0;
+        for (int64_t k = 2 * m; k <= 2 * m + 1; ++k) {
+            double gk = 0.0;
+            for (int64_t t = 0; t + k < N; ++t) gk += (x[t] - mean) * (x[t + k] - mean);
+            G += gk / (double)N;
+        }
+        if (m > 0 && !(G > 0.0)) break;
+        if (G < run_min) run_min = G;
+        sum += run_min;
+        if (!(G > 0.0)) break; /* m == 0 with Gamma_0 <= 0 */
+    }
+    double kappa = (-g0 + 2.0 * sum) / g0;
+    double floor_k = 1.0 / log10((double)N);
+    return kappa < floor_k ? floor_k : kappa;
+}
+
+/* Potential scale reduction factor of m chains of N values each, x[c*N + t] (Gelman & Rubin
+ * 1992, with the (m + 1)/m factor of Brooks & Gelman 1998):
+ *   W = mean over chains of the within-chain variance (divisor N - 1),
+ *   B/N = variance of the chain means (divisor m - 1),
+ *   V = (N - 1)/N W + (m + 1)/m B/N,   R = sqrt(V / W).
+ * NaN when m < 2, N < 2 or W = 0. */
+double ora_psrf_moments(const double *mean, const double *var, int32_t m, int64_t N)
+{
+    if (m < 2 || N < 2) return NAN;
+    double W = 0.0, mm = 0.0;
+    for (int32_t c = 0; c < m; ++c) {
+        W += var[c];
+        mm += mean[c];
+    }
+    W /= (double)m;
+    mm /= (double)m;
+    double BN = 0.0;
+    for (int32_t c = 0; c < m; ++c) BN += (mean[c] - mm) * (mean[c] - mm);
+    BN /= (double)(m - 1);
+    if (!(W > 0.0)) return NAN;
+    double V = (double)(N - 1) / (double)N * W + (double)(m + 1) / (double)m * BN;
+    return sqrt(V / W);
+}
+
+double ora_psrf(const double *x, int32_t m, int64_t N)
+{
+    if (m < 2 || N < 2) return NAN;
+    double *mean = (double *)malloc(sizeof(double) * (size_t)m);
+    double *var = (double *)malloc(sizeof(double) * (size_t)m);
+    for (int32_t c = 0; c < m; ++c) {
+        const double *xc = x + (int64_t)c * N;
+        double s = 0.0;
+        for (int64_t t = 0; t < N; ++t) s += xc[t];
+        mean[c] = s / (double)N;
+        double v = 0.0;
+        for (int64_t t = 0; t < N; ++t) v += (xc[t] - mean[c]) * (xc[t] - mean[c]);
+        var[c] = v / (double)(N - 1);
+    }
+    double r = ora_psrf_moments(mean, var, m, N);
+    free(mean);
+    free(var);
+    return r;
+}
