@@ -422,6 +422,19 @@ def run_ours(args):
     dev_s_max = max_over_ranks(dev_s, world, device="cuda")
     value = world * units * args.steps / dev_s_max
 
+    # Statistical efficiency of the last timed run (Sec. 3.1): IAT and ESS of the tau^2 chains
+    # over the retained sweeps, on the device, and the cost per effective sample
+    # CES = kappa T / N with T the run's time; pooled over the chains: T / sum of their ESS.
+    efficiency = None
+    retained = spec["sweeps"] - spec["burn_in"]
+    if len(spec["fields"]) == 1 and retained >= 4:
+        d = s.trace_diagnostics(0, g.PARAM_TAU2, retained)
+        t_run = dev_s / args.steps
+        efficiency = {"param": "tau^2", "retained": retained, "iat": [float(v) for v in d["iat"]],
+                      "ess": [float(v) for v in d["ess"]],
+                      "psrf": None if d["psrf"] != d["psrf"] else float(d["psrf"]),
+                      "ces_s": t_run / float(np.sum(d["ess"])), "run_s": t_run}
+
     # Each stage of a sweep alone: back-to-back launches, CUDA events on the launching stream
     # (accumulation off); the dominant stage is the one with the longest launch.
     reps = 50
@@ -526,7 +539,8 @@ def run_ours(args):
             "gpu_launches": launches,
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "plain_fp64": plain}
+            "plain_fp64": plain,
+            "efficiency": efficiency}
     if plain:
         plain["speedup"] = value / plain["value"]
     print(json.dumps(line))

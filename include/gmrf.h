@@ -250,6 +250,41 @@ gmrf_status gmrf_fetch_samples(gmrf_sampler *s, int32_t field, int32_t chain, do
 gmrf_status gmrf_fetch_intercept(gmrf_sampler *s, int32_t field, int32_t chain, int64_t trace_cap,
                                  double *beta0_trace, int64_t *n_trace, double *beta0_now);
 
+/* Parameters whose traces gmrf_trace_diagnostics reads. */
+typedef enum {
+    GMRF_PARAM_TAU2 = 0,      /* tau^2 = 1/tau, the paper's variance parameter of the prior  */
+    GMRF_PARAM_SIGMA2 = 1,
+    GMRF_PARAM_BETA0 = 2,     /* only with model.intercept                                   */
+    GMRF_PARAM_TAU = 3        /* the precision tau itself                                    */
+} gmrf_param;
+
+/*
+ * Chain diagnostics of one parameter of one field (Sec. 3.1 compares samplers by the IAT kappa
+ * and effective sample size of the tau^2 chain and by the cost per effective sample
+ * CES = kappa T / N, T the run time and N the retained sample).  Over the last n_last values of
+ * the trace (0: all available; at most opts.trace_capacity), on the device:
+ *   iat[chains]: kappa by Geyer's initial monotone sequence estimator (Geyer 1992, Sec. 3.3):
+ *     gamma(k) = (1/N) sum_t (x_t - mean)(x_{t+k} - mean), Gamma_m = gamma(2m) + gamma(2m+1),
+ *     kappa = (-gamma(0) + 2 sum_{m<=M} min(Gamma_0..Gamma_m)) / gamma(0), M the last m of the
+ *     initial positive sequence, floored at 1/log10(N); NaN for N < 4 or a constant chain;
+ *   ess[chains]: N / kappa;
+ *   psrf: potential scale reduction factor over the chains (Gelman & Rubin 1992 with the
+ *     (m + 1)/m factor of Brooks & Gelman 1998), NaN with one chain.
+ * Any output may be NULL.  Synchronises the stream.  Errors: GMRF_E_INVALID (bad field or
+ * param, fewer than 2 values), GMRF_E_UNSUPPORTED (plain algorithm), GMRF_E_STATE, GMRF_E_CUDA.
+ */
+gmrf_status gmrf_trace_diagnostics(gmrf_sampler *s, int32_t field, int32_t param, int64_t n_last,
+                                   double *iat, double *ess, double *psrf);
+
+/*
+ * Potential scale reduction factor of every site of one field over the chains, from the running
+ * means and variances of the accumulated sweeps (same formula as gmrf_trace_diagnostics with N
+ * = accumulated sweeps): psrf[n] in natural site order (host, may be NULL) and its maximum over
+ * the sites (NaN sites skipped).  Needs >= 2 chains and >= 2 accumulated sweeps (else
+ * GMRF_E_INVALID).  Synchronises the stream.
+ */
+gmrf_status gmrf_site_psrf(gmrf_sampler *s, int32_t field, double *psrf, double *psrf_max);
+
 /*
  * Restart the run: state, tau, sigma^2 and beta0 back to their values at creation, sweep counter back
  * to opts.start_sweep, accumulators cleared.  Asynchronous (device copies on the sampler's

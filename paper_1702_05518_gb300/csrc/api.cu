@@ -93,6 +93,8 @@ struct gmrf_sampler {
     double *gpre = nullptr;     // [gpre_batch][F * Cp][4] precomputed variates of a batch
     int32_t gpre_batch = 0;     // sweeps per batch of precomputed variates
     double *staging = nullptr;  // [max_n] doubles for fetch
+    double *diag_work = nullptr;  // [Cp][trace_capacity] scratch of the trace diagnostics
+    double *diag_out = nullptr;   // [Cp][4] per-chain results, then the PSRF and a max slot
     void *x_init = nullptr;     // state at creation (for gmrf_sampler_reset)
     double *tau_init = nullptr, *sig2_init = nullptr, *beta_init = nullptr;
     void *hyp_init = nullptr;
@@ -958,6 +960,8 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     CK(s->alloc_t(&s->trace_tau, nh * s->opts.trace_capacity, sizeof(double)));
     CK(s->alloc_t(&s->trace_sig, nh * s->opts.trace_capacity, sizeof(double)));
     if (s->model.intercept) CK(s->alloc_t(&s->trace_beta, nh * s->opts.trace_capacity, sizeof(double)));
+    CK(s->alloc_t(&s->diag_work, static_cast<size_t>(Cp) * s->opts.trace_capacity, sizeof(double)));
+    CK(s->alloc_t(&s->diag_out, static_cast<size_t>(Cp) * 4 + 2, sizeof(double)));
     // Initial state kept for gmrf_sampler_reset.
     s->nh = nh;
     s->x_bytes = static_cast<size_t>(slots) * Cp * T;
@@ -1232,6 +1236,88 @@ gmrf_status gmrf_fetch_intercept(gmrf_sampler *s, int32_t field, int32_t chain, 
         }
         if (beta0_now) CK(cudaMemcpyAsync(beta0_now, s->beta + hc, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));
+    } catch (const CudaFail &f) {
+        s->poisoned = true;
+        return cuda_status(f);
+    }
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_trace_diagnostics(gmrf_sampler *s, int32_t field, int32_t param, int64_t n_last, double *iat,
+                                   double *ess, double *psrf)
+{
+    g_last_error.clear();
+    if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
+    if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "diagnostics of the plain sweep");
+    if (field < 0 || field >= s->nfields) return fail(GMRF_E_INVALID, "field out of range");
+    if (param < GMRF_PARAM_TAU2 || param > GMRF_PARAM_TAU) return fail(GMRF_E_INVALID, "param");
+    if (param == GMRF_PARAM_BETA0 && !s->model.intercept) return fail(GMRF_E_INVALID, "the model has no intercept");
+    if (n_last < 0) return fail(GMRF_E_INVALID, "n_last must be >= 0");
+    try {
+        SweepCtl c{};
+        CK(cudaMemcpyAsync(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        const int64_t cap = s->opts.trace_capacity;
+        const int64_t avail = std::min<int64_t>(c.sweep - s->opts.start_sweep, cap);
+        const int64_t N = n_last == 0 ? avail : std::min<int64_t>(n_last, avail);
+        if (N < 2) return fail(GMRF_E_INVALID, "fewer than 2 trace values available");
+        const double *base = param == GMRF_PARAM_SIGMA2 ? s->trace_sig
+                             : param == GMRF_PARAM_BETA0 ? s->trace_beta : s->trace_tau;
+        DiagArgs a{};
+        a.trace = base + static_cast<int64_t>(field) * s->Cp * cap;
+        a.cap = cap;
+        a.sweep = c.sweep;
+        a.N = N;
+        a.reciprocal = param == GMRF_PARAM_TAU2 ? 1 : 0;
+        a.chains = s->C;
+        a.work = s->diag_work;
+        a.out = s->diag_out;
+        a.psrf = s->diag_out + static_cast<int64_t>(s->Cp) * 4;
+        CK(launch_trace_diagnostics(a, s->stream));
+        std::vector<double> h(static_cast<size_t>(s->C) * 4 + 1);
+        CK(cudaMemcpyAsync(h.data(), s->diag_out, sizeof(double) * s->C * 4, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaMemcpyAsync(h.data() + s->C * 4, a.psrf, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        for (int q = 0; q < s->C; ++q) {
+            if (iat) iat[q] = h[q * 4];
+            if (ess) ess[q] = h[q * 4 + 1];
+        }
+        if (psrf) *psrf = h[s->C * 4];
+    } catch (const CudaFail &f) {
+        s->poisoned = true;
+        return cuda_status(f);
+    }
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_site_psrf(gmrf_sampler *s, int32_t field, double *psrf, double *psrf_max)
+{
+    g_last_error.clear();
+    if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
+    if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "diagnostics of the plain sweep");
+    if (field < 0 || field >= s->nfields) return fail(GMRF_E_INVALID, "field out of range");
+    if (s->C < 2) return fail(GMRF_E_INVALID, "the PSRF needs at least 2 chains");
+    try {
+        SweepCtl c{};
+        CK(cudaMemcpyAsync(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        if (c.acc_count < 2) return fail(GMRF_E_INVALID, "the PSRF needs at least 2 accumulated sweeps");
+        unsigned long long *mx = reinterpret_cast<unsigned long long *>(s->diag_out + static_cast<int64_t>(s->Cp) * 4 + 1);
+        CK(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s->stream));
+        CK(launch_site_psrf(s->precision, s->fields_dev, s->fd[field], field, s->Cp, s->C, s->mean, s->m2, c.acc_count,
+                            s->perm_inv, s->staging, mx, s->stream));
+        const int64_t n = s->hf[field].n;
+        if (psrf) CK(cudaMemcpyAsync(psrf, s->staging, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+        unsigned long long bits = 0;
+        CK(cudaMemcpyAsync(&bits, mx, sizeof(bits), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        if (psrf_max) {
+            double v = NAN;
+            if (bits) std::memcpy(&v, &bits, sizeof(v));
+            *psrf_max = v;
+        }
     } catch (const CudaFail &f) {
         s->poisoned = true;
         return cuda_status(f);

@@ -137,6 +137,25 @@ cudaError_t prepare_lattice_fused(int precision, int V, int kind, size_t smem);
 cudaError_t launch_lattice_fused(int precision, int V, int kind, const FusedArgs &a, size_t smem,
                                  cudaStream_t stream);
 
+// Chain diagnostics (diagnostics.cu): one parameter trace of every chain of one field.
+struct DiagArgs {
+    const double *trace;   // [chains][cap] ring buffers; the value of sweep t sits at t % cap
+    long long cap;
+    long long sweep;       // sweeps done: the last N values are those of sweeps sweep-N .. sweep-1
+    long long N;           // values used (4 <= N <= min(cap, available) for an IAT)
+    int32_t reciprocal;    // 1: use 1 / value (tau^2 from the tau trace)
+    int32_t chains;
+    double *work;          // [chains][N] scratch
+    double *out;           // [chains][4]: IAT, ESS, mean, variance (divisor N - 1)
+    double *psrf;          // [1] potential scale reduction factor over the chains
+};
+cudaError_t launch_trace_diagnostics(const DiagArgs &a, cudaStream_t stream);
+// Per-site potential scale reduction from the running means and M2 (count accumulated sweeps),
+// natural order into out[n]; the maximum's bit pattern into *max_bits (atomic max, caller zeroes).
+cudaError_t launch_site_psrf(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx, int32_t Cp,
+                             int32_t C, const void *mean, const void *m2, long long count, const int32_t *perm_inv,
+                             double *out, unsigned long long *max_bits, cudaStream_t stream);
+
 // Records msg as the calling thread's gmrf_last_error() text and returns st (api.cu).
 int record_error(int st, const char *msg);
 

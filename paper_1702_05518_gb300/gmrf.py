@@ -21,10 +21,12 @@ PRIOR_ICAR, PRIOR_PCAR = 0, 1
 FP32, FP64 = 0, 1
 ALGO_CHROMATIC, ALGO_PLAIN = 0, 1
 FLAG_PER_COLOUR = 1
+PARAM_TAU2, PARAM_SIGMA2, PARAM_BETA0, PARAM_TAU = range(4)
 
 EXPORTED = ["gmrf_color_graph", "gmrf_color_graph_noalloc", "gmrf_sampler_create", "gmrf_sampler_destroy", "gmrf_sweep",
             "gmrf_hyper_update", "gmrf_fetch_samples", "gmrf_field_colors", "gmrf_sampler_info",
             "gmrf_sampler_reset", "gmrf_launch_stage", "gmrf_fetch_intercept",
+            "gmrf_trace_diagnostics", "gmrf_site_psrf",
             "gmrf_validate_csr", "gmrf_philox_words", "gmrf_site_normals", "gmrf_last_error",
             "gmrf_version"]
 
@@ -112,6 +114,11 @@ def lib() -> ctypes.CDLL:
             L.gmrf_fetch_intercept.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, f64p, i64p,
                                                f64p]
             L.gmrf_fetch_intercept.restype = st
+            L.gmrf_trace_diagnostics.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, f64p, f64p,
+                                                 f64p]
+            L.gmrf_trace_diagnostics.restype = st
+            L.gmrf_site_psrf.argtypes = [vp, ctypes.c_int32, f64p, f64p]
+            L.gmrf_site_psrf.restype = st
             L.gmrf_field_colors.argtypes = [vp, ctypes.c_int32, i32p, i32p]
             L.gmrf_field_colors.restype = st
             L.gmrf_sampler_info.argtypes = [vp, P(Info)]
@@ -344,6 +351,23 @@ class Sampler:
                                           ctypes.byref(nt), ctypes.byref(b)))
         m = min(int(trace), nt.value)
         return {"beta0": b.value, "beta0_trace": tb[:m], "n_trace": nt.value}
+
+    def trace_diagnostics(self, field=0, param=PARAM_TAU2, n_last=0):
+        """IAT (Geyer's initial monotone sequence), ESS per chain and the PSRF over chains of the
+        last n_last trace values (0: all) of one parameter, computed on the device."""
+        iat = np.zeros(self.chains)
+        ess = np.zeros(self.chains)
+        ps = ctypes.c_double(0)
+        _check(lib().gmrf_trace_diagnostics(self._h, field, int(param), int(n_last), _p(iat, ctypes.c_double),
+                                            _p(ess, ctypes.c_double), ctypes.byref(ps)))
+        return {"iat": iat, "ess": ess, "psrf": ps.value}
+
+    def site_psrf(self, field=0):
+        """Per-site PSRF over chains (natural order) and its maximum."""
+        out = np.zeros(int(self.fields[field]["n"]))
+        mx = ctypes.c_double(0)
+        _check(lib().gmrf_site_psrf(self._h, field, _p(out, ctypes.c_double), ctypes.byref(mx)))
+        return out, mx.value
 
     def fetch_x(self, field=0, chain=0):
         n = int(self.fields[field]["n"])
