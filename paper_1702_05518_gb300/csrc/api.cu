@@ -78,6 +78,10 @@ struct gmrf_sampler {
     TileXY *ftiles_dev = nullptr;
     int32_t ftile_off[4] = {0, 0, 0, 0}, ftile_cnt[4] = {0, 0, 0, 0};
     int32_t fTR[4] = {0, 0, 0, 0}, fTC[4] = {0, 0, 0, 0}, fNT[4] = {512, 512, 512, 512};
+    // Quad kernel (lattice_quad.cu) for single-chain FP32 8-neighbour lattices: quad columns per
+    // staged row (0: not used) and quads per thread.
+    int32_t fQCS[4] = {0, 0, 0, 0}, fNQ[4] = {0, 0, 0, 0};
+    size_t fsmem_gen[4] = {0, 0, 0, 0};  // the quad tiling's shared memory in lattice_fused_kernel
     size_t fsmem[4] = {0, 0, 0, 0};
     FieldDev *fields_dev = nullptr;
     Tile *tiles_dev = nullptr;
@@ -480,9 +484,15 @@ cudaError_t enqueue_stage(gmrf_sampler *s, size_t k, int update, int accumulate,
                           int end_of_sweep, cudaStream_t st)
 {
     const gmrf_sampler::Stage &g = s->stages[k];
-    if (g.type == 1)
-        return launch_lattice_fused(s->precision, s->V, g.kind, fused_args(s, g.kind, update, accumulate),
-                                    s->fsmem[g.kind], st);
+    if (g.type == 1) {
+        FusedArgs fa = fused_args(s, g.kind, update, accumulate);
+        if (s->fQCS[g.kind]) {
+            if (update) return launch_lattice_quad(s->fQCS[g.kind], s->fNT[g.kind], s->fNQ[g.kind], fa, s->fsmem[g.kind], st);
+            fa.threads = 1024;
+            return launch_lattice_fused(s->precision, s->V, g.kind, fa, s->fsmem_gen[g.kind], st);
+        }
+        return launch_lattice_fused(s->precision, s->V, g.kind, fa, s->fsmem[g.kind], st);
+    }
     if (g.type == 0)
         return launch_colour_step(s->precision, s->V, g.kind, step_args(s, g.colour, g.kind, update, accumulate), st);
     return launch_hyper(s->precision, hyper_args(s, draw, draw_beta, end_of_sweep), st);
@@ -776,6 +786,55 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
         if (!allow_fused || side < 16) continue;
         for (auto &h : s->hf)
             if (h.kind == kind) fused_kind[kind] = true;
+        // Quad kernel: one chain, FP32, every field of the kind with a row length that is a
+        // multiple of 4 (Philox blocks then never straddle rows).
+        bool quad_ok = kind == GMRF_LATTICE2D_8 && s->Cp == 1 && s->precision == GMRF_FP32 && fused_kind[kind];
+        for (auto &h : s->hf)
+            if (h.kind == kind && h.dims[1] % 4 != 0) quad_ok = false;
+        if (const char *env = std::getenv("GMRF_FUSED_QUAD"))
+            if (env[0] == '0') quad_ok = false;
+        if (quad_ok) {
+            // Configurations (quad columns, threads, quads per thread); tile TR x TC with
+            // TC = 2 qcs - 8 and (TR/2 + 4) qcs <= threads * quads per thread.  Cost: waves of
+            // one block per SM times quads per thread.
+            static const int cfg[4][3] = {{64, 768, 3}, {64, 1024, 2}, {32, 1024, 2}, {32, 512, 2}};
+            double best = 1e300;
+            int bq = 0, bn = 0, bm = 0, btr = 0;
+            for (auto &cf : cfg) {
+                const int qcs = cf[0], nt = cf[1], nq = cf[2];
+                const int qr_max = nq * nt / qcs;
+                const int tc = 2 * qcs - 8;
+                for (int tr = 8; (tr / 2 + 4) <= qr_max; tr += 2) {
+                    if (lattice_quad_smem(qcs, tr) > 200 * 1024) break;
+                    int64_t tiles = 0;
+                    for (auto &h : s->hf)
+                        if (h.kind == kind) tiles += static_cast<int64_t>((h.dims[0] + tr - 1) / tr) * ((h.dims[1] + tc - 1) / tc);
+                    const int quads = (tr / 2 + 4) * qcs;
+                    const double per_thread = std::ceil(static_cast<double>(quads) / nt);
+                    const double cost = std::ceil(static_cast<double>(tiles) / 152.0) * per_thread;
+                    if (cost < best * 0.999) {
+                        best = cost;
+                        bq = qcs;
+                        bn = nt;
+                        bm = nq;
+                        btr = tr;
+                    }
+                }
+            }
+            if (bq > 0) {
+                s->fQCS[kind] = bq;
+                s->fNQ[kind] = bm;
+                s->fNT[kind] = bn;
+                s->fTR[kind] = btr;
+                s->fTC[kind] = 2 * bq - 8;
+                s->fsmem[kind] = lattice_quad_smem(bq, btr);
+                CK(prepare_lattice_quad(bq, bn, bm, s->fsmem[kind]));
+                // Reduce-only passes (gmrf_hyper_update) run lattice_fused_kernel on the same tiles.
+                s->fsmem_gen[kind] = lattice_fused_smem(s->precision, kind, s->Cp, btr, 2 * bq - 8);
+                CK(prepare_lattice_fused(s->precision, s->V, kind, s->fsmem_gen[kind]));
+                continue;
+            }
+        }
         if (fused_kind[kind]) {
             int tr = side, tc = side;
             // Cost model over tile shapes and block sizes: waves of blocks (152 SMs, one block of
@@ -1365,6 +1424,7 @@ gmrf_status gmrf_launch_stage(gmrf_sampler *s, int32_t stage, int32_t accumulate
         {"hyperparameter draw", "hyperparameter draw", "hyperparameter draw", "hyperparameter draw"}};
     const gmrf_sampler::Stage &g = s->stages[stage];
     if (name) *name = kNames[g.type][g.kind < 0 ? 0 : g.kind];
+    if (name && g.type == 1 && s->fQCS[g.kind]) *name = "fused quad sweep, 2-D 8-neighbour lattice";
     const int draw = s->model.fix_hyper ? 0 : 1;
     cudaError_t e = enqueue_stage(s, static_cast<size_t>(stage), 1, accumulate ? 1 : 0, draw, 1, 1, s->stream);
     if (e != cudaSuccess) return poison(s, e, "stage launch");

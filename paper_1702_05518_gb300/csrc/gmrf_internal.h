@@ -159,6 +159,12 @@ cudaError_t launch_site_psrf(int precision, const FieldDev *fields_dev, const Fi
 // Records msg as the calling thread's gmrf_last_error() text and returns st (api.cu).
 int record_error(int st, const char *msg);
 
+// Quad kernel for single-chain FP32 8-neighbour lattices (lattice_quad.cu); tiles TR x (2 qcs - 8)
+// with TR even and origins at even rows and columns that are multiples of 4.
+size_t lattice_quad_smem(int qcs, int TR);
+cudaError_t prepare_lattice_quad(int qcs, int nt, int nq, size_t smem);
+cudaError_t launch_lattice_quad(int qcs, int nt, int nq, const FusedArgs &a, size_t smem, cudaStream_t stream);
+
 // Jones-Plassmann colouring and colour-permuted CSR layout (csr_build.cu).
 struct CsrBuild {
     int32_t n;

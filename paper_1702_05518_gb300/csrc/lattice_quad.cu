@@ -1,0 +1,297 @@
+// lattice_quad.cu -- one launch per sweep for single-chain 8-neighbour lattices in single
+// precision, with a fixed thread-to-site map.
+//
+// The 2 x 2 colouring c = 2 (i & 1) + (j & 1) of the 8-neighbour lattice puts one site of each
+// colour in every aligned 2 x 2 block of sites (a "quad").  In the colour-split layout quad
+// (u, v) is slot (u, v) of all four sub-arrays.  A block owns a TR x TC tile of sites, stages
+// the tile plus a halo of 4 sites (2 quads) into shared memory, and every thread keeps the same
+// quads through the whole sweep: it stages them, draws their four normals into registers, draws
+// its colour-c site of each quad at colour step c (Algorithm 1; step c covers the tile grown by
+// 3 - c sites, so the owned sites end exact, as in lattice_fused.cu), and writes back the owned
+// ones.  Consecutive threads hold consecutive quads of a row, so every shared-memory access of
+// a warp is to consecutive words, and the eight neighbour offsets of each colour are constants.
+//
+// Normals (the layout of include/gmrf.h with one chain: a Philox block serves 4 consecutive
+// sites of a row, site s taking normal s mod 4).  With the row length W a multiple of 4 and the
+// staged origin at a column multiple of 4, the two quads of a lane pair (v even, v + 1) cover
+// the four columns of one Philox block in each of their two rows.  The even lane draws the block
+// of the upper row and the odd lane that of the lower row; each passes the other the two words
+// it needs (one shuffle pair) and both run two Box-Muller pairs: four normals per quad and one
+// Philox block per quad, with no shared-memory traffic.
+#include <cuda_runtime.h>
+
+#include "gmrf_device.cuh"
+#include "gmrf_internal.h"
+
+namespace gmrf {
+namespace {
+
+// Direction k of the 8-neighbour stencil: (di, dj) row by row.
+__host__ __device__ constexpr int qdi(int k) { return k < 3 ? -1 : (k < 5 ? 0 : 1); }
+__host__ __device__ constexpr int qdj(int k) { return k < 3 ? k - 1 : (k == 3 ? -1 : (k == 4 ? 1 : k - 6)); }
+// Colour-(a, b) site, direction k: sub-array of the neighbour and its quad offset (floor halves).
+__host__ __device__ constexpr int qsub(int a, int b, int k) { return 2 * ((a + qdi(k)) & 1) + ((b + qdj(k)) & 1); }
+__host__ __device__ constexpr int qdu(int a, int k) { return (a + qdi(k)) >= 0 ? (a + qdi(k)) / 2 : -1; }
+__host__ __device__ constexpr int qdv(int b, int k) { return (b + qdj(k)) >= 0 ? (b + qdj(k)) / 2 : -1; }
+
+struct QuadCtx {
+    float tau, isig, beta, rho;
+    float accS, accR, accA;
+};
+
+// Colour step C for the thread's quads.
+template <int C, int QCS, int NQ, int NT>
+__device__ __forceinline__ void quad_colour_step(float *xs, const float *ys, int SUB, const float (&z)[NQ][4],
+                                                 int gi0, int gj0, int Hl, int Wl, int lo_i, int hi_i, int lo_j,
+                                                 int hi_j, int own_i0, int own_i1, int own_j0, int own_j1,
+                                                 bool interior, int nquads, QuadCtx &cx)
+{
+    constexpr int A = C >> 1, B = C & 1;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        const int q = threadIdx.x + k * NT;
+        if (q >= nquads) break;
+        const int u = q / QCS, v = q % QCS;
+        const int i = gi0 + 2 * u + A, j = gj0 + 2 * v + B;
+        if (i < lo_i || i >= hi_i || j < lo_j || j >= hi_j) continue;
+        const int base = u * QCS + v;
+        float nb[8];
+        float s = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            nb[d] = xs[qsub(A, B, d) * SUB + base + qdu(A, d) * QCS + qdv(B, d)];
+            s += nb[d];
+        }
+        float deg = 8.0f;
+        uint32_t valid = 0xffu;
+        if (!interior && (i == 0 || j == 0 || i == Hl - 1 || j == Wl - 1)) {
+            valid = 0;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const int ii = i + qdi(d), jj = j + qdj(d);
+                valid |= (ii >= 0 && ii < Hl && jj >= 0 && jj < Wl) ? (1u << d) : 0u;
+            }
+            deg = static_cast<float>(__popc(valid));
+        }
+        const float yb = ys[C * SUB + base] - cx.beta;
+        const float P = cx.tau * deg + cx.isig;
+        const float m = (cx.tau * cx.rho * s + yb * cx.isig) * rcp_approx(P);
+        const float x = m + z[k][C] * rsqrt_approx(P);
+        xs[C * SUB + base] = x;
+        if (i >= own_i0 && i < own_i1 && j >= own_j0 && j < own_j1) {
+            float e2 = 0.0f;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                if (qsub(A, B, d) < C) {  // neighbour of lower colour: final before this step
+                    const float df = x - nb[d];
+                    e2 += ((valid >> d) & 1u) ? df * df : 0.0f;
+                }
+            }
+            cx.accS += (1.0f - cx.rho) * deg * x * x + cx.rho * e2;
+            const float r = yb - x;
+            cx.accR += r * r;
+            cx.accA += r;
+        }
+    }
+}
+
+template <int QCS, int NT, int NQ>
+__global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
+{
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileXY t = a.tiles[blockIdx.x];
+    const FieldDev f = a.fields[t.field];
+    const int Hl = f.dims[0], Wl = f.dims[1];
+    const int TR = a.TR, TC = a.TC;
+    const int QR = TR / 2 + 4;         // staged quad rows
+    const int SUB = QR * QCS;          // slots per staged sub-array
+    const int nquads = SUB;
+    float *xs = reinterpret_cast<float *>(smem_raw);  // [4][QR][QCS]
+    float *ys = xs + 4 * SUB;                         // [4][QR][QCS]
+    const int gi0 = t.i0 - 4, gj0 = t.j0 - 4;        // staged origin (site units, even / multiple of 4)
+    const int gu0 = gi0 >> 1, gv0 = gj0 >> 1;         // in quads
+    const bool interior = gi0 >= 0 && gj0 >= 0 && gi0 + 2 * QR <= Hl && gj0 + 2 * QCS <= Wl;
+    const long long sweep_ll = a.ctl->sweep;
+    const uint32_t sweep = static_cast<uint32_t>(sweep_ll);
+    const float *X = static_cast<const float *>((sweep_ll & 1) ? a.x_alt : a.x) + f.slot0;
+    float *XW = static_cast<float *>((sweep_ll & 1) ? a.x : a.x_alt) + f.slot0;
+    const float *Y = static_cast<const float *>(a.y) + f.slot0;
+    const int gsub = f.rows * f.cols, gcols = f.cols;
+    QuadCtx cx;
+    {
+        const float *hyp = static_cast<const float *>(a.hyp) + static_cast<int64_t>(t.field) * kHypStride;
+        cx.tau = hyp[0];
+        cx.isig = hyp[1];
+        cx.beta = hyp[2];
+        cx.rho = static_cast<float>(a.rho);
+        cx.accS = 0.0f;
+        cx.accR = 0.0f;
+        cx.accA = 0.0f;
+    }
+
+    // Stage the thread's quads: slot (u, v) of the four sub-arrays; sites off the lattice are 0.
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        const int q = threadIdx.x + k * NT;
+        if (q >= nquads) break;
+        const int u = q / QCS, v = q % QCS;
+        const int gu = gu0 + u, gv = gv0 + v;
+        const int go = gu * gcols + gv;
+        float xv[4], yv[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int i = 2 * gu + (s >> 1), j = 2 * gv + (s & 1);
+            const bool ok = interior || (gu >= 0 && gv >= 0 && i < Hl && j < Wl);
+            xv[s] = ok ? X[s * gsub + go] : 0.0f;
+            yv[s] = ok ? Y[s * gsub + go] : 0.0f;
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            xs[s * SUB + q] = xv[s];
+            ys[s * SUB + q] = yv[s];
+        }
+    }
+
+    // Normals of the thread's quads (z[k][c]: the colour-c site of quad k), in registers.
+    float z[NQ][4];
+    {
+        const uint32_t wq = static_cast<uint32_t>(Wl) >> 2;  // Philox blocks per row
+        const bool odd = threadIdx.x & 1;
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const int q = threadIdx.x + k * NT;  // the partner lane holds q ^ 1 (NT even, QCS even)
+            const int u = q / QCS, v = q % QCS;
+            const int row = 2 * (gu0 + u) + (odd ? 1 : 0);
+            const int grp = (gv0 + (v & ~1)) >> 1;  // column group: natural columns 4 grp .. 4 grp + 3
+            const uint32_t blk = static_cast<uint32_t>(row) * wq + static_cast<uint32_t>(grp);
+            const uint4 w = philox4x32_10(make_uint4(blk, sweep, f.stream, kTagX << 24), a.key);
+            // even lane: keeps (w0, w1) of the upper row, gets (w0, w1) of the lower row;
+            // odd lane: keeps (w2, w3) of the lower row, gets (w2, w3) of the upper row.
+            const uint32_t p0 = __shfl_xor_sync(0xffffffffu, odd ? w.x : w.z, 1);
+            const uint32_t p1 = __shfl_xor_sync(0xffffffffu, odd ? w.y : w.w, 1);
+            float c0, s0, c1, s1;
+            box_muller_f32(odd ? w.z : w.x, odd ? w.w : w.y, c0, s0);  // own row
+            box_muller_f32(p0, p1, c1, s1);                          // partner's row
+            // colour c = 2a + b: row a (0 upper, 1 lower), column b within the lane's two columns
+            if (odd) {
+                z[k][0] = c1;
+                z[k][1] = s1;
+                z[k][2] = c0;
+                z[k][3] = s0;
+            } else {
+                z[k][0] = c0;
+                z[k][1] = s0;
+                z[k][2] = c1;
+                z[k][3] = s1;
+            }
+        }
+    }
+    __syncthreads();
+
+    // Colour steps 0..3; step c covers the tile grown by 3 - c sites (clipped to the lattice).
+    const int own_i0 = t.i0, own_i1 = min(Hl, t.i0 + TR), own_j0 = t.j0, own_j1 = min(Wl, t.j0 + TC);
+#define GMRF_QUAD_STEP(C)                                                                                        \
+    quad_colour_step<C, QCS, NQ, NT>(xs, ys, SUB, z, gi0, gj0, Hl, Wl, max(0, t.i0 - (3 - C)),                \
+                                     min(Hl, t.i0 + TR + (3 - C)), max(0, t.j0 - (3 - C)),                     \
+                                     min(Wl, t.j0 + TC + (3 - C)), own_i0, own_i1, own_j0, own_j1, interior, \
+                                     nquads, cx);                                                              \
+    __syncthreads();
+    GMRF_QUAD_STEP(0)
+    GMRF_QUAD_STEP(1)
+    GMRF_QUAD_STEP(2)
+    GMRF_QUAD_STEP(3)
+#undef GMRF_QUAD_STEP
+
+    // Write-back of the owned quads' sites and the running mean / M2.
+    {
+        const bool acc = a.acc_enabled && sweep_accumulated(sweep_ll, a.burn_in, a.thin);
+        float inv_k = 0.0f;
+        if (acc) inv_k = 1.0f / static_cast<float>(a.ctl->acc_count + 1);
+        float *MEAN = static_cast<float *>(a.mean) + f.slot0;
+        float *M2 = static_cast<float *>(a.m2) + f.slot0;
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const int q = threadIdx.x + k * NT;
+            if (q >= nquads) break;
+            const int u = q / QCS, v = q % QCS;
+            if (u < 2 || u >= QR - 2 || v < 2 || v >= 2 + TC / 2) continue;
+            const int gu = gu0 + u, gv = gv0 + v;
+            const int go = gu * gcols + gv;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int i = 2 * gu + (s >> 1), j = 2 * gv + (s & 1);
+                if (i >= Hl || j >= Wl) continue;
+                const float xn = xs[s * SUB + q];
+                XW[s * gsub + go] = xn;
+                if (acc) {
+                    float mu = MEAN[s * gsub + go], mm = M2[s * gsub + go];
+                    const float delta = xn - mu;
+                    mu += delta * inv_k;
+                    mm += delta * (xn - mu);
+                    MEAN[s * gsub + go] = mu;
+                    M2[s * gsub + go] = mm;
+                }
+            }
+        }
+    }
+
+    // Block reduction: warp shuffle tree, then the warps' sums in order.
+    __syncthreads();
+    float *red = ys;  // [NW][3], the observations are dead
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float sS = cx.accS, sR = cx.accR, sA = cx.accA;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        sS += __shfl_xor_sync(0xffffffffu, sS, o);
+        sR += __shfl_xor_sync(0xffffffffu, sR, o);
+        sA += __shfl_xor_sync(0xffffffffu, sA, o);
+    }
+    if (lane == 0) {
+        red[warp * 3] = sS;
+        red[warp * 3 + 1] = sR;
+        red[warp * 3 + 2] = sA;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        float sum = 0.0f;
+        for (int w = 0; w < NW; ++w) sum += red[w * 3 + threadIdx.x];
+        reinterpret_cast<double *>(a.partials + t.part)[threadIdx.x] = static_cast<double>(sum);
+    }
+}
+
+}  // namespace
+
+// Configurations: (quad columns per staged row, threads, quads per thread).
+size_t lattice_quad_smem(int qcs, int TR) { return static_cast<size_t>(8) * (TR / 2 + 4) * qcs * sizeof(float); }
+
+cudaError_t prepare_lattice_quad(int qcs, int nt, int nq, size_t smem)
+{
+#define GMRF_QUAD_CFG(Q, N, M)                                                                                   \
+    if (qcs == Q && nt == N && nq == M)                                                                       \
+        return cudaFuncSetAttribute(lattice_quad_kernel<Q, N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    static_cast<int>(smem));
+    GMRF_QUAD_CFG(64, 768, 3)
+    GMRF_QUAD_CFG(64, 1024, 2)
+    GMRF_QUAD_CFG(32, 1024, 2)
+    GMRF_QUAD_CFG(32, 512, 2)
+#undef GMRF_QUAD_CFG
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_lattice_quad(int qcs, int nt, int nq, const FusedArgs &a, size_t smem, cudaStream_t stream)
+{
+#define GMRF_QUAD_CFG(Q, N, M)                                                          \
+    if (qcs == Q && nt == N && nq == M) {                                              \
+        lattice_quad_kernel<Q, N, M><<<a.ntiles, N, smem, stream>>>(a);                \
+        return cudaGetLastError();                                                     \
+    }
+    GMRF_QUAD_CFG(64, 768, 3)
+    GMRF_QUAD_CFG(64, 1024, 2)
+    GMRF_QUAD_CFG(32, 1024, 2)
+    GMRF_QUAD_CFG(32, 512, 2)
+#undef GMRF_QUAD_CFG
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace gmrf
