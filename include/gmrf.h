@@ -144,6 +144,8 @@ typedef struct {
     int64_t hyper_fallbacks;  /* Gamma draws that hit the 64-attempt limit (normally 0)     */
     int64_t device_bytes;     /* device memory held by the sampler                          */
     int64_t launches_per_sweep; /* kernels launched per sweep                               */
+    int64_t early_start_misses; /* sweep kernels that started before their predecessor ended */
+                                /* with a wrong sweep-number prediction (normals redrawn)    */
 } gmrf_info;
 
 typedef struct gmrf_sampler gmrf_sampler;

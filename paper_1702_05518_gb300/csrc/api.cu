@@ -46,6 +46,15 @@ struct HostField {
 
 }  // namespace
 
+bool gmrf::pdl_enabled()
+{
+    static const bool on = [] {
+        const char *env = std::getenv("GMRF_PDL");
+        return !(env && env[0] == '0');
+    }();
+    return on;
+}
+
 int gmrf::record_error(int st, const char *msg)
 {
     g_last_error = msg;
@@ -1464,6 +1473,7 @@ gmrf_status gmrf_sampler_info(gmrf_sampler *s, gmrf_info *out)
     out->hyper_fallbacks = c.fallbacks;
     out->device_bytes = s->bytes;
     out->launches_per_sweep = s->launches_per_sweep;
+    out->early_start_misses = c.fmiss;
     return GMRF_OK;
 }
 

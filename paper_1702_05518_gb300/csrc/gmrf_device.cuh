@@ -89,7 +89,10 @@ struct SweepCtl {
     unsigned long long ticket;  // blocks of the current hyper launch that have finished
     long long batch_base;  // first sweep of the current batch of precomputed Gamma variates
     long long batch_count; // sweeps in that batch
-    long long pad;
+    long long fnext;       // the sweep number a sweep kernel that starts early predicts (the
+                           // last such kernel's sweep + 1); checked against `sweep` before use
+    unsigned long long fticket;  // blocks of that kernel that have read fnext
+    long long fmiss;       // launches whose prediction was wrong (their normals were redrawn)
 };
 
 // Whether sweep number `sweep` is accumulated (burn-in, then every thin-th sweep).
@@ -118,6 +121,16 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 __host__ __device__ __forceinline__ uint2 philox_key(uint64_t seed)
 {
     return make_uint2(static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32));
+}
+
+// Programmatic dependent launch: a sweep kernel launched with programmatic stream serialization
+// may be scheduled before its predecessor in the stream has finished.  It waits here, before
+// it reads anything a predecessor wrote, and then lets its own successor be scheduled (which in
+// turn waits for this grid to finish).  Without that launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait_then_release()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // ------------------------------------------------------------------------------------------

@@ -2,11 +2,33 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "gmrf_device.cuh"
 
 namespace gmrf {
+
+// Sweep kernels are launched with programmatic stream serialization (see
+// pdl_wait_then_release) unless the environment sets GMRF_PDL=0.
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_sweep_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                                Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Arguments of one colour-step launch (one colour class of every field, or a reduce-only pass
 // over the current state when `update` is 0).
@@ -63,7 +85,7 @@ struct FusedArgs {
     void *m2;
     const void *hyp;     // [F * Cp][kHypStride]
     Part3 *partials;
-    const SweepCtl *ctl;
+    SweepCtl *ctl;       // the quad kernel writes ctl->fnext
     uint2 key;
     int32_t Cp;
     int32_t lanes;       // normals per site of one Philox block: min(4, Cp)

@@ -76,6 +76,7 @@ template <typename T, int V, int KIND, int kFusedBlock>
 __global__ void __launch_bounds__(kFusedBlock, (kFusedBlock == 512 && sizeof(T) == 4 && V <= 2) ? 2 : 1)
     lattice_fused_kernel(const FusedArgs a)
 {
+    pdl_wait_then_release();
     using D = Dirs<KIND>;
     constexpr bool E8 = (KIND == kLat2D8);
     constexpr int K = E8 ? 4 : 2;   // colours = halo width
@@ -451,6 +452,7 @@ __global__ void __launch_bounds__(kFusedBlock, (kFusedBlock == 512 && sizeof(T) 
 template <typename T, int KIND, int NT, int CP>
 __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4) ? 2 : 1) lattice_fused_fast(const FusedArgs a)
 {
+    pdl_wait_then_release();
     using D = Dirs<KIND>;
     constexpr bool E8 = (KIND == kLat2D8);
     constexpr int K = E8 ? 4 : 2;
@@ -757,13 +759,11 @@ cudaError_t launch_t(const FusedArgs &a, size_t smem, cudaStream_t stream)
 {
     const bool fast = a.update && a.Cp == V;  // every thread holds all chains
     if (a.threads == 1024) {
-        if (fast) lattice_fused_fast<T, KIND, 1024, V><<<a.ntiles, 1024, smem, stream>>>(a);
-        else lattice_fused_kernel<T, V, KIND, 1024><<<a.ntiles, 1024, smem, stream>>>(a);
-    } else {
-        if (fast) lattice_fused_fast<T, KIND, 512, V><<<a.ntiles, 512, smem, stream>>>(a);
-        else lattice_fused_kernel<T, V, KIND, 512><<<a.ntiles, 512, smem, stream>>>(a);
+        if (fast) return launch_sweep_kernel(lattice_fused_fast<T, KIND, 1024, V>, a.ntiles, 1024, smem, stream, a);
+        return launch_sweep_kernel(lattice_fused_kernel<T, V, KIND, 1024>, a.ntiles, 1024, smem, stream, a);
     }
-    return cudaGetLastError();
+    if (fast) return launch_sweep_kernel(lattice_fused_fast<T, KIND, 512, V>, a.ntiles, 512, smem, stream, a);
+    return launch_sweep_kernel(lattice_fused_kernel<T, V, KIND, 512>, a.ntiles, 512, smem, stream, a);
 }
 
 template <typename T, int V, int KIND>

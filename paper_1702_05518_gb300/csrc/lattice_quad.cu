@@ -18,6 +18,13 @@
 // of the upper row and the odd lane that of the lower row; each passes the other the two words
 // it needs (one shuffle pair) and both run two Box-Muller pairs: four normals per quad and one
 // Philox block per quad, with no shared-memory traffic.
+//
+// Overlap with the previous sweep's hyperparameter draw: the kernel is launched as a
+// programmatic dependent of that draw, so it may start while the draw runs.  Before waiting on
+// it, it stages the observations (constant) and draws the normals for the predicted sweep number
+// (the previous sweep kernel's number + 1); after the wait it reads the real number and draws
+// the normals again in the rare case the prediction was wrong (a reset, or stages launched
+// one by one), so the results never depend on the prediction.
 #include <cuda_runtime.h>
 
 #include "gmrf_device.cuh"
@@ -95,6 +102,36 @@ __device__ __forceinline__ void quad_colour_step(float *xs, const float *ys, int
     }
 }
 
+// Normals of the thread's quads for sweep `sweep` (z[k][c]: the colour-c site of quad k).  Every
+// lane of the warp takes part (the lane pairs exchange words), whether or not its quads exist.
+template <int QCS, int NT, int NQ>
+__device__ __forceinline__ void quad_normals(float (&z)[NQ][4], uint2 key, uint32_t sweep, uint32_t stream,
+                                             uint32_t blocks_per_row, int gu0, int gv0)
+{
+    const bool odd = threadIdx.x & 1;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        const int q = threadIdx.x + k * NT;  // the partner lane holds q ^ 1 (NT even, QCS even)
+        const int u = q / QCS, v = q % QCS;
+        const int row = 2 * (gu0 + u) + (odd ? 1 : 0);
+        const int grp = (gv0 + (v & ~1)) >> 1;  // column group: natural columns 4 grp .. 4 grp + 3
+        const uint32_t blk = static_cast<uint32_t>(row) * blocks_per_row + static_cast<uint32_t>(grp);
+        const uint4 w = philox4x32_10(make_uint4(blk, sweep, stream, kTagX << 24), key);
+        // even lane: keeps (w0, w1) of the upper row, gets (w0, w1) of the lower row;
+        // odd lane: keeps (w2, w3) of the lower row, gets (w2, w3) of the upper row.
+        const uint32_t p0 = __shfl_xor_sync(0xffffffffu, odd ? w.x : w.z, 1);
+        const uint32_t p1 = __shfl_xor_sync(0xffffffffu, odd ? w.y : w.w, 1);
+        float c0, s0, c1, s1;
+        box_muller_f32(odd ? w.z : w.x, odd ? w.w : w.y, c0, s0);  // own row
+        box_muller_f32(p0, p1, c1, s1);                          // partner's row
+        // colour c = 2a + b: row a (0 upper, 1 lower), column b within the lane's two columns
+        z[k][0] = odd ? c1 : c0;
+        z[k][1] = odd ? s1 : s0;
+        z[k][2] = odd ? c0 : c1;
+        z[k][3] = odd ? s0 : s1;
+    }
+}
+
 template <int QCS, int NT, int NQ>
 __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
 {
@@ -112,12 +149,54 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
     const int gi0 = t.i0 - 4, gj0 = t.j0 - 4;        // staged origin (site units, even / multiple of 4)
     const int gu0 = gi0 >> 1, gv0 = gj0 >> 1;         // in quads
     const bool interior = gi0 >= 0 && gj0 >= 0 && gi0 + 2 * QR <= Hl && gj0 + 2 * QCS <= Wl;
-    const long long sweep_ll = a.ctl->sweep;
-    const uint32_t sweep = static_cast<uint32_t>(sweep_ll);
-    const float *X = static_cast<const float *>((sweep_ll & 1) ? a.x_alt : a.x) + f.slot0;
-    float *XW = static_cast<float *>((sweep_ll & 1) ? a.x : a.x_alt) + f.slot0;
     const float *Y = static_cast<const float *>(a.y) + f.slot0;
     const int gsub = f.rows * f.cols, gcols = f.cols;
+
+    // Before the wait: observations (never written by a sweep) and the normals of the predicted
+    // sweep.
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        const int q = threadIdx.x + k * NT;
+        if (q >= nquads) break;
+        const int u = q / QCS, v = q % QCS;
+        const int gu = gu0 + u, gv = gv0 + v;
+        const int go = gu * gcols + gv;
+        float yv[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int i = 2 * gu + (s >> 1), j = 2 * gv + (s & 1);
+            const bool ok = interior || (gu >= 0 && gv >= 0 && i < Hl && j < Wl);
+            yv[s] = ok ? Y[s * gsub + go] : 0.0f;
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) ys[s * SUB + q] = yv[s];
+    }
+    // The prediction: thread 0 reads it and counts the block; the last block to read it
+    // replaces it (after the wait) with this sweep's number + 1.
+    __shared__ long long s_pred;
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        s_pred = *reinterpret_cast<volatile const long long *>(&a.ctl->fnext);
+        s_last = atomicAdd(&a.ctl->fticket, 1ull) == gridDim.x - 1;
+    }
+    __syncthreads();
+    const long long predicted = s_pred;
+    float z[NQ][4];
+    quad_normals<QCS, NT, NQ>(z, a.key, static_cast<uint32_t>(predicted), f.stream, static_cast<uint32_t>(Wl) >> 2, gu0,
+                              gv0);
+
+    pdl_wait_then_release();
+    const long long sweep_ll = a.ctl->sweep;
+    if (sweep_ll != predicted)
+        quad_normals<QCS, NT, NQ>(z, a.key, static_cast<uint32_t>(sweep_ll), f.stream, static_cast<uint32_t>(Wl) >> 2,
+                                  gu0, gv0);
+    if (threadIdx.x == 0 && s_last) {
+        a.ctl->fnext = sweep_ll + 1;
+        a.ctl->fticket = 0;
+        if (sweep_ll != predicted) a.ctl->fmiss += 1;
+    }
+    const float *X = static_cast<const float *>((sweep_ll & 1) ? a.x_alt : a.x) + f.slot0;
+    float *XW = static_cast<float *>((sweep_ll & 1) ? a.x : a.x_alt) + f.slot0;
     QuadCtx cx;
     {
         const float *hyp = static_cast<const float *>(a.hyp) + static_cast<int64_t>(t.field) * kHypStride;
@@ -130,7 +209,8 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
         cx.accA = 0.0f;
     }
 
-    // Stage the thread's quads: slot (u, v) of the four sub-arrays; sites off the lattice are 0.
+    // Stage the state of the thread's quads: slot (u, v) of the four sub-arrays; sites off the
+    // lattice are 0.
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
         const int q = threadIdx.x + k * NT;
@@ -138,54 +218,15 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
         const int u = q / QCS, v = q % QCS;
         const int gu = gu0 + u, gv = gv0 + v;
         const int go = gu * gcols + gv;
-        float xv[4], yv[4];
+        float xv[4];
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const int i = 2 * gu + (s >> 1), j = 2 * gv + (s & 1);
             const bool ok = interior || (gu >= 0 && gv >= 0 && i < Hl && j < Wl);
             xv[s] = ok ? X[s * gsub + go] : 0.0f;
-            yv[s] = ok ? Y[s * gsub + go] : 0.0f;
         }
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            xs[s * SUB + q] = xv[s];
-            ys[s * SUB + q] = yv[s];
-        }
-    }
-
-    // Normals of the thread's quads (z[k][c]: the colour-c site of quad k), in registers.
-    float z[NQ][4];
-    {
-        const uint32_t wq = static_cast<uint32_t>(Wl) >> 2;  // Philox blocks per row
-        const bool odd = threadIdx.x & 1;
-#pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-            const int q = threadIdx.x + k * NT;  // the partner lane holds q ^ 1 (NT even, QCS even)
-            const int u = q / QCS, v = q % QCS;
-            const int row = 2 * (gu0 + u) + (odd ? 1 : 0);
-            const int grp = (gv0 + (v & ~1)) >> 1;  // column group: natural columns 4 grp .. 4 grp + 3
-            const uint32_t blk = static_cast<uint32_t>(row) * wq + static_cast<uint32_t>(grp);
-            const uint4 w = philox4x32_10(make_uint4(blk, sweep, f.stream, kTagX << 24), a.key);
-            // even lane: keeps (w0, w1) of the upper row, gets (w0, w1) of the lower row;
-            // odd lane: keeps (w2, w3) of the lower row, gets (w2, w3) of the upper row.
-            const uint32_t p0 = __shfl_xor_sync(0xffffffffu, odd ? w.x : w.z, 1);
-            const uint32_t p1 = __shfl_xor_sync(0xffffffffu, odd ? w.y : w.w, 1);
-            float c0, s0, c1, s1;
-            box_muller_f32(odd ? w.z : w.x, odd ? w.w : w.y, c0, s0);  // own row
-            box_muller_f32(p0, p1, c1, s1);                          // partner's row
-            // colour c = 2a + b: row a (0 upper, 1 lower), column b within the lane's two columns
-            if (odd) {
-                z[k][0] = c1;
-                z[k][1] = s1;
-                z[k][2] = c0;
-                z[k][3] = s0;
-            } else {
-                z[k][0] = c0;
-                z[k][1] = s0;
-                z[k][2] = c1;
-                z[k][3] = s1;
-            }
-        }
+        for (int s = 0; s < 4; ++s) xs[s * SUB + q] = xv[s];
     }
     __syncthreads();
 
@@ -283,8 +324,7 @@ cudaError_t launch_lattice_quad(int qcs, int nt, int nq, const FusedArgs &a, siz
 {
 #define GMRF_QUAD_CFG(Q, N, M)                                                          \
     if (qcs == Q && nt == N && nq == M) {                                              \
-        lattice_quad_kernel<Q, N, M><<<a.ntiles, N, smem, stream>>>(a);                \
-        return cudaGetLastError();                                                     \
+        return launch_sweep_kernel(lattice_quad_kernel<Q, N, M>, a.ntiles, N, smem, stream, a); \
     }
     GMRF_QUAD_CFG(64, 768, 3)
     GMRF_QUAD_CFG(64, 1024, 2)

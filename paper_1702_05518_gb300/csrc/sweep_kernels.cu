@@ -322,6 +322,7 @@ __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, Si
 template <typename T, int V, int KIND>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_kernel(const StepArgs a)
 {
+    pdl_wait_then_release();
     const Tile t = a.tiles[blockIdx.x];
     const FieldDev f = a.fields[t.field];
     const int CV = a.Cp / V;
@@ -408,6 +409,7 @@ constexpr int kHyperWarps = 8;
 template <typename T>
 __global__ void __launch_bounds__(kHyperWarps * 32) hyper_kernel(const HyperArgs a)
 {
+    pdl_wait_then_release();
     const int lane = threadIdx.x & 31;
     const int task = blockIdx.x * kHyperWarps + (threadIdx.x >> 5);
     const int ntasks = a.nfields * a.Cp * 2;
@@ -576,6 +578,7 @@ __global__ void site_normals_kernel(uint2 key, uint32_t sweep, uint32_t stream, 
 // per-sweep draw reduces to a division by the rate (and a shift for the intercept).
 __global__ void gamma_pre_kernel(const GammaPreArgs a)
 {
+    pdl_wait_then_release();
     const long long base = a.ctl->sweep;
     const int npairs = a.nfields * a.Cp;
     const int total = a.count * npairs * 4;
@@ -611,6 +614,7 @@ __global__ void ctl_reset_kernel(SweepCtl *ctl, long long start_sweep)
 {
     SweepCtl c{};
     c.sweep = start_sweep;
+    c.fnext = start_sweep;
     *ctl = c;
 }
 
@@ -625,16 +629,16 @@ int grid_for(int64_t n, int block)
 }  // namespace
 
 template <int KIND>
-void launch_kind(int precision, int V, const StepArgs &a, cudaStream_t stream)
+cudaError_t launch_kind(int precision, int V, const StepArgs &a, cudaStream_t stream)
 {
     const dim3 grid(a.ntiles), block(kBlock);
     if (precision == 0) {
-        if (V == 4) colour_step_kernel<float, 4, KIND><<<grid, block, 0, stream>>>(a);
-        else if (V == 2) colour_step_kernel<float, 2, KIND><<<grid, block, 0, stream>>>(a);
-        else colour_step_kernel<float, 1, KIND><<<grid, block, 0, stream>>>(a);
+        if (V == 4) return launch_sweep_kernel(colour_step_kernel<float, 4, KIND>, grid, block, 0, stream, a);
+        if (V == 2) return launch_sweep_kernel(colour_step_kernel<float, 2, KIND>, grid, block, 0, stream, a);
+        return launch_sweep_kernel(colour_step_kernel<float, 1, KIND>, grid, block, 0, stream, a);
     } else {
-        if (V == 2) colour_step_kernel<double, 2, KIND><<<grid, block, 0, stream>>>(a);
-        else colour_step_kernel<double, 1, KIND><<<grid, block, 0, stream>>>(a);
+        if (V == 2) return launch_sweep_kernel(colour_step_kernel<double, 2, KIND>, grid, block, 0, stream, a);
+        return launch_sweep_kernel(colour_step_kernel<double, 1, KIND>, grid, block, 0, stream, a);
     }
 }
 
@@ -642,20 +646,18 @@ cudaError_t launch_colour_step(int precision, int V, int kind, const StepArgs &a
 {
     if (a.ntiles <= 0) return cudaSuccess;
     switch (kind) {
-    case kLat2D4: launch_kind<kLat2D4>(precision, V, a, stream); break;
-    case kLat2D8: launch_kind<kLat2D8>(precision, V, a, stream); break;
-    case kLat3D6: launch_kind<kLat3D6>(precision, V, a, stream); break;
-    default: launch_kind<kCsr>(precision, V, a, stream); break;
+    case kLat2D4: return launch_kind<kLat2D4>(precision, V, a, stream);
+    case kLat2D8: return launch_kind<kLat2D8>(precision, V, a, stream);
+    case kLat3D6: return launch_kind<kLat3D6>(precision, V, a, stream);
+    default: return launch_kind<kCsr>(precision, V, a, stream);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_hyper(int precision, const HyperArgs &a, cudaStream_t stream)
 {
     const int grid = (a.nfields * a.Cp * 2 + kHyperWarps - 1) / kHyperWarps;
-    if (precision == 0) hyper_kernel<float><<<grid, kHyperWarps * 32, 0, stream>>>(a);
-    else hyper_kernel<double><<<grid, kHyperWarps * 32, 0, stream>>>(a);
-    return cudaGetLastError();
+    if (precision == 0) return launch_sweep_kernel(hyper_kernel<float>, grid, kHyperWarps * 32, 0, stream, a);
+    return launch_sweep_kernel(hyper_kernel<double>, grid, kHyperWarps * 32, 0, stream, a);
 }
 
 cudaError_t launch_pack(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx, int32_t C,
@@ -690,8 +692,7 @@ cudaError_t launch_gamma_pre(const GammaPreArgs &a, cudaStream_t stream)
 {
     const int total = a.count * a.nfields * a.Cp * 4;
     if (total <= 0) return cudaSuccess;
-    gamma_pre_kernel<<<(total + 127) / 128, 128, 0, stream>>>(a);
-    return cudaGetLastError();
+    return launch_sweep_kernel(gamma_pre_kernel, (total + 127) / 128, 128, 0, stream, a);
 }
 
 cudaError_t launch_ctl_reset(SweepCtl *ctl, long long start_sweep, cudaStream_t stream)

@@ -70,7 +70,7 @@ class Info(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("max_colors", ctypes.c_int32),
                 ("sweeps_done", ctypes.c_int64), ("accumulated", ctypes.c_int64),
                 ("hyper_fallbacks", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("launches_per_sweep", ctypes.c_int64)]
+                ("launches_per_sweep", ctypes.c_int64), ("early_start_misses", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
