@@ -1205,8 +1205,8 @@ gmrf_status gmrf_hyper_update(gmrf_sampler *s)
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
     if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "hyper_update on the plain sweep");
     cudaError_t e = cudaSuccess;
-    for (size_t k = 0; k + 1 < s->stages.size() && e == cudaSuccess; ++k)
-        e = enqueue_stage(s, k, 0, 0, 0, 0, 0, s->stream);
+    for (size_t k = 0; k < s->stages.size() && e == cudaSuccess; ++k)
+        if (s->stages[k].type != 2) e = enqueue_stage(s, k, 0, 0, 0, 0, 0, s->stream);
     if (e == cudaSuccess) e = launch_hyper(s->precision, hyper_args(s, 1, 1, 0), s->stream);
     if (e != cudaSuccess) return poison(s, e, "hyper update launch");
     return GMRF_OK;

@@ -60,6 +60,32 @@ struct StepArgs {
     int32_t update;      // 1: draw the colour class; 0: only recompute the partial sums
 };
 
+struct HyperArgs {
+    const FieldDev *fields;
+    int32_t nfields;
+    int32_t Cp;
+    const Part3 *partials;
+    double *tau;          // [F * Cp]
+    double *sig2;         // [F * Cp]
+    double *beta;         // [F * Cp] intercepts (read and drawn only when draw_beta)
+    void *hyp;            // [F * Cp][kHypStride] copies in precision T
+    double *trace_tau;    // [F * Cp][cap]
+    double *trace_sig;
+    double *trace_beta;
+    int32_t trace_cap;
+    SweepCtl *ctl;
+    uint2 key;
+    double a_tau, b_tau, a_sig, b_sig;
+    int32_t draw;         // 0: keep tau, sigma^2
+    int32_t draw_beta;    // 1: draw the intercept beta0 (before sigma^2)
+    int32_t end_of_sweep; // 1: sweep counter, traces; 0: extra draw (tags 5 and 6)
+    long long burn_in;    // accumulation schedule (to advance the accumulation count)
+    int32_t thin;
+    int32_t acc_enabled;
+    const double *gpre;   // [batch][F * Cp][4]: unit-rate Gamma variates of tau and 1/sigma^2 and
+                          // the intercept's standard normal, for the batch's sweeps
+};
+
 // A tile of the fused 2-D lattice sweep: natural coordinates of its first site.
 struct TileXY {
     int32_t field;
@@ -96,31 +122,6 @@ struct FusedArgs {
     int32_t update;      // 1: run the colour steps; 0: only recompute the partial sums
 };
 
-struct HyperArgs {
-    const FieldDev *fields;
-    int32_t nfields;
-    int32_t Cp;
-    const Part3 *partials;
-    double *tau;          // [F * Cp]
-    double *sig2;         // [F * Cp]
-    double *beta;         // [F * Cp] intercepts (read and drawn only when draw_beta)
-    void *hyp;            // [F * Cp][kHypStride] copies in precision T
-    double *trace_tau;    // [F * Cp][cap]
-    double *trace_sig;
-    double *trace_beta;
-    int32_t trace_cap;
-    SweepCtl *ctl;
-    uint2 key;
-    double a_tau, b_tau, a_sig, b_sig;
-    int32_t draw;         // 0: keep tau, sigma^2
-    int32_t draw_beta;    // 1: draw the intercept beta0 (before sigma^2)
-    int32_t end_of_sweep; // 1: sweep counter, traces; 0: extra draw (tags 5 and 6)
-    long long burn_in;    // accumulation schedule (to advance the accumulation count)
-    int32_t thin;
-    int32_t acc_enabled;
-    const double *gpre;   // [batch][F * Cp][4]: unit-rate Gamma variates of tau and 1/sigma^2 and
-                          // the intercept's standard normal, for the batch's sweeps
-};
 
 // Unit-rate Gamma variates (tau and 1/sigma^2 of every field and chain) for sweeps
 // ctl->sweep .. ctl->sweep + count - 1, one thread each; records the batch in ctl.

@@ -22,6 +22,7 @@
 
 #include "gmrf_device.cuh"
 #include "gmrf_internal.h"
+#include "hyper_task.cuh"
 
 namespace gmrf {
 namespace {
@@ -386,125 +387,18 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_ke
     }
 }
 
-// One warp per task: task 2p draws tau of (field, chain) pair p, task 2p + 1 the intercept (when
-// present) and then 1/sigma^2 of pair p (given x, tau is conditionally independent of beta0 and
-// sigma^2, Sec. 3.1); eight tasks per block.  A warp sums what it needs over the field's tile
-// partials in a fixed order (lane strides, then a shuffle tree), and lane 0 draws from the full
-// conditionals, refreshes the precision-T copies the colour kernels read, and records the
-// traces.  FP64 arithmetic has a long dependent-operation latency on this GPU, so everything a
-// draw needs is loaded before the sums and the draws of all tasks run in parallel.  With a
-// single block its thread 0 advances the sweep counter (or the accumulation count or the
-// extra-draw counter) after a barrier; with several, the last block to finish does (ticket
-// counter; no block waits for another).
-//
-// Intercept: the partials hold R = sum e_i^2 and A = sum e_i with e_i = y_i - b - x_i, b the
-// copy of beta0 the sweep used.  beta0 | x, sigma^2 ~ N(1'(y - x)/n, sigma^2/n) is drawn as
-// b + delta, delta = A/n + sqrt(sigma^2/n) z, and the sigma^2 draw takes
-// sum (e_i - delta)^2 = R - 2 delta A + n delta^2 (exact algebra; delta is small next to e).
-//
-// Gamma draws: G = Marsaglia-Tsang variate at rate 1 (precomputed for the batch, or drawn here);
-// tau = G / rate, sigma^2 = rate / G (the reciprocal of the precision draw G / rate).
+// The hyperparameter stage: one warp per task of hyper_task (eight per block).  With a single
+// block its thread 0 advances the counters after a barrier; with several, the last block to
+// finish does (ticket counter; no block waits for another).
 constexpr int kHyperWarps = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(kHyperWarps * 32) hyper_kernel(const HyperArgs a)
 {
     pdl_wait_then_release();
-    const int lane = threadIdx.x & 31;
     const int task = blockIdx.x * kHyperWarps + (threadIdx.x >> 5);
-    const int ntasks = a.nfields * a.Cp * 2;
     const long long sweep = a.ctl->sweep;
-    if (task < ntasks) {
-        const int pidx = task >> 1, which = task & 1;  // which: 0 tau, 1 beta0 and sigma^2
-        const int fi = pidx / a.Cp, chain = pidx - fi * a.Cp;
-        const int64_t hc = static_cast<int64_t>(fi) * a.Cp + chain;
-        const int32_t part0 = a.fields[fi].part0, nparts = a.fields[fi].nparts;
-        // Loads of lane 0 first, so their latency overlaps the partial sums.
-        T *hyp = static_cast<T *>(a.hyp);
-        double cur = 0.0, s2old = 0.0, b = 0.0, gpv = 0.0, zb = 0.0;
-        long long extra = 0, kb = -1, bcount = 0;
-        uint32_t fstream = 0;
-        int32_t fn = 0, frank = 0;
-        if (lane == 0) {
-            cur = which ? a.sig2[hc] : a.tau[hc];
-            s2old = a.sig2[hc];
-            b = static_cast<double>(hyp[hc * kHypStride + 2]);
-            extra = a.ctl->extra;
-            kb = sweep - a.ctl->batch_base;
-            bcount = a.ctl->batch_count;
-            fstream = a.fields[fi].stream;
-            fn = a.fields[fi].n;
-            frank = a.fields[fi].rank;
-        }
-        const bool pre = a.end_of_sweep && a.gpre && kb >= 0 && kb < bcount;
-        if (lane == 0 && pre) {
-            const double *gp = a.gpre + (kb * a.nfields * a.Cp + pidx) * 4;
-            gpv = gp[which];
-            zb = gp[2];
-        }
-        const bool need_sum = which ? (a.draw || a.draw_beta) : a.draw;
-        const bool need_a = which && a.draw_beta;
-        double S = 0.0, A = 0.0;
-        if (need_sum) {
-            for (int k = lane; k < nparts; k += 32) {
-                const Part3 p = a.partials[static_cast<int64_t>(part0 + k) * a.Cp + chain];
-                S += which ? p.R : p.S;
-                if (need_a) A += p.A;
-            }
-            for (int off = 16; off >= 1; off >>= 1) S += __shfl_xor_sync(0xffffffffu, S, off);
-            if (need_a)
-                for (int off = 16; off >= 1; off >>= 1) A += __shfl_xor_sync(0xffffffffu, A, off);
-        }
-        if (lane == 0) {
-            const uint32_t word1 = static_cast<uint32_t>(a.end_of_sweep ? sweep : extra);
-            double val = cur, bval = 0.0;
-            if (which && a.draw_beta) {
-                if (!pre) {
-                    const uint32_t tag = a.end_of_sweep ? kTagBeta : kTagBetaExtra;
-                    const uint4 w = philox4x32_10(
-                        make_uint4(0u, word1, fstream, (tag << 24) | static_cast<uint32_t>(chain)), a.key);
-                    double unused;
-                    box_muller_f64(w.x, w.y, zb, unused);
-                }
-                const double delta = A / fn + sqrt(s2old / fn) * zb;
-                bval = b + delta;
-                a.beta[hc] = bval;
-                hyp[hc * kHypStride + 2] = static_cast<T>(bval);
-                S = S - 2.0 * delta * A + fn * (delta * delta);
-            } else if (which && a.trace_beta) {
-                bval = a.beta[hc];
-            }
-            if (a.draw) {
-                const double rate = which ? a.b_sig + 0.5 * S : a.b_tau + 0.5 * S;
-                double G = gpv;
-                if (!pre) {
-                    const uint32_t tag =
-                        which ? (a.end_of_sweep ? kTagSig : kTagSigExtra) : (a.end_of_sweep ? kTagTau : kTagTauExtra);
-                    const double shape = which ? a.a_sig + 0.5 * fn : a.a_tau + 0.5 * frank;
-                    int fb = 0;
-                    G = gamma_mt(shape, 1.0, a.key, word1, fstream, (tag << 24) | static_cast<uint32_t>(chain), fb);
-                    if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), 1ull);
-                }
-                if (which) {
-                    // The sweep kernels use 1/sigma^2 recomputed from sigma^2, so a run resumed
-                    // from a fetched sigma^2 continues bit for bit.
-                    val = rate / G;
-                    a.sig2[hc] = val;
-                    hyp[hc * kHypStride + 1] = static_cast<T>(1.0 / val);
-                } else {
-                    val = G / rate;
-                    a.tau[hc] = val;
-                    hyp[hc * kHypStride] = static_cast<T>(val);
-                }
-            }
-            if (a.end_of_sweep && a.trace_cap > 0) {
-                const int64_t slot = hc * a.trace_cap + (sweep % a.trace_cap);
-                (which ? a.trace_sig : a.trace_tau)[slot] = val;
-                if (which && a.trace_beta) a.trace_beta[slot] = bval;
-            }
-        }
-    }
-    // Counters: after every task of the launch has read them.
+    if (task < a.nfields * a.Cp * 2) hyper_task<T>(a, task, sweep);
     bool last = gridDim.x == 1;
     __syncthreads();
     if (!last && threadIdx.x == 0) {
@@ -512,12 +406,7 @@ __global__ void __launch_bounds__(kHyperWarps * 32) hyper_kernel(const HyperArgs
         last = atomicAdd(&a.ctl->ticket, 1ull) == gridDim.x - 1;
     }
     if (threadIdx.x == 0 && last) {
-        if (a.end_of_sweep) {
-            if (a.acc_enabled && sweep_accumulated(sweep, a.burn_in, a.thin)) a.ctl->acc_count += 1;
-            a.ctl->sweep = sweep + 1;
-        } else {
-            a.ctl->extra += 1;
-        }
+        hyper_advance(a, sweep);
         a.ctl->ticket = 0;
     }
 }
