@@ -104,6 +104,14 @@ __device__ __forceinline__ void quad_colour_step(float *xs, const float *ys, int
 
 // Normals of the thread's quads for sweep `sweep` (z[k][c]: the colour-c site of quad k).  Every
 // lane of the warp takes part (the lane pairs exchange words), whether or not its quads exist.
+// Whether site s (sub-array s = 2a + b) of staged quad (u, v) is owned by the tile and on the
+// lattice.
+__device__ __forceinline__ bool quad_owned_site(int u, int v, int s, int QR, int TC, int gu0, int gv0, int Hl, int Wl)
+{
+    if (u < 2 || u >= QR - 2 || v < 2 || v >= 2 + TC / 2) return false;
+    return 2 * (gu0 + u) + (s >> 1) < Hl && 2 * (gv0 + v) + (s & 1) < Wl;
+}
+
 template <int QCS, int NT, int NQ>
 __device__ __forceinline__ void quad_normals(float (&z)[NQ][4], uint2 key, uint32_t sweep, uint32_t stream,
                                              uint32_t blocks_per_row, int gu0, int gv0)
@@ -209,6 +217,26 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
         cx.accA = 0.0f;
     }
 
+    // The running moments of accumulated sweeps: their lines into L1 now, read after the steps.
+    const bool acc = a.acc_enabled && sweep_accumulated(sweep_ll, a.burn_in, a.thin);
+    const float inv_k = acc ? 1.0f / static_cast<float>(a.ctl->acc_count + 1) : 0.0f;
+    float *MEAN = static_cast<float *>(a.mean) + f.slot0;
+    float *M2 = static_cast<float *>(a.m2) + f.slot0;
+    if (acc) {
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const int q = threadIdx.x + k * NT;
+            const int u = q / QCS, v = q % QCS;
+            if (q >= nquads || u < 2 || u >= QR - 2 || v < 2 || v >= 2 + TC / 2) continue;
+            const int go = (gu0 + u) * gcols + gv0 + v;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(MEAN + s * gsub + go));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(M2 + s * gsub + go));
+            }
+        }
+    }
+
     // Stage the state of the thread's quads: slot (u, v) of the four sub-arrays; sites off the
     // lattice are 0.
 #pragma unroll
@@ -244,36 +272,49 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
     GMRF_QUAD_STEP(3)
 #undef GMRF_QUAD_STEP
 
-    // Write-back of the owned quads' sites and the running mean / M2.
-    {
-        const bool acc = a.acc_enabled && sweep_accumulated(sweep_ll, a.burn_in, a.thin);
-        float inv_k = 0.0f;
-        if (acc) inv_k = 1.0f / static_cast<float>(a.ctl->acc_count + 1);
-        float *MEAN = static_cast<float *>(a.mean) + f.slot0;
-        float *M2 = static_cast<float *>(a.m2) + f.slot0;
+    // Write-back of the owned quads' sites and the running mean / M2: every load of the running
+    // moments is issued before any store (the stores could alias them for the compiler), so a
+    // thread pays one memory round trip, and those lines were prefetched into L1 before the
+    // colour steps.
+    if (acc) {
+        float mu[NQ][4], mm[NQ][4];
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
             const int q = threadIdx.x + k * NT;
-            if (q >= nquads) break;
             const int u = q / QCS, v = q % QCS;
-            if (u < 2 || u >= QR - 2 || v < 2 || v >= 2 + TC / 2) continue;
-            const int gu = gu0 + u, gv = gv0 + v;
-            const int go = gu * gcols + gv;
+            const int go = (gu0 + u) * gcols + gv0 + v;
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                const int i = 2 * gu + (s >> 1), j = 2 * gv + (s & 1);
-                if (i >= Hl || j >= Wl) continue;
-                const float xn = xs[s * SUB + q];
-                XW[s * gsub + go] = xn;
-                if (acc) {
-                    float mu = MEAN[s * gsub + go], mm = M2[s * gsub + go];
-                    const float delta = xn - mu;
-                    mu += delta * inv_k;
-                    mm += delta * (xn - mu);
-                    MEAN[s * gsub + go] = mu;
-                    M2[s * gsub + go] = mm;
-                }
+                const bool ok = q < nquads && quad_owned_site(u, v, s, QR, TC, gu0, gv0, Hl, Wl);
+                mu[k][s] = ok ? MEAN[s * gsub + go] : 0.0f;
+                mm[k][s] = ok ? M2[s * gsub + go] : 0.0f;
             }
+        }
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const int q = threadIdx.x + k * NT;
+            const int u = q / QCS, v = q % QCS;
+            const int go = (gu0 + u) * gcols + gv0 + v;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                if (!(q < nquads && quad_owned_site(u, v, s, QR, TC, gu0, gv0, Hl, Wl))) continue;
+                const float xn = xs[s * SUB + q];
+                const float delta = xn - mu[k][s];
+                const float m1 = mu[k][s] + delta * inv_k;
+                XW[s * gsub + go] = xn;
+                MEAN[s * gsub + go] = m1;
+                M2[s * gsub + go] = mm[k][s] + delta * (xn - m1);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const int q = threadIdx.x + k * NT;
+            const int u = q / QCS, v = q % QCS;
+            const int go = (gu0 + u) * gcols + gv0 + v;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                if (q < nquads && quad_owned_site(u, v, s, QR, TC, gu0, gv0, Hl, Wl)) XW[s * gsub + go] = xs[s * SUB + q];
         }
     }
 
