@@ -404,6 +404,7 @@ StepArgs step_args(gmrf_sampler *s, int colour, int kind, int update, int accumu
     a.thin = s->opts.thin;
     a.acc_enabled = accumulate;
     a.update = update;
+    a.intercept = s->model.intercept ? 1 : 0;
     return a;
 }
 

@@ -58,6 +58,7 @@ struct StepArgs {
     int32_t thin;
     int32_t acc_enabled;
     int32_t update;      // 1: draw the colour class; 0: only recompute the partial sums
+    int32_t intercept;   // the model has the intercept beta0
 };
 
 struct HyperArgs {

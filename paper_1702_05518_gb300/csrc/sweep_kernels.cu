@@ -57,6 +57,14 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
 {
     const T rho = static_cast<T>(a.rho);
     T xn[V];
+    // Running moments first, so their loads do not wait behind the store of x (possible alias);
+    // with four chains per thread the registers are better spent elsewhere.
+    T mu[V], mm[V];
+    constexpr bool kEarly = V <= 2;
+    if (kEarly && cx.acc) {
+        Vec<T, V>::ld(meanp, mu);
+        Vec<T, V>::ld(m2p, mm);
+    }
     if (a.update) {
         T z[V];
         site_normals<T, V>(a.key, site, sweep, stream, chain0, a.lanes, z);
@@ -86,9 +94,10 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
         cx.accA[v] += r;
     }
     if (cx.acc) {
-        T mu[V], mm[V];
-        Vec<T, V>::ld(meanp, mu);
-        Vec<T, V>::ld(m2p, mm);
+        if (!kEarly) {
+            Vec<T, V>::ld(meanp, mu);
+            Vec<T, V>::ld(m2p, mm);
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const T delta = xn[v] - mu[v];
@@ -320,7 +329,9 @@ __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, Si
     }
 }
 
-template <typename T, int V, int KIND>
+// IC: the model has the intercept (without it beta0 = 0 and the third sum is not needed, which
+// the compiler then removes, registers included).
+template <typename T, int V, int KIND, bool IC>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_kernel(const StepArgs a)
 {
     pdl_wait_then_release();
@@ -338,7 +349,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_ke
         const int64_t hc = (static_cast<int64_t>(t.field) * a.Cp + cv * V + v) * kHypStride;
         cx.tau[v] = hyp[hc];
         cx.isig[v] = hyp[hc + 1];
-        cx.beta[v] = hyp[hc + 2];
+        cx.beta[v] = IC ? hyp[hc + 2] : static_cast<T>(0);
         cx.accS[v] = 0;
         cx.accR[v] = 0;
         cx.accA[v] = 0;
@@ -365,11 +376,11 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_ke
     for (int v = 0; v < V; ++v) {
         T sS = cx.accS[v];
         T sR = cx.accR[v];
-        T sA = cx.accA[v];
+        T sA = IC ? cx.accA[v] : static_cast<T>(0);
         for (int off = 16; off >= CV; off >>= 1) {
             sS += __shfl_xor_sync(0xffffffffu, sS, off);
             sR += __shfl_xor_sync(0xffffffffu, sR, off);
-            sA += __shfl_xor_sync(0xffffffffu, sA, off);
+            if (IC) sA += __shfl_xor_sync(0xffffffffu, sA, off);
         }
         if (lane < CV) {
             red[warp][lane * V + v][0] = sS;
@@ -521,14 +532,22 @@ template <int KIND>
 cudaError_t launch_kind(int precision, int V, const StepArgs &a, cudaStream_t stream)
 {
     const dim3 grid(a.ntiles), block(kBlock);
-    if (precision == 0) {
-        if (V == 4) return launch_sweep_kernel(colour_step_kernel<float, 4, KIND>, grid, block, 0, stream, a);
-        if (V == 2) return launch_sweep_kernel(colour_step_kernel<float, 2, KIND>, grid, block, 0, stream, a);
-        return launch_sweep_kernel(colour_step_kernel<float, 1, KIND>, grid, block, 0, stream, a);
-    } else {
-        if (V == 2) return launch_sweep_kernel(colour_step_kernel<double, 2, KIND>, grid, block, 0, stream, a);
-        return launch_sweep_kernel(colour_step_kernel<double, 1, KIND>, grid, block, 0, stream, a);
+    if (a.intercept) {
+        if (precision == 0) {
+            if (V == 4) return launch_sweep_kernel(colour_step_kernel<float, 4, KIND, true>, grid, block, 0, stream, a);
+            if (V == 2) return launch_sweep_kernel(colour_step_kernel<float, 2, KIND, true>, grid, block, 0, stream, a);
+            return launch_sweep_kernel(colour_step_kernel<float, 1, KIND, true>, grid, block, 0, stream, a);
+        }
+        if (V == 2) return launch_sweep_kernel(colour_step_kernel<double, 2, KIND, true>, grid, block, 0, stream, a);
+        return launch_sweep_kernel(colour_step_kernel<double, 1, KIND, true>, grid, block, 0, stream, a);
     }
+    if (precision == 0) {
+        if (V == 4) return launch_sweep_kernel(colour_step_kernel<float, 4, KIND, false>, grid, block, 0, stream, a);
+        if (V == 2) return launch_sweep_kernel(colour_step_kernel<float, 2, KIND, false>, grid, block, 0, stream, a);
+        return launch_sweep_kernel(colour_step_kernel<float, 1, KIND, false>, grid, block, 0, stream, a);
+    }
+    if (V == 2) return launch_sweep_kernel(colour_step_kernel<double, 2, KIND, false>, grid, block, 0, stream, a);
+    return launch_sweep_kernel(colour_step_kernel<double, 1, KIND, false>, grid, block, 0, stream, a);
 }
 
 cudaError_t launch_colour_step(int precision, int V, int kind, const StepArgs &a, cudaStream_t stream)
