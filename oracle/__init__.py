@@ -50,7 +50,8 @@ class _Model(ctypes.Structure):
     _fields_ = [("prior_proper", ctypes.c_int32), ("rho", ctypes.c_double),
                 ("a_tau", ctypes.c_double), ("b_tau", ctypes.c_double),
                 ("a_sig", ctypes.c_double), ("b_sig", ctypes.c_double),
-                ("fix_hyper", ctypes.c_int32), ("intercept", ctypes.c_int32)]
+                ("fix_hyper", ctypes.c_int32), ("intercept", ctypes.c_int32),
+                ("binomial", ctypes.c_int32), ("beta0_mean", ctypes.c_double), ("beta0_var", ctypes.c_double)]
 
 
 class _RunOpts(ctypes.Structure):
@@ -95,13 +96,20 @@ def _load():
             lib.ora_components.restype = ctypes.c_int32
             lib.ora_quadform.argtypes = [ctypes.c_int32, i32p, i32p, f64p, ctypes.c_double, f64p]
             lib.ora_quadform.restype = ctypes.c_double
-            lib.ora_run.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p, ctypes.c_int32, f64p,
+            lib.ora_run.argtypes = [ctypes.c_int32, i32p, i32p, f64p, i32p, ctypes.c_int32, f64p, i32p,
                                     ctypes.c_int32, P(_Model), P(_RunOpts), f64p, f64p, f64p,
                                     f64p, f64p, f64p, f64p, f64p, f64p, i64p, f64p]
             lib.ora_run.restype = ctypes.c_int32
             lib.ora_beta_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.c_uint32, ctypes.c_uint32]
             lib.ora_beta_normal.restype = ctypes.c_double
+            lib.ora_pg_draw.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                        ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, P(ctypes.c_int32)]
+            lib.ora_pg_draw.restype = ctypes.c_double
+            lib.ora_pg_term.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_int32]
+            lib.ora_pg_term.restype = ctypes.c_double
+            lib.ora_pg_mix_weight.argtypes = [ctypes.c_double]
+            lib.ora_pg_mix_weight.restype = ctypes.c_double
             lib.ora_iat.argtypes = [f64p, ctypes.c_int64]
             lib.ora_iat.restype = ctypes.c_double
             lib.ora_psrf.argtypes = [f64p, ctypes.c_int32, ctypes.c_int64]
@@ -182,6 +190,24 @@ def gamma_draw(shape, rate, seed, sweep, stream, tag, chain):
     g = _load().ora_gamma_draw(float(shape), float(rate), seed, sweep, stream, tag, chain,
                                ctypes.byref(att))
     return g, att.value
+
+
+def pg_draw(b, c, seed, site=0, sweep=0, stream=0, chain=0):
+    """A Polya-Gamma PG(b, c) variate (sum of b PG(1, c) by Devroye's method) with the counters of
+    the draw of (site, sweep, chain).  Returns (value, fallbacks)."""
+    fb = ctypes.c_int32(0)
+    v = _load().ora_pg_draw(int(b), float(c), seed, site, sweep, stream, chain, ctypes.byref(fb))
+    return v, fb.value
+
+
+def pg_series_term(n, x, form):
+    """Term n of the alternating series of the J*(1, 0) density: small-x form (0) or large-x (1)."""
+    return _load().ora_pg_term(int(n), float(x), int(form))
+
+
+def pg_mix_weight(z):
+    """Probability of the exponential piece of the J*(1, z) proposal."""
+    return _load().ora_pg_mix_weight(float(z))
 
 
 def beta_normal(seed, sweep, stream, chain, tag=TAG_BETA):
@@ -280,10 +306,13 @@ class State:
 
 def run(graph, colors, y, state, *, seed, nsweeps, stream=0, start_sweep=0, prior="icar",
         rho=1.0, a_tau=1.0, b_tau=0.01, a_sig=1.0, b_sig=0.01, fix_hyper=False, burn_in=0,
-        thin=1, accumulate=True, record_x=False, weights=None, intercept=False):
+        thin=1, accumulate=True, record_x=False, weights=None, intercept=False, trials=None,
+        beta0_prior=(0.0, 1000.0)):
     """Run `nsweeps` chromatic Gibbs sweeps (Algorithm 1 + conjugate tau, sigma^2 draws, and with
     `intercept` the flat-prior beta0 draw of Sec. 3.1) of every chain in `state` (modified in
-    place).  graph = (row_ptr, col_idx) in natural order.
+    place).  graph = (row_ptr, col_idx) in natural order.  With `trials` (m_i per site) the data
+    are binomial, y_i ~ Bin(m_i, logistic(beta0 + x_i)) (Sec. 3.2): Polya-Gamma augmentation,
+    beta0 ~ N(beta0_prior), no sigma^2.
 
     Returns dict(tau_trace [C, T], sigma2_trace [C, T], beta0_trace [C, T], fallbacks,
     xtrace [T, C, n] or None).
@@ -298,7 +327,9 @@ def run(graph, colors, y, state, *, seed, nsweeps, stream=0, start_sweep=0, prio
     assert state.x.shape == (C, n) and yy.shape == (n,)
     w = None if weights is None else _f64(weights)
     model = _Model(1 if prior == "pcar" else 0, float(rho), float(a_tau), float(b_tau),
-                   float(a_sig), float(b_sig), 1 if fix_hyper else 0, 1 if intercept else 0)
+                   float(a_sig), float(b_sig), 1 if fix_hyper else 0, 1 if intercept else 0,
+                   0 if trials is None else 1, float(beta0_prior[0]), float(beta0_prior[1]))
+    tr = None if trials is None else _i32(trials)
     opts = _RunOpts(int(seed), int(stream), int(start_sweep), int(nsweeps), int(burn_in),
                     int(thin))
     tt = np.zeros((C, max(nsweeps, 1)))
@@ -308,7 +339,8 @@ def run(graph, colors, y, state, *, seed, nsweeps, stream=0, start_sweep=0, prio
     cnt = ctypes.c_int64(state.count)
     fb = lib.ora_run(n, _ptr(rp, ctypes.c_int32), _ptr(ci, ctypes.c_int32),
                      _ptr(w, ctypes.c_double), _ptr(col, ctypes.c_int32), k,
-                     _ptr(yy, ctypes.c_double), C, ctypes.byref(model), ctypes.byref(opts),
+                     _ptr(yy, ctypes.c_double), _ptr(tr, ctypes.c_int32), C, ctypes.byref(model),
+                     ctypes.byref(opts),
                      _ptr(state.x, ctypes.c_double), _ptr(state.tau, ctypes.c_double),
                      _ptr(state.sigma2, ctypes.c_double), _ptr(state.beta0, ctypes.c_double),
                      _ptr(tt, ctypes.c_double), _ptr(st, ctypes.c_double), _ptr(bt, ctypes.c_double),

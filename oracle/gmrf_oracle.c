@@ -369,6 +369,173 @@ double ora_quadform(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, c
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Polya-Gamma variates (Sec. 3.2: binomial data with the logistic link, augmented as in        */
+/* Polson, Scott & Windle, JASA 2013).  PG(b, c) for an integer b >= 0 is the sum of b          */
+/* independent PG(1, c) = J*(1, |c|/2) / 4 variates, each drawn by Devroye's alternating-series */
+/* method (PSW 2013, Sec. 4 and appendix): a proposal from a mixture of an exponential tail on  */
+/* (t, inf) and a truncated inverse-Gaussian on (0, t), t = 0.64, accepted by the partial sums  */
+/* of the series a_0 - a_1 + a_2 - ...                                                          */
+/*                                                                                              */
+/* Random numbers: draw k (k < b) of (site, sweep, chain) reads a stream of uniforms            */
+/* u = (w + 1/2) 2^-32 from the Philox blocks at counters (site, sweep, stream,                 */
+/* 0xA << 28 | chain << 22 | k << 10 | j), j = 0, 1, ..., words w0..w3 in order; a normal takes */
+/* two uniforms (Box-Muller cosine).  If a draw exhausts its 1024 blocks (never seen) it       */
+/* returns the mean tanh(z)/(4z) and counts a fallback.                                        */
+/* ------------------------------------------------------------------------------------------ */
+#define ORA_PG_T 0.64
+#define ORA_PI 3.14159265358979323846
+
+typedef struct {
+    uint32_t key[2];
+    uint32_t ctr[4];
+    uint32_t w[4];
+    int32_t idx;     /* next word of w (4: fetch a block) */
+    int32_t j;       /* next block */
+    int32_t exhausted;
+} ora_ustream;
+
+static void ora_us_init(ora_ustream *u, uint64_t seed, uint32_t site, uint32_t sweep, uint32_t stream,
+                        uint32_t chain, uint32_t k)
+{
+    ora_key_of_seed(seed, u->key);
+    u->ctr[0] = site;
+    u->ctr[1] = sweep;
+    u->ctr[2] = stream;
+    u->ctr[3] = (0xAu << 28) | (chain << 22) | (k << 10);
+    u->idx = 4;
+    u->j = 0;
+    u->exhausted = 0;
+}
+
+static double ora_us_next(ora_ustream *u)
+{
+    if (u->idx == 4) {
+        if (u->j >= 1024) {
+            u->exhausted = 1;
+            return 0.5;
+        }
+        uint32_t c[4] = {u->ctr[0], u->ctr[1], u->ctr[2], u->ctr[3] | (uint32_t)u->j};
+        ora_philox4x32_10(c, u->key, u->w);
+        u->j += 1;
+        u->idx = 0;
+    }
+    return ora_uniform(u->w[u->idx++]);
+}
+
+static double ora_us_normal(ora_ustream *u)
+{
+    double a = ora_us_next(u), b = ora_us_next(u);
+    return sqrt(-2.0 * log(a)) * cos(2.0 * ORA_PI * b);
+}
+
+/* Standard normal CDF. */
+static double ora_phi(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
+/* n-th coefficient of the alternating series of the J*(1, 0) density (Devroye 2009, PSW 2013). */
+double ora_pg_term(int32_t n, double x, int32_t form);
+static double ora_pg_a(int32_t n, double x) { return ora_pg_term(n, x, x <= ORA_PG_T ? 0 : 1); }
+
+/* Mixture weight of the exponential piece: p / (p + q), with
+ *   p = pi / (2K) exp(-K t),  K = pi^2/8 + z^2/2,
+ *   q = 2 exp(-z) F_IG(t; mu = 1/z, lambda = 1)  (z > 0),  q = 4 Phi(-1/sqrt(t))  (z = 0),
+ * F_IG(t) = Phi((t z - 1)/sqrt(t)) + exp(2z) Phi(-(t z + 1)/sqrt(t)).  For z > 40 the
+ * inverse-Gaussian piece (weight below 1e-17) is dropped. */
+static double ora_pg_mix(double z)
+{
+    const double t = ORA_PG_T;
+    double K = ORA_PI * ORA_PI / 8.0 + z * z / 2.0;
+    double p = ORA_PI / (2.0 * K) * exp(-K * t);
+    double q;
+    if (z > 40.0) return 1.0;
+    if (z == 0.0) q = 4.0 * ora_phi(-1.0 / sqrt(t));
+    else q = 2.0 * exp(-z) * (ora_phi((t * z - 1.0) / sqrt(t)) + exp(2.0 * z) * ora_phi(-(t * z + 1.0) / sqrt(t)));
+    return p / (p + q);
+}
+
+/* Inverse Gaussian IG(mu = 1/z, lambda = 1) truncated to (0, t) (PSW 2013, appendix). */
+static double ora_pg_tig(double z, ora_ustream *u)
+{
+    const double t = ORA_PG_T;
+    double x;
+    if (z == 0.0 || 1.0 / z > t) {
+        for (;;) {
+            double e1, e2;
+            do {
+                e1 = -log(ora_us_next(u));
+                e2 = -log(ora_us_next(u));
+                if (u->exhausted) return t / 2.0;
+            } while (e1 * e1 > 2.0 * e2 / t);
+            x = t / ((1.0 + t * e1) * (1.0 + t * e1));
+            double alpha = exp(-0.5 * z * z * x);
+            if (ora_us_next(u) <= alpha || u->exhausted) return x;
+        }
+    }
+    double mu = 1.0 / z;
+    for (;;) {
+        double y = ora_us_normal(u);
+        y = y * y;
+        x = mu + 0.5 * mu * mu * y - 0.5 * mu * sqrt(4.0 * mu * y + (mu * y) * (mu * y));
+        if (ora_us_next(u) > mu / (mu + x)) x = mu * mu / x;
+        if (x <= t || u->exhausted) return x;
+    }
+}
+
+/* One J*(1, z) variate (z >= 0); PG(1, c) is J*(1, |c|/2) / 4. */
+static double ora_pg_jstar(double z, double mix, ora_ustream *u)
+{
+    const double t = ORA_PG_T;
+    double K = ORA_PI * ORA_PI / 8.0 + z * z / 2.0;
+    for (;;) {
+        double U = ora_us_next(u), V = ora_us_next(u);
+        double x = (U < mix) ? t - log(ora_us_next(u)) / K : ora_pg_tig(z, u);
+        if (u->exhausted) return -1.0;
+        double S = ora_pg_a(0, x), Y = V * S;
+        for (int32_t n = 1; n < 1000; ++n) {
+            if (n & 1) {
+                S -= ora_pg_a(n, x);
+                if (Y <= S) return x;
+            } else {
+                S += ora_pg_a(n, x);
+                if (Y > S) break;
+            }
+        }
+    }
+}
+
+/* Term n of the small-x (form 0) or large-x (form 1) series of the J*(1, 0) density:
+ *   form 0: pi (n + 1/2) (2 / (pi x))^{3/2} exp(-2 (n + 1/2)^2 / x),
+ *   form 1: pi (n + 1/2) exp(-(n + 1/2)^2 pi^2 x / 2);
+ * the sampler uses form 0 for x <= t and form 1 above. */
+double ora_pg_term(int32_t n, double x, int32_t form)
+{
+    double k = n + 0.5;
+    if (form == 0) return ORA_PI * k * pow(2.0 / (ORA_PI * x), 1.5) * exp(-2.0 * k * k / x);
+    return ORA_PI * k * exp(-k * k * ORA_PI * ORA_PI * x / 2.0);
+}
+
+/* The exponential-piece weight p / (p + q) (test access). */
+double ora_pg_mix_weight(double z) { return ora_pg_mix(z); }
+
+/* PG(b, c) as the sum of b PG(1, c) draws with the counters above; *fallbacks counts draws
+ * that exhausted their stream. */
+double ora_pg_draw(int32_t b, double c, uint64_t seed, uint32_t site, uint32_t sweep, uint32_t stream,
+                   uint32_t chain, int32_t *fallbacks)
+{
+    double z = fabs(c) / 2.0, mix = ora_pg_mix(z), sum = 0.0;
+    for (int32_t k = 0; k < b; ++k) {
+        ora_ustream u;
+        ora_us_init(&u, seed, site, sweep, stream, chain, (uint32_t)k);
+        double j = ora_pg_jstar(z, mix, &u);
+        if (j < 0.0) {
+            if (fallbacks) ++*fallbacks;
+            j = z > 0.0 ? tanh(z) / z : 1.0;
+        }
+        sum += j / 4.0;
+    }
+    return sum;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* The sampler                                                                                  */
 /* ------------------------------------------------------------------------------------------ */
 typedef struct {
@@ -378,6 +545,9 @@ typedef struct {
     double a_sig, b_sig;   /* 1/sigma^2 ~ Gamma(a_sig, rate b_sig)                       */
     int32_t fix_hyper;     /* 1: tau and sigma^2 stay at their initial values             */
     int32_t intercept;     /* 1: y = beta0 1 + x + noise, flat prior on beta0 (Sec. 3.1)  */
+    int32_t binomial;      /* 1: y_i ~ Bin(m_i, logistic(beta0 + x_i)) (Sec. 3.2), beta0 ~  */
+    double beta0_mean;     /*    N(beta0_mean, beta0_var), Polya-Gamma augmentation; no     */
+    double beta0_var;      /*    sigma^2                                                    */
 } ora_model;
 
 typedef struct {
@@ -402,7 +572,7 @@ typedef struct {
  * Returns the number of Gamma draws that hit the attempt limit (normally 0).
  */
 int32_t ora_run(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const double *weights,
-                const int32_t *colors, int32_t ncolors, const double *y, int32_t C,
+                const int32_t *colors, int32_t ncolors, const double *y, const int32_t *trials, int32_t C,
                 const ora_model *model, const ora_run_opts *opts, double *x, double *tau,
                 double *sig2, double *beta0, double *tau_trace, double *sig2_trace,
                 double *beta0_trace, double *mean, double *m2, int64_t *acc_count, double *xtrace)
@@ -422,7 +592,9 @@ int32_t ora_run(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const
         for (int32_t c = 0; c < C; ++c) {
             double *xc = x + (int64_t)c * n;
             double prec_noise = 1.0 / sig2[c];
-            double b0 = model->intercept ? beta0[c] : 0.0;
+            int binom = model->binomial != 0;
+            double b0 = (model->intercept || binom) ? beta0[c] : 0.0;
+            double sum_psi = 0.0, sum_kx = 0.0; /* binomial: sums of psi_i and kappa_i - psi_i x_i */
             /* Algorithm 1: colour classes in order, every site of the class from its local
              * characteristics given the newest values of the other classes (Sec. 3.1: the
              * observations enter through b = (y - beta0 1) / sigma^2). */
@@ -432,14 +604,35 @@ int32_t ora_run(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const
                     double s = 0.0;
                     for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
                         s += (weights ? weights[e] : 1.0) * xc[col_idx[e]];
+                    double z = ora_site_normal(opts->seed, (uint32_t)i, sweep, opts->stream, (uint32_t)c, lanes);
+                    if (binom) {
+                        /* psi_i | beta0, x_i ~ PG(m_i, beta0 + x_i), then x_i given psi_i (Sec. 3.2):
+                         * precision tau d_i + psi_i, mean (tau rho s_i + kappa_i - psi_i beta0) / P */
+                        double psi = ora_pg_draw(trials[i], b0 + xc[i], opts->seed, (uint32_t)i, sweep,
+                                                 opts->stream, (uint32_t)c, &fallbacks);
+                        double kappa = y[i] - 0.5 * trials[i];
+                        double P = tau[c] * deg[i] + psi;
+                        double m = (tau[c] * rho * s + kappa - psi * b0) / P;
+                        xc[i] = m + z / sqrt(P);
+                        sum_psi += psi;
+                        sum_kx += kappa - psi * xc[i];
+                        continue;
+                    }
                     double P = tau[c] * deg[i] + prec_noise;
                     double m = (tau[c] * rho * s + (y[i] - b0) * prec_noise) / P;
-                    double z = ora_site_normal(opts->seed, (uint32_t)i, sweep, opts->stream, (uint32_t)c, lanes);
                     xc[i] = m + z / sqrt(P);
                 }
             /* Intercept (Sec. 3.1, flat prior): beta0 | y, x, sigma^2 ~ N(1'(y - x) / n, sigma^2 / n),
              * drawn before sigma^2, whose conditional then uses the new beta0. */
-            if (model->intercept) {
+            if (binom) {
+                /* beta0 | x, psi ~ N(mean, 1/Pb), Pb = 1/v0 + sum psi_i,
+                 * mean = (mu0/v0 + sum (kappa_i - psi_i x_i)) / Pb */
+                double Pb = 1.0 / model->beta0_var + sum_psi;
+                double mb = (model->beta0_mean / model->beta0_var + sum_kx) / Pb;
+                double zb = ora_beta_normal(opts->seed, sweep, opts->stream, ORA_TAG_BETA, (uint32_t)c);
+                b0 = mb + zb / sqrt(Pb);
+                beta0[c] = b0;
+            } else if (model->intercept) {
                 double A = 0.0;
                 for (int32_t i = 0; i < n; ++i) A += y[i] - xc[i];
                 double zb = ora_beta_normal(opts->seed, sweep, opts->stream, ORA_TAG_BETA, (uint32_t)c);
@@ -454,10 +647,12 @@ int32_t ora_run(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const
                 tau[c] = ora_gamma_draw(model->a_tau + 0.5 * rank, model->b_tau + 0.5 * S,
                                         opts->seed, sweep, opts->stream, ORA_TAG_TAU, (uint32_t)c, &att);
                 if (att < 0) ++fallbacks;
-                double prec = ora_gamma_draw(model->a_sig + 0.5 * n, model->b_sig + 0.5 * R,
-                                             opts->seed, sweep, opts->stream, ORA_TAG_SIG, (uint32_t)c, &att);
-                if (att < 0) ++fallbacks;
-                sig2[c] = 1.0 / prec;
+                if (!binom) {
+                    double prec = ora_gamma_draw(model->a_sig + 0.5 * n, model->b_sig + 0.5 * R, opts->seed,
+                                                 sweep, opts->stream, ORA_TAG_SIG, (uint32_t)c, &att);
+                    if (att < 0) ++fallbacks;
+                    sig2[c] = 1.0 / prec;
+                }
             }
             if (tau_trace) tau_trace[(int64_t)c * opts->nsweeps + t] = tau[c];
             if (sig2_trace) sig2_trace[(int64_t)c * opts->nsweeps + t] = sig2[c];

@@ -207,3 +207,104 @@ def test_intercept_posterior_matches_block_gibbs(prior, rho):
     for q in (0.1, 0.5, 0.9):
         qc, qb = np.quantile(chrom, q, axis=0), np.quantile(block, q, axis=0)
         assert np.all(np.abs(qc - qb) < 0.06 * chrom.std(0) + 5 * se), (q, qc, qb)
+
+
+# --------------------------------------------------------------------------------------------
+# Binomial data with the logistic link (Sec. 3.2): Polya-Gamma augmentation
+# --------------------------------------------------------------------------------------------
+def _pg_moments(b, c):
+    if c == 0.0:
+        return b / 4.0, b / 24.0
+    return (b / (2 * c) * np.tanh(c / 2),
+            b / (4 * c ** 3) * (np.sinh(c) - c) / np.cosh(c / 2) ** 2)
+
+
+@pytest.mark.parametrize("b,c", [(1, 0.0), (1, 0.7), (1, 3.0), (1, 25.0), (3, 1.5), (7, -2.0)])
+def test_polya_gamma_moments(b, c):
+    # E and Var of PG(b, c) in closed form (Polson, Scott & Windle 2013, Sec. 2).
+    N = 200_000
+    v = np.array([oracle.pg_draw(b, c, 21, site=i, sweep=1)[0] for i in range(N)])
+    m, var = _pg_moments(b, c)
+    assert abs(v.mean() - m) < 5 * np.sqrt(var / N)
+    assert abs(v.var() / var - 1) < 0.03
+    assert v.min() > 0
+
+
+def test_polya_gamma_sum_and_zero():
+    # PG(0, c) = 0; PG(b, c) is the sum of the b PG(1, c) draws of the same counters.
+    assert oracle.pg_draw(0, 1.3, 5)[0] == 0.0
+    v3 = oracle.pg_draw(3, 1.3, 5, site=4, sweep=2)[0]
+    assert v3 > 0
+
+
+def _logistic_posterior_by_quadrature(rp, ci, trials, y, tau, rho, prior_var):
+    """Posterior means of x and beta0 and of the success probabilities, by summing the exact
+    joint density (Gaussian CAR prior, normal prior on beta0, binomial likelihood) on a grid."""
+    n = len(rp) - 1
+    Wm, D = _dense(rp, ci)
+    Q = tau * (D - rho * Wm)
+    axes = [np.linspace(-7, 7, 57)] * n + [np.linspace(-9, 9, 73)]
+    grids = np.meshgrid(*axes, indexing="ij")
+    X = np.stack([g.ravel() for g in grids[:n]], 1)
+    b0 = grids[n].ravel()
+    logp = -0.5 * np.einsum("ki,ij,kj->k", X, Q, X) - 0.5 * b0 ** 2 / prior_var
+    eta = X + b0[:, None]
+    logp += np.sum(y * eta - trials * np.logaddexp(0, eta), 1)
+    w = np.exp(logp - logp.max())
+    w /= w.sum()
+    pi = 1 / (1 + np.exp(-eta))
+    return (w @ X), float(w @ b0), (w @ pi)
+
+
+def test_binomial_posterior_matches_quadrature():
+    # Three sites on a path, proper CAR (rho 0.5), tau fixed at 2, beta0 ~ N(0, 4); the middle
+    # site has no trials (its update is then the prior conditional).
+    rp, ci = wl.path_graph(3)
+    trials = np.array([6, 0, 9], np.int32)
+    y = np.array([4.0, 0.0, 2.0])
+    tau = 2.0
+    colors, _ = oracle.color_graph(rp, ci, 2)
+    st = oracle.initial_state(y, 1, tau0=tau, x0=np.zeros(3))
+    T = 150_000
+    out = oracle.run((rp, ci), colors, y, st, seed=13, nsweeps=T, prior="pcar", rho=0.5, fix_hyper=True,
+                     accumulate=False, record_x=True, trials=trials, beta0_prior=(0.0, 4.0))
+    xs = out["xtrace"][2000:, 0, :]
+    bs = out["beta0_trace"][0, 2000:]
+    pis = 1 / (1 + np.exp(-(xs + bs[:, None])))
+    mx, mb, mpi = _logistic_posterior_by_quadrature(rp, ci, trials, y, tau, 0.5, 4.0)
+    z = np.concatenate([xs, bs[:, None], pis], 1)
+    want = np.concatenate([mx, [mb], mpi])
+    se = _batch_se(z)
+    assert np.all(np.abs(z.mean(0) - want) < 5 * se + 1e-3), (z.mean(0), want, se)
+    assert out["fallbacks"] == 0
+
+
+def test_polya_gamma_series_forms_agree():
+    # The two series of the J*(1, 0) density (Devroye 2009) are the two sides of a Jacobi
+    # theta-function identity: summed to convergence they agree at every x > 0; the density
+    # integrates to 1 and has mean 1 (E J*(1, 0) = 1).
+    from scipy import integrate
+
+    def dens(x, form):
+        return sum((-1) ** n * oracle.pg_series_term(n, x, form) for n in range(60))
+
+    for x in (0.15, 0.3, 0.64, 1.0, 2.5):
+        assert dens(x, 0) == pytest.approx(dens(x, 1), rel=1e-9)
+    f = lambda x: dens(x, 0) if x <= 0.64 else dens(x, 1)  # noqa: E731
+    mass = integrate.quad(f, 1e-6, 0.64)[0] + integrate.quad(f, 0.64, 60)[0]
+    mean = integrate.quad(lambda x: x * f(x), 1e-6, 0.64)[0] + integrate.quad(lambda x: x * f(x), 0.64, 60)[0]
+    assert mass == pytest.approx(1.0, abs=1e-8) and mean == pytest.approx(1.0, abs=1e-8)
+
+
+@pytest.mark.parametrize("z", [0.0, 0.3, 1.0, 1 / 0.64, 4.0, 12.0])
+def test_polya_gamma_proposal_weights(z):
+    # The envelope is exp(-z^2 x / 2) a_0(x); the weight of its exponential piece (x > t) must
+    # equal the ratio of the envelope's integrals, computed here by quadrature.
+    from scipy import integrate
+
+    t = 0.64
+    env0 = lambda x: np.exp(-z * z * x / 2) * oracle.pg_series_term(0, x, 0)  # noqa: E731
+    env1 = lambda x: np.exp(-z * z * x / 2) * oracle.pg_series_term(0, x, 1)  # noqa: E731
+    q = integrate.quad(env0, 0, t, limit=200)[0]
+    p = integrate.quad(env1, t, np.inf, limit=200)[0]
+    assert oracle.pg_mix_weight(z) == pytest.approx(p / (p + q), rel=1e-8)
