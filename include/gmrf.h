@@ -102,7 +102,18 @@ typedef struct {
     const double *sigma2_0;   /* [chains] initial sigma^2 or NULL: model.sigma2_0           */
     uint32_t stream_id;       /* Philox counter word 2 of this field's draws                */
     const double *beta0;      /* [chains] initial intercept or NULL: model.beta0_0           */
+    const int32_t *trials;    /* binomial likelihood: [n] trials m_i (0..4095), y = successes */
+                              /* (0 <= y_i <= m_i); NULL for the Gaussian likelihood          */
 } gmrf_field_desc;
+
+/* Likelihoods.  Gaussian: y_i = [beta0 +] x_i + N(0, sigma^2) (Sec. 3.1).  Binomial:
+ * y_i ~ Bin(m_i, logistic(beta0 + x_i)) with beta0 ~ N(beta0_mean, beta0_var) and no sigma^2
+ * (Sec. 3.2); each sweep draws psi_i ~ PG(m_i, beta0 + x_i) (Polya-Gamma augmentation, counters
+ * (site, sweep, stream, 0xA << 28 | chain << 22 | k << 10 | j) for the k-th PG(1) summand's j-th
+ * Philox block) right before site i's update, whose precision is tau d_i + psi_i and mean
+ * (tau rho s_i + y_i - m_i/2 - psi_i beta0) / P, then beta0 given x and psi, then tau.  The
+ * binomial likelihood runs on the per-colour kernels, with default x0 = 0. */
+typedef enum { GMRF_LIKELIHOOD_GAUSSIAN = 0, GMRF_LIKELIHOOD_BINOMIAL = 1 } gmrf_likelihood;
 
 typedef struct {
     int32_t prior;            /* gmrf_prior_kind                                            */
@@ -115,6 +126,8 @@ typedef struct {
                               /* beta0 | x, sigma^2 ~ N(1'(y - x)/n, sigma^2/n) drawn before */
                               /* sigma^2 (Sec. 3.1); 0: no intercept                         */
     double beta0_0;           /* default initial intercept (used when intercept = 1)        */
+    int32_t likelihood;       /* gmrf_likelihood                                            */
+    double beta0_mean, beta0_var; /* binomial likelihood: beta0 ~ N(beta0_mean, beta0_var)   */
 } gmrf_model;
 
 typedef struct {

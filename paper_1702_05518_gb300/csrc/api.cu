@@ -99,6 +99,7 @@ struct gmrf_sampler {
     int32_t *rp = nullptr, *ci = nullptr, *perm = nullptr, *perm_inv = nullptr, *coff = nullptr;
     void *w = nullptr, *deg = nullptr;
     double *tau = nullptr, *sig2 = nullptr, *beta = nullptr;
+    int32_t *trials = nullptr;  // binomial likelihood: [slots] trials in the colour-split layout
     void *hyp = nullptr;        // [F * Cp][kHypStride] copies in precision T
     Part3 *partials = nullptr;
     double *trace_tau = nullptr, *trace_sig = nullptr, *trace_beta = nullptr;
@@ -261,6 +262,11 @@ gmrf_status check_model(const gmrf_model *m)
         return fail(GMRF_E_INVALID, "model: tau0 >= 0 and sigma2_0 > 0 required");
     if (m->intercept != 0 && m->intercept != 1) return fail(GMRF_E_INVALID, "model.intercept must be 0 or 1");
     if (!finite(m->beta0_0)) return fail(GMRF_E_INVALID, "model.beta0_0 must be finite");
+    if (m->likelihood != GMRF_LIKELIHOOD_GAUSSIAN && m->likelihood != GMRF_LIKELIHOOD_BINOMIAL)
+        return fail(GMRF_E_INVALID, "model.likelihood");
+    if (m->likelihood == GMRF_LIKELIHOOD_BINOMIAL &&
+        !(finite(m->beta0_mean) && finite(m->beta0_var) && m->beta0_var > 0))
+        return fail(GMRF_E_INVALID, "model: beta0_mean finite and beta0_var > 0 required for binomial data");
     return GMRF_OK;
 }
 
@@ -372,6 +378,10 @@ void free_tmp(std::vector<void *> &tmp)
     tmp.clear();
 }
 
+bool binomial_model(const gmrf_sampler *s) { return s->model.likelihood == GMRF_LIKELIHOOD_BINOMIAL; }
+// beta0 is a parameter of the model (the Gaussian intercept, or always with binomial data).
+bool has_beta(const gmrf_sampler *s) { return s->model.intercept || binomial_model(s); }
+
 // ---------------------------------------------------------------------------------------------
 // Sweep launches
 // ---------------------------------------------------------------------------------------------
@@ -405,6 +415,8 @@ StepArgs step_args(gmrf_sampler *s, int colour, int kind, int update, int accumu
     a.acc_enabled = accumulate;
     a.update = update;
     a.intercept = s->model.intercept ? 1 : 0;
+    a.binomial = binomial_model(s) ? 1 : 0;
+    a.trials = s->trials;
     return a;
 }
 
@@ -421,7 +433,7 @@ HyperArgs hyper_args(gmrf_sampler *s, int draw, int draw_beta, int end_of_sweep)
     h.hyp = s->hyp;
     h.trace_tau = s->trace_tau;
     h.trace_sig = s->trace_sig;
-    h.trace_beta = s->model.intercept ? s->trace_beta : nullptr;
+    h.trace_beta = has_beta(s) ? s->trace_beta : nullptr;
     h.trace_cap = s->opts.trace_capacity;
     h.ctl = s->ctl;
     h.key = philox_key(s->opts.seed);
@@ -430,7 +442,10 @@ HyperArgs hyper_args(gmrf_sampler *s, int draw, int draw_beta, int end_of_sweep)
     h.a_sig = s->model.a_sigma;
     h.b_sig = s->model.b_sigma;
     h.draw = draw;
-    h.draw_beta = s->model.intercept ? draw_beta : 0;
+    h.draw_beta = has_beta(s) ? draw_beta : 0;
+    h.binomial = binomial_model(s) ? 1 : 0;
+    h.beta0_mean = s->model.beta0_mean;
+    h.beta0_var = s->model.beta0_var;
     h.end_of_sweep = end_of_sweep;
     h.burn_in = s->opts.burn_in;
     h.thin = s->opts.thin;
@@ -450,7 +465,7 @@ cudaError_t launch_pre(gmrf_sampler *s, int count, cudaStream_t st)
     g.a_tau = s->model.a_tau;
     g.a_sig = s->model.a_sigma;
     g.count = count;
-    g.intercept = s->model.intercept ? 1 : 0;
+    g.intercept = has_beta(s) ? 1 : 0;
     g.gpre = s->gpre;
     return launch_gamma_pre(g, st);
 }
@@ -514,7 +529,7 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int with_hyper, cudaStr
 {
     cudaError_t e = cudaSuccess;
     const int draw = (with_hyper && !s->model.fix_hyper) ? 1 : 0;
-    const int draw_beta = (with_hyper && s->model.intercept) ? 1 : 0;
+    const int draw_beta = (with_hyper && has_beta(s)) ? 1 : 0;
     for (int k = 0; k < nsweeps && e == cudaSuccess; ++k) {
         // A batch of sweeps starts with the parallel draw of its unit-rate Gamma variates.
         if ((draw || draw_beta) && s->gpre && k % s->gpre_batch == 0)
@@ -787,7 +802,7 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     // halo (state, normals and y) fits the 72 KiB shared-memory budget (3 blocks per SM) and it
     // is not switched off.
     bool fused_kind[4] = {false, false, false, false};
-    const bool allow_fused = (s->opts.flags & GMRF_FLAG_PER_COLOUR) == 0;
+    const bool allow_fused = (s->opts.flags & GMRF_FLAG_PER_COLOUR) == 0 && !binomial_model(s);
     for (int kind : {static_cast<int>(GMRF_LATTICE2D_4), static_cast<int>(GMRF_LATTICE2D_8)}) {
         const int K = kind == GMRF_LATTICE2D_8 ? 4 : 2;
         const double per_site = static_cast<double>(T) * (2 * s->Cp + 1);
@@ -995,6 +1010,20 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
         const HostField &h = s->hf[fi];
         double *y_d = upload(f.y, h.n, s->stream, tmp);
         double *x0_d = f.x0 ? upload(f.x0, static_cast<int64_t>(h.n) * s->C, s->stream, tmp) : nullptr;
+        if (!f.x0 && binomial_model(s)) {  // binomial: x0 = 0 (the logit scale) unless given
+            const std::vector<double> zeros(static_cast<size_t>(h.n) * s->C, 0.0);
+            x0_d = upload(zeros.data(), static_cast<int64_t>(h.n) * s->C, s->stream, tmp);
+            CK(cudaStreamSynchronize(s->stream));
+        }
+        if (binomial_model(s)) {
+            if (!s->trials) {
+                CK(s->alloc_t(&s->trials, static_cast<size_t>(std::max<int64_t>(s->slots, 1)), sizeof(int32_t)));
+                CK(cudaMemsetAsync(s->trials, 0, sizeof(int32_t) * static_cast<size_t>(std::max<int64_t>(s->slots, 1)),
+                                   s->stream));
+            }
+            int32_t *m_d = upload_t(f.trials, h.n, s->stream, tmp);
+            CK(launch_pack_int(s->fields_dev, s->fd[fi], fi, m_d, s->perm_inv, s->trials, s->stream));
+        }
         CK(launch_pack(s->precision, s->fields_dev, s->fd[fi], fi, s->C, s->Cp, y_d, x0_d, s->perm_inv, s->x, s->y,
                        s->stream));
     }
@@ -1009,7 +1038,7 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
             const gmrf_field_desc &f = fields[fi];
             t0[k] = (f.tau0 && c < s->C) ? f.tau0[c] : s->model.tau0;
             s0[k] = (f.sigma2_0 && c < s->C) ? f.sigma2_0[c] : s->model.sigma2_0;
-            b0[k] = !s->model.intercept ? 0.0 : ((f.beta0 && c < s->C) ? f.beta0[c] : s->model.beta0_0);
+            b0[k] = !has_beta(s) ? 0.0 : ((f.beta0 && c < s->C) ? f.beta0[c] : s->model.beta0_0);
             const double v[3] = {t0[k], 1.0 / s0[k], b0[k]};
             for (int q = 0; q < 3; ++q) {
                 if (s->precision == GMRF_FP32) reinterpret_cast<float *>(hypT.data())[kHypStride * k + q] = static_cast<float>(v[q]);
@@ -1028,7 +1057,7 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     CK(cudaMemcpyAsync(s->hyp, hypT.data(), hypT.size(), cudaMemcpyHostToDevice, s->stream));
     CK(s->alloc_t(&s->trace_tau, nh * s->opts.trace_capacity, sizeof(double)));
     CK(s->alloc_t(&s->trace_sig, nh * s->opts.trace_capacity, sizeof(double)));
-    if (s->model.intercept) CK(s->alloc_t(&s->trace_beta, nh * s->opts.trace_capacity, sizeof(double)));
+    if (has_beta(s)) CK(s->alloc_t(&s->trace_beta, nh * s->opts.trace_capacity, sizeof(double)));
     CK(s->alloc_t(&s->diag_work, static_cast<size_t>(Cp) * s->opts.trace_capacity, sizeof(double)));
     CK(s->alloc_t(&s->diag_out, static_cast<size_t>(Cp) * 4 + 2, sizeof(double)));
     // Initial state kept for gmrf_sampler_reset.
@@ -1111,10 +1140,21 @@ gmrf_status gmrf_sampler_create(gmrf_sampler **out, const gmrf_field_desc *field
     std::vector<HostField> hf(nfields);
     for (int i = 0; i < nfields; ++i)
         if ((st = check_field(fields[i], i, opts->chains, hf[i])) != GMRF_OK) return st;
+    if (model->likelihood == GMRF_LIKELIHOOD_BINOMIAL)
+        for (int i = 0; i < nfields; ++i) {
+            const std::string at = "field " + std::to_string(i) + ": ";
+            if (!fields[i].trials) return fail(GMRF_E_INVALID, at + "binomial data need trials");
+            for (int32_t k = 0; k < hf[i].n; ++k) {
+                const int32_t m = fields[i].trials[k];
+                if (m < 0 || m > 4095) return fail(GMRF_E_INVALID, at + "trials must be in 0..4095");
+                if (!(fields[i].y[k] >= 0.0 && fields[i].y[k] <= m))
+                    return fail(GMRF_E_INVALID, at + "successes y must be in [0, trials]");
+            }
+        }
     if (opts->algorithm == GMRF_ALGO_PLAIN && (nfields != 1 || opts->precision != GMRF_FP64))
         return fail(GMRF_E_UNSUPPORTED, "the plain sweep takes exactly one field in FP64");
-    if (opts->algorithm == GMRF_ALGO_PLAIN && model->intercept)
-        return fail(GMRF_E_UNSUPPORTED, "the plain sweep has no intercept");
+    if (opts->algorithm == GMRF_ALGO_PLAIN && (model->intercept || model->likelihood != GMRF_LIKELIHOOD_GAUSSIAN))
+        return fail(GMRF_E_UNSUPPORTED, "the plain sweep has neither the intercept nor the binomial likelihood");
 
     gmrf_sampler *s = new gmrf_sampler();
     s->model = *model;
@@ -1205,6 +1245,7 @@ gmrf_status gmrf_hyper_update(gmrf_sampler *s)
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
     if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "hyper_update on the plain sweep");
+    if (binomial_model(s)) return fail(GMRF_E_UNSUPPORTED, "hyper_update with the binomial likelihood");
     cudaError_t e = cudaSuccess;
     for (size_t k = 0; k < s->stages.size() && e == cudaSuccess; ++k)
         if (s->stages[k].type != 2) e = enqueue_stage(s, k, 0, 0, 0, 0, 0, s->stream);
@@ -1284,7 +1325,7 @@ gmrf_status gmrf_fetch_intercept(gmrf_sampler *s, int32_t field, int32_t chain, 
     g_last_error.clear();
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
-    if (!s->model.intercept) return fail(GMRF_E_INVALID, "the model has no intercept");
+    if (!has_beta(s)) return fail(GMRF_E_INVALID, "the model has no intercept");
     if (field < 0 || field >= s->nfields || chain < 0 || chain >= s->C)
         return fail(GMRF_E_INVALID, "field or chain out of range");
     if (trace_cap < 0) return fail(GMRF_E_INVALID, "trace_cap must be >= 0");
@@ -1321,7 +1362,7 @@ gmrf_status gmrf_trace_diagnostics(gmrf_sampler *s, int32_t field, int32_t param
     if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "diagnostics of the plain sweep");
     if (field < 0 || field >= s->nfields) return fail(GMRF_E_INVALID, "field out of range");
     if (param < GMRF_PARAM_TAU2 || param > GMRF_PARAM_TAU) return fail(GMRF_E_INVALID, "param");
-    if (param == GMRF_PARAM_BETA0 && !s->model.intercept) return fail(GMRF_E_INVALID, "the model has no intercept");
+    if (param == GMRF_PARAM_BETA0 && !has_beta(s)) return fail(GMRF_E_INVALID, "the model has no intercept");
     if (n_last < 0) return fail(GMRF_E_INVALID, "n_last must be >= 0");
     try {
         SweepCtl c{};

@@ -49,7 +49,7 @@ struct StepArgs {
     const int32_t *coff; // CSR: colour offsets (ncolors + 1 per field)
     const void *hyp;     // [F * Cp][kHypStride]: tau, 1/sigma^2, beta0 in precision T
     Part3 *partials;     // [parts][Cp]: per tile and chain sums (S, R, A)
-    const SweepCtl *ctl;
+    SweepCtl *ctl;
     uint2 key;
     int32_t Cp;          // chains in the layout (power of two >= chains)
     int32_t lanes;       // normals per site of one Philox block: min(4, Cp)
@@ -59,6 +59,8 @@ struct StepArgs {
     int32_t acc_enabled;
     int32_t update;      // 1: draw the colour class; 0: only recompute the partial sums
     int32_t intercept;   // the model has the intercept beta0
+    int32_t binomial;    // binomial counts (successes in y) with the logistic link
+    const int32_t *trials;  // [slots] binomial trials m_i (binomial model only)
 };
 
 struct HyperArgs {
@@ -79,6 +81,8 @@ struct HyperArgs {
     double a_tau, b_tau, a_sig, b_sig;
     int32_t draw;         // 0: keep tau, sigma^2
     int32_t draw_beta;    // 1: draw the intercept beta0 (before sigma^2)
+    int32_t binomial;     // binomial model: beta0 from its normal conditional, no sigma^2
+    double beta0_mean, beta0_var;  // binomial model: normal prior of beta0
     int32_t end_of_sweep; // 1: sweep counter, traces; 0: extra draw (tags 5 and 6)
     long long burn_in;    // accumulation schedule (to advance the accumulation count)
     int32_t thin;
@@ -149,6 +153,8 @@ cudaError_t launch_pack(int precision, const FieldDev *fields_dev, const FieldDe
 cudaError_t launch_unpack(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx,
                           int32_t Cp, int32_t chain, const void *src, const void *m2, double inv_km1,
                           const int32_t *perm_inv, double *out, cudaStream_t stream);
+cudaError_t launch_pack_int(const FieldDev *fields_dev, const FieldDev &f, int32_t fidx, const int32_t *v_nat,
+                            const int32_t *perm_inv, int32_t *v, cudaStream_t stream);
 cudaError_t launch_ctl_reset(SweepCtl *ctl, long long start_sweep, cudaStream_t stream);
 cudaError_t launch_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, int64_t count,
                                 uint32_t *out, cudaStream_t stream);

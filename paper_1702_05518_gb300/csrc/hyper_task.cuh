@@ -16,6 +16,9 @@ namespace gmrf {
 // the sums, and tasks run in parallel warps.  Once every task of a launch has run,
 // hyper_advance moves the counters on.
 //
+// Binomial model (Sec. 3.2): task 2p + 1 draws beta0 from its normal conditional given the sums
+// of psi_i and kappa_i - psi_i x_i that the partials then hold; there is no sigma^2.
+//
 // Intercept: the partials hold R = sum e_i^2 and A = sum e_i with e_i = y_i - b - x_i, b the
 // copy of beta0 the sweep used.  beta0 | x, sigma^2 ~ N(1'(y - x)/n, sigma^2/n) is drawn as
 // b + delta, delta = A/n + sqrt(sigma^2/n) z, and the sigma^2 draw takes
@@ -80,15 +83,22 @@ __device__ __forceinline__ void hyper_task(const HyperArgs &a, int task, long lo
                 double unused;
                 box_muller_f64(w.x, w.y, zb, unused);
             }
-            const double delta = A / fn + sqrt(s2old / fn) * zb;
-            bval = b + delta;
+            if (a.binomial) {
+                // beta0 | x, psi ~ N(mean, 1/Pb), Pb = 1/v0 + sum psi_i,
+                // mean = (mu0/v0 + sum (kappa_i - psi_i x_i)) / Pb  (S and A hold the two sums).
+                const double Pb = 1.0 / a.beta0_var + S;
+                bval = (a.beta0_mean / a.beta0_var + A) / Pb + zb / sqrt(Pb);
+            } else {
+                const double delta = A / fn + sqrt(s2old / fn) * zb;
+                bval = b + delta;
+                S = S - 2.0 * delta * A + fn * (delta * delta);
+            }
             a.beta[hc] = bval;
             hyp[hc * kHypStride + 2] = static_cast<T>(bval);
-            S = S - 2.0 * delta * A + fn * (delta * delta);
         } else if (which && a.trace_beta) {
             bval = a.beta[hc];
         }
-        if (a.draw) {
+        if (a.draw && !(which && a.binomial)) {
             const double rate = which ? a.b_sig + 0.5 * S : a.b_tau + 0.5 * S;
             double G = gpv;
             if (!pre) {

@@ -23,6 +23,7 @@
 #include "gmrf_device.cuh"
 #include "gmrf_internal.h"
 #include "hyper_task.cuh"
+#include "pg.cuh"
 
 namespace gmrf {
 namespace {
@@ -38,6 +39,11 @@ template <> struct Arith<double> {
     __device__ __forceinline__ static double rsq(double x) { return 1.0 / sqrt(x); }
 };
 
+// Observation models of the colour kernels (compile-time): Gaussian noise without or with the
+// intercept beta0 (Sec. 3.1), or binomial counts with the logistic link and Polya-Gamma
+// augmentation (Sec. 3.2; y holds the successes, the trials come separately).
+enum : int { kModelGauss = 0, kModelGaussIntercept = 1, kModelBinomial = 2 };
+
 template <typename T, int V>
 struct SiteCtx {
     T tau[V], isig[V], beta[V];  // per chain of this thread
@@ -49,9 +55,14 @@ struct SiteCtx {
 // Draw (or, in reduce-only mode, read) the V chain values of one site given its neighbour sum s
 // and the neighbour values nb[k] of the neighbours flagged in `lower_mask` (those of lower
 // colour), and fold the site's terms into the partial sums.
-template <typename T, int V, int NB>
+//
+// Binomial model: first psi | beta0, x_i ~ PG(m_i, beta0 + x_i) from the site's current value, then
+// x_i with precision tau d_i + psi and mean (tau rho s_i + kappa_i - psi beta0) / P,
+// kappa_i = y_i - m_i / 2; the partial sums then collect psi and kappa_i - psi x_i (for beta0)
+// in place of the Gaussian residual sums.
+template <typename T, int V, int NB, int MODEL>
 __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx, T *xp, T *meanp, T *m2p,
-                                            T yv, T d, uint32_t site, uint32_t sweep, uint32_t stream,
+                                            T yv, int mtr, T d, uint32_t site, uint32_t sweep, uint32_t stream,
                                             uint32_t chain0, const T (&s)[V], const T (&nb)[NB][V],
                                             uint32_t lower_mask, const T (&wnb)[NB])
 {
@@ -65,7 +76,24 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
         Vec<T, V>::ld(meanp, mu);
         Vec<T, V>::ld(m2p, mm);
     }
-    if (a.update) {
+    T psi[V];
+    const T kappa = yv - static_cast<T>(0.5) * static_cast<T>(mtr);
+    if (MODEL == kModelBinomial && a.update) {
+        T xo[V], z[V];
+        Vec<T, V>::ld(xp, xo);
+        site_normals<T, V>(a.key, site, sweep, stream, chain0, a.lanes, z);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            int fb = 0;
+            psi[v] = static_cast<T>(pg_draw(mtr, static_cast<double>(cx.beta[v]) + static_cast<double>(xo[v]), a.key,
+                                            site, sweep, stream, chain0 + v, fb));
+            if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), static_cast<unsigned long long>(fb));
+            const T P = cx.tau[v] * d + psi[v];
+            const T m = (cx.tau[v] * rho * s[v] + kappa - psi[v] * cx.beta[v]) * Arith<T>::rcp(P);
+            xn[v] = m + z[v] * Arith<T>::rsq(P);
+        }
+        Vec<T, V>::st(xp, xn);
+    } else if (a.update) {
         T z[V];
         site_normals<T, V>(a.key, site, sweep, stream, chain0, a.lanes, z);
 #pragma unroll
@@ -77,6 +105,8 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
         Vec<T, V>::st(xp, xn);
     } else {
         Vec<T, V>::ld(xp, xn);
+#pragma unroll
+        for (int v = 0; v < V; ++v) psi[v] = 0;  // reduce-only passes are not used with this model
     }
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -89,9 +119,14 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
             }
         }
         cx.accS[v] += (static_cast<T>(1) - rho) * d * xn[v] * xn[v] + rho * e;
-        const T r = (yv - cx.beta[v]) - xn[v];
-        cx.accR[v] += r * r;
-        cx.accA[v] += r;
+        if (MODEL == kModelBinomial) {
+            cx.accR[v] += psi[v];
+            cx.accA[v] += kappa - psi[v] * xn[v];
+        } else {
+            const T r = (yv - cx.beta[v]) - xn[v];
+            cx.accR[v] += r * r;
+            cx.accA[v] += r;
+        }
     }
     if (cx.acc) {
         if (!kEarly) {
@@ -114,7 +149,7 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
 // neighbours are columns h - 1 + p and h + p of the other colour's row r, the others column h
 // of rows r -+ 1 (i -+ 1) and r -+ H (l -+ 1).  Neighbour k has a fixed position in nb[k];
 // missing ones (outside the lattice) are masked.
-template <typename T, int V, bool THREE_D>
+template <typename T, int V, bool THREE_D, int MODEL>
 __device__ void lattice_parity_tile(const StepArgs &a, const FieldDev &f, const Tile &t, SiteCtx<T, V> &cx,
                                     int CV, int cv_shift, uint32_t sweep)
 {
@@ -180,7 +215,8 @@ __device__ void lattice_parity_tile(const StepArgs &a, const FieldDev &f, const 
             for (int v = 0; v < V; ++v) s[v] += nb[k][v];
         }
         const uint32_t site = static_cast<uint32_t>(r * W + j);
-        finish_site<T, V, NB>(a, cx, XS + rb * Cp, MS + rb * Cp, QS + rb * Cp, YS[rb], static_cast<T>(__popc(valid)),
+        const int mtr = MODEL == kModelBinomial ? a.trials[self_base + rb] : 0;
+        finish_site<T, V, NB, MODEL>(a, cx, XS + rb * Cp, MS + rb * Cp, QS + rb * Cp, YS[rb], mtr, static_cast<T>(__popc(valid)),
                               site, sweep, f.stream, static_cast<uint32_t>(cv * V), s, nb, lower_all & valid, wnb);
     }
 }
@@ -188,7 +224,7 @@ __device__ void lattice_parity_tile(const StepArgs &a, const FieldDev &f, const 
 // 2-D 8-neighbour lattice with the 2x2 colouring c = 2 (i & 1) + (j & 1): the site of colour
 // c = 2a + b at sub-array (u, v) is (2u + a, 2v + b); neighbour (i + di, j + dj) lives in
 // colour 2((a + di) & 1) + ((b + dj) & 1) at sub-array (u + ((a + di) >> 1), v + ((b + dj) >> 1)).
-template <typename T, int V>
+template <typename T, int V, int MODEL>
 __device__ void lattice8_tile(const StepArgs &a, const FieldDev &f, const Tile &t, SiteCtx<T, V> &cx, int CV,
                               int cv_shift, uint32_t sweep)
 {
@@ -258,7 +294,8 @@ __device__ void lattice8_tile(const StepArgs &a, const FieldDev &f, const Tile &
             for (int v = 0; v < V; ++v) s[v] += nb[k][v];
         }
         const uint32_t site = static_cast<uint32_t>(i * W + j);
-        finish_site<T, V, NB>(a, cx, XS + base * Cp, MS + base * Cp, QS + base * Cp, YS[base],
+        const int mtr = MODEL == kModelBinomial ? a.trials[f.slot0 + static_cast<int64_t>(c) * sub + base] : 0;
+        finish_site<T, V, NB, MODEL>(a, cx, XS + base * Cp, MS + base * Cp, QS + base * Cp, YS[base], mtr,
                               static_cast<T>(__popc(valid)), site, sweep, f.stream, static_cast<uint32_t>(cv * V),
                               s, nb, lower & valid, wnb);
     }
@@ -267,7 +304,7 @@ __device__ void lattice8_tile(const StepArgs &a, const FieldDev &f, const Tile &
 // CSR field: permuted positions [start, start + count) of one colour class; neighbours are read
 // through the permuted row; a neighbour has lower colour iff its position is below the class's
 // first position.  The lower-colour terms of the reduction take a second pass over the row.
-template <typename T, int V>
+template <typename T, int V, int MODEL>
 __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, SiteCtx<T, V> &cx, int CV,
                          int cv_shift, uint32_t sweep)
 {
@@ -304,8 +341,9 @@ __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, Si
         const uint32_t site = static_cast<uint32_t>(a.perm[f.csr0 + pos]);
         T nb0[1][V];
         T w0[1] = {0};
-        finish_site<T, V, 1>(a, cx, X + self * Cp + cv * V, MEAN + self * Cp + cv * V, M2 + self * Cp + cv * V, yv,
-                             d, site, sweep, f.stream, static_cast<uint32_t>(cv * V), s, nb0, 0u, w0);
+        const int mtr = MODEL == kModelBinomial ? a.trials[self] : 0;
+        finish_site<T, V, 1, MODEL>(a, cx, X + self * Cp + cv * V, MEAN + self * Cp + cv * V, M2 + self * Cp + cv * V, yv,
+                             mtr, d, site, sweep, f.stream, static_cast<uint32_t>(cv * V), s, nb0, 0u, w0);
         // finish_site added (1 - rho) d x^2 and the likelihood term; add the lower-colour edges.
         T xn[V];
         Vec<T, V>::ld(X + self * Cp + cv * V, xn);
@@ -329,9 +367,9 @@ __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, Si
     }
 }
 
-// IC: the model has the intercept (without it beta0 = 0 and the third sum is not needed, which
-// the compiler then removes, registers included).
-template <typename T, int V, int KIND, bool IC>
+// MODEL: the observation model; without the intercept beta0 = 0 and the third sum is not
+// needed, which the compiler then removes, registers included.
+template <typename T, int V, int KIND, int MODEL>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_kernel(const StepArgs a)
 {
     pdl_wait_then_release();
@@ -349,7 +387,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_ke
         const int64_t hc = (static_cast<int64_t>(t.field) * a.Cp + cv * V + v) * kHypStride;
         cx.tau[v] = hyp[hc];
         cx.isig[v] = hyp[hc + 1];
-        cx.beta[v] = IC ? hyp[hc + 2] : static_cast<T>(0);
+        cx.beta[v] = MODEL != kModelGauss ? hyp[hc + 2] : static_cast<T>(0);
         cx.accS[v] = 0;
         cx.accR[v] = 0;
         cx.accA[v] = 0;
@@ -362,10 +400,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_ke
     }
 
     const int cv_shift = __ffs(CV) - 1;
-    if constexpr (KIND == kLat2D4) lattice_parity_tile<T, V, false>(a, f, t, cx, CV, cv_shift, sweep);
-    else if constexpr (KIND == kLat3D6) lattice_parity_tile<T, V, true>(a, f, t, cx, CV, cv_shift, sweep);
-    else if constexpr (KIND == kLat2D8) lattice8_tile<T, V>(a, f, t, cx, CV, cv_shift, sweep);
-    else csr_tile<T, V>(a, f, t, cx, CV, cv_shift, sweep);
+    if constexpr (KIND == kLat2D4) lattice_parity_tile<T, V, false, MODEL>(a, f, t, cx, CV, cv_shift, sweep);
+    else if constexpr (KIND == kLat3D6) lattice_parity_tile<T, V, true, MODEL>(a, f, t, cx, CV, cv_shift, sweep);
+    else if constexpr (KIND == kLat2D8) lattice8_tile<T, V, MODEL>(a, f, t, cx, CV, cv_shift, sweep);
+    else csr_tile<T, V, MODEL>(a, f, t, cx, CV, cv_shift, sweep);
 
     // Deterministic block reduction of the 3 V partial sums of each chain in the state precision:
     // a shuffle tree over the lanes that share a chain vector (lanes equal mod CV), then the
@@ -376,11 +414,11 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_ke
     for (int v = 0; v < V; ++v) {
         T sS = cx.accS[v];
         T sR = cx.accR[v];
-        T sA = IC ? cx.accA[v] : static_cast<T>(0);
+        T sA = MODEL != kModelGauss ? cx.accA[v] : static_cast<T>(0);
         for (int off = 16; off >= CV; off >>= 1) {
             sS += __shfl_xor_sync(0xffffffffu, sS, off);
             sR += __shfl_xor_sync(0xffffffffu, sR, off);
-            if (IC) sA += __shfl_xor_sync(0xffffffffu, sA, off);
+            if (MODEL != kModelGauss) sA += __shfl_xor_sync(0xffffffffu, sA, off);
         }
         if (lane < CV) {
             red[warp][lane * V + v][0] = sS;
@@ -436,6 +474,18 @@ __global__ void pack_kernel(const FieldDev *fields, int32_t fidx, int32_t C, int
         y[slot] = static_cast<T>(yv);
         for (int c = 0; c < Cp; ++c)
             x[slot * Cp + c] = static_cast<T>((x0_nat && c < C) ? x0_nat[static_cast<int64_t>(c) * f.n + i] : yv);
+    }
+}
+
+// Natural order -> colour-split layout of a per-site integer array (binomial trials).
+__global__ void pack_int_kernel(const FieldDev *fields, int32_t fidx, const int32_t *v_nat, const int32_t *perm_inv,
+                                int32_t *v)
+{
+    const FieldDev f = fields[fidx];
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < f.n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t slot = f.slot0 + (f.kind == kCsr ? perm_inv[f.csr0 + i] : lattice_slot_of_site(f, i));
+        v[slot] = v_nat[i];
     }
 }
 
@@ -528,26 +578,25 @@ int grid_for(int64_t n, int block)
 
 }  // namespace
 
+template <int KIND, int MODEL>
+cudaError_t launch_model(int precision, int V, const StepArgs &a, cudaStream_t stream)
+{
+    const dim3 grid(a.ntiles), block(kBlock);
+    if (precision == 0) {
+        if (V == 4) return launch_sweep_kernel(colour_step_kernel<float, 4, KIND, MODEL>, grid, block, 0, stream, a);
+        if (V == 2) return launch_sweep_kernel(colour_step_kernel<float, 2, KIND, MODEL>, grid, block, 0, stream, a);
+        return launch_sweep_kernel(colour_step_kernel<float, 1, KIND, MODEL>, grid, block, 0, stream, a);
+    }
+    if (V == 2) return launch_sweep_kernel(colour_step_kernel<double, 2, KIND, MODEL>, grid, block, 0, stream, a);
+    return launch_sweep_kernel(colour_step_kernel<double, 1, KIND, MODEL>, grid, block, 0, stream, a);
+}
+
 template <int KIND>
 cudaError_t launch_kind(int precision, int V, const StepArgs &a, cudaStream_t stream)
 {
-    const dim3 grid(a.ntiles), block(kBlock);
-    if (a.intercept) {
-        if (precision == 0) {
-            if (V == 4) return launch_sweep_kernel(colour_step_kernel<float, 4, KIND, true>, grid, block, 0, stream, a);
-            if (V == 2) return launch_sweep_kernel(colour_step_kernel<float, 2, KIND, true>, grid, block, 0, stream, a);
-            return launch_sweep_kernel(colour_step_kernel<float, 1, KIND, true>, grid, block, 0, stream, a);
-        }
-        if (V == 2) return launch_sweep_kernel(colour_step_kernel<double, 2, KIND, true>, grid, block, 0, stream, a);
-        return launch_sweep_kernel(colour_step_kernel<double, 1, KIND, true>, grid, block, 0, stream, a);
-    }
-    if (precision == 0) {
-        if (V == 4) return launch_sweep_kernel(colour_step_kernel<float, 4, KIND, false>, grid, block, 0, stream, a);
-        if (V == 2) return launch_sweep_kernel(colour_step_kernel<float, 2, KIND, false>, grid, block, 0, stream, a);
-        return launch_sweep_kernel(colour_step_kernel<float, 1, KIND, false>, grid, block, 0, stream, a);
-    }
-    if (V == 2) return launch_sweep_kernel(colour_step_kernel<double, 2, KIND, false>, grid, block, 0, stream, a);
-    return launch_sweep_kernel(colour_step_kernel<double, 1, KIND, false>, grid, block, 0, stream, a);
+    if (a.binomial) return launch_model<KIND, kModelBinomial>(precision, V, a, stream);
+    if (a.intercept) return launch_model<KIND, kModelGaussIntercept>(precision, V, a, stream);
+    return launch_model<KIND, kModelGauss>(precision, V, a, stream);
 }
 
 cudaError_t launch_colour_step(int precision, int V, int kind, const StepArgs &a, cudaStream_t stream)
@@ -579,6 +628,13 @@ cudaError_t launch_pack(int precision, const FieldDev *fields_dev, const FieldDe
     else
         pack_kernel<double><<<grid, 256, 0, stream>>>(fields_dev, fidx, C, Cp, y_nat, x0_nat, perm_inv,
                                                       static_cast<double *>(x), static_cast<double *>(y));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_int(const FieldDev *fields_dev, const FieldDev &f, int32_t fidx, const int32_t *v_nat,
+                            const int32_t *perm_inv, int32_t *v, cudaStream_t stream)
+{
+    pack_int_kernel<<<grid_for(f.n, 256), 256, 0, stream>>>(fields_dev, fidx, v_nat, perm_inv, v);
     return cudaGetLastError();
 }
 

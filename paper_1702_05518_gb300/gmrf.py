@@ -22,6 +22,7 @@ FP32, FP64 = 0, 1
 ALGO_CHROMATIC, ALGO_PLAIN = 0, 1
 FLAG_PER_COLOUR = 1
 PARAM_TAU2, PARAM_SIGMA2, PARAM_BETA0, PARAM_TAU = range(4)
+LIKELIHOOD_GAUSSIAN, LIKELIHOOD_BINOMIAL = 0, 1
 
 EXPORTED = ["gmrf_color_graph", "gmrf_color_graph_noalloc", "gmrf_sampler_create", "gmrf_sampler_destroy", "gmrf_sweep",
             "gmrf_hyper_update", "gmrf_fetch_samples", "gmrf_field_colors", "gmrf_sampler_info",
@@ -46,7 +47,8 @@ class FieldDesc(ctypes.Structure):
                 ("y", ctypes.POINTER(ctypes.c_double)), ("x0", ctypes.POINTER(ctypes.c_double)),
                 ("tau0", ctypes.POINTER(ctypes.c_double)),
                 ("sigma2_0", ctypes.POINTER(ctypes.c_double)), ("stream_id", ctypes.c_uint32),
-                ("beta0", ctypes.POINTER(ctypes.c_double))]
+                ("beta0", ctypes.POINTER(ctypes.c_double)),
+                ("trials", ctypes.POINTER(ctypes.c_int32))]
 
 
 class Model(ctypes.Structure):
@@ -54,7 +56,8 @@ class Model(ctypes.Structure):
                 ("b_tau", ctypes.c_double), ("a_sigma", ctypes.c_double),
                 ("b_sigma", ctypes.c_double), ("fix_hyper", ctypes.c_int32),
                 ("tau0", ctypes.c_double), ("sigma2_0", ctypes.c_double),
-                ("intercept", ctypes.c_int32), ("beta0_0", ctypes.c_double)]
+                ("intercept", ctypes.c_int32), ("beta0_0", ctypes.c_double),
+                ("likelihood", ctypes.c_int32), ("beta0_mean", ctypes.c_double), ("beta0_var", ctypes.c_double)]
 
 
 class Opts(ctypes.Structure):
@@ -234,14 +237,16 @@ class Sampler:
     fields: list of dicts with keys kind, dims, n, y and, for CSR fields, row_ptr, col_idx and
     optionally weights, colors, color_seed; optional per field: x0 ([chains, n]), tau0,
     sigma2_0 and beta0 ([chains]), stream_id (default: the field's index).  intercept=True adds
-    the flat-prior intercept beta0 of Sec. 3.1 (initial value beta0_0).
+    the flat-prior intercept beta0 of Sec. 3.1 (initial value beta0_0).  With
+    likelihood=LIKELIHOOD_BINOMIAL every field carries `trials` ([n] ints) and y holds the
+    successes; beta0 ~ N(beta0_prior) (Sec. 3.2).
     """
 
     def __init__(self, fields, *, precision=FP32, chains=1, seed=0, prior=PRIOR_ICAR, rho=1.0,
                  a_tau=1.0, b_tau=0.01, a_sigma=1.0, b_sigma=0.01, fix_hyper=False, tau0=1.0,
                  sigma2_0=1.0, start_sweep=0, burn_in=0, thin=1, trace_capacity=4096,
                  algorithm=ALGO_CHROMATIC, graph_sweeps=0, flags=0, stream=None, intercept=False,
-                 beta0_0=0.0):
+                 beta0_0=0.0, likelihood=LIKELIHOOD_GAUSSIAN, beta0_prior=(0.0, 1000.0)):
         L = lib()
         self._h = ctypes.c_void_p()
         self.chains = int(chains)
@@ -276,6 +281,9 @@ class Sampler:
             d.tau0 = _p(arrs.get("tau0"), ctypes.c_double)
             d.sigma2_0 = _p(arrs.get("sigma2_0"), ctypes.c_double)
             d.beta0 = _p(arrs.get("beta0"), ctypes.c_double)
+            if f.get("trials") is not None:
+                arrs["trials"] = _i32(f["trials"])
+            d.trials = _p(arrs.get("trials"), ctypes.c_int32)
             d.row_ptr = _p(arrs.get("row_ptr"), ctypes.c_int32)
             d.col_idx = _p(arrs.get("col_idx"), ctypes.c_int32)
             d.weights = _p(arrs.get("weights"), ctypes.c_double)
@@ -284,7 +292,8 @@ class Sampler:
             keep.append(arrs)
         model = Model(int(prior), float(rho), float(a_tau), float(b_tau), float(a_sigma),
                       float(b_sigma), 1 if fix_hyper else 0, float(tau0), float(sigma2_0),
-                      1 if intercept else 0, float(beta0_0))
+                      1 if intercept else 0, float(beta0_0), int(likelihood), float(beta0_prior[0]),
+                      float(beta0_prior[1]))
         opts = Opts(int(precision), self.chains, int(seed), int(start_sweep), int(burn_in),
                     int(thin), int(trace_capacity), int(algorithm), int(graph_sweeps), int(flags))
         self.stream = current_stream() if stream is None else stream

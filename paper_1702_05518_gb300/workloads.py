@@ -198,6 +198,24 @@ def delaunay_pcar(seed: int = 3, npts: int = 16384, tau_true: float = 4.0, rho: 
              "row_ptr": rp, "col_idx": ci, "points": pts}]
 
 
+def binomial_delaunay(seed: int = 7, npts: int = 14926, tau_true: float = 2.0, rho: float = 0.995,
+                      beta0_true: float = 0.4, trials_range=(1, 64), missing: float = 0.022):
+    """Stand-in for the precinct vote counts of Sec. 3.2 (the election data are not available):
+    a Delaunay graph of `npts` uniform points, x_true from the proper CAR prior at tau_true,
+    success probability logistic(beta0_true + x_true), trials log-uniform in trials_range
+    (integers), a fraction `missing` of sites without data (0 trials), successes binomial."""
+    g = rng(seed)
+    rp, ci, pts = delaunay_graph(npts, g)
+    xt = prior_draw(rp, ci, tau_true, rho, g)
+    lo, hi = np.log(trials_range[0]), np.log(trials_range[1] + 1)
+    m = np.floor(np.exp(g.uniform(lo, hi, npts))).astype(np.int32)
+    m[g.uniform(size=npts) < missing] = 0
+    p = 1.0 / (1.0 + np.exp(-(beta0_true + xt)))
+    y = g.binomial(m, p).astype(np.float64)
+    return [{"kind": CSR, "dims": (npts, 0, 0), "n": npts, "y": y, "trials": m, "truth": xt,
+             "row_ptr": rp, "col_idx": ci, "points": pts}]
+
+
 def batched_uneven(seed: int = 4, nlat: int = 224, ngraph: int = 32, side_range=(32, 512),
                    n_range=(1000, 50000)):
     """Many independent fields of uneven sizes: `nlat` 4-neighbour lattices with sides
