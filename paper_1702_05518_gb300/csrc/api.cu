@@ -79,7 +79,8 @@ struct gmrf_sampler {
     std::vector<int32_t> tile_off, tile_cnt;  // per (colour, kind): index colour * 4 + kind
     // Stages of one sweep, in launch order.
     struct Stage {
-        int type;    // 0: colour step, 1: fused 2-D lattice sweep, 2: hyperparameter draw
+        int type;    // 0: colour step, 1: fused 2-D lattice sweep, 2: hyperparameter draw,
+                     // 3: Polya-Gamma draws (binomial likelihood, first in the sweep)
         int kind;
         int colour;
     };
@@ -100,6 +101,7 @@ struct gmrf_sampler {
     void *w = nullptr, *deg = nullptr;
     double *tau = nullptr, *sig2 = nullptr, *beta = nullptr;
     int32_t *trials = nullptr;  // binomial likelihood: [slots] trials in the colour-split layout
+    void *psi = nullptr;        // binomial likelihood: [slots][Cp] Polya-Gamma draws of the sweep
     void *hyp = nullptr;        // [F * Cp][kHypStride] copies in precision T
     Part3 *partials = nullptr;
     double *trace_tau = nullptr, *trace_sig = nullptr, *trace_beta = nullptr;
@@ -417,6 +419,7 @@ StepArgs step_args(gmrf_sampler *s, int colour, int kind, int update, int accumu
     a.intercept = s->model.intercept ? 1 : 0;
     a.binomial = binomial_model(s) ? 1 : 0;
     a.trials = s->trials;
+    a.psi = s->psi;
     return a;
 }
 
@@ -520,6 +523,23 @@ cudaError_t enqueue_stage(gmrf_sampler *s, size_t k, int update, int accumulate,
     }
     if (g.type == 0)
         return launch_colour_step(s->precision, s->V, g.kind, step_args(s, g.colour, g.kind, update, accumulate), st);
+    if (g.type == 3) {
+        if (!update) return cudaSuccess;
+        PgArgs p{};
+        p.fields = s->fields_dev;
+        p.nfields = s->nfields;
+        p.slots = s->slots;
+        p.Cp = s->Cp;
+        p.C = s->C;
+        p.x = s->x;
+        p.hyp = s->hyp;
+        p.trials = s->trials;
+        p.perm = s->perm;
+        p.psi = s->psi;
+        p.ctl = s->ctl;
+        p.key = philox_key(s->opts.seed);
+        return launch_pg_stage(s->precision, p, st);
+    }
     return launch_hyper(s->precision, hyper_args(s, draw, draw_beta, end_of_sweep), st);
 }
 
@@ -991,6 +1011,7 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
             if (s->tile_cnt[slot] > 0) s->stages.push_back({0, kind, c});
         }
     s->stages.push_back({2, -1, -1});
+    if (binomial_model(s)) s->stages.insert(s->stages.begin(), {3, -1, -1});
     s->launches_per_sweep = static_cast<int64_t>(s->stages.size());
     CK(s->alloc_t(&s->tiles_dev, std::max<size_t>(all.size(), 1), sizeof(Tile)));
     if (!all.empty())
@@ -1017,6 +1038,7 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
         }
         if (binomial_model(s)) {
             if (!s->trials) {
+                CK(s->alloc(&s->psi, static_cast<size_t>(std::max<int64_t>(s->slots, 1)) * s->Cp * T));
                 CK(s->alloc_t(&s->trials, static_cast<size_t>(std::max<int64_t>(s->slots, 1)), sizeof(int32_t)));
                 CK(cudaMemsetAsync(s->trials, 0, sizeof(int32_t) * static_cast<size_t>(std::max<int64_t>(s->slots, 1)),
                                    s->stream));
@@ -1468,11 +1490,12 @@ gmrf_status gmrf_launch_stage(gmrf_sampler *s, int32_t stage, int32_t accumulate
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
     if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "stages of the plain sweep");
     if (stage < 0 || stage >= static_cast<int32_t>(s->stages.size())) return fail(GMRF_E_INVALID, "stage out of range");
-    static const char *kNames[3][4] = {
+    static const char *kNames[4][4] = {
         {"colour step, 2-D 4-neighbour lattice", "colour step, 2-D 8-neighbour lattice",
          "colour step, 3-D 6-neighbour lattice", "colour step, CSR graph"},
         {"fused sweep, 2-D 4-neighbour lattice", "fused sweep, 2-D 8-neighbour lattice", "", ""},
-        {"hyperparameter draw", "hyperparameter draw", "hyperparameter draw", "hyperparameter draw"}};
+        {"hyperparameter draw", "hyperparameter draw", "hyperparameter draw", "hyperparameter draw"},
+        {"Polya-Gamma draws", "Polya-Gamma draws", "Polya-Gamma draws", "Polya-Gamma draws"}};
     const gmrf_sampler::Stage &g = s->stages[stage];
     if (name) *name = kNames[g.type][g.kind < 0 ? 0 : g.kind];
     if (name && g.type == 1 && s->fQCS[g.kind]) *name = "fused quad sweep, 2-D 8-neighbour lattice";

@@ -61,6 +61,7 @@ struct StepArgs {
     int32_t intercept;   // the model has the intercept beta0
     int32_t binomial;    // binomial counts (successes in y) with the logistic link
     const int32_t *trials;  // [slots] binomial trials m_i (binomial model only)
+    const void *psi;     // [slots][Cp] Polya-Gamma draws of this sweep (binomial model only)
 };
 
 struct HyperArgs {
@@ -142,6 +143,24 @@ struct GammaPreArgs {
     double *gpre;
 };
 cudaError_t launch_gamma_pre(const GammaPreArgs &a, cudaStream_t stream);
+
+// Polya-Gamma stage of the binomial model (sweep_kernels.cu): psi[slot][chain] ~ PG(m_i, beta0 +
+// x_i) for every site from the state at the start of the sweep, one warp per (slot, chain)
+// with the m_i summands spread over the lanes.
+struct PgArgs {
+    const FieldDev *fields;
+    int32_t nfields;
+    int64_t slots;         // total slots (every field)
+    int32_t Cp, C;
+    const void *x;         // [slots][Cp] state (precision T)
+    const void *hyp;       // [F * Cp][kHypStride]
+    const int32_t *trials; // [slots]
+    const int32_t *perm;   // CSR: slot -> natural site
+    void *psi;             // [slots][Cp] out (precision T)
+    SweepCtl *ctl;
+    uint2 key;
+};
+cudaError_t launch_pg_stage(int precision, const PgArgs &a, cudaStream_t stream);
 
 // Launchers (each enqueues on `stream` and returns the launch status).
 // One colour step of the tiles in `a` (all of field kind `kind`).

@@ -56,8 +56,9 @@ struct SiteCtx {
 // and the neighbour values nb[k] of the neighbours flagged in `lower_mask` (those of lower
 // colour), and fold the site's terms into the partial sums.
 //
-// Binomial model: first psi | beta0, x_i ~ PG(m_i, beta0 + x_i) from the site's current value, then
-// x_i with precision tau d_i + psi and mean (tau rho s_i + kappa_i - psi beta0) / P,
+// Binomial model: psi | beta0, x_i ~ PG(m_i, beta0 + x_i) was drawn from the site's value at the
+// start of the sweep (the Polya-Gamma stage); x_i gets precision tau d_i + psi and mean
+// (tau rho s_i + kappa_i - psi beta0) / P,
 // kappa_i = y_i - m_i / 2; the partial sums then collect psi and kappa_i - psi x_i (for beta0)
 // in place of the Gaussian residual sums.
 template <typename T, int V, int NB, int MODEL>
@@ -79,15 +80,12 @@ __device__ __forceinline__ void finish_site(const StepArgs &a, SiteCtx<T, V> &cx
     T psi[V];
     const T kappa = yv - static_cast<T>(0.5) * static_cast<T>(mtr);
     if (MODEL == kModelBinomial && a.update) {
-        T xo[V], z[V];
-        Vec<T, V>::ld(xp, xo);
+        T z[V];
+        // psi of this site and chain, drawn by the Polya-Gamma stage from the start-of-sweep state
+        Vec<T, V>::ld(static_cast<const T *>(a.psi) + (xp - static_cast<T *>(a.x)), psi);
         site_normals<T, V>(a.key, site, sweep, stream, chain0, a.lanes, z);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            int fb = 0;
-            psi[v] = static_cast<T>(pg_draw(mtr, static_cast<double>(cx.beta[v]) + static_cast<double>(xo[v]), a.key,
-                                            site, sweep, stream, chain0 + v, fb));
-            if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), static_cast<unsigned long long>(fb));
             const T P = cx.tau[v] * d + psi[v];
             const T m = (cx.tau[v] * rho * s[v] + kappa - psi[v] * cx.beta[v]) * Arith<T>::rcp(P);
             xn[v] = m + z[v] * Arith<T>::rsq(P);
@@ -460,6 +458,74 @@ __global__ void __launch_bounds__(kHyperWarps * 32) hyper_kernel(const HyperArgs
     }
 }
 
+// The Polya-Gamma stage of the binomial model: one warp per (slot, chain).  The slot's natural
+// site gives the counters; lane l draws the PG(1, c) summands k = l, l + 32, ... < m_i and the
+// warp adds them in a fixed order (shuffle tree); psi = 0 for sites without trials and for
+// padding slots.
+template <typename T>
+__global__ void pg_stage_kernel(const PgArgs a)
+{
+    pdl_wait_then_release();
+    const int lane = threadIdx.x & 31;
+    const uint32_t sweep = static_cast<uint32_t>(a.ctl->sweep);
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    const T *X = static_cast<const T *>(a.x);
+    const T *hyp = static_cast<const T *>(a.hyp);
+    T *PSI = static_cast<T *>(a.psi);
+    int fb = 0;
+    for (int64_t task = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; task < a.slots * a.C;
+         task += warps) {
+        const int64_t slot = task / a.C;
+        const int chain = static_cast<int>(task - slot * a.C);
+        int fi = 0;  // field of the slot (fields are few; their slot ranges are in order)
+        while (fi + 1 < a.nfields && a.fields[fi + 1].slot0 <= slot) ++fi;
+        const FieldDev &f = a.fields[fi];
+        const int64_t rel = slot - f.slot0;
+        // natural site of the slot (padding slots of the lattice layouts have none)
+        int64_t site = -1;
+        if (f.kind == kCsr) {
+            site = a.perm[f.csr0 + rel];
+        } else {
+            const int64_t sub = static_cast<int64_t>(f.rows) * f.cols;
+            const int64_t c = rel / sub, r = (rel - c * sub) / f.cols, h = rel - c * sub - r * f.cols;
+            if (f.kind == kLat2D8) {
+                const int64_t i = 2 * r + (c >> 1), j = 2 * h + (c & 1);
+                if (i < f.dims[0] && j < f.dims[1]) site = i * f.dims[1] + j;
+            } else if (f.kind == kLat2D4) {
+                const int64_t j = 2 * h + ((c + r) & 1);
+                if (j < f.dims[1]) site = r * f.dims[1] + j;
+            } else {
+                const int64_t l = r / f.dims[1], i = r - l * f.dims[1], j = 2 * h + ((c + l + i) & 1);
+                if (j < f.dims[2]) site = r * f.dims[2] + j;
+            }
+        }
+        const int m = site >= 0 ? a.trials[slot] : 0;
+        double sum = 0.0;
+        if (m > 0) {
+            const double eta = static_cast<double>(hyp[(static_cast<int64_t>(fi) * a.Cp + chain) * kHypStride + 2]) +
+                               static_cast<double>(X[slot * a.Cp + chain]);
+            const double z = 0.5 * fabs(eta);
+            // the proposal's mixture weight, once per warp (FP64 special functions are costly here)
+            double wexp = lane == 0 ? pg_exp_weight(z) : 0.0;
+            wexp = __shfl_sync(0xffffffffu, wexp, 0);
+            for (int k = lane; k < m; k += 32) {
+                PgStream st;
+                pg_stream_init(st, a.key, static_cast<uint32_t>(site), sweep, f.stream, static_cast<uint32_t>(chain),
+                               static_cast<uint32_t>(k));
+                double j = pg_jstar(z, wexp, st);
+                if (j < 0.0) {
+                    ++fb;
+                    j = z > 0.0 ? tanh(z) / z : 1.0;
+                }
+                sum += 0.25 * j;
+            }
+        }
+        for (int off = 16; off >= 1; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        if (lane == 0) PSI[slot * a.Cp + chain] = static_cast<T>(sum);
+    }
+    if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), static_cast<unsigned long long>(fb));
+}
+
 // Natural order -> colour-split layout: y and the chains' initial states (x0 = y by default;
 // chains >= C of the padded layout start at y too).
 template <typename T>
@@ -629,6 +695,16 @@ cudaError_t launch_pack(int precision, const FieldDev *fields_dev, const FieldDe
         pack_kernel<double><<<grid, 256, 0, stream>>>(fields_dev, fidx, C, Cp, y_nat, x0_nat, perm_inv,
                                                       static_cast<double *>(x), static_cast<double *>(y));
     return cudaGetLastError();
+}
+
+cudaError_t launch_pg_stage(int precision, const PgArgs &a, cudaStream_t stream)
+{
+    const int64_t tasks = a.slots * a.C;
+    int64_t blocks = (tasks + 7) / 8;  // eight warps per block
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks < 1) blocks = 1;
+    if (precision == 0) return launch_sweep_kernel(pg_stage_kernel<float>, static_cast<int>(blocks), 256, 0, stream, a);
+    return launch_sweep_kernel(pg_stage_kernel<double>, static_cast<int>(blocks), 256, 0, stream, a);
 }
 
 cudaError_t launch_pack_int(const FieldDev *fields_dev, const FieldDev &f, int32_t fidx, const int32_t *v_nat,
