@@ -158,12 +158,16 @@ def stage_algorithmic_bytes(spec, stage_name, colour, colourings, S=4):
 # a workload, from one ncu capture (cold L2: ncu flushes caches before the launch), with the
 # SHA-256 of the kernel's sources at capture time.  Reported only while the sources are unchanged.
 MEASURED_TRAFFIC = {
-    "image1024": dict(kernel="lattice_fused_fast<float, 1, 1024, 1>", bytes=8_423_680,
-                      sources={"lattice_fused.cu": "b6111251199cbb41ea739f5c7090a09820f357d19c462fb06c5d1b7ab966e84f",
-                               "gmrf_device.cuh": "cc325fbeac4dd2dba381352aa93b6e47b62b3124fa03fd20bb1a0876904aefdc"}),
-    "volume256": dict(kernel="colour_step_kernel<float, 4, 2>", bytes=313_337_088 + 234_184_448,
-                      sources={"sweep_kernels.cu": "565e05f93e74b79094a34aa8c3fb8d8122291d3bcfb201348b83ee20246286a1",
-                               "gmrf_device.cuh": "cc325fbeac4dd2dba381352aa93b6e47b62b3124fa03fd20bb1a0876904aefdc"}),
+    "image1024": dict(kernel="lattice_quad_kernel<64, 768, 3>", bytes=8_454_656,
+                      sources={"lattice_quad.cu": "6b31162ebf69de24725c91110ababc5e7446622d1284a7126d8df363adf451e1",
+                               "gmrf_device.cuh": "f0ee38c95478d3b4b0953c6a4cf0ccf52504e3b2725d76bb088d41248fe545ff",
+                               "gmrf_internal.h": "700a3a0ccd7023345538e50a104b849269aa70390db665ea8f1513afff3d1260"}),
+    "volume256": dict(kernel="colour_step_kernel<float, 4, 2, 0>", bytes=315_974_144 + 233_456_640,
+                      sources={"sweep_kernels.cu": "85317fc97e2838ba9d5752d8fc9ee1c0d910e4fc43c8f9d99cf047ece515f5f4",
+                               "gmrf_device.cuh": "f0ee38c95478d3b4b0953c6a4cf0ccf52504e3b2725d76bb088d41248fe545ff",
+                               "gmrf_internal.h": "700a3a0ccd7023345538e50a104b849269aa70390db665ea8f1513afff3d1260",
+                               "hyper_task.cuh": "4ae97f8805bbc9b81b1de7a15033378938ff5c6f043099f737952c1948691545",
+                               "pg.cuh": "fbe6fe245f036210f0dd57a94a1023430acae2c4dfeb85b98d50ed3675bf9dc3"}),
 }
 
 
