@@ -815,8 +815,9 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     }
 
     // Tiles: per colour, each field's colour class cut into tiles of `target` (site, chain
-    // vector) elements, sized so a colour step has several blocks per SM (at least 512 and at
-    // most 16384 elements per tile); partial-sum slots are contiguous per field.
+    // vector) elements, sized so a colour step has several blocks per SM (at least one element
+    // per thread, so small classes spread over many SMs, and at most 16384 elements per tile);
+    // partial-sum slots are contiguous per field.
     const int CV = s->Cp / s->V;
     // 2-D lattice fields take the fused sweep when a tile of at least 16 x 16 sites with its
     // halo (state, normals and y) fits the 72 KiB shared-memory budget (3 blocks per SM) and it
@@ -936,7 +937,7 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     for (int fi = 0; fi < s->nfields; ++fi)
         if (!fused_kind[s->hf[fi].kind]) total_elems += static_cast<int64_t>(s->hf[fi].n) * CV;
     const int64_t per_colour = total_elems / 2;
-    const int64_t target = std::min<int64_t>(16384, std::max<int64_t>(512, per_colour / (152 * 4)));
+    const int64_t target = std::min<int64_t>(16384, std::max<int64_t>(kBlock, per_colour / (152 * 4)));
     s->kmax = 0;
     for (auto &h : s->hf) s->kmax = std::max(s->kmax, h.ncolors);
     std::vector<std::vector<Tile>> by_colour(s->kmax);

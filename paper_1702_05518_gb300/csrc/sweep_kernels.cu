@@ -301,7 +301,7 @@ __device__ void lattice8_tile(const StepArgs &a, const FieldDev &f, const Tile &
 
 // CSR field: permuted positions [start, start + count) of one colour class; neighbours are read
 // through the permuted row; a neighbour has lower colour iff its position is below the class's
-// first position.  The lower-colour terms of the reduction take a second pass over the row.
+// first position.
 template <typename T, int V, int MODEL>
 __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, SiteCtx<T, V> &cx, int CV,
                          int cv_shift, uint32_t sweep)
@@ -323,10 +323,30 @@ __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, Si
         const int cv = e & (CV - 1);
         const int pos = t.start + (e >> cv_shift);
         const int rb = rp[pos], re = rp[pos + 1];
-        T s[V];
+        // The first R neighbours stay in registers: their loads are all issued before any is
+        // used, and the lower-colour terms of the prior sum need no second pass over them.
+        constexpr int R = V == 4 ? 6 : 8;
+        T nb[R][V], wnb[R], s[V];
+        uint32_t lower = 0;
 #pragma unroll
         for (int v = 0; v < V; ++v) s[v] = 0;
-        for (int k = rb; k < re; ++k) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int k = rb + q;
+            if (k < re) {
+                const int jn = ci[k];
+                Vec<T, V>::ld(X + (f.slot0 + jn) * Cp + cv * V, nb[q]);
+                wnb[q] = wr ? wr[k] : static_cast<T>(1);
+                lower |= (jn < lo ? 1u : 0u) << q;
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) nb[q][v] = 0;
+                wnb[q] = 0;
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) s[v] += wnb[q] * nb[q][v];
+        }
+        for (int k = rb + R; k < re; ++k) {  // rows longer than R
             T xv[V];
             Vec<T, V>::ld(X + (f.slot0 + ci[k]) * Cp + cv * V, xv);
             const T wv = wr ? wr[k] : static_cast<T>(1);
@@ -337,38 +357,37 @@ __device__ void csr_tile(const StepArgs &a, const FieldDev &f, const Tile &t, Si
         const T yv = Y[self];
         const T d = DEG[f.csr0 + pos];
         const uint32_t site = static_cast<uint32_t>(a.perm[f.csr0 + pos]);
-        T nb0[1][V];
-        T w0[1] = {0};
         const int mtr = MODEL == kModelBinomial ? a.trials[self] : 0;
-        finish_site<T, V, 1, MODEL>(a, cx, X + self * Cp + cv * V, MEAN + self * Cp + cv * V, M2 + self * Cp + cv * V, yv,
-                             mtr, d, site, sweep, f.stream, static_cast<uint32_t>(cv * V), s, nb0, 0u, w0);
-        // finish_site added (1 - rho) d x^2 and the likelihood term; add the lower-colour edges.
-        T xn[V];
-        Vec<T, V>::ld(X + self * Cp + cv * V, xn);
-        T e2[V];
+        finish_site<T, V, R, MODEL>(a, cx, X + self * Cp + cv * V, MEAN + self * Cp + cv * V, M2 + self * Cp + cv * V, yv,
+                                    mtr, d, site, sweep, f.stream, static_cast<uint32_t>(cv * V), s, nb, lower, wnb);
+        if (re - rb > R) {
+            // the lower-colour edges beyond the first R
+            T xn[V], e2[V];
+            Vec<T, V>::ld(X + self * Cp + cv * V, xn);
 #pragma unroll
-        for (int v = 0; v < V; ++v) e2[v] = 0;
-        for (int k = rb; k < re; ++k) {
-            const int jn = ci[k];
-            if (jn >= lo) continue;
-            T xv[V];
-            Vec<T, V>::ld(X + (f.slot0 + jn) * Cp + cv * V, xv);
-            const T wv = wr ? wr[k] : static_cast<T>(1);
+            for (int v = 0; v < V; ++v) e2[v] = 0;
+            for (int k = rb + R; k < re; ++k) {
+                const int jn = ci[k];
+                if (jn >= lo) continue;
+                T xv[V];
+                Vec<T, V>::ld(X + (f.slot0 + jn) * Cp + cv * V, xv);
+                const T wv = wr ? wr[k] : static_cast<T>(1);
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const T df = xn[v] - xv[v];
-                e2[v] += wv * df * df;
+                for (int v = 0; v < V; ++v) {
+                    const T df = xn[v] - xv[v];
+                    e2[v] += wv * df * df;
+                }
             }
-        }
 #pragma unroll
-        for (int v = 0; v < V; ++v) cx.accS[v] += rho * e2[v];
+            for (int v = 0; v < V; ++v) cx.accS[v] += rho * e2[v];
+        }
     }
 }
 
 // MODEL: the observation model; without the intercept beta0 = 0 and the third sum is not
 // needed, which the compiler then removes, registers included.
 template <typename T, int V, int KIND, int MODEL>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 3 : 1) colour_step_kernel(const StepArgs a)
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (KIND == kCsr ? 2 : 3) : 1) colour_step_kernel(const StepArgs a)
 {
     pdl_wait_then_release();
     const Tile t = a.tiles[blockIdx.x];
