@@ -519,28 +519,28 @@ __global__ void pg_stage_kernel(const PgArgs a)
             }
         }
         const int m = site >= 0 ? a.trials[slot] : 0;
-        double sum = 0.0;
+        // the sampler's arithmetic follows the state precision (pg.cuh)
+        T sum = 0;
         if (m > 0) {
-            const double eta = static_cast<double>(hyp[(static_cast<int64_t>(fi) * a.Cp + chain) * kHypStride + 2]) +
-                               static_cast<double>(X[slot * a.Cp + chain]);
-            const double z = 0.5 * fabs(eta);
-            // the proposal's mixture weight, once per warp (FP64 special functions are costly here)
-            double wexp = lane == 0 ? pg_exp_weight(z) : 0.0;
+            const T eta = hyp[(static_cast<int64_t>(fi) * a.Cp + chain) * kHypStride + 2] + X[slot * a.Cp + chain];
+            const T z = static_cast<T>(0.5) * fabs(eta);
+            // the proposal's mixture weight, once per warp (the special functions are costly)
+            T wexp = lane == 0 ? pg_exp_weight<T>(z) : static_cast<T>(0);
             wexp = __shfl_sync(0xffffffffu, wexp, 0);
             for (int k = lane; k < m; k += 32) {
                 PgStream st;
                 pg_stream_init(st, a.key, static_cast<uint32_t>(site), sweep, f.stream, static_cast<uint32_t>(chain),
                                static_cast<uint32_t>(k));
-                double j = pg_jstar(z, wexp, st);
-                if (j < 0.0) {
+                T j = pg_jstar<T>(z, wexp, st);
+                if (j < static_cast<T>(0)) {
                     ++fb;
-                    j = z > 0.0 ? tanh(z) / z : 1.0;
+                    j = z > static_cast<T>(0) ? tanh(z) / z : static_cast<T>(1);
                 }
-                sum += 0.25 * j;
+                sum += static_cast<T>(0.25) * j;
             }
         }
         for (int off = 16; off >= 1; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-        if (lane == 0) PSI[slot * a.Cp + chain] = static_cast<T>(sum);
+        if (lane == 0) PSI[slot * a.Cp + chain] = sum;
     }
     if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), static_cast<unsigned long long>(fb));
 }
