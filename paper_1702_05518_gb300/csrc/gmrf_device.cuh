@@ -127,10 +127,12 @@ __host__ __device__ __forceinline__ uint2 philox_key(uint64_t seed)
 // may be scheduled before its predecessor in the stream has finished.  It waits here, before
 // it reads anything a predecessor wrote, and then lets its own successor be scheduled (which in
 // turn waits for this grid to finish).  Without that launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait_then_release()
 {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    pdl_wait();
+    pdl_release();
 }
 
 // ------------------------------------------------------------------------------------------

@@ -193,16 +193,17 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
     quad_normals<QCS, NT, NQ>(z, a.key, static_cast<uint32_t>(predicted), f.stream, static_cast<uint32_t>(Wl) >> 2, gu0,
                               gv0);
 
-    pdl_wait_then_release();
+    pdl_wait();
     const long long sweep_ll = a.ctl->sweep;
-    if (sweep_ll != predicted)
-        quad_normals<QCS, NT, NQ>(z, a.key, static_cast<uint32_t>(sweep_ll), f.stream, static_cast<uint32_t>(Wl) >> 2,
-                                  gu0, gv0);
-    if (threadIdx.x == 0 && s_last) {
+    if (threadIdx.x == 0 && s_last) {  // the next launch's prediction, before it may start
         a.ctl->fnext = sweep_ll + 1;
         a.ctl->fticket = 0;
         if (sweep_ll != predicted) a.ctl->fmiss += 1;
     }
+    pdl_release();
+    if (sweep_ll != predicted)
+        quad_normals<QCS, NT, NQ>(z, a.key, static_cast<uint32_t>(sweep_ll), f.stream, static_cast<uint32_t>(Wl) >> 2,
+                                  gu0, gv0);
     const float *X = static_cast<const float *>((sweep_ll & 1) ? a.x_alt : a.x) + f.slot0;
     float *XW = static_cast<float *>((sweep_ll & 1) ? a.x : a.x_alt) + f.slot0;
     QuadCtx cx;

@@ -461,7 +461,10 @@ constexpr int kHyperWarps = 8;
 template <typename T>
 __global__ void __launch_bounds__(kHyperWarps * 32) hyper_kernel(const HyperArgs a)
 {
-    pdl_wait_then_release();
+    // Let the next sweep kernel be scheduled now: it does its own early work (observations,
+    // predicted normals) while this draw waits for and runs after the current sweep.
+    pdl_release();
+    pdl_wait();
     const int task = blockIdx.x * kHyperWarps + (threadIdx.x >> 5);
     const long long sweep = a.ctl->sweep;
     if (task < a.nfields * a.Cp * 2) hyper_task<T>(a, task, sweep);
