@@ -502,23 +502,47 @@ def run_ours(args):
             prate = spec["fields"][0]["n"] * spec["chains"] * ps / (ev0.elapsed_time(ev1) * 1e-3)
         plain = {"value": prate, "unit": UNIT, "dtype": "f64", "sweeps": ps, "speedup": None}
 
-    # End to end through the C ABI with host buffers: create (H2D copy of y), all sweeps, fetch
-    # of the posterior mean (D2H), destroy.
+    # End to end through the C ABI with host buffers.  Serving: one sampler built for the graph
+    # (outside the timed region); per step the observations (and trials) go up from pinned host
+    # memory (gmrf_sampler_set_data, which also restarts the chains), all sweeps run, and every
+    # chain's posterior mean comes back into pinned host memory.  Cold: the same plus creating and
+    # destroying the sampler (colouring, layout, tiles, graph capture) inside every step.
     e2e_steps = max(1, min(3, args.steps))
     n_total = sum(f["n"] for f in spec["fields"])
-    h2d = 8 * n_total
+    binom = spec.get("likelihood") == "binomial"
+    host_y = [torch.from_numpy(np.ascontiguousarray(f["y"], np.float64)).pin_memory() for f in spec["fields"]]
+    host_m = [torch.from_numpy(np.ascontiguousarray(f["trials"], np.int32)).pin_memory() if binom else None
+              for f in spec["fields"]]
+    host_mean = [[torch.empty(f["n"], dtype=torch.float64, pin_memory=True) for _ in range(spec["chains"])]
+                 for f in spec["fields"]]
+    h2d = (8 + (4 if binom else 0)) * n_total
     d2h = 8 * n_total * spec["chains"]
+
+    def e2e_step(sampler):
+        for fi in range(len(spec["fields"])):
+            sampler.set_data(fi, host_y[fi].numpy(), None if host_m[fi] is None else host_m[fi].numpy())
+        sampler.sweep(spec["sweeps"])
+        for fi in range(len(spec["fields"])):
+            for c in range(spec["chains"]):
+                sampler.fetch_mean(fi, c, out=host_mean[fi][c].numpy())
+
+    with g.Sampler(spec["fields"], **kw) as s2:
+        e2e_step(s2)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step(s2)
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
+    e2e_value = world * units * e2e_steps / e2e_s
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         with g.Sampler(spec["fields"], **kw) as s2:
-            s2.sweep(spec["sweeps"])
-            for fi in range(len(spec["fields"])):
-                for c in range(spec["chains"]):
-                    s2.fetch(fi, c)
+            e2e_step(s2)
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
-    e2e_value = world * units * e2e_steps / e2e_s
+    cold_s = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
+    e2e_cold = world * units * e2e_steps / cold_s
 
     peaks = {}
     try:
@@ -560,7 +584,12 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "wall_ms_per_step": 1e3 * wall / args.steps,
             "clocks": clocks,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps,
+                    "per_step": "observations H2D (pinned) + restart, all sweeps, posterior means D2H (pinned); "
+                                "sampler built once outside the timed region",
+                    "cold_value": e2e_cold,
+                    "cold_per_step": "the same with sampler creation and destruction inside every step"},
             "gpu_launches": launches,
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -309,6 +309,28 @@ gmrf_status gmrf_site_psrf(gmrf_sampler *s, int32_t field, double *psrf, double 
 gmrf_status gmrf_sampler_reset(gmrf_sampler *s);
 
 /*
+ * Replace the data of one field and restart the run: a sampler built once for a graph then
+ * serves many data sets of that graph (the observations y of Sec. 3.1, or the successes and
+ * trials of the binomial model of Sec. 3.2) without rebuilding its layout, tiles or graphs.
+ *   y: host [n] observations in natural site order (finite; for the binomial likelihood the
+ *      successes, 0 <= y[i] <= trials[i]).
+ *   trials: host [n], required for the binomial likelihood (0..4095; 0 = site unobserved),
+ *      ignored otherwise.
+ *   x0: host [chains][n] initial states, or NULL for the creation default (y for the Gaussian
+ *      likelihood, 0 for the binomial one).
+ * Afterwards the sampler is in the state gmrf_sampler_create with these arrays followed by
+ * gmrf_sampler_reset would give (all fields restart, as gmrf_sampler_reset does; the other
+ * fields keep their data).  The host arrays are read before the call returns (it synchronises
+ * the sampler's stream after its uploads); the rest is enqueued asynchronously.  The first call
+ * allocates a device staging buffer of (1 + chains) doubles (+ one int32 for binomial data) per
+ * site of the largest field; later calls allocate nothing.
+ * Errors: GMRF_E_INVALID (bad field index or data; nothing changes), GMRF_E_STATE, GMRF_E_OOM,
+ * GMRF_E_CUDA.
+ */
+gmrf_status gmrf_sampler_set_data(gmrf_sampler *s, int32_t field, const double *y, const int32_t *trials,
+                                  const double *x0);
+
+/*
  * Diagnostic: enqueue exactly one launch of stage `stage` of a sweep on the sampler's stream.
  * A sweep is gmrf_info.launches_per_sweep stages in order: the fused 2-D lattice sweeps (one
  * per lattice kind present), the colour steps of the other fields (one per colour and field

@@ -109,6 +109,8 @@ struct gmrf_sampler {
     double *gpre = nullptr;     // [gpre_batch][F * Cp][4] precomputed variates of a batch
     int32_t gpre_batch = 0;     // sweeps per batch of precomputed variates
     double *staging = nullptr;  // [max_n] doubles for fetch
+    double *data_stage = nullptr;    // [max_n][1 + C] doubles: uploads of gmrf_sampler_set_data
+    int32_t *trials_stage = nullptr; // [max_n] trials uploaded by gmrf_sampler_set_data
     double *diag_work = nullptr;  // [Cp][trace_capacity] scratch of the trace diagnostics
     double *diag_out = nullptr;   // [Cp][4] per-chain results, then the PSRF and a max slot
     void *x_init = nullptr;     // state at creation (for gmrf_sampler_reset)
@@ -1482,6 +1484,73 @@ gmrf_status gmrf_sampler_reset(gmrf_sampler *s)
         return cuda_status(f);
     }
     return GMRF_OK;
+}
+
+gmrf_status gmrf_sampler_set_data(gmrf_sampler *s, int32_t field, const double *y, const int32_t *trials,
+                                  const double *x0)
+{
+    g_last_error.clear();
+    if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
+    if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (field < 0 || field >= s->nfields) return fail(GMRF_E_INVALID, "field out of range");
+    const int64_t n = s->hf[field].n;
+    const bool binomial = binomial_model(s);
+    if (!y) return fail(GMRF_E_INVALID, "y is required");
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(y[i])) return fail(GMRF_E_INVALID, "y must be finite");
+    if (binomial) {
+        if (!trials) return fail(GMRF_E_INVALID, "binomial data need trials");
+        for (int64_t i = 0; i < n; ++i) {
+            if (trials[i] < 0 || trials[i] > 4095) return fail(GMRF_E_INVALID, "trials must be in 0..4095");
+            if (!(y[i] >= 0.0 && y[i] <= trials[i]))
+                return fail(GMRF_E_INVALID, "successes y must be in [0, trials]");
+        }
+    }
+    if (x0)
+        for (int64_t i = 0; i < n * s->C; ++i)
+            if (!std::isfinite(x0[i])) return fail(GMRF_E_INVALID, "x0 must be finite");
+    const bool plain = s->algorithm == GMRF_ALGO_PLAIN;
+    if (!plain && !s->data_stage) {
+        // One staging area for the largest field: y, then x0 (or its default) for every chain.
+        int64_t max_n = 1;
+        for (const HostField &h : s->hf) max_n = std::max<int64_t>(max_n, h.n);
+        cudaError_t e = s->alloc_t(&s->data_stage, static_cast<size_t>(max_n) * (1 + s->C), sizeof(double));
+        if (e == cudaSuccess && binomial)
+            e = s->alloc_t(&s->trials_stage, static_cast<size_t>(max_n), sizeof(int32_t));
+        if (e != cudaSuccess) {
+            cudaGetLastError();  // an allocation failure leaves the context usable
+            return cuda_status(CudaFail{e, "staging buffer for gmrf_sampler_set_data"});
+        }
+    }
+    try {
+        const size_t yb = sizeof(double) * static_cast<size_t>(n);
+        if (plain) {
+            CK(cudaMemcpyAsync(const_cast<double *>(s->plain.y), y, yb, cudaMemcpyHostToDevice, s->stream));
+            for (int c = 0; c < s->C; ++c)
+                CK(cudaMemcpyAsync(static_cast<double *>(s->x_init) + c * n, x0 ? x0 + c * n : y, yb,
+                                   cudaMemcpyHostToDevice, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+        } else {
+            double *y_d = s->data_stage, *x0_d = s->data_stage + n;
+            CK(cudaMemcpyAsync(y_d, y, yb, cudaMemcpyHostToDevice, s->stream));
+            if (x0) CK(cudaMemcpyAsync(x0_d, x0, yb * s->C, cudaMemcpyHostToDevice, s->stream));
+            else if (binomial) CK(cudaMemsetAsync(x0_d, 0, yb * s->C, s->stream));  // all-zero bits: +0.0
+            if (binomial)
+                CK(cudaMemcpyAsync(s->trials_stage, trials, sizeof(int32_t) * static_cast<size_t>(n),
+                                   cudaMemcpyHostToDevice, s->stream));
+            CK(cudaStreamSynchronize(s->stream));  // the host arrays may be reused from here on
+            if (binomial)
+                CK(launch_pack_int(s->fields_dev, s->fd[field], field, s->trials_stage, s->perm_inv, s->trials,
+                                   s->stream));
+            // The same packing as at creation, into the restart state.
+            CK(launch_pack(s->precision, s->fields_dev, s->fd[field], field, s->C, s->Cp, y_d,
+                           (x0 || binomial) ? x0_d : nullptr, s->perm_inv, s->x_init, s->y, s->stream));
+        }
+    } catch (const CudaFail &f) {
+        s->poisoned = true;
+        return cuda_status(f);
+    }
+    return gmrf_sampler_reset(s);
 }
 
 gmrf_status gmrf_launch_stage(gmrf_sampler *s, int32_t stage, int32_t accumulate, const char **name)

@@ -26,7 +26,7 @@ LIKELIHOOD_GAUSSIAN, LIKELIHOOD_BINOMIAL = 0, 1
 
 EXPORTED = ["gmrf_color_graph", "gmrf_color_graph_noalloc", "gmrf_sampler_create", "gmrf_sampler_destroy", "gmrf_sweep",
             "gmrf_hyper_update", "gmrf_fetch_samples", "gmrf_field_colors", "gmrf_sampler_info",
-            "gmrf_sampler_reset", "gmrf_launch_stage", "gmrf_fetch_intercept",
+            "gmrf_sampler_reset", "gmrf_sampler_set_data", "gmrf_launch_stage", "gmrf_fetch_intercept",
             "gmrf_trace_diagnostics", "gmrf_site_psrf",
             "gmrf_validate_csr", "gmrf_philox_words", "gmrf_site_normals", "gmrf_last_error",
             "gmrf_version"]
@@ -107,6 +107,8 @@ def lib() -> ctypes.CDLL:
             L.gmrf_sweep.restype = st
             L.gmrf_sampler_reset.argtypes = [vp]
             L.gmrf_sampler_reset.restype = st
+            L.gmrf_sampler_set_data.argtypes = [vp, ctypes.c_int32, f64p, i32p, f64p]
+            L.gmrf_sampler_set_data.restype = st
             L.gmrf_launch_stage.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_char_p)]
             L.gmrf_launch_stage.restype = st
             L.gmrf_hyper_update.argtypes = [vp]
@@ -384,6 +386,30 @@ class Sampler:
         _check(lib().gmrf_fetch_samples(self._h, field, chain, _p(x, ctypes.c_double), None, None,
                                         0, None, None, None, None, None))
         return x
+
+    def fetch_mean(self, field=0, chain=0, out=None):
+        """Posterior mean of one (field, chain) over the accumulated sweeps, natural order, into
+        `out` (a float64 host array of n, e.g. a pinned tensor's numpy view) or a new array."""
+        n = int(self.fields[field]["n"])
+        m = np.zeros(n) if out is None else out
+        if m.dtype != np.float64 or m.shape != (n,) or not m.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"out must be a contiguous float64 array of {n}")
+        _check(lib().gmrf_fetch_samples(self._h, field, chain, None, _p(m, ctypes.c_double), None,
+                                        0, None, None, None, None, None))
+        return m
+
+    def set_data(self, field, y, trials=None, x0=None):
+        """Replace one field's observations (and binomial trials, initial states) and restart
+        every chain, as a sampler created with these arrays would start."""
+        ya = _f64(y)
+        ta = _i32(trials)
+        # an out-of-range field goes to the library, which rejects it
+        n = int(self.fields[field]["n"]) if 0 <= int(field) < len(self.fields) else ya.size
+        xa = None if x0 is None else _f64(np.broadcast_to(np.asarray(x0, np.float64), (self.chains, n)))
+        if ya.shape != (n,) or (ta is not None and ta.shape != (n,)):
+            raise ValueError(f"y and trials must have {n} entries")
+        _check(lib().gmrf_sampler_set_data(self._h, int(field), _p(ya, ctypes.c_double), _p(ta, ctypes.c_int32),
+                                           _p(xa, ctypes.c_double)))
 
     def colors(self, field=0):
         n = int(self.fields[field]["n"])
