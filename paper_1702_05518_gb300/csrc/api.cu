@@ -126,6 +126,12 @@ struct gmrf_sampler {
     int64_t bytes = 0;
     bool poisoned = false;
     int64_t launches_per_sweep = 0;
+    // Resident path (lattice_resident.cu): whole sweeps of a small single 2-D lattice field in one
+    // launch, one block per chain; 0 when the field takes the per-sweep stages.
+    int resident = 0, res_NI = 0, res_NT = 0, res_batch = 0;
+    int32_t res_SR = 0, res_SC = 0;
+    size_t res_smem = 0;
+    void *res_z = nullptr;  // [res_batch][C][colours][NI][site threads] normals of a batch
 
     cudaError_t alloc(void **p, size_t b)
     {
@@ -475,6 +481,93 @@ cudaError_t launch_pre(gmrf_sampler *s, int count, cudaStream_t st)
     return launch_gamma_pre(g, st);
 }
 
+// The resident path applies to a single fused 2-D lattice field with the Gaussian likelihood whose
+// chain fits in shared memory (state, observations, mean and M2 with a ring of zeros: cells below
+// 2^16, sites below 2^16) and whose colour classes have at most 2 x 576 (8-neighbour) or 4 x 576
+// (4-neighbour) positions.  It is the
+// default for FP32 samplers; GMRF_FLAG_RESIDENT asks for it in FP64 too and GMRF_FLAG_NO_RESIDENT
+// switches it off.
+cudaError_t plan_resident(gmrf_sampler *s)
+{
+    s->resident = 0;
+    const int flags = s->opts.flags;
+    if (s->algorithm == GMRF_ALGO_PLAIN || s->nfields != 1 || !s->hf[0].fused || binomial_model(s)) return cudaSuccess;
+    if (flags & GMRF_FLAG_NO_RESIDENT) return cudaSuccess;
+    if (s->precision != GMRF_FP32 && !(flags & GMRF_FLAG_RESIDENT)) return cudaSuccess;
+    const FieldDev &f = s->fd[0];
+    if (f.kind != GMRF_LATTICE2D_4 && f.kind != GMRF_LATTICE2D_8) return cudaSuccess;
+    const bool e8 = f.kind == GMRF_LATTICE2D_8;
+    const int K = e8 ? 4 : 2;
+    const int64_t SR = f.rows + 2, SC = f.cols + 2, cells = K * SR * SC;
+    // positions per colour class: the largest class (8-neighbour) or rows x columns (4-neighbour)
+    const int64_t maxq = e8 ? static_cast<int64_t>((f.dims[0] + 1) / 2) * ((f.dims[1] + 1) / 2)
+                            : static_cast<int64_t>(f.dims[0]) * f.cols;
+    // up to 640 site threads with one position per class each, or 576 with 2 or 4 (4-neighbour
+    // lattice only)
+    int NI = 0;
+    for (int ni : {1, 2, 4})
+        if (!NI && (ni < 4 || !e8) && (maxq + ni - 1) / ni <= (ni == 1 ? 640 : 576)) NI = ni;
+    if (!NI || cells >= 65536 || f.n >= 65536) return cudaSuccess;
+    int NTS = static_cast<int>((maxq + NI - 1) / NI);
+    NTS = (NTS + 31) / 32 * 32;
+    const size_t smem = 4 * static_cast<size_t>(cells) * tsize(s->precision) + 8 * static_cast<size_t>(K) * NI * NTS;
+    if (smem > 220 * 1024) return cudaSuccess;  // with the static reduction scratch, under 227 KiB
+    const int NT = NTS + 64;  // and the two drawing warps
+    cudaError_t e = prepare_lattice_resident(s->precision, f.kind, NI, smem);
+    if (e != cudaSuccess) return e;
+    // Sweeps per launch: the Gamma-variate batch, at most 128 (the normals buffer holds a batch).
+    const int batch = std::min(128, std::max(64, s->opts.graph_sweeps));
+    e = s->alloc(&s->res_z, static_cast<size_t>(batch) * s->C * K * NI * NTS * tsize(s->precision));
+    if (e != cudaSuccess) return e;
+    s->res_batch = batch;
+    s->resident = 1;
+    s->res_NI = NI;
+    s->res_NT = NT;
+    s->res_SR = static_cast<int32_t>(SR);
+    s->res_SC = static_cast<int32_t>(SC);
+    s->res_smem = smem;
+    return cudaSuccess;
+}
+
+ResidentArgs resident_args(gmrf_sampler *s, int count, int draw, int draw_beta)
+{
+    ResidentArgs r{};
+    r.fields = s->fields_dev;
+    r.h = hyper_args(s, draw, draw_beta, 1);
+    r.x = s->x;
+    r.x_alt = s->x_alt;
+    r.y = s->y;
+    r.mean = s->mean;
+    r.m2 = s->m2;
+    r.count = count;
+    r.SR = s->res_SR;
+    r.SC = s->res_SC;
+    r.lanes = std::min(s->Cp, 4);
+    r.C = s->C;
+    r.rho = s->model.prior == GMRF_PRIOR_PCAR ? s->model.rho : 1.0;
+    r.zbuf = s->res_z;
+    return r;
+}
+
+cudaError_t launch_res_normals(gmrf_sampler *s, int count, cudaStream_t st)
+{
+    ResNormArgs r{};
+    r.fields = s->fields_dev;
+    r.ctl = s->ctl;
+    r.key = philox_key(s->opts.seed);
+    r.lanes = std::min(s->Cp, 4);
+    r.C = s->C;
+    r.Cp = s->Cp;
+    r.count = count;
+    r.NI = s->res_NI;
+    r.NTS = s->res_NT - 64;
+    r.out = s->res_z;
+    const int gs = r.lanes == 4 ? 0 : (r.lanes == 2 ? 1 : 2);
+    const int64_t groups = (static_cast<int64_t>(s->fd[0].n) + (1 << gs) - 1) >> gs;
+    const int64_t quads = r.lanes == 4 ? s->Cp / 4 : 1;
+    return launch_resident_normals(s->precision, r, groups * quads * count, st);
+}
+
 FusedArgs fused_args(gmrf_sampler *s, int kind, int update, int accumulate)
 {
     FusedArgs a{};
@@ -552,6 +645,20 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int with_hyper, cudaStr
     cudaError_t e = cudaSuccess;
     const int draw = (with_hyper && !s->model.fix_hyper) ? 1 : 0;
     const int draw_beta = (with_hyper && has_beta(s)) ? 1 : 0;
+    if (s->resident) {
+        // Batches of sweeps: the batch's unit-rate Gamma variates and normals, then all its sweeps
+        // in one launch.
+        for (int k = 0; k < nsweeps && e == cudaSuccess;) {
+            const int cnt = std::min(s->res_batch, nsweeps - k);
+            if (draw || draw_beta) e = launch_pre(s, cnt, st);
+            if (e == cudaSuccess) e = launch_res_normals(s, cnt, st);
+            if (e == cudaSuccess)
+                e = launch_lattice_resident(s->precision, s->fd[0].kind, s->res_NI, s->res_NT, s->C,
+                                            resident_args(s, cnt, draw, draw_beta), s->res_smem, st);
+            k += cnt;
+        }
+        return e;
+    }
     for (int k = 0; k < nsweeps && e == cudaSuccess; ++k) {
         // A batch of sweeps starts with the parallel draw of its unit-rate Gamma variates.
         if ((draw || draw_beta) && s->gpre && k % s->gpre_batch == 0)
@@ -1016,6 +1123,7 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     s->stages.push_back({2, -1, -1});
     if (binomial_model(s)) s->stages.insert(s->stages.begin(), {3, -1, -1});
     s->launches_per_sweep = static_cast<int64_t>(s->stages.size());
+    CK(plan_resident(s));
     CK(s->alloc_t(&s->tiles_dev, std::max<size_t>(all.size(), 1), sizeof(Tile)));
     if (!all.empty())
         CK(cudaMemcpyAsync(s->tiles_dev, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice, s->stream));
@@ -1609,6 +1717,7 @@ gmrf_status gmrf_sampler_info(gmrf_sampler *s, gmrf_info *out)
     out->device_bytes = s->bytes;
     out->launches_per_sweep = s->launches_per_sweep;
     out->early_start_misses = c.fmiss;
+    out->resident = s->resident;
     return GMRF_OK;
 }
 

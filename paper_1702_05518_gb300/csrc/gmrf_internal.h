@@ -92,6 +92,35 @@ struct HyperArgs {
                           // the intercept's standard normal, for the batch's sweeps
 };
 
+// Arguments of one launch of the resident kernel (lattice_resident.cu): `count` whole sweeps of
+// the single 2-D lattice field 0, one block per chain, the chain in shared memory.
+struct ResidentArgs {
+    const FieldDev *fields;
+    HyperArgs h;          // the conjugate draws at the end of each sweep (end_of_sweep = 1)
+    void *x;              // state buffer 0 (the state at the start of even sweeps)
+    void *x_alt;          // state buffer 1 (odd sweeps)
+    const void *y;
+    void *mean;
+    void *m2;
+    int32_t count;        // sweeps of this launch
+    int32_t SR, SC;       // rows and columns of a shared sub-array: the global ones + a ring of zeros
+    int32_t lanes;        // normals per site of one Philox block: min(4, Cp)
+    int32_t C;            // chains (one block each)
+    double rho;
+    const void *zbuf;     // [count][C][colour][NI][site thread] normals of the batch (precision T)
+};
+
+// Arguments of the producer of the resident kernel's normals (resident_normals_kernel).
+struct ResNormArgs {
+    const FieldDev *fields;
+    SweepCtl *ctl;        // the batch starts at ctl->sweep
+    uint2 key;
+    int32_t lanes, C, Cp;
+    int32_t count;        // sweeps of the batch
+    int32_t NI, NTS;      // positions per thread and class, site threads
+    void *out;
+};
+
 // A tile of the fused 2-D lattice sweep: natural coordinates of its first site.
 struct TileXY {
     int32_t field;
@@ -185,6 +214,14 @@ size_t lattice_fused_smem(int precision, int kind, int Cp, int TR, int TC);
 cudaError_t prepare_lattice_fused(int precision, int V, int kind, size_t smem);
 cudaError_t launch_lattice_fused(int precision, int V, int kind, const FusedArgs &a, size_t smem,
                                  cudaStream_t stream);
+// Resident path: NI colour-class positions per thread (1, 2 or 4), `threads` (<= 704) per block, one block per
+// chain; prepare_lattice_resident raises the kernel's dynamic shared-memory limit (call once,
+// before any capture).
+cudaError_t prepare_lattice_resident(int precision, int kind, int NI, size_t smem);
+cudaError_t launch_lattice_resident(int precision, int kind, int NI, int threads, int chains, const ResidentArgs &a,
+                                    size_t smem, cudaStream_t stream);
+// One thread per Philox block of the batch: `blocks_needed` = sweeps x groups x chain quadruples.
+cudaError_t launch_resident_normals(int precision, const ResNormArgs &a, int64_t blocks_needed, cudaStream_t stream);
 
 // Chain diagnostics (diagnostics.cu): one parameter trace of every chain of one field.
 struct DiagArgs {

@@ -26,7 +26,76 @@ namespace gmrf {
 //
 // Gamma draws: G = Marsaglia-Tsang variate at rate 1 (precomputed for the batch, or drawn here);
 // tau = G / rate, sigma^2 = rate / G (the reciprocal of the precision draw G / rate).
-//
+
+// The draw of one task given its sums, by one thread (see hyper_task): `cur` is the current value
+// of the parameter drawn (tau, or sigma^2), `s2old` the current sigma^2, `b` the beta0 copy the
+// sweep used, gpv and zb the precomputed Gamma variate and normal when `pre`.  Writes the FP64
+// values, the precision-T copies and the traces; returns the parameter's new value (tau or
+// sigma^2) in val and, for task 1, beta0 in bval.
+template <typename T>
+__device__ __forceinline__ void hyper_draw(const HyperArgs &a, int which, int chain, int64_t hc, long long sweep,
+                                           double S, double A, double cur, double s2old, double b, double gpv,
+                                           double zb, bool pre, long long extra, uint32_t fstream, int32_t fn,
+                                           int32_t frank, double &val_out, double &bval_out)
+{
+    T *hyp = static_cast<T *>(a.hyp);
+    const uint32_t word1 = static_cast<uint32_t>(a.end_of_sweep ? sweep : extra);
+    double val = cur, bval = 0.0;
+    if (which && a.draw_beta) {
+        if (!pre) {
+            const uint32_t tag = a.end_of_sweep ? kTagBeta : kTagBetaExtra;
+            const uint4 w = philox4x32_10(
+                make_uint4(0u, word1, fstream, (tag << 24) | static_cast<uint32_t>(chain)), a.key);
+            double unused;
+            box_muller_f64(w.x, w.y, zb, unused);
+        }
+        if (a.binomial) {
+            // beta0 | x, psi ~ N(mean, 1/Pb), Pb = 1/v0 + sum psi_i,
+            // mean = (mu0/v0 + sum (kappa_i - psi_i x_i)) / Pb  (S and A hold the two sums).
+            const double Pb = 1.0 / a.beta0_var + S;
+            bval = (a.beta0_mean / a.beta0_var + A) / Pb + zb / sqrt(Pb);
+        } else {
+            const double delta = A / fn + sqrt(s2old / fn) * zb;
+            bval = b + delta;
+            S = S - 2.0 * delta * A + fn * (delta * delta);
+        }
+        a.beta[hc] = bval;
+        hyp[hc * kHypStride + 2] = static_cast<T>(bval);
+    } else if (which && a.trace_beta) {
+        bval = a.beta[hc];
+    }
+    if (a.draw && !(which && a.binomial)) {
+        const double rate = which ? a.b_sig + 0.5 * S : a.b_tau + 0.5 * S;
+        double G = gpv;
+        if (!pre) {
+            const uint32_t tag =
+                which ? (a.end_of_sweep ? kTagSig : kTagSigExtra) : (a.end_of_sweep ? kTagTau : kTagTauExtra);
+            const double shape = which ? a.a_sig + 0.5 * fn : a.a_tau + 0.5 * frank;
+            int fb = 0;
+            G = gamma_mt(shape, 1.0, a.key, word1, fstream, (tag << 24) | static_cast<uint32_t>(chain), fb);
+            if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), 1ull);
+        }
+        if (which) {
+            // The sweep kernels use 1/sigma^2 recomputed from sigma^2, so a run resumed
+            // from a fetched sigma^2 continues bit for bit.
+            val = rate / G;
+            a.sig2[hc] = val;
+            hyp[hc * kHypStride + 1] = static_cast<T>(1.0 / val);
+        } else {
+            val = G / rate;
+            a.tau[hc] = val;
+            hyp[hc * kHypStride] = static_cast<T>(val);
+        }
+    }
+    if (a.end_of_sweep && a.trace_cap > 0) {
+        const int64_t slot = hc * a.trace_cap + (sweep % a.trace_cap);
+        (which ? a.trace_sig : a.trace_tau)[slot] = val;
+        if (which && a.trace_beta) a.trace_beta[slot] = bval;
+    }
+    val_out = val;
+    bval_out = bval;
+}
+
 // One task, run by all 32 lanes of the calling warp; `sweep` is the sweep being finished.
 template <typename T>
 __device__ __forceinline__ void hyper_task(const HyperArgs &a, int task, long long sweep)
@@ -73,59 +142,9 @@ __device__ __forceinline__ void hyper_task(const HyperArgs &a, int task, long lo
             for (int off = 16; off >= 1; off >>= 1) A += __shfl_xor_sync(0xffffffffu, A, off);
     }
     if (lane == 0) {
-        const uint32_t word1 = static_cast<uint32_t>(a.end_of_sweep ? sweep : extra);
-        double val = cur, bval = 0.0;
-        if (which && a.draw_beta) {
-            if (!pre) {
-                const uint32_t tag = a.end_of_sweep ? kTagBeta : kTagBetaExtra;
-                const uint4 w = philox4x32_10(
-                    make_uint4(0u, word1, fstream, (tag << 24) | static_cast<uint32_t>(chain)), a.key);
-                double unused;
-                box_muller_f64(w.x, w.y, zb, unused);
-            }
-            if (a.binomial) {
-                // beta0 | x, psi ~ N(mean, 1/Pb), Pb = 1/v0 + sum psi_i,
-                // mean = (mu0/v0 + sum (kappa_i - psi_i x_i)) / Pb  (S and A hold the two sums).
-                const double Pb = 1.0 / a.beta0_var + S;
-                bval = (a.beta0_mean / a.beta0_var + A) / Pb + zb / sqrt(Pb);
-            } else {
-                const double delta = A / fn + sqrt(s2old / fn) * zb;
-                bval = b + delta;
-                S = S - 2.0 * delta * A + fn * (delta * delta);
-            }
-            a.beta[hc] = bval;
-            hyp[hc * kHypStride + 2] = static_cast<T>(bval);
-        } else if (which && a.trace_beta) {
-            bval = a.beta[hc];
-        }
-        if (a.draw && !(which && a.binomial)) {
-            const double rate = which ? a.b_sig + 0.5 * S : a.b_tau + 0.5 * S;
-            double G = gpv;
-            if (!pre) {
-                const uint32_t tag =
-                    which ? (a.end_of_sweep ? kTagSig : kTagSigExtra) : (a.end_of_sweep ? kTagTau : kTagTauExtra);
-                const double shape = which ? a.a_sig + 0.5 * fn : a.a_tau + 0.5 * frank;
-                int fb = 0;
-                G = gamma_mt(shape, 1.0, a.key, word1, fstream, (tag << 24) | static_cast<uint32_t>(chain), fb);
-                if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), 1ull);
-            }
-            if (which) {
-                // The sweep kernels use 1/sigma^2 recomputed from sigma^2, so a run resumed
-                // from a fetched sigma^2 continues bit for bit.
-                val = rate / G;
-                a.sig2[hc] = val;
-                hyp[hc * kHypStride + 1] = static_cast<T>(1.0 / val);
-            } else {
-                val = G / rate;
-                a.tau[hc] = val;
-                hyp[hc * kHypStride] = static_cast<T>(val);
-            }
-        }
-        if (a.end_of_sweep && a.trace_cap > 0) {
-            const int64_t slot = hc * a.trace_cap + (sweep % a.trace_cap);
-            (which ? a.trace_sig : a.trace_tau)[slot] = val;
-            if (which && a.trace_beta) a.trace_beta[slot] = bval;
-        }
+        double val, bval;
+        hyper_draw<T>(a, which, chain, hc, sweep, S, A, cur, s2old, b, gpv, zb, pre, extra, fstream, fn, frank, val,
+                      bval);
     }
 }
 

@@ -21,6 +21,8 @@ PRIOR_ICAR, PRIOR_PCAR = 0, 1
 FP32, FP64 = 0, 1
 ALGO_CHROMATIC, ALGO_PLAIN = 0, 1
 FLAG_PER_COLOUR = 1
+FLAG_NO_RESIDENT = 2
+FLAG_RESIDENT = 4
 PARAM_TAU2, PARAM_SIGMA2, PARAM_BETA0, PARAM_TAU = range(4)
 LIKELIHOOD_GAUSSIAN, LIKELIHOOD_BINOMIAL = 0, 1
 
@@ -73,7 +75,8 @@ class Info(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("max_colors", ctypes.c_int32),
                 ("sweeps_done", ctypes.c_int64), ("accumulated", ctypes.c_int64),
                 ("hyper_fallbacks", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("launches_per_sweep", ctypes.c_int64), ("early_start_misses", ctypes.c_int64)]
+                ("launches_per_sweep", ctypes.c_int64), ("early_start_misses", ctypes.c_int64),
+                ("resident", ctypes.c_int64)]
 
 
 _lock = threading.Lock()

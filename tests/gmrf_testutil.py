@@ -56,4 +56,7 @@ def trace_relerr(got, want):
     want = np.asarray(want, np.float64)
     if got.size == 0:
         return 0.0
-    return float(np.max(np.abs(got - want) / np.abs(want)))
+    # relative to the value; absolute where the value is 0 (a trace of tau fixed at 0)
+    diff = np.abs(got - want)
+    den = np.abs(want)
+    return float(np.max(np.where(den > 0, diff / np.where(den > 0, den, 1.0), diff)))

@@ -23,6 +23,7 @@ SHAPES = [(300, 244), (257, 128), (9, 16), (1, 4), (2, 8), (130, 1000)]
 
 
 def _run(f, nsweeps, **kw):
+    kw.setdefault("flags", g.FLAG_NO_RESIDENT)  # small shapes would take the resident path
     with g.Sampler([f], precision=g.FP32, chains=1, seed=101, **kw) as s:
         s.sweep(nsweeps)
         r = s.fetch(0, 0, trace=nsweeps)
@@ -69,7 +70,7 @@ def test_row_length_not_multiple_of_4_uses_general_kernel():
 def test_quad_extra_draw_and_intercept():
     f = wl.small_lattice(wl.LATTICE2D_8, (150, 124), 35)
     f = dict(f, y=f["y"] + 1.0)
-    with g.Sampler([f], precision=g.FP32, chains=1, seed=103, intercept=True) as s:
+    with g.Sampler([f], precision=g.FP32, chains=1, seed=103, intercept=True, flags=g.FLAG_NO_RESIDENT) as s:
         s.sweep(20)
         s.hyper_update()
         s.sweep(5)
