@@ -158,16 +158,16 @@ def stage_algorithmic_bytes(spec, stage_name, colour, colourings, S=4):
 # a workload, from one ncu capture (cold L2: ncu flushes caches before the launch), with the
 # SHA-256 of the kernel's sources at capture time.  Reported only while the sources are unchanged.
 MEASURED_TRAFFIC = {
-    "image1024": dict(kernel="lattice_quad_kernel<64, 768, 3>", bytes=8_454_656,
-                      sources={"lattice_quad.cu": "6b31162ebf69de24725c91110ababc5e7446622d1284a7126d8df363adf451e1",
-                               "gmrf_device.cuh": "f0ee38c95478d3b4b0953c6a4cf0ccf52504e3b2725d76bb088d41248fe545ff",
-                               "gmrf_internal.h": "700a3a0ccd7023345538e50a104b849269aa70390db665ea8f1513afff3d1260"}),
-    "volume256": dict(kernel="colour_step_kernel<float, 4, 2, 0>", bytes=315_974_144 + 233_456_640,
-                      sources={"sweep_kernels.cu": "85317fc97e2838ba9d5752d8fc9ee1c0d910e4fc43c8f9d99cf047ece515f5f4",
-                               "gmrf_device.cuh": "f0ee38c95478d3b4b0953c6a4cf0ccf52504e3b2725d76bb088d41248fe545ff",
-                               "gmrf_internal.h": "700a3a0ccd7023345538e50a104b849269aa70390db665ea8f1513afff3d1260",
-                               "hyper_task.cuh": "4ae97f8805bbc9b81b1de7a15033378938ff5c6f043099f737952c1948691545",
-                               "pg.cuh": "fbe6fe245f036210f0dd57a94a1023430acae2c4dfeb85b98d50ed3675bf9dc3"}),
+    "image1024": dict(kernel="lattice_quad_kernel<64, 768, 3>", bytes=8_454_144,
+                      sources={"lattice_quad.cu": "2b9c9e68e12ed5086a3d7f5588932efb9d133913218ad023c9461dd1932fb432",
+                               "gmrf_device.cuh": "39dd162e40198562e4f6096d6291842e9ce4389b3f5971fd3146620dcaa1a298",
+                               "gmrf_internal.h": "adb33c7c8dc5a03a43c0653e97feba06731dfd297d12efc95cedef4fc694396a"}),
+    "volume256": dict(kernel="colour_step_kernel<float, 4, 2, 0>", bytes=316_182_016 + 234_704_384,
+                      sources={"sweep_kernels.cu": "0f1e48d4f67ee7f979ef20d149556a2c3a75972a7672664d1ae82cb5cfb34537",
+                               "gmrf_device.cuh": "39dd162e40198562e4f6096d6291842e9ce4389b3f5971fd3146620dcaa1a298",
+                               "gmrf_internal.h": "adb33c7c8dc5a03a43c0653e97feba06731dfd297d12efc95cedef4fc694396a",
+                               "hyper_task.cuh": "e7620aed367398193ec57f6849982c2ef006397e28915b666bf0df830d8b9f40",
+                               "pg.cuh": "d1460f4eea6d3f7c796777025d8fda58da5c30ed9af7bcdae72621c5016bae1b"}),
 }
 
 
@@ -458,6 +458,25 @@ def run_ours(args):
                                  "psrf": None if d["psrf"] != d["psrf"] else float(d["psrf"]),
                                  "ces_s": t_run / float(np.sum(d["ess"]))}
 
+    # Resident samplers (a small single 2-D lattice): a batch of sweeps is three launches (unit-
+    # rate Gamma variates, normals, the resident kernel); timed as whole batches.
+    resident_batch = None
+    if info["resident"]:
+        G = spec["graph_sweeps"]
+        rb = min(128, max(64, G))
+        nb = min(rb, G) if G > 0 else rb
+        ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.reset()
+        s.sweep(nb)
+        torch.cuda.synchronize()
+        ev_a.record(stream)
+        for _ in range(10):
+            s.sweep(nb)
+        ev_b.record(stream)
+        torch.cuda.synchronize()
+        batch_us = ev_a.elapsed_time(ev_b) * 1e3 / 10
+        resident_batch = {"sweeps": nb, "us": batch_us}
+
     # Each stage of a sweep alone: back-to-back launches, CUDA events on the launching stream
     # (accumulation off); the dominant stage is the longest one that moves the state.
     reps = 50
@@ -557,6 +576,24 @@ def run_ours(args):
                 "frac": achieved / hbm, "traffic": measured_traffic(args.workload), "peak_source": peak_note,
                 "kernel": dom[1], "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": kernel_us,
                 "stages_us": {f"{st}:{name}": round(us, 3) for st, name, us in stages}}
+    if resident_batch:
+        # The resident kernel keeps the chain in shared memory for the whole batch: its HBM bytes
+        # per batch are one read and one write of state, mean and M2, one read of y, and the
+        # batch's normals (written by their producer, read once), so the bound is the latency of
+        # a sweep (colour steps, barriers, the draws), not a roofline; the figures say so.
+        nb = resident_batch["sweeps"]
+        n = spec["fields"][0]["n"]
+        C = spec["chains"]
+        res_bytes = 4 * (n * C * 6 + n + 2 * nb * n * C)
+        ach = res_bytes / (resident_batch["us"] * 1e-6) / 1e9
+        roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": None, "peak_source": peak_note,
+                    "kernel": "resident batch: Gamma variates, normals, lattice_resident_kernel",
+                    "algorithmic_bytes_per_launch": res_bytes, "avg_launch_us": resident_batch["us"],
+                    "sweeps_per_launch": nb, "us_per_sweep": resident_batch["us"] / nb,
+                    "note": "latency-bound (whole sweeps in shared memory, one block per chain): the HBM "
+                            "fraction only counts the batch's staging and normals",
+                    "per_sweep_path_stages_us": {f"{st}:{name}": round(us, 3) for st, name, us in stages}}
 
     if rank != 0:
         if world > 1:
@@ -572,9 +609,16 @@ def run_ours(args):
                "sample": f"{spec['cpu_sweeps']} sweeps of the full workload ({u} site-updates, {dt:.1f} s); "
                          f"CPU: {cpu_model()}"}
     # per step: every stage of every sweep, one Gamma-variate batch per 64 (or graph_sweeps)
-    # sweeps, and the restart kernel
+    # sweeps, and the restart kernel; resident samplers: three launches per batch of sweeps (a
+    # graph of graph_sweeps sweeps holds ceil(graph_sweeps / batch) batches, a left-over sweep one)
     batch = max(64, spec["graph_sweeps"])
     launches = args.steps * (spec["sweeps"] * info["launches_per_sweep"] + -(-spec["sweeps"] // batch) + 1)
+    if info["resident"]:
+        G = spec["graph_sweeps"]
+        rb = min(128, max(64, G))
+        full, rem = divmod(spec["sweeps"], G) if G > 0 else (0, spec["sweeps"])
+        chunks = full * -(-G // rb) + (rem if G > 0 else -(-rem // rb))
+        launches = args.steps * (3 * chunks + 1)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

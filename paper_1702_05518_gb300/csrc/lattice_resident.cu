@@ -17,7 +17,7 @@
 //     squared differences to lower-colour neighbours, and e^2 and e with e = y - beta0 - x;
 //   * after the last step a shuffle tree per warp, one barrier, and two warps finish the sums in
 //     FP64 and draw tau and (beta0, then sigma^2) in parallel (the conditionals of Sec. 3.1, from
-//     the batch's precomputed unit-rate variates), as hyper_draw does for the per-sweep path;
+//     the batch's precomputed unit-rate variates), with the formulas of the per-sweep path;
 //   * a barrier publishes the new values to the next sweep.
 // A sweep thus costs K + 1 barriers (K - 1 of the site threads alone) and no launch.  State and accumulators go back to
 // global memory at the end of the launch (into the buffer the per-sweep path reads next), and the
@@ -26,7 +26,6 @@
 
 #include "gmrf_device.cuh"
 #include "gmrf_internal.h"
-#include "hyper_task.cuh"
 #include "lattice_common.cuh"
 
 namespace gmrf {
