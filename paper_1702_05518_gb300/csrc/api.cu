@@ -128,6 +128,9 @@ struct gmrf_sampler {
     int64_t launches_per_sweep = 0;
     // Resident path (lattice_resident.cu): whole sweeps of a small single 2-D lattice field in one
     // launch, one block per chain; 0 when the field takes the per-sweep stages.
+    // The 2-D lattice kind whose fused sweep is the only sweep kernel of a sweep (it then starts
+    // on a predicted sweep number, see lattice_fused_fast), or -1.
+    int early_kind = -1;
     int resident = 0, res_NI = 0, res_NT = 0, res_batch = 0;
     int32_t res_SR = 0, res_SC = 0;
     size_t res_smem = 0;
@@ -598,6 +601,7 @@ FusedArgs fused_args(gmrf_sampler *s, int kind, int update, int accumulate)
     a.thin = s->opts.thin;
     a.acc_enabled = accumulate;
     a.update = update;
+    a.early = (update && kind == s->early_kind) ? 1 : 0;
     return a;
 }
 
@@ -1123,6 +1127,15 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     s->stages.push_back({2, -1, -1});
     if (binomial_model(s)) s->stages.insert(s->stages.begin(), {3, -1, -1});
     s->launches_per_sweep = static_cast<int64_t>(s->stages.size());
+    {
+        int sweep_kernels = 0, kind = -1;
+        for (const auto &st : s->stages)
+            if (st.type != 2) {
+                ++sweep_kernels;
+                kind = st.type == 1 ? st.kind : -2;
+            }
+        s->early_kind = (sweep_kernels == 1 && kind >= 0) ? kind : -1;
+    }
     CK(plan_resident(s));
     CK(s->alloc_t(&s->tiles_dev, std::max<size_t>(all.size(), 1), sizeof(Tile)));
     if (!all.empty())

@@ -155,6 +155,7 @@ struct FusedArgs {
     int32_t thin;
     int32_t acc_enabled;
     int32_t update;      // 1: run the colour steps; 0: only recompute the partial sums
+    int32_t early;       // the sweep's only sweep kernel: start on a predicted sweep number
 };
 
 

@@ -426,7 +426,6 @@ __global__ void __launch_bounds__(kFusedBlock, (kFusedBlock == 512 && sizeof(T) 
 template <typename T, int KIND, int NT, int CP>
 __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4) ? 2 : 1) lattice_fused_fast(const FusedArgs a)
 {
-    pdl_wait_then_release();
     using D = Dirs<KIND>;
     constexpr bool E8 = (KIND == kLat2D8);
     constexpr int K = E8 ? 4 : 2;
@@ -445,13 +444,116 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4) ? 2 : 1) lat
     const int gi0 = t.i0 - K, gj0 = t.j0 - K;
     const int gu0 = E8 ? (gi0 >> 1) : gi0, gv0 = gj0 >> 1;
     const bool interior = gi0 >= 0 && gj0 >= 0 && gi0 + RR <= Hl && gj0 + RC <= Wl;
-    const long long sweep_ll = a.ctl->sweep;
-    const uint32_t sweep = static_cast<uint32_t>(sweep_ll);
-    const T *X = static_cast<const T *>((sweep_ll & 1) ? a.x_alt : a.x) + f.slot0 * CP;
-    T *XW = static_cast<T *>((sweep_ll & 1) ? a.x : a.x_alt) + f.slot0 * CP;
     const T *Y = static_cast<const T *>(a.y) + f.slot0;
     const int gsub = f.rows * f.cols, gcols = f.cols, grows = f.rows;
     const T rho = static_cast<T>(a.rho);
+    const float rcp_sc = __frcp_rn(static_cast<float>(SC)), rcp_sr = __frcp_rn(static_cast<float>(SR));
+
+    // Stage rows of the sub-arrays into shared memory (four loads in flight per thread): the
+    // observations (src_y) or the state (src_x, CP chains).  The staged index q is the
+    // shared-memory index; positions off the lattice are 0.
+    auto stage = [&](const T *src_x, const T *src_y) {
+        constexpr int UNR = 4;
+        const int total = NS * SUB;
+        for (int q0 = threadIdx.x; q0 < total; q0 += UNR * NT) {
+            T val[UNR][CP];
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const int q = q0 + k * NT;
+                if (q >= total) continue;
+                const int rr = div_small(q, rcp_sc), v = q - rr * SC;
+                const int sa = div_small(rr, rcp_sr), r = rr - sa * SR;
+                const int gu = gu0 + r, gv = gv0 + v;
+                const bool ok = interior || (gu >= 0 && gu < grows && gv >= 0 && gv < gcols);
+                const int go = sa * gsub + gu * gcols + gv;
+#pragma unroll
+                for (int w = 0; w < CP; ++w) val[k][w] = 0;
+                if (ok) {
+                    if (src_x) Vec<T, CP>::ld(src_x + go * CP, val[k]);
+                    else val[k][0] = src_y[go];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const int q = q0 + k * NT;
+                if (q >= total) continue;
+                if (src_x) Vec<T, CP>::st(xs + q * CP, val[k]);
+                else ys[q] = val[k][0];
+            }
+        }
+    };
+
+    // Phase A: normals of every staged site for sweep `sweep` (those outside the drawn regions
+    // are unused).
+    auto normals = [&](uint32_t sweep) {
+        if (CP == 4) {
+            for (int q = threadIdx.x; q < NS * SUB; q += NT) {
+                const int rr = div_small(q, rcp_sc), v = q - rr * SC;
+                const int sa = div_small(rr, rcp_sr), r = rr - sa * SR;
+                const int i = E8 ? gi0 + 2 * r + (sa >> 1) : gi0 + r;
+                const int j = E8 ? gj0 + 2 * v + (sa & 1) : gj0 + 2 * v + ((sa + i) & 1);
+                if (!interior && (i < 0 || i >= Hl || j < 0 || j >= Wl)) continue;
+                T z[CP];
+                site_normals<T, CP>(a.key, static_cast<uint32_t>(i * Wl + j), sweep, f.stream, 0u, 4, z);
+                Vec<T, CP>::st(zs + q * CP, z);
+            }
+        } else {
+            // Groups of G = 4 / CP consecutive natural sites share a Philox block.
+            constexpr int GS = (CP == 2) ? 1 : 2, G = 1 << GS;
+            const int NG = (RC >> GS) + 2;
+            const float rcp_ng = __frcp_rn(static_cast<float>(NG));
+            const int jl = max(0, gj0), jh = min(Wl, gj0 + RC);
+            for (int q = threadIdx.x; q < RR * NG; q += NT) {
+                const int ri = div_small(q, rcp_ng), k = q - ri * NG;
+                const int i = gi0 + ri;
+                if (i < 0 || i >= Hl || jl >= jh) continue;
+                const int s0 = i * Wl + jl, s1 = i * Wl + jh;
+                const int g = (s0 >> GS) + k;
+                if ((g << GS) >= s1) continue;
+                T n4[4];
+                block_normals<T>(a.key, static_cast<uint32_t>(g), sweep, f.stream, 0u, n4);
+#pragma unroll
+                for (int r = 0; r < G; ++r) {
+                    const int st = (g << GS) + r;
+                    if (st < s0 || st >= s1) continue;
+                    const int j = st - i * Wl;
+                    T *zp = zs + sm_index<KIND>(i, j, gi0, gj0, SR, SC) * CP;
+#pragma unroll
+                    for (int ch = 0; ch < CP; ++ch) zp[ch] = n4[r * CP + ch];
+                }
+            }
+        }
+    };
+
+    // Before the dependency wait: the observations (never written by a sweep) and, when this is
+    // the sweep's only sweep kernel (a.early), the normals of the predicted sweep number, as in
+    // lattice_quad.cu (the last block to read the prediction replaces it after the wait; a wrong
+    // prediction only costs drawing the normals again).
+    stage(nullptr, Y);
+    __shared__ long long s_pred;
+    __shared__ int s_last;
+    long long predicted = -1;
+    if (a.early) {
+        if (threadIdx.x == 0) {
+            s_pred = *reinterpret_cast<volatile const long long *>(&a.ctl->fnext);
+            s_last = atomicAdd(&a.ctl->fticket, 1ull) == gridDim.x - 1;
+        }
+        __syncthreads();
+        predicted = s_pred;
+        normals(static_cast<uint32_t>(predicted));
+    }
+    pdl_wait();
+    const long long sweep_ll = a.ctl->sweep;
+    if (a.early && threadIdx.x == 0 && s_last) {
+        a.ctl->fnext = sweep_ll + 1;
+        a.ctl->fticket = 0;
+        if (sweep_ll != predicted) a.ctl->fmiss += 1;
+    }
+    pdl_release();
+    const uint32_t sweep = static_cast<uint32_t>(sweep_ll);
+    if (!a.early || sweep_ll != predicted) normals(sweep);
+    const T *X = static_cast<const T *>((sweep_ll & 1) ? a.x_alt : a.x) + f.slot0 * CP;
+    T *XW = static_cast<T *>((sweep_ll & 1) ? a.x : a.x_alt) + f.slot0 * CP;
     T tau[CP], isig[CP], beta[CP];
     {
         const T *hyp = static_cast<const T *>(a.hyp) + static_cast<int64_t>(t.field) * CP * kHypStride;
@@ -462,80 +564,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4) ? 2 : 1) lat
             beta[v] = hyp[kHypStride * v + 2];
         }
     }
-    const float rcp_sc = __frcp_rn(static_cast<float>(SC)), rcp_sr = __frcp_rn(static_cast<float>(SR));
-
-    // Stage (four loads in flight per thread).  The staged index q is the shared-memory index.
-    {
-        constexpr int UNR = 4;
-        const int total = NS * SUB;
-        for (int q0 = threadIdx.x; q0 < total; q0 += UNR * NT) {
-            T val[UNR][CP], yv[UNR];
-#pragma unroll
-            for (int k = 0; k < UNR; ++k) {
-                const int q = q0 + k * NT;
-                if (q >= total) continue;
-                const int rr = div_small(q, rcp_sc), v = q - rr * SC;
-                const int sa = div_small(rr, rcp_sr), r = rr - sa * SR;
-                const int gu = gu0 + r, gv = gv0 + v;
-                const bool ok = interior || (gu >= 0 && gu < grows && gv >= 0 && gv < gcols);
-                const int go = sa * gsub + gu * gcols + gv;
-                if (ok) {
-                    Vec<T, CP>::ld(X + go * CP, val[k]);
-                    yv[k] = Y[go];
-                } else {
-#pragma unroll
-                    for (int w = 0; w < CP; ++w) val[k][w] = 0;
-                    yv[k] = 0;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < UNR; ++k) {
-                const int q = q0 + k * NT;
-                if (q >= total) continue;
-                Vec<T, CP>::st(xs + q * CP, val[k]);
-                ys[q] = yv[k];
-            }
-        }
-    }
-
-    // Phase A: normals of every staged site (those outside the drawn regions are unused).
-    if (CP == 4) {
-        for (int q = threadIdx.x; q < NS * SUB; q += NT) {
-            const int rr = div_small(q, rcp_sc), v = q - rr * SC;
-            const int sa = div_small(rr, rcp_sr), r = rr - sa * SR;
-            const int i = E8 ? gi0 + 2 * r + (sa >> 1) : gi0 + r;
-            const int j = E8 ? gj0 + 2 * v + (sa & 1) : gj0 + 2 * v + ((sa + i) & 1);
-            if (!interior && (i < 0 || i >= Hl || j < 0 || j >= Wl)) continue;
-            T z[CP];
-            site_normals<T, CP>(a.key, static_cast<uint32_t>(i * Wl + j), sweep, f.stream, 0u, 4, z);
-            Vec<T, CP>::st(zs + q * CP, z);
-        }
-    } else {
-        // Groups of G = 4 / CP consecutive natural sites share a Philox block.
-        constexpr int GS = (CP == 2) ? 1 : 2, G = 1 << GS;
-        const int NG = (RC >> GS) + 2;
-        const float rcp_ng = __frcp_rn(static_cast<float>(NG));
-        const int jl = max(0, gj0), jh = min(Wl, gj0 + RC);
-        for (int q = threadIdx.x; q < RR * NG; q += NT) {
-            const int ri = div_small(q, rcp_ng), k = q - ri * NG;
-            const int i = gi0 + ri;
-            if (i < 0 || i >= Hl || jl >= jh) continue;
-            const int s0 = i * Wl + jl, s1 = i * Wl + jh;
-            const int g = (s0 >> GS) + k;
-            if ((g << GS) >= s1) continue;
-            T n4[4];
-            block_normals<T>(a.key, static_cast<uint32_t>(g), sweep, f.stream, 0u, n4);
-#pragma unroll
-            for (int r = 0; r < G; ++r) {
-                const int st = (g << GS) + r;
-                if (st < s0 || st >= s1) continue;
-                const int j = st - i * Wl;
-                T *zp = zs + sm_index<KIND>(i, j, gi0, gj0, SR, SC) * CP;
-#pragma unroll
-                for (int ch = 0; ch < CP; ++ch) zp[ch] = n4[r * CP + ch];
-            }
-        }
-    }
+    stage(X, nullptr);
     __syncthreads();
 
     // Phase B: colour steps; owned sites fold their terms of the hyperparameter sums.

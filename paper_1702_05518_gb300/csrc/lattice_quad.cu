@@ -44,6 +44,14 @@ __host__ __device__ constexpr int qdv(int b, int k) { return (b + qdj(k)) >= 0 ?
 struct QuadCtx {
     float tau, isig, beta, rho;
     float accS, accR, accA;
+    // Write-back of the owned sites, issued right after their colour step: the state buffer of
+    // the next sweep and, in accumulated sweeps, the running mean and M2 (Welford, from the
+    // shared-memory copies ms, m2s).
+    float *XW, *MEAN, *M2;
+    const float *ms, *m2s;
+    int gsub, gcols, gu0, gv0;
+    bool acc;
+    float inv_k;
 };
 
 // Colour step C for the thread's quads.
@@ -98,6 +106,17 @@ __device__ __forceinline__ void quad_colour_step(float *xs, const float *ys, int
             const float r = yb - x;
             cx.accR += r * r;
             cx.accA += r;
+            // The site is final for this sweep: its stores leave now and drain under the later
+            // steps (all blocks storing at the end of the kernel would queue behind each other).
+            const int go = C * cx.gsub + (cx.gu0 + u) * cx.gcols + cx.gv0 + v;
+            cx.XW[go] = x;
+            if (cx.acc) {
+                const float mu = cx.ms[C * SUB + base], mm = cx.m2s[C * SUB + base];
+                const float delta = x - mu;
+                const float m1 = mu + delta * cx.inv_k;
+                cx.MEAN[go] = m1;
+                cx.M2[go] = mm + delta * (x - m1);
+            }
         }
     }
 }
@@ -154,6 +173,8 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
     const int nquads = SUB;
     float *xs = reinterpret_cast<float *>(smem_raw);  // [4][QR][QCS]
     float *ys = xs + 4 * SUB;                         // [4][QR][QCS]
+    float *ms = ys + 4 * SUB;                         // [4][QR][QCS] running mean of owned sites
+    float *m2s = ms + 4 * SUB;                        // [4][QR][QCS] running M2 of owned sites
     const int gi0 = t.i0 - 4, gj0 = t.j0 - 4;        // staged origin (site units, even / multiple of 4)
     const int gu0 = gi0 >> 1, gv0 = gj0 >> 1;         // in quads
     const bool interior = gi0 >= 0 && gj0 >= 0 && gi0 + 2 * QR <= Hl && gj0 + 2 * QCS <= Wl;
@@ -218,7 +239,9 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
         cx.accA = 0.0f;
     }
 
-    // The running moments of accumulated sweeps: their lines into L1 now, read after the steps.
+    // The running moments of accumulated sweeps: asynchronous copies (cp.async) of the thread's
+    // owned sites into shared memory now, waited for (by this thread only, which alone reads
+    // them) at the write-back, so their latency runs under the colour steps.
     const bool acc = a.acc_enabled && sweep_accumulated(sweep_ll, a.burn_in, a.thin);
     const float inv_k = acc ? 1.0f / static_cast<float>(a.ctl->acc_count + 1) : 0.0f;
     float *MEAN = static_cast<float *>(a.mean) + f.slot0;
@@ -228,14 +251,17 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
         for (int k = 0; k < NQ; ++k) {
             const int q = threadIdx.x + k * NT;
             const int u = q / QCS, v = q % QCS;
-            if (q >= nquads || u < 2 || u >= QR - 2 || v < 2 || v >= 2 + TC / 2) continue;
             const int go = (gu0 + u) * gcols + gv0 + v;
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(MEAN + s * gsub + go));
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(M2 + s * gsub + go));
+                if (!(q < nquads && quad_owned_site(u, v, s, QR, TC, gu0, gv0, Hl, Wl))) continue;
+                const uint32_t dm = static_cast<uint32_t>(__cvta_generic_to_shared(ms + s * SUB + q));
+                const uint32_t d2 = static_cast<uint32_t>(__cvta_generic_to_shared(m2s + s * SUB + q));
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dm), "l"(MEAN + s * gsub + go) : "memory");
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d2), "l"(M2 + s * gsub + go) : "memory");
             }
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
 
     // Stage the state of the thread's quads: slot (u, v) of the four sub-arrays; sites off the
@@ -257,9 +283,22 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
 #pragma unroll
         for (int s = 0; s < 4; ++s) xs[s * SUB + q] = xv[s];
     }
+    cx.XW = XW;
+    cx.MEAN = MEAN;
+    cx.M2 = M2;
+    cx.ms = ms;
+    cx.m2s = m2s;
+    cx.gsub = gsub;
+    cx.gcols = gcols;
+    cx.gu0 = gu0;
+    cx.gv0 = gv0;
+    cx.acc = acc;
+    cx.inv_k = inv_k;
+    if (acc) asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's copies of the moments
     __syncthreads();
 
-    // Colour steps 0..3; step c covers the tile grown by 3 - c sites (clipped to the lattice).
+    // Colour steps 0..3; step c covers the tile grown by 3 - c sites (clipped to the lattice);
+    // each step writes back its owned sites.
     const int own_i0 = t.i0, own_i1 = min(Hl, t.i0 + TR), own_j0 = t.j0, own_j1 = min(Wl, t.j0 + TC);
 #define GMRF_QUAD_STEP(C)                                                                                        \
     quad_colour_step<C, QCS, NQ, NT>(xs, ys, SUB, z, gi0, gj0, Hl, Wl, max(0, t.i0 - (3 - C)),                \
@@ -273,54 +312,8 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
     GMRF_QUAD_STEP(3)
 #undef GMRF_QUAD_STEP
 
-    // Write-back of the owned quads' sites and the running mean / M2: every load of the running
-    // moments is issued before any store (the stores could alias them for the compiler), so a
-    // thread pays one memory round trip, and those lines were prefetched into L1 before the
-    // colour steps.
-    if (acc) {
-        float mu[NQ][4], mm[NQ][4];
-#pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-            const int q = threadIdx.x + k * NT;
-            const int u = q / QCS, v = q % QCS;
-            const int go = (gu0 + u) * gcols + gv0 + v;
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const bool ok = q < nquads && quad_owned_site(u, v, s, QR, TC, gu0, gv0, Hl, Wl);
-                mu[k][s] = ok ? MEAN[s * gsub + go] : 0.0f;
-                mm[k][s] = ok ? M2[s * gsub + go] : 0.0f;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-            const int q = threadIdx.x + k * NT;
-            const int u = q / QCS, v = q % QCS;
-            const int go = (gu0 + u) * gcols + gv0 + v;
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                if (!(q < nquads && quad_owned_site(u, v, s, QR, TC, gu0, gv0, Hl, Wl))) continue;
-                const float xn = xs[s * SUB + q];
-                const float delta = xn - mu[k][s];
-                const float m1 = mu[k][s] + delta * inv_k;
-                XW[s * gsub + go] = xn;
-                MEAN[s * gsub + go] = m1;
-                M2[s * gsub + go] = mm[k][s] + delta * (xn - m1);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < NQ; ++k) {
-            const int q = threadIdx.x + k * NT;
-            const int u = q / QCS, v = q % QCS;
-            const int go = (gu0 + u) * gcols + gv0 + v;
-#pragma unroll
-            for (int s = 0; s < 4; ++s)
-                if (q < nquads && quad_owned_site(u, v, s, QR, TC, gu0, gv0, Hl, Wl)) XW[s * gsub + go] = xs[s * SUB + q];
-        }
-    }
-
-    // Block reduction: warp shuffle tree, then the warps' sums in order.
-    __syncthreads();
+    // Block reduction: warp shuffle tree, then the warps' sums in order (the last colour step
+    // ended with a barrier, so the observations are dead).
     float *red = ys;  // [NW][3], the observations are dead
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float sS = cx.accS, sR = cx.accR, sA = cx.accA;
@@ -346,7 +339,8 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
 }  // namespace
 
 // Configurations: (quad columns per staged row, threads, quads per thread).
-size_t lattice_quad_smem(int qcs, int TR) { return static_cast<size_t>(8) * (TR / 2 + 4) * qcs * sizeof(float); }
+// (state, observations, running mean and M2: four sub-arrays each)
+size_t lattice_quad_smem(int qcs, int TR) { return static_cast<size_t>(16) * (TR / 2 + 4) * qcs * sizeof(float); }
 
 cudaError_t prepare_lattice_quad(int qcs, int nt, int nq, size_t smem)
 {
