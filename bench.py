@@ -409,11 +409,15 @@ def run_ours(args):
     spec = workload_spec(args.workload)
     seed = replica_seed(spec["seed"], rank)
     kw = sampler_kwargs(spec, g, seed)
+    if getattr(args, "tune", False):
+        kw["tuning"] = "auto"
+        kw["autotune_sweeps"] = max(10, min(100, spec["graph_sweeps"] or 10))
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     units = site_updates_per_step(spec)
 
     s = g.Sampler(spec["fields"], **kw)
+    tuned = s.tuning if kw.get("tuning") == "auto" else None
     info = s.info()
     for _ in range(args.warmup):
         s.reset()
@@ -625,7 +629,8 @@ def run_ours(args):
             "config": {"workload": spec["name"], "chains": spec["chains"], "sweeps_per_step": spec["sweeps"],
                        "burn_in": spec["burn_in"], "sites": n_total, "graph_sweeps": spec["graph_sweeps"],
                        "l2": "flushed between steps (512 MiB write), outside the timed events",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "launch_config": "autotuned: " + json.dumps(tuned) if tuned else "cost models"},
             "wall_ms_per_step": 1e3 * wall / args.steps,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -659,6 +664,9 @@ def main(argv=None):
                     choices=["image1024", "image64", "volume256", "delaunay16k", "batched", "paper50",
                              "paper512", "election"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--tune", action="store_true",
+                    help="launch configuration by gmrf_autotune (measured on this GPU, untimed) instead of the "
+                         "library's cost models")
     ap.add_argument("--profile-sweeps", type=int, default=0, metavar="S",
                     help="untimed: run S sweeps of the workload with one launch per stage (no graphs) "
                          "and exit; a short, fixed launch sequence for a profiler to capture")

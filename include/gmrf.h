@@ -130,6 +130,25 @@ typedef struct {
     double beta0_mean, beta0_var; /* binomial likelihood: beta0 ~ N(beta0_mean, beta0_var)   */
 } gmrf_model;
 
+/*
+ * Launch configuration of a sampler (the kernels' work decomposition; it changes the results only
+ * through the rounding of the partial sums).  Zero fields keep the library's cost models; a
+ * tuning is usually found by gmrf_autotune.  Invalid values make gmrf_sampler_create return
+ * GMRF_E_INVALID.
+ */
+typedef struct {
+    int32_t chains_per_thread;   /* chains one thread updates together: 1, 2 or 4 (FP64: 1 or 2),   */
+                                 /* at most the chains rounded up to a power of two; 0: automatic   */
+    int32_t step_tile;           /* per-colour kernels (3-D lattices, graphs): (site, chain group)   */
+                                 /* elements per block, 256..16384; 0: automatic                     */
+    int32_t fused_rows[2];       /* fused 2-D sweep, per kind (index GMRF_LATTICE2D_4, _8): tile rows */
+    int32_t fused_cols[2];       /* and columns, 8..256 (made even); 0: automatic                    */
+    int32_t fused_threads[2];    /* threads per block, 512 or 1024; 0: automatic                     */
+    int32_t quad_config;         /* 8-neighbour lattices, one chain, FP32: quad kernel configuration  */
+                                 /* 1..4, -1 for the general fused kernel; 0: automatic               */
+    int32_t quad_rows;           /* the quad kernel's tile rows (even, >= 8); 0: automatic            */
+} gmrf_tuning;
+
 typedef struct {
     int32_t precision;        /* gmrf_precision: state and site arithmetic                  */
     int32_t chains;           /* independent chains per field, 1..64                        */
@@ -141,6 +160,7 @@ typedef struct {
     int32_t algorithm;        /* gmrf_algorithm                                             */
     int32_t graph_sweeps;     /* sweeps captured per CUDA graph; 0 = launch kernels directly */
     int32_t flags;            /* GMRF_FLAG_* bits; 0 for the defaults                        */
+    const gmrf_tuning *tuning; /* launch configuration (host, copied) or NULL: automatic       */
 } gmrf_opts;
 
 /* gmrf_opts.flags: GMRF_FLAG_PER_COLOUR makes 2-D lattice fields use one launch per colour
@@ -318,6 +338,22 @@ gmrf_status gmrf_site_psrf(gmrf_sampler *s, int32_t field, double *psrf, double 
  * Errors: GMRF_E_STATE, GMRF_E_CUDA.
  */
 gmrf_status gmrf_sampler_reset(gmrf_sampler *s);
+
+/*
+ * Autotuner: measure launch configurations for these fields, model and options on the device and
+ * return the fastest in *out (and its time per sweep in *us_per_sweep, may be NULL).  Candidates
+ * are tried by coordinate descent from the automatic configuration: the chains per thread, the
+ * colour-step tile, each 2-D kind's fused tile shape and block size, and the quad kernel's
+ * configuration; each one is a sampler built from the same arguments (opts.tuning ignored) and
+ * timed with CUDA events over `sweeps` sweeps (>= 1; graphs as in opts) after a warm-up, on
+ * `cuda_stream`.  The result is cached for the process by (field kinds and sizes, chains,
+ * precision, model and option switches): a later call with the same key returns it without
+ * measuring.  Synchronises the stream; the device memory of one sampler at a time.
+ * Errors: those of gmrf_sampler_create and gmrf_sweep.
+ */
+gmrf_status gmrf_autotune(const gmrf_field_desc *fields, int32_t nfields, const gmrf_model *model,
+                          const gmrf_opts *opts, int32_t sweeps, void *cuda_stream, gmrf_tuning *out,
+                          double *us_per_sweep);
 
 /*
  * Replace the data of one field and restart the run: a sampler built once for a graph then

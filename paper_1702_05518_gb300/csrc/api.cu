@@ -131,6 +131,7 @@ struct gmrf_sampler {
     // The 2-D lattice kind whose fused sweep is the only sweep kernel of a sweep (it then starts
     // on a predicted sweep number, see lattice_fused_fast), or -1.
     int early_kind = -1;
+    gmrf_tuning tune{};  // launch configuration overrides (zeros: the cost models)
     int resident = 0, res_NI = 0, res_NT = 0, res_batch = 0;
     int32_t res_SR = 0, res_SC = 0;
     size_t res_smem = 0;
@@ -294,6 +295,25 @@ gmrf_status check_opts(const gmrf_opts *o)
     if (o->graph_sweeps < 0) return fail(GMRF_E_INVALID, "opts.graph_sweeps must be >= 0");
     if (o->algorithm != GMRF_ALGO_CHROMATIC && o->algorithm != GMRF_ALGO_PLAIN)
         return fail(GMRF_E_INVALID, "opts.algorithm");
+    if (const gmrf_tuning *t = o->tuning) {
+        int cp = 1;
+        while (cp < o->chains) cp <<= 1;
+        const int v = t->chains_per_thread;
+        if (v != 0 && v != 1 && v != 2 && v != 4) return fail(GMRF_E_INVALID, "tuning.chains_per_thread must be 0, 1, 2 or 4");
+        if (v > cp || (o->precision == GMRF_FP64 && v > 2))
+            return fail(GMRF_E_INVALID, "tuning.chains_per_thread exceeds the chains (or 2 in FP64)");
+        if (t->step_tile != 0 && (t->step_tile < 256 || t->step_tile > 16384))
+            return fail(GMRF_E_INVALID, "tuning.step_tile must be 0 or in 256..16384");
+        for (int k = 0; k < 2; ++k) {
+            const int r = t->fused_rows[k], c = t->fused_cols[k], n = t->fused_threads[k];
+            if ((r != 0 && (r < 8 || r > 256)) || (c != 0 && (c < 8 || c > 256)) || ((r == 0) != (c == 0)))
+                return fail(GMRF_E_INVALID, "tuning.fused_rows/cols must both be 0 or in 8..256");
+            if (n != 0 && n != 512 && n != 1024) return fail(GMRF_E_INVALID, "tuning.fused_threads must be 0, 512 or 1024");
+        }
+        if (t->quad_config < -1 || t->quad_config > 4) return fail(GMRF_E_INVALID, "tuning.quad_config must be in -1..4");
+        if (t->quad_rows != 0 && (t->quad_rows < 8 || (t->quad_rows & 1)))
+            return fail(GMRF_E_INVALID, "tuning.quad_rows must be 0 or even and >= 8");
+    }
     return GMRF_OK;
 }
 
@@ -952,6 +972,7 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
             if (h.kind == kind && h.dims[1] % 4 != 0) quad_ok = false;
         if (const char *env = std::getenv("GMRF_FUSED_QUAD"))
             if (env[0] == '0') quad_ok = false;
+        if (s->tune.quad_config < 0) quad_ok = false;
         if (quad_ok) {
             // Configurations (quad columns, threads, quads per thread); tile TR x TC with
             // TC = 2 qcs - 8 and (TR/2 + 4) qcs <= threads * quads per thread.  Cost: waves of
@@ -959,12 +980,15 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
             static const int cfg[4][3] = {{64, 768, 3}, {64, 1024, 2}, {32, 1024, 2}, {32, 512, 2}};
             double best = 1e300;
             int bq = 0, bn = 0, bm = 0, btr = 0;
-            for (auto &cf : cfg) {
+            for (int ci = 0; ci < 4; ++ci) {
+                if (s->tune.quad_config > 0 && ci != s->tune.quad_config - 1) continue;
+                const int *cf = cfg[ci];
                 const int qcs = cf[0], nt = cf[1], nq = cf[2];
                 const int qr_max = nq * nt / qcs;
                 const int tc = 2 * qcs - 8;
                 for (int tr = 8; (tr / 2 + 4) <= qr_max; tr += 2) {
                     if (lattice_quad_smem(qcs, tr) > 200 * 1024) break;
+                    if (s->tune.quad_rows && tr != s->tune.quad_rows) continue;
                     int64_t tiles = 0;
                     for (auto &h : s->hf)
                         if (h.kind == kind) tiles += static_cast<int64_t>((h.dims[0] + tr - 1) / tr) * ((h.dims[1] + tc - 1) / tc);
@@ -980,6 +1004,8 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
                     }
                 }
             }
+            if (bq == 0 && s->tune.quad_rows)
+                return fail(GMRF_E_INVALID, "tuning.quad_rows does not fit the quad configuration");
             if (bq > 0) {
                 s->fQCS[kind] = bq;
                 s->fNQ[kind] = bm;
@@ -998,8 +1024,10 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
             int tr = side, tc = side;
             // Cost model over tile shapes and block sizes: waves of blocks (152 SMs, one block of
             // 1024 or two of 512 threads per SM) times the sites a wave computes per SM, halo
-            // recomputation included.  Deterministic, so a sampler's tiling (and with it the
-            // rounding of the tile partial sums) does not change from run to run.
+            // recomputation included, plus a fixed cost per block (staging, barriers, reduction)
+            // worth 1024 site updates (fitted to measured 20 x 22 and 64 x 64 tilings of many
+            // small lattices).  Deterministic, so a sampler's tiling (and with it the rounding of
+            // the tile partial sums) does not change from run to run.
             double best = 1e300;
             for (int nt : {512, 1024}) {
                 const int bps = nt == 1024 ? 1 : 2;
@@ -1012,7 +1040,7 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
                         for (auto &h : s->hf)
                             if (h.kind == kind)
                                 tiles += static_cast<int64_t>((h.dims[0] + cr - 1) / cr) * ((h.dims[1] + cc - 1) / cc);
-                        double work = 0;  // sites computed per tile over the K colour steps
+                        double work = 1024.0;  // per block: fixed cost + sites computed over the K steps
                         for (int e = 0; e < K; ++e) work += static_cast<double>(cr + 2 * e) * (cc + 2 * e) / K;
                         const double waves = std::ceil(static_cast<double>(tiles) / (152.0 * bps));
                         const double cost = waves * bps * work;
@@ -1038,6 +1066,18 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
                     s->fNT[kind] = nt;
                 }
             }
+            if (s->tune.fused_rows[kind]) {
+                const int r = s->tune.fused_rows[kind] & ~1, c = s->tune.fused_cols[kind] & ~1;
+                const int nt = s->tune.fused_threads[kind] ? s->tune.fused_threads[kind] : s->fNT[kind];
+                if (lattice_fused_smem(s->precision, kind, s->Cp, r, c) > 200 * 1024 ||
+                    static_cast<int64_t>(r + 2 * K) * (c + 2 * K) * (s->Cp / s->V) >= 65536)
+                    return fail(GMRF_E_INVALID, "tuning: the fused tile does not fit shared memory");
+                tr = r;
+                tc = c;
+                s->fNT[kind] = nt;
+            } else if (s->tune.fused_threads[kind]) {
+                s->fNT[kind] = s->tune.fused_threads[kind];
+            }
             // The kernel's flattened loops divide indices below 2^16 by one float multiply.
             while (static_cast<int64_t>(tr + 2 * K) * (tc + 2 * K) * (s->Cp / s->V) >= 65536 && tr > 8) tr -= 8;
             s->fTR[kind] = tr;
@@ -1050,7 +1090,8 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     for (int fi = 0; fi < s->nfields; ++fi)
         if (!fused_kind[s->hf[fi].kind]) total_elems += static_cast<int64_t>(s->hf[fi].n) * CV;
     const int64_t per_colour = total_elems / 2;
-    const int64_t target = std::min<int64_t>(16384, std::max<int64_t>(kBlock, per_colour / (152 * 4)));
+    const int64_t target = s->tune.step_tile ? s->tune.step_tile
+                                             : std::min<int64_t>(16384, std::max<int64_t>(kBlock, per_colour / (152 * 4)));
     s->kmax = 0;
     for (auto &h : s->hf) s->kmax = std::max(s->kmax, h.ncolors);
     std::vector<std::vector<Tile>> by_colour(s->kmax);
@@ -1305,10 +1346,12 @@ gmrf_status gmrf_sampler_create(gmrf_sampler **out, const gmrf_field_desc *field
     gmrf_sampler *s = new gmrf_sampler();
     s->model = *model;
     s->opts = *opts;
+    if (opts->tuning) s->tune = *opts->tuning;
+    s->opts.tuning = nullptr;  // no caller memory is retained
     s->precision = opts->precision;
     s->C = opts->chains;
     s->Cp = pow2_at_least(opts->chains);
-    s->V = std::min(s->Cp, opts->precision == GMRF_FP32 ? 4 : 2);
+    s->V = s->tune.chains_per_thread ? s->tune.chains_per_thread : std::min(s->Cp, opts->precision == GMRF_FP32 ? 4 : 2);
     s->algorithm = opts->algorithm;
     s->nfields = nfields;
     s->hf = std::move(hf);

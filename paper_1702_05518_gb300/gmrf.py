@@ -29,7 +29,7 @@ LIKELIHOOD_GAUSSIAN, LIKELIHOOD_BINOMIAL = 0, 1
 EXPORTED = ["gmrf_color_graph", "gmrf_color_graph_noalloc", "gmrf_sampler_create", "gmrf_sampler_destroy", "gmrf_sweep",
             "gmrf_hyper_update", "gmrf_fetch_samples", "gmrf_field_colors", "gmrf_sampler_info",
             "gmrf_sampler_reset", "gmrf_sampler_set_data", "gmrf_launch_stage", "gmrf_fetch_intercept",
-            "gmrf_trace_diagnostics", "gmrf_site_psrf",
+            "gmrf_trace_diagnostics", "gmrf_site_psrf", "gmrf_autotune",
             "gmrf_validate_csr", "gmrf_philox_words", "gmrf_site_normals", "gmrf_last_error",
             "gmrf_version"]
 
@@ -62,12 +62,39 @@ class Model(ctypes.Structure):
                 ("likelihood", ctypes.c_int32), ("beta0_mean", ctypes.c_double), ("beta0_var", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("chains_per_thread", ctypes.c_int32), ("step_tile", ctypes.c_int32),
+                ("fused_rows", ctypes.c_int32 * 2), ("fused_cols", ctypes.c_int32 * 2),
+                ("fused_threads", ctypes.c_int32 * 2), ("quad_config", ctypes.c_int32),
+                ("quad_rows", ctypes.c_int32)]
+
+    @classmethod
+    def from_dict(cls, d):
+        t = cls()
+        for k, v in (d or {}).items():
+            if k in ("fused_rows", "fused_cols", "fused_threads"):
+                arr = getattr(t, k)
+                for i, x in enumerate(v):
+                    arr[i] = int(x)
+            else:
+                setattr(t, k, int(v))
+        return t
+
+    def to_dict(self):
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if k.startswith("fused_") else int(v)
+        return out
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("chains", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("start_sweep", ctypes.c_int64),
                 ("burn_in", ctypes.c_int64), ("thin", ctypes.c_int32),
                 ("trace_capacity", ctypes.c_int32), ("algorithm", ctypes.c_int32),
-                ("graph_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("graph_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("tuning", ctypes.POINTER(Tuning))]
 
 
 class Info(ctypes.Structure):
@@ -112,6 +139,9 @@ def lib() -> ctypes.CDLL:
             L.gmrf_sampler_reset.restype = st
             L.gmrf_sampler_set_data.argtypes = [vp, ctypes.c_int32, f64p, i32p, f64p]
             L.gmrf_sampler_set_data.restype = st
+            L.gmrf_autotune.argtypes = [P(FieldDesc), ctypes.c_int32, P(Model), P(Opts), ctypes.c_int32, vp,
+                                        P(Tuning), f64p]
+            L.gmrf_autotune.restype = st
             L.gmrf_launch_stage.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_char_p)]
             L.gmrf_launch_stage.restype = st
             L.gmrf_hyper_update.argtypes = [vp]
@@ -251,7 +281,8 @@ class Sampler:
                  a_tau=1.0, b_tau=0.01, a_sigma=1.0, b_sigma=0.01, fix_hyper=False, tau0=1.0,
                  sigma2_0=1.0, start_sweep=0, burn_in=0, thin=1, trace_capacity=4096,
                  algorithm=ALGO_CHROMATIC, graph_sweeps=0, flags=0, stream=None, intercept=False,
-                 beta0_0=0.0, likelihood=LIKELIHOOD_GAUSSIAN, beta0_prior=(0.0, 1000.0)):
+                 beta0_0=0.0, likelihood=LIKELIHOOD_GAUSSIAN, beta0_prior=(0.0, 1000.0), tuning=None,
+                 autotune_sweeps=30):
         L = lib()
         self._h = ctypes.c_void_p()
         self.chains = int(chains)
@@ -300,8 +331,25 @@ class Sampler:
                       1 if intercept else 0, float(beta0_0), int(likelihood), float(beta0_prior[0]),
                       float(beta0_prior[1]))
         opts = Opts(int(precision), self.chains, int(seed), int(start_sweep), int(burn_in),
-                    int(thin), int(trace_capacity), int(algorithm), int(graph_sweeps), int(flags))
+                    int(thin), int(trace_capacity), int(algorithm), int(graph_sweeps), int(flags), None)
         self.stream = current_stream() if stream is None else stream
+        # tuning: None (the library's cost models), a dict of gmrf_tuning fields, or "auto"
+        # (gmrf_autotune on these arguments, cached per process)
+        self.tuning_us_per_sweep = None
+        tun = None
+        if isinstance(tuning, str):
+            if tuning != "auto":
+                raise ValueError("tuning must be None, a dict or 'auto'")
+            tun = Tuning()
+            us = ctypes.c_double(0)
+            _check(L.gmrf_autotune(descs, len(fields), ctypes.byref(model), ctypes.byref(opts), int(autotune_sweeps),
+                                   self.stream, ctypes.byref(tun), ctypes.byref(us)))
+            self.tuning_us_per_sweep = us.value
+        elif tuning is not None:
+            tun = Tuning.from_dict(tuning)
+        if tun is not None:
+            opts.tuning = ctypes.pointer(tun)
+        self.tuning = None if tun is None else tun.to_dict()
         _check(L.gmrf_sampler_create(ctypes.byref(self._h), descs, len(fields), ctypes.byref(model),
                                      ctypes.byref(opts), self.stream))
         self.precision = int(precision)
