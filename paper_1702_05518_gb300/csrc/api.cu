@@ -1351,7 +1351,22 @@ gmrf_status gmrf_sampler_create(gmrf_sampler **out, const gmrf_field_desc *field
     s->precision = opts->precision;
     s->C = opts->chains;
     s->Cp = pow2_at_least(opts->chains);
-    s->V = s->tune.chains_per_thread ? s->tune.chains_per_thread : std::min(s->Cp, opts->precision == GMRF_FP32 ? 4 : 2);
+    s->V = std::min(s->Cp, opts->precision == GMRF_FP32 ? 4 : 2);
+    {
+        // Samplers whose sweeps are per-colour launches only (3-D lattices, graphs): when a step
+        // has too few (site, chain group) elements to fill the GPU (below 2048 threads on each of
+        // the 152 SMs, four times over), fewer chains per thread give more threads.  (Fused 2-D
+        // sweeps keep all chains in a thread: their fast kernel needs it.)
+        bool lattice2d = false;
+        int64_t sites = 0;
+        for (const HostField &h : hf) {
+            lattice2d |= (h.kind == GMRF_LATTICE2D_4 || h.kind == GMRF_LATTICE2D_8) &&
+                         !(opts->flags & GMRF_FLAG_PER_COLOUR);
+            sites += h.n;
+        }
+        while (!lattice2d && s->V > 1 && sites * s->Cp / s->V < int64_t(152) * 2048 * 4) s->V >>= 1;
+    }
+    if (s->tune.chains_per_thread) s->V = s->tune.chains_per_thread;
     s->algorithm = opts->algorithm;
     s->nfields = nfields;
     s->hf = std::move(hf);

@@ -170,9 +170,11 @@ def test_batched_equals_single_fields_and_oracle(precision):
     T, C = 12, 2
     res, _ = gpu_run(fields, C, T, precision, seed=41, graph_sweeps=5)
     for fi, f in enumerate(fields):
-        # the per-sweep kernels on one field (a small single 2-D lattice would take the resident
-        # path, equal to these up to rounding only)
-        single, _ = gpu_run([dict(f, stream_id=fi)], C, T, precision, seed=41, flags=g.FLAG_NO_RESIDENT)
+        # the per-sweep kernels on one field with the batch's launch configuration (a small single
+        # 2-D lattice would take the resident path, a lone graph fewer chains per thread: equal
+        # to these up to rounding only)
+        single, _ = gpu_run([dict(f, stream_id=fi)], C, T, precision, seed=41, flags=g.FLAG_NO_RESIDENT,
+                            tuning={"chains_per_thread": 2})
         for c in range(C):
             assert np.array_equal(single[0][c]["x"], res[fi][c]["x"])
             assert np.array_equal(single[0][c]["tau_trace"], res[fi][c]["tau_trace"])
