@@ -168,11 +168,12 @@ typedef struct {
  * Resident path: a sampler of one small 2-D lattice field (Gaussian likelihood; each chain's
  * state, observations, mean and M2 fit one block's shared memory; at most 1152 sites per colour
  * class on the 8-neighbour lattice, e.g. 64 x 72, and 72 x 64 sites or the like on the
- * 4-neighbour one) runs a
- * batch of whole sweeps per launch, one block per chain (same draws and counters, results equal
- * up to rounding).  On by default in FP32; GMRF_FLAG_RESIDENT asks for
- * it in FP64 as well, GMRF_FLAG_NO_RESIDENT keeps the per-sweep launches.  gmrf_info.resident
- * tells which path a sampler took. */
+ * 4-neighbour one), or of one small graph (unit weights, Gaussian likelihood, fewer than 32768
+ * sites with state, mean and M2 in shared memory, at most 16 neighbours, 64 colours and 4096
+ * sites per colour class), runs a batch of whole sweeps per launch, one block per chain (same
+ * draws and counters, results equal up to rounding).  On by default in FP32; GMRF_FLAG_RESIDENT
+ * asks for it in FP64 as well, GMRF_FLAG_NO_RESIDENT keeps the per-sweep launches.
+ * gmrf_info.resident tells which path a sampler took. */
 #define GMRF_FLAG_PER_COLOUR 1
 #define GMRF_FLAG_NO_RESIDENT 2
 #define GMRF_FLAG_RESIDENT 4
@@ -189,7 +190,7 @@ typedef struct {
     int64_t launches_per_sweep; /* kernels launched per sweep                               */
     int64_t early_start_misses; /* sweep kernels that started before their predecessor ended */
                                 /* with a wrong sweep-number prediction (normals redrawn)    */
-    int64_t resident;         /* 1: sweeps run on the resident path (GMRF_FLAG_RESIDENT)     */
+    int64_t resident;         /* sweeps run on the resident path: 1 lattice, 2 graph; 0 not  */
 } gmrf_info;
 
 typedef struct gmrf_sampler gmrf_sampler;

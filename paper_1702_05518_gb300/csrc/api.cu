@@ -42,6 +42,8 @@ struct HostField {
     int32_t components = 1;
     bool fused = false;           // sampled by the fused 2-D lattice sweep (ping-pong state)
     std::vector<int32_t> colors;  // CSR: natural-order colouring used
+    int32_t max_degree = 0;       // CSR: largest row
+    bool weighted = false;        // CSR: weights given
 };
 
 }  // namespace
@@ -132,7 +134,8 @@ struct gmrf_sampler {
     // on a predicted sweep number, see lattice_fused_fast), or -1.
     int early_kind = -1;
     gmrf_tuning tune{};  // launch configuration overrides (zeros: the cost models)
-    int resident = 0, res_NI = 0, res_NT = 0, res_batch = 0;
+    int resident = 0, res_NI = 0, res_NT = 0, res_batch = 0;  // resident: 1 lattice, 2 graph
+    uint4 *res_nbr = nullptr, *res_nbr2 = nullptr;            // graph: neighbour records
     int32_t res_SR = 0, res_SC = 0;
     size_t res_smem = 0;
     void *res_z = nullptr;  // [res_batch][C][colours][NI][site threads] normals of a batch
@@ -327,6 +330,8 @@ gmrf_status check_field(const gmrf_field_desc &f, int idx, int chains, HostField
         h.dims[0] = f.n;
         gmrf_status st = validate_csr(f.n, f.row_ptr, f.col_idx, f.weights, &h.components);
         if (st != GMRF_OK) return fail(st, at + g_last_error);
+        for (int32_t i = 0; i < f.n; ++i) h.max_degree = std::max(h.max_degree, f.row_ptr[i + 1] - f.row_ptr[i]);
+        h.weighted = f.weights != nullptr;
         if (f.colors) {
             int32_t k = 0;
             st = validate_colors(f.n, f.row_ptr, f.col_idx, f.colors, &k);
@@ -510,14 +515,38 @@ cudaError_t launch_pre(gmrf_sampler *s, int count, cudaStream_t st)
 // (4-neighbour) positions.  It is the
 // default for FP32 samplers; GMRF_FLAG_RESIDENT asks for it in FP64 too and GMRF_FLAG_NO_RESIDENT
 // switches it off.
-cudaError_t plan_resident(gmrf_sampler *s)
+cudaError_t plan_resident(gmrf_sampler *s, const std::vector<int32_t> &coff0)
 {
     s->resident = 0;
     const int flags = s->opts.flags;
-    if (s->algorithm == GMRF_ALGO_PLAIN || s->nfields != 1 || !s->hf[0].fused || binomial_model(s)) return cudaSuccess;
+    if (s->algorithm == GMRF_ALGO_PLAIN || s->nfields != 1 || binomial_model(s)) return cudaSuccess;
     if (flags & GMRF_FLAG_NO_RESIDENT) return cudaSuccess;
     if (s->precision != GMRF_FP32 && !(flags & GMRF_FLAG_RESIDENT)) return cudaSuccess;
     const FieldDev &f = s->fd[0];
+    const int batch = std::min(128, std::max(64, s->opts.graph_sweeps));
+    if (f.kind == GMRF_CSR) {
+        // Graph: unit weights, 16-bit positions, at most 16 neighbours and 64 colours, every class
+        // within the site threads' positions, and state, mean and M2 in shared memory.
+        const HostField &h = s->hf[0];
+        if (h.weighted || f.n >= 32768 || h.max_degree > 16 || h.ncolors > 64 || coff0.size() != size_t(h.ncolors) + 1)
+            return cudaSuccess;
+        for (int c = 0; c < h.ncolors; ++c)
+            if (coff0[c + 1] - coff0[c] > csr_resident_max_positions()) return cudaSuccess;
+        const size_t smem = (3 * static_cast<size_t>(f.n) + 1) * tsize(s->precision);
+        if (smem > 220 * 1024) return cudaSuccess;
+        cudaError_t e = prepare_csr_resident(s->precision, smem);
+        if (e == cudaSuccess) e = s->alloc_t(&s->res_nbr, static_cast<size_t>(f.n), sizeof(uint4));
+        if (e == cudaSuccess) e = s->alloc_t(&s->res_nbr2, static_cast<size_t>(f.n), sizeof(uint4));
+        if (e == cudaSuccess)
+            e = launch_pack_csr_records(f.n, s->rp + f.rp0, s->ci + f.nnz0, s->res_nbr, s->res_nbr2, s->stream);
+        if (e == cudaSuccess) e = s->alloc(&s->res_z, static_cast<size_t>(batch) * s->C * f.n * tsize(s->precision));
+        if (e != cudaSuccess) return e;
+        s->res_batch = batch;
+        s->res_smem = smem;
+        s->resident = 2;
+        return cudaSuccess;
+    }
+    if (!s->hf[0].fused) return cudaSuccess;
     if (f.kind != GMRF_LATTICE2D_4 && f.kind != GMRF_LATTICE2D_8) return cudaSuccess;
     const bool e8 = f.kind == GMRF_LATTICE2D_8;
     const int K = e8 ? 4 : 2;
@@ -539,7 +568,6 @@ cudaError_t plan_resident(gmrf_sampler *s)
     cudaError_t e = prepare_lattice_resident(s->precision, f.kind, NI, smem);
     if (e != cudaSuccess) return e;
     // Sweeps per launch: the Gamma-variate batch, at most 128 (the normals buffer holds a batch).
-    const int batch = std::min(128, std::max(64, s->opts.graph_sweeps));
     e = s->alloc(&s->res_z, static_cast<size_t>(batch) * s->C * K * NI * NTS * tsize(s->precision));
     if (e != cudaSuccess) return e;
     s->res_batch = batch;
@@ -572,6 +600,26 @@ ResidentArgs resident_args(gmrf_sampler *s, int count, int draw, int draw_beta)
     return r;
 }
 
+ResCsrArgs csr_resident_args(gmrf_sampler *s, int count, int draw, int draw_beta)
+{
+    ResCsrArgs r{};
+    r.fields = s->fields_dev;
+    r.h = hyper_args(s, draw, draw_beta, 1);
+    r.x = s->x;
+    r.y = s->y;
+    r.mean = s->mean;
+    r.m2 = s->m2;
+    r.nbr = s->res_nbr;
+    r.nbr2 = s->res_nbr2;
+    r.coff = s->coff + s->fd[0].coff0;
+    r.ncolors = s->hf[0].ncolors;
+    r.count = count;
+    r.C = s->C;
+    r.rho = s->model.prior == GMRF_PRIOR_PCAR ? s->model.rho : 1.0;
+    r.zbuf = s->res_z;
+    return r;
+}
+
 cudaError_t launch_res_normals(gmrf_sampler *s, int count, cudaStream_t st)
 {
     ResNormArgs r{};
@@ -584,6 +632,7 @@ cudaError_t launch_res_normals(gmrf_sampler *s, int count, cudaStream_t st)
     r.count = count;
     r.NI = s->res_NI;
     r.NTS = s->res_NT - 64;
+    r.perm_inv = s->resident == 2 ? s->perm_inv : nullptr;
     r.out = s->res_z;
     const int gs = r.lanes == 4 ? 0 : (r.lanes == 2 ? 1 : 2);
     const int64_t groups = (static_cast<int64_t>(s->fd[0].n) + (1 << gs) - 1) >> gs;
@@ -676,7 +725,9 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int with_hyper, cudaStr
             const int cnt = std::min(s->res_batch, nsweeps - k);
             if (draw || draw_beta) e = launch_pre(s, cnt, st);
             if (e == cudaSuccess) e = launch_res_normals(s, cnt, st);
-            if (e == cudaSuccess)
+            if (e == cudaSuccess && s->resident == 2)
+                e = launch_csr_resident(s->precision, s->C, csr_resident_args(s, cnt, draw, draw_beta), s->res_smem, st);
+            else if (e == cudaSuccess)
                 e = launch_lattice_resident(s->precision, s->fd[0].kind, s->res_NI, s->res_NT, s->C,
                                             resident_args(s, cnt, draw, draw_beta), s->res_smem, st);
             k += cnt;
@@ -1177,7 +1228,7 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
             }
         s->early_kind = (sweep_kernels == 1 && kind >= 0) ? kind : -1;
     }
-    CK(plan_resident(s));
+    CK(plan_resident(s, coff_host[0]));
     CK(s->alloc_t(&s->tiles_dev, std::max<size_t>(all.size(), 1), sizeof(Tile)));
     if (!all.empty())
         CK(cudaMemcpyAsync(s->tiles_dev, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice, s->stream));

@@ -110,15 +110,35 @@ struct ResidentArgs {
     const void *zbuf;     // [count][C][colour][NI][site thread] normals of the batch (precision T)
 };
 
-// Arguments of the producer of the resident kernel's normals (resident_normals_kernel).
+// Arguments of the producer of the resident kernels' normals (resident_normals_kernel).
 struct ResNormArgs {
     const FieldDev *fields;
     SweepCtl *ctl;        // the batch starts at ctl->sweep
     uint2 key;
     int32_t lanes, C, Cp;
     int32_t count;        // sweeps of the batch
-    int32_t NI, NTS;      // positions per thread and class, site threads
+    int32_t NI, NTS;      // lattice: positions per thread and class, site threads
+    const int32_t *perm_inv;  // graph: natural site -> permuted position (then out is [count][C][n])
     void *out;
+};
+
+// Arguments of one launch of the graph resident kernel (csr_resident.cu): `count` whole sweeps
+// of the single graph field 0, one block per chain.
+struct ResCsrArgs {
+    const FieldDev *fields;
+    HyperArgs h;
+    void *x;              // [slots][Cp] state (permuted positions)
+    const void *y;
+    void *mean;
+    void *m2;
+    const uint4 *nbr;     // [n] eight 16-bit neighbour positions (pad = n; bit 15 of the first:
+                          // more in nbr2)
+    const uint4 *nbr2;    // [n] neighbours 9..16 of the flagged positions
+    const int32_t *coff;  // colour offsets (ncolors + 1)
+    int32_t ncolors;
+    int32_t count, C;
+    double rho;
+    const void *zbuf;     // [count][C][n] normals by permuted position
 };
 
 // A tile of the fused 2-D lattice sweep: natural coordinates of its first site.
@@ -223,6 +243,14 @@ cudaError_t launch_lattice_resident(int precision, int kind, int NI, int threads
                                     size_t smem, cudaStream_t stream);
 // One thread per Philox block of the batch: `blocks_needed` = sweeps x groups x chain quadruples.
 cudaError_t launch_resident_normals(int precision, const ResNormArgs &a, int64_t blocks_needed, cudaStream_t stream);
+// Graph resident path: the neighbour records from the permuted CSR, the kernel's shared-memory
+// limit, and a launch (one block of csr_resident_threads() per chain).
+int csr_resident_threads();
+int csr_resident_max_positions();  // per site thread and colour class
+cudaError_t launch_pack_csr_records(int32_t n, const int32_t *rp, const int32_t *ci, uint4 *nbr, uint4 *nbr2,
+                                    cudaStream_t stream);
+cudaError_t prepare_csr_resident(int precision, size_t smem);
+cudaError_t launch_csr_resident(int precision, int chains, const ResCsrArgs &a, size_t smem, cudaStream_t stream);
 
 // Chain diagnostics (diagnostics.cu): one parameter trace of every chain of one field.
 struct DiagArgs {

@@ -27,6 +27,7 @@
 #include "gmrf_device.cuh"
 #include "gmrf_internal.h"
 #include "lattice_common.cuh"
+#include "resident_draws.cuh"
 
 namespace gmrf {
 namespace {
@@ -73,16 +74,11 @@ __global__ void __launch_bounds__(res_threads<NI>(), 1) lattice_resident_kernel(
     const long long sweep0 = h.ctl->sweep;
     long long acc = h.ctl->acc_count;
     const long long bbase = h.ctl->batch_base, bcount = h.ctl->batch_count;
-    const int64_t hc = chain;  // field 0
-    T *hyp = static_cast<T *>(h.hyp) + hc * kHypStride;
-    if (tid < 3) hs[tid] = hyp[tid];
-    // The FP64 values the drawing lanes carry from sweep to sweep.
-    double tau_d = 0.0, sig2_d = 0.0, beta_d = 0.0;
-    if (drawer && lane == 0) {
-        tau_d = h.tau[hc];
-        sig2_d = h.sig2[hc];
-        beta_d = h.beta[hc];
-    }
+    if (tid < 3) hs[tid] = static_cast<const T *>(h.hyp)[static_cast<int64_t>(chain) * kHypStride + tid];
+    // The drawing lanes' state lives in shared memory (no thread keeps registers for it).
+    __shared__ ResidentDraws<T> drs[2];
+    ResidentDraws<T> &dr = drs[drawer ? dw : 0];
+    if (drawer && lane == 0) dr.init(h, dw, chain, f);
 
     // Stage the chain: every cell of every sub-array, the ring and padding as zeros.
     {
@@ -172,80 +168,8 @@ __global__ void __launch_bounds__(res_threads<NI>(), 1) lattice_resident_kernel(
     // Position in the accumulation schedule and in the trace ring, advanced sweep by sweep.
     int thin_phase = sweep0 >= h.burn_in ? static_cast<int>((sweep0 - h.burn_in) % h.thin) : 0;
     long long slot = h.trace_cap > 0 ? sweep0 % h.trace_cap : 0;
-    const double fn = static_cast<double>(f.n);
-    // FP32 state: the drawing lanes draw in single precision from the block's single-precision
-    // sums (a few operations of short latency between the sums and the barrier), and store and
-    // trace those values widened to FP64 (sigma^2 as the FP64 reciprocal of the 1/sigma^2 used)
-    // while the next sweep runs, so a run resumed from fetched values continues bit for bit.
-    // FP64 state: the FP64 draws of hyper_draw before the barrier.
-    constexpr bool kSplit = sizeof(T) == 4;
-    double G = 0.0, dz = 0.0;       // this sweep's unit-rate Gamma variate and intercept term
-    float Gf = 0.0f, dzf = 0.0f;     // the same in single precision (kSplit)
-    const float b_tau_f = static_cast<float>(h.b_tau), b_sig_f = static_cast<float>(h.b_sig);
-    const float fn_f = static_cast<float>(f.n), inv_n_f = static_cast<float>(1.0 / f.n);
-    float tau_f = 0.0f, isig_f = 0.0f, beta_f = 0.0f;  // kSplit: the last sweep's draws
-    long long slot_used = 0;
-    // kSplit: store and trace the last sweep's draws.
-    auto record_fp32 = [&]() {
-        if (dw == 0) {
-            if (h.draw) {
-                tau_d = static_cast<double>(tau_f);
-                h.tau[hc] = tau_d;
-                hyp[0] = static_cast<T>(tau_f);
-            }
-            if (h.trace_cap > 0) h.trace_tau[hc * h.trace_cap + slot_used] = tau_d;
-        } else {
-            if (h.draw_beta) {
-                beta_d = static_cast<double>(beta_f);
-                h.beta[hc] = beta_d;
-                hyp[2] = static_cast<T>(beta_f);
-            }
-            if (h.draw) {
-                sig2_d = 1.0 / static_cast<double>(isig_f);
-                h.sig2[hc] = sig2_d;
-                hyp[1] = static_cast<T>(isig_f);
-            }
-            if (h.trace_cap > 0) {
-                h.trace_sig[hc * h.trace_cap + slot_used] = sig2_d;
-                if (h.trace_beta) h.trace_beta[hc * h.trace_cap + slot_used] = beta_d;
-            }
-        }
-    };
-    // FP64 state: the draws of hyper_draw from the block's sums, published to the block.
-    auto draw_fp64 = [&](double S, double R, double A, double b) {
-        if (dw == 0) {
-            if (h.draw) {
-                tau_d = G / (h.b_tau + 0.5 * S);
-                hs[0] = static_cast<T>(tau_d);
-                h.tau[hc] = tau_d;
-                hyp[0] = static_cast<T>(tau_d);
-            }
-            if (h.trace_cap > 0) h.trace_tau[hc * h.trace_cap + slot_used] = tau_d;
-        } else {
-            if (h.draw_beta) {
-                const double delta = A / fn + dz;
-                beta_d = b + delta;
-                R = R - 2.0 * delta * A + fn * (delta * delta);
-                hs[2] = static_cast<T>(beta_d);
-                h.beta[hc] = beta_d;
-                hyp[2] = static_cast<T>(beta_d);
-            }
-            if (h.draw) {
-                sig2_d = (h.b_sig + 0.5 * R) / G;
-                const double prec = 1.0 / sig2_d;  // from sigma^2, as the per-sweep path
-                hs[1] = static_cast<T>(prec);
-                h.sig2[hc] = sig2_d;
-                hyp[1] = static_cast<T>(prec);
-            }
-            if (h.trace_cap > 0) {
-                h.trace_sig[hc * h.trace_cap + slot_used] = sig2_d;
-                if (h.trace_beta) h.trace_beta[hc * h.trace_cap + slot_used] = beta_d;
-            }
-        }
-    };
     for (int t = 0; t < a.count; ++t) {
         const long long sw = sweep0 + t;
-        const uint32_t sweep = static_cast<uint32_t>(sw);
         const bool more = t + 1 < a.count;
         if (!drawer && more) {
 #pragma unroll
@@ -253,43 +177,9 @@ __global__ void __launch_bounds__(res_threads<NI>(), 1) lattice_resident_kernel(
 #pragma unroll
                 for (int k = 0; k < NI; ++k) zn[c][k] = ZB[(t + 1) * zstride + (c * NI + k) * NTS];
         }
-        // Drawing lanes: the FP64 part of the last sweep's draws (kSplit), then what this sweep's
-        // draws need that does not depend on its state (the unit-rate Gamma variates, the
-        // intercept's normal and scale), while the site threads run the colour steps.
-        if (drawer && lane == 0) {
-            if (kSplit && t > 0) record_fp32();
-            const long long kb = sw - bbase;
-            const bool pre = h.gpre != nullptr && kb >= 0 && kb < bcount;
-            const double *gp = pre ? h.gpre + (kb * h.nfields * Cp + chain) * 4 : nullptr;
-            G = 0.0;
-            dz = 0.0;
-            if (h.draw) {
-                if (pre) {
-                    G = gp[dw];
-                } else {
-                    const uint32_t tag = dw ? kTagSig : kTagTau;
-                    const double shape = dw ? h.a_sig + 0.5 * fn : h.a_tau + 0.5 * f.rank;
-                    int fb = 0;
-                    G = gamma_mt(shape, 1.0, h.key, sweep, f.stream, (tag << 24) | static_cast<uint32_t>(chain), fb);
-                    if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&h.ctl->fallbacks), 1ull);
-                }
-            }
-            if (dw == 1 && h.draw_beta) {
-                double zb = 0.0;
-                if (pre) {
-                    zb = gp[2];
-                } else {
-                    const uint4 w = philox4x32_10(
-                        make_uint4(0u, sweep, f.stream, (kTagBeta << 24) | static_cast<uint32_t>(chain)), h.key);
-                    double unused;
-                    box_muller_f64(w.x, w.y, zb, unused);
-                }
-                dz = sqrt(sig2_d / fn) * zb;
-            }
-            Gf = static_cast<float>(G);
-            dzf = static_cast<float>(dz);
-            slot_used = slot;
-        }
+        // Drawing lanes: the record of the last sweep's draws (FP32 state), then what this sweep's
+        // draws need that does not depend on its state, while the site threads run the colour steps.
+        if (drawer && lane == 0) dr.prep(h, sw, slot, t > 0, bbase, bcount, Cp);
         const T tau = hs[0], isig = hs[1], beta = hs[2];
         const bool acc_now = acc_on && sw >= h.burn_in && thin_phase == 0;
         const T inv_k = acc_now ? static_cast<T>(1) / static_cast<T>(acc + 1) : static_cast<T>(0);
@@ -384,31 +274,7 @@ __global__ void __launch_bounds__(res_threads<NI>(), 1) lattice_resident_kernel(
                 v0 += __shfl_xor_sync(0xffffffffu, v0, o);
                 v1 += __shfl_xor_sync(0xffffffffu, v1, o);
             }
-            if (lane == 0) {
-                if constexpr (kSplit) {
-                    if (dw == 0) {
-                        if (h.draw) {
-                            tau_f = Gf / (b_tau_f + 0.5f * v0);
-                            hs[0] = tau_f;
-                        }
-                    } else {
-                        float R = v0;
-                        if (h.draw_beta) {
-                            const float delta = v1 * inv_n_f + dzf;
-                            beta_f = beta + delta;
-                            hs[2] = beta_f;
-                            R = R - 2.0f * delta * v1 + fn_f * (delta * delta);
-                        }
-                        if (h.draw) {
-                            isig_f = Gf / (b_sig_f + 0.5f * R);
-                            hs[1] = isig_f;
-                        }
-                    }
-                } else {
-                    draw_fp64(static_cast<double>(v0), static_cast<double>(v0), static_cast<double>(v1),
-                              static_cast<double>(beta));
-                }
-            }
+            if (lane == 0) dr.draw(h, v0, v1, beta, hs);
         }
         if (!drawer && more) {
 #pragma unroll
@@ -421,7 +287,7 @@ __global__ void __launch_bounds__(res_threads<NI>(), 1) lattice_resident_kernel(
         if (h.trace_cap > 0) slot = (slot + 1 == h.trace_cap) ? 0 : slot + 1;
         __syncthreads();
     }
-    if (kSplit && drawer && lane == 0 && a.count > 0) record_fp32();
+    if (drawer && lane == 0 && a.count > 0) dr.finish(h);
     pdl_release();
 
     // State and accumulators back to global memory; the state into the buffer that holds the
@@ -452,8 +318,9 @@ __global__ void __launch_bounds__(res_threads<NI>(), 1) lattice_resident_kernel(
     }
 }
 
-// The normals of a batch of `count` sweeps for the resident kernel, in its per-thread order
-// [sweep][chain][colour][k][site thread]: one thread per Philox block (a group of G = 4 / lanes
+// The normals of a batch of `count` sweeps for the resident kernels: lattices in the lattice
+// kernel's per-thread order [sweep][chain][colour][k][site thread], graphs by permuted position
+// [sweep][chain][position]; one thread per Philox block (a group of G = 4 / lanes
 // sites and a quadruple of chains, as in site_normals), whose four normals go to the positions of
 // their (site, chain) pairs.  Position q of colour class c belongs to site thread q mod NTS, slot
 // q / NTS; the class positions are those of lattice_resident_kernel.
@@ -486,6 +353,10 @@ __global__ void resident_normals_kernel(const ResNormArgs a)
             const int64_t site = (g << gs) + r / L;
             const int chain = cq * 4 + (r & (L - 1));
             if (site >= n || chain >= a.C) continue;
+            if (a.perm_inv) {  // graph: by permuted position
+                out[(t * a.C + chain) * n + a.perm_inv[f.csr0 + site]] = n4[r];
+                continue;
+            }
             const int i = static_cast<int>(site / Wl), j = static_cast<int>(site - static_cast<int64_t>(i) * Wl);
             int c, pos;
             if (e8) {

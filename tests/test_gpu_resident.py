@@ -176,3 +176,105 @@ def test_fix_hyper_and_reset():
         assert np.array_equal(r1[c]["x"], r2[c]["x"])
         assert relerr(r1[c]["x"], st.x[c]) <= TOL_FP64
         assert np.all(r1[c]["tau_trace"] == 2.0) and np.all(r1[c]["sigma2_trace"] == 0.5)
+
+
+# --------------------------------------------------------------------------------------------
+# Graphs: one block per chain, neighbour records, the same draws
+# --------------------------------------------------------------------------------------------
+def _delaunay(npts, seed, shift=0.0):
+    rp, ci, _ = wl.delaunay_graph(npts, wl.rng(seed))
+    f = wl.graph_field(rp, ci, seed=seed + 100)
+    f["color_seed"] = seed
+    f["y"] = f["y"] + shift
+    return f
+
+
+def _wheels(nw, spokes, seed):
+    """nw wheels (a hub joined to a cycle of `spokes` rim sites): hubs of degree `spokes`."""
+    rows = []
+    for w in range(nw):
+        hub = w * (spokes + 1)
+        rim = [hub + 1 + k for k in range(spokes)]
+        for k, r in enumerate(rim):
+            rows.append((hub, r))
+            rows.append((r, rim[(k + 1) % spokes]))
+    n = nw * (spokes + 1)
+    adj = [set() for _ in range(n)]
+    for a_, b_ in rows:
+        adj[a_].add(b_)
+        adj[b_].add(a_)
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum([len(s) for s in adj])
+    ci = np.concatenate([sorted(s) for s in adj]).astype(np.int32)
+    f = wl.graph_field(rp, ci, seed=seed)
+    f["color_seed"] = seed
+    return f
+
+
+GRAPHS = [("delaunay_1500", lambda: _delaunay(1500, 21)), ("delaunay_9000", lambda: _delaunay(9000, 22)),
+          ("wheels_16", lambda: _wheels(40, 16, 23)), ("wheels_9", lambda: _wheels(30, 9, 24)),
+          ("delaunay_12", lambda: _delaunay(12, 25))]
+
+
+def test_graphs_which_take_it():
+    small = _delaunay(2000, 1)
+    big = _delaunay(20000, 2)  # state, mean and M2 do not fit shared memory
+
+    def res(fields, **kw):
+        with g.Sampler(fields, seed=1, **kw) as s:
+            return s.info()["resident"]
+
+    assert res([small], chains=8) == 2
+    assert res([dict(small, weights=np.ones(len(small["col_idx"])))]) == 0
+    assert res([big]) == 0
+    assert res([small], precision=g.FP64) == 0
+    assert res([small], precision=g.FP64, flags=g.FLAG_RESIDENT) == 2
+    assert res([small], flags=g.FLAG_NO_RESIDENT) == 0
+    assert res([small, small]) == 0
+
+
+@pytest.mark.parametrize("name,make", GRAPHS, ids=[g_[0] for g_ in GRAPHS])
+@pytest.mark.parametrize("chains", [1, 3])
+def test_graph_fp64_parity(name, make, chains):
+    f = make()
+    res, info = _run([f], chains, 40, g.FP64, seed=7, flags=g.FLAG_RESIDENT, burn_in=10, graph_sweeps=16,
+                     prior=g.PRIOR_PCAR, rho=0.95)
+    assert info["resident"] == 2 and info["sweeps_done"] == 40 and info["accumulated"] == 30
+    _check_oracle(f, res, chains, 40, 7, TOL_FP64, burn_in=10, prior="pcar", rho=0.95)
+
+
+@pytest.mark.parametrize("name,make", GRAPHS, ids=[g_[0] for g_ in GRAPHS])
+def test_graph_fp32(name, make):
+    f = make()
+    res, info = _run([f], 4, 1, g.FP32, seed=9)
+    assert info["resident"] == 2
+    _check_oracle(f, res, 4, 1, 9, TOL_FP32_1)
+
+
+def test_graph_fp32_1000_sweeps_and_intercept():
+    f = _delaunay(4000, 26, shift=2.0)
+    res, info = _run([f], 2, 1000, g.FP32, seed=11, burn_in=300, graph_sweeps=100, intercept=True)
+    assert info["resident"] == 2 and info["hyper_fallbacks"] == 0
+    _check_oracle(f, res, 2, 1000, 11, TOL_FP32_1000, burn_in=300, intercept=True)
+
+
+@pytest.mark.parametrize("intercept", [False, True])
+def test_graph_agrees_with_per_sweep_kernels(intercept):
+    f = _delaunay(3000, 27, shift=2.0 if intercept else 0.0)
+    out = []
+    for flags in (g.FLAG_RESIDENT, g.FLAG_NO_RESIDENT):
+        with g.Sampler([f], precision=g.FP64, chains=3, seed=17, flags=flags, burn_in=20, thin=3,
+                       graph_sweeps=8, intercept=intercept) as s:
+            _sequence(s, STEPS)
+            info = s.info()
+            r = [s.fetch(0, c, trace=200) for c in range(3)]
+            if intercept:
+                for c in range(3):
+                    r[c].update(s.fetch_intercept(0, c, trace=200))
+            out.append((r, info))
+    (a, ia), (b, ib) = out
+    assert ia["resident"] == 2 and ib["resident"] == 0
+    assert ia["sweeps_done"] == ib["sweeps_done"] and ia["accumulated"] == ib["accumulated"]
+    for c in range(3):
+        for key in ("x", "mean", "var", "tau_trace", "sigma2_trace") + (("beta0_trace",) if intercept else ()):
+            assert relerr(a[c][key], b[c][key]) <= TOL_FP64, key
