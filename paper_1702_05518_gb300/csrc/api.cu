@@ -1081,7 +1081,9 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
             // the tile partial sums) does not change from run to run.
             double best = 1e300;
             for (int nt : {512, 1024}) {
-                const int bps = nt == 1024 ? 1 : 2;
+                // blocks per SM: two of 512 threads where the kernel is compiled for 64 registers
+                // (FP32 with up to two chains per thread), else one (four chains keep 128)
+                const int bps = (nt == 512 && s->precision == GMRF_FP32 && s->Cp < 4) ? 2 : 1;
                 for (int cr = 16; cr <= 160; cr += 2)
                     for (int cc = 16; cc <= 128; cc += 2) {
                         const size_t sm = lattice_fused_smem(s->precision, kind, s->Cp, cr, cc);

@@ -423,8 +423,10 @@ __global__ void __launch_bounds__(kFusedBlock, (kFusedBlock == 512 && sizeof(T) 
 // field-relative 32-bit offsets, staging indices equal to the shared-memory index, normals
 // drawn for every staged site (no per-site region tests), neighbour offsets fixed per colour
 // step, lower-colour terms as 0/1 weights, and bounds tests only for sites on the lattice edge.
+// Two 512-thread blocks per SM (64 registers) for FP32 with up to two chains per thread; with four
+// chains the 128 registers of one block per SM avoid spilling the neighbours' chain vectors.
 template <typename T, int KIND, int NT, int CP>
-__global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4) ? 2 : 1) lattice_fused_fast(const FusedArgs a)
+__global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4 && CP < 4) ? 2 : 1) lattice_fused_fast(const FusedArgs a)
 {
     using D = Dirs<KIND>;
     constexpr bool E8 = (KIND == kLat2D8);
