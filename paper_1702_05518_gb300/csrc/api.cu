@@ -67,6 +67,11 @@ struct gmrf_sampler {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t capture_stream = nullptr;
+    // Sweeps with both fused 2-D stages and per-colour stages (disjoint fields) run the per-colour
+    // stages on a second stream, forked after the sweep's first stages and joined before the
+    // parameter draws.
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     gmrf_model model{};
     gmrf_opts opts{};
     int precision = 0, C = 1, Cp = 1, V = 1;
@@ -170,6 +175,11 @@ struct gmrf_sampler {
         allocs.clear();
         if (capture_stream) cudaStreamDestroy(capture_stream);
         capture_stream = nullptr;
+        if (side_stream) cudaStreamDestroy(side_stream);
+        side_stream = nullptr;
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        ev_fork = ev_join = nullptr;
     }
 };
 
@@ -746,6 +756,24 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int with_hyper, cudaStr
             e = launch_plain_sweep(a, st, &l);
             continue;
         }
+        if (s->side_stream) {
+            // Fused 2-D stages on `st`, per-colour stages (in their order) on the side stream, then
+            // the draws after both; a Polya-Gamma stage (all fields) runs before the fork.
+            size_t k = 0;
+            for (; k < s->stages.size() && e == cudaSuccess && s->stages[k].type == 3; ++k)
+                e = enqueue_stage(s, k, 1, 1, draw, draw_beta, 1, st);
+            if (e == cudaSuccess) e = cudaEventRecord(s->ev_fork, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side_stream, s->ev_fork, 0);
+            for (size_t q = k; q < s->stages.size() && e == cudaSuccess; ++q)
+                if (s->stages[q].type == 0) e = enqueue_stage(s, q, 1, 1, draw, draw_beta, 1, s->side_stream);
+            for (size_t q = k; q < s->stages.size() && e == cudaSuccess; ++q)
+                if (s->stages[q].type == 1) e = enqueue_stage(s, q, 1, 1, draw, draw_beta, 1, st);
+            if (e == cudaSuccess) e = cudaEventRecord(s->ev_join, s->side_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->ev_join, 0);
+            for (size_t q = k; q < s->stages.size() && e == cudaSuccess; ++q)
+                if (s->stages[q].type == 2) e = enqueue_stage(s, q, 1, 1, draw, draw_beta, 1, st);
+            continue;
+        }
         for (size_t k = 0; k < s->stages.size() && e == cudaSuccess; ++k)
             e = enqueue_stage(s, k, 1, 1, draw, draw_beta, 1, st);
     }
@@ -1231,6 +1259,19 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
         s->early_kind = (sweep_kernels == 1 && kind >= 0) ? kind : -1;
     }
     CK(plan_resident(s, coff_host[0]));
+    {
+        // fused 2-D stages and per-colour stages in one sweep: the latter get a side stream
+        bool fused = false, step = false;
+        for (const auto &st : s->stages) {
+            fused |= st.type == 1;
+            step |= st.type == 0;
+        }
+        if (fused && step && !s->resident) {
+            CK(cudaStreamCreateWithFlags(&s->side_stream, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
+        }
+    }
     CK(s->alloc_t(&s->tiles_dev, std::max<size_t>(all.size(), 1), sizeof(Tile)));
     if (!all.empty())
         CK(cudaMemcpyAsync(s->tiles_dev, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice, s->stream));
