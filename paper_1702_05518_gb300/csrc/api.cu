@@ -141,6 +141,7 @@ struct gmrf_sampler {
     gmrf_tuning tune{};  // launch configuration overrides (zeros: the cost models)
     int resident = 0, res_NI = 0, res_NT = 0, res_batch = 0;  // resident: 1 lattice, 2 graph
     uint4 *res_nbr = nullptr, *res_nbr2 = nullptr;            // graph: neighbour records
+    int res_cluster = 1, res_own_max = 0;                      // graph: blocks per chain, their share
     int32_t res_SR = 0, res_SC = 0;
     size_t res_smem = 0;
     void *res_z = nullptr;  // [res_batch][C][colours][NI][site threads] normals of a batch
@@ -540,9 +541,16 @@ cudaError_t plan_resident(gmrf_sampler *s, const std::vector<int32_t> &coff0)
         const HostField &h = s->hf[0];
         if (h.weighted || f.n >= 32768 || h.max_degree > 16 || h.ncolors > 64 || coff0.size() != size_t(h.ncolors) + 1)
             return cudaSuccess;
-        for (int c = 0; c < h.ncolors; ++c)
-            if (coff0[c + 1] - coff0[c] > csr_resident_max_positions()) return cudaSuccess;
-        const size_t smem = (3 * static_cast<size_t>(f.n) + 1) * tsize(s->precision);
+        // A cluster of CL blocks per chain (at most 152 blocks in all): one block per 2048 sites.
+        int cl = 1;
+        while (cl < 8 && f.n >= 2048 * 2 * cl && s->C * 2 * cl <= 152) cl *= 2;
+        int own_max = 0;
+        for (int c = 0; c < h.ncolors; ++c) {
+            const int len = coff0[c + 1] - coff0[c], q = (len + cl - 1) / cl;
+            if (q > csr_resident_max_positions()) return cudaSuccess;
+            own_max += q;
+        }
+        const size_t smem = (static_cast<size_t>(f.n) + 1 + 2 * static_cast<size_t>(own_max)) * tsize(s->precision);
         if (smem > 220 * 1024) return cudaSuccess;
         cudaError_t e = prepare_csr_resident(s->precision, smem);
         if (e == cudaSuccess) e = s->alloc_t(&s->res_nbr, static_cast<size_t>(f.n), sizeof(uint4));
@@ -553,6 +561,8 @@ cudaError_t plan_resident(gmrf_sampler *s, const std::vector<int32_t> &coff0)
         if (e != cudaSuccess) return e;
         s->res_batch = batch;
         s->res_smem = smem;
+        s->res_cluster = cl;
+        s->res_own_max = own_max;
         s->resident = 2;
         return cudaSuccess;
     }
@@ -625,6 +635,7 @@ ResCsrArgs csr_resident_args(gmrf_sampler *s, int count, int draw, int draw_beta
     r.ncolors = s->hf[0].ncolors;
     r.count = count;
     r.C = s->C;
+    r.own_max = s->res_own_max;
     r.rho = s->model.prior == GMRF_PRIOR_PCAR ? s->model.rho : 1.0;
     r.zbuf = s->res_z;
     return r;
@@ -736,7 +747,8 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int with_hyper, cudaStr
             if (draw || draw_beta) e = launch_pre(s, cnt, st);
             if (e == cudaSuccess) e = launch_res_normals(s, cnt, st);
             if (e == cudaSuccess && s->resident == 2)
-                e = launch_csr_resident(s->precision, s->C, csr_resident_args(s, cnt, draw, draw_beta), s->res_smem, st);
+                e = launch_csr_resident(s->precision, s->res_cluster, s->C, csr_resident_args(s, cnt, draw, draw_beta),
+                                        s->res_smem, st);
             else if (e == cudaSuccess)
                 e = launch_lattice_resident(s->precision, s->fd[0].kind, s->res_NI, s->res_NT, s->C,
                                             resident_args(s, cnt, draw, draw_beta), s->res_smem, st);

@@ -1,11 +1,18 @@
-// csr_resident.cu -- many whole sweeps of a small graph field in one launch, one block per chain.
+// csr_resident.cu -- many whole sweeps of a small graph field in one launch, one thread-block
+// cluster per chain.
 //
 // The graph counterpart of lattice_resident.cu, for a single CSR field with unit weights and
 // the Gaussian likelihood (the precinct-sized graphs of Sec. 3.2: a few thousand to ~18,000
 // sites).  On the per-sweep path such a field's sweep is k launches of a few thousand sites each
 // plus the draws, bound by launch latency.  Here one block holds a chain: its state, running mean
 // and M2 in shared memory by permuted position (colour classes contiguous, Sec. 2.3), and runs
-// `count` sweeps of Algorithm 1 back to back.  What a sweep reads from L2 is the neighbour lists
+// `count` sweeps of Algorithm 1 back to back.  A chain is shared by a cluster of CL blocks (on CL
+// SMs): every block keeps the chain's whole state in its shared memory and owns a contiguous share
+// of each colour class; after updating its share it stores the new values into the other blocks'
+// copies (distributed shared memory, st.shared::cluster), and a cluster barrier (release /
+// acquire) ends the colour step, so each block reads all neighbours locally.  The block sums go to
+// block 0, whose drawing warps draw and store the new parameters into every block.
+// What a sweep reads from L2 is the neighbour lists
 // -- re-packed for this kernel as one 16-byte record of eight 16-bit positions per site (a second
 // record for sites of degree 9 to 16), so a site's neighbours arrive in one load -- the
 // observations and the sweep's normals (produced ahead for the whole batch by
@@ -50,47 +57,96 @@ __global__ void pack_csr_records_kernel(int32_t n, const int32_t *rp, const int3
     }
 }
 
-template <typename T>
+// Cluster primitives (PTX): this block's rank in its cluster, the address of the same shared
+// location in block `rank`, a store there, and the cluster barrier (arrive with release, wait
+// with acquire: stores to other blocks before the arrive are visible after the wait).
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t remote_addr(const void *p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(r)
+                 : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_remote(uint32_t addr, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_remote(uint32_t addr, double v)
+{
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+template <typename T, int CL>
 __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResCsrArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T red[kCsrThreads / 32][3];
-    __shared__ T hs[3];  // tau, 1/sigma^2, beta0 of the current sweep
+    __shared__ T red_cl[8][3];  // block 0: the blocks' sums
+    __shared__ T hs[3];         // tau, 1/sigma^2, beta0 of the current sweep
     __shared__ int coffs[kCsrMaxColours + 1];
+    __shared__ int own_lo[kCsrMaxColours], own_hi[kCsrMaxColours], own_off[kCsrMaxColours];
 
     pdl_wait();
     const HyperArgs &h = a.h;
-    const int chain = blockIdx.x, tid = threadIdx.x, NT = blockDim.x, NTS = kCsrSiteThreads;
+    const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
+    const int chain = blockIdx.x / CL, tid = threadIdx.x, NT = blockDim.x, NTS = kCsrSiteThreads;
     const int lane = tid & 31, warp = tid >> 5, nsw = NTS >> 5;
     const bool drawer = tid >= NTS;
-    const int dw = warp - nsw;  // drawing warp: 0 tau, 1 beta0 and sigma^2
+    const int dw = warp - nsw;  // drawing warp: 0 tau, 1 beta0 and sigma^2 (block 0 only)
     const FieldDev f = a.fields[0];
     const int n = f.n, K = a.ncolors, Cp = h.Cp;
-    T *xs = reinterpret_cast<T *>(smem_raw);  // [n + 1]: position n is a zero (the records' pad)
-    T *ms = xs + n + 1;
-    T *m2s = ms + n;
+    T *xs = reinterpret_cast<T *>(smem_raw);  // [n + 1] the whole chain; position n is a zero (pad)
+    T *ms = xs + n + 1;                       // the owned positions' mean and M2
+    T *m2s = ms + a.own_max;
 
     const long long sweep0 = h.ctl->sweep;
     long long acc = h.ctl->acc_count;
     const long long bbase = h.ctl->batch_base, bcount = h.ctl->batch_count;
     if (tid < 3) hs[tid] = static_cast<const T *>(h.hyp)[static_cast<int64_t>(chain) * kHypStride + tid];
     if (tid <= K) coffs[tid] = a.coff[tid];
-    // The drawing lanes' state lives in shared memory (no thread keeps registers for it).
+    __syncthreads();
+    if (tid == 0) {  // this block's share of every colour class and its place in ms / m2s
+        int off = 0;
+        for (int c = 0; c < K; ++c) {
+            const int lo = coffs[c], len = coffs[c + 1] - lo, q = (len + CL - 1) / CL;
+            own_lo[c] = lo + min(static_cast<int>(rank) * q, len);
+            own_hi[c] = lo + min((static_cast<int>(rank) + 1) * q, len);
+            own_off[c] = off;
+            off += own_hi[c] - own_lo[c];
+        }
+    }
+    // The drawing lanes' state (block 0) lives in shared memory.
     __shared__ ResidentDraws<T> drs[2];
     ResidentDraws<T> &dr = drs[drawer ? dw : 0];
-    if (drawer && lane == 0) dr.init(h, dw, chain, f);
+    const bool draws = drawer && lane == 0 && rank == 0;
+    if (draws) dr.init(h, dw, chain, f);
+    __syncthreads();
     {
         const T *X = static_cast<const T *>(a.x) + f.slot0 * Cp + chain;
         const T *MEAN = static_cast<const T *>(a.mean) + f.slot0 * Cp + chain;
         const T *M2 = static_cast<const T *>(a.m2) + f.slot0 * Cp + chain;
-        for (int p = tid; p < n; p += NT) {
-            xs[p] = X[static_cast<int64_t>(p) * Cp];
-            ms[p] = MEAN[static_cast<int64_t>(p) * Cp];
-            m2s[p] = M2[static_cast<int64_t>(p) * Cp];
-        }
+        for (int p = tid; p < n; p += NT) xs[p] = X[static_cast<int64_t>(p) * Cp];
         if (tid == 0) xs[n] = 0;
+        for (int c = 0; c < K; ++c)
+            for (int p = own_lo[c] + tid; p < own_hi[c]; p += NT) {
+                const int l = own_off[c] + p - own_lo[c];
+                ms[l] = MEAN[static_cast<int64_t>(p) * Cp];
+                m2s[l] = M2[static_cast<int64_t>(p) * Cp];
+            }
     }
     __syncthreads();
+    if (CL > 1) cluster_sync();  // every block of the cluster has its copy before any store into it
 
     const T *Y = static_cast<const T *>(a.y) + f.slot0;
     const T *ZB = static_cast<const T *>(a.zbuf) + static_cast<int64_t>(chain) * n;
@@ -99,9 +155,13 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
     const bool acc_on = h.acc_enabled != 0;
     int thin_phase = sweep0 >= h.burn_in ? static_cast<int>((sweep0 - h.burn_in) % h.thin) : 0;
     long long slot = h.trace_cap > 0 ? sweep0 % h.trace_cap : 0;
+    // In a cluster the drawing warps arrive at the first colour barrier of a sweep before block
+    // 0's drawing lanes do their part of the draws, so that work never holds the barrier.
+    const bool early = CL > 1 && K > 1 && drawer;
     for (int t = 0; t < a.count; ++t) {
         const long long sw = sweep0 + t;
-        if (drawer && lane == 0) dr.prep(h, sw, slot, t > 0, bbase, bcount, Cp);
+        if (early) asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+        if (draws) dr.prep(h, sw, slot, t > 0, bbase, bcount, Cp);
         const T tau = hs[0], isig = hs[1], beta = hs[2];
         const bool acc_now = acc_on && sw >= h.burn_in && thin_phase == 0;
         const T inv_k = acc_now ? static_cast<T>(1) / static_cast<T>(acc + 1) : static_cast<T>(0);
@@ -109,14 +169,14 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
         T accS = 0, accR = 0, accA = 0;
         for (int c = 0; c < K; ++c) {
             if (!drawer) {
-                const int lo = coffs[c], hi = coffs[c + 1];
-                // Loads of all of this thread's positions of the class first (one round trip).
+                const int lo = coffs[c], a0 = own_lo[c], a1 = own_hi[c], ob = own_off[c] - a0;
+                // Loads of all of this thread's positions of the share first (one round trip).
                 uint4 rec[kCsrMaxPos];
                 T yv[kCsrMaxPos], zv[kCsrMaxPos];
 #pragma unroll
                 for (int j = 0; j < kCsrMaxPos; ++j) {
-                    const int p = lo + tid + j * NTS;
-                    if (p < hi) {
+                    const int p = a0 + tid + j * NTS;
+                    if (p < a1) {
                         rec[j] = a.nbr[p];
                         yv[j] = Y[p];
                         zv[j] = Z[p];
@@ -124,8 +184,8 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
                 }
 #pragma unroll
                 for (int j = 0; j < kCsrMaxPos; ++j) {
-                    const int p = lo + tid + j * NTS;
-                    if (p >= hi) continue;
+                    const int p = a0 + tid + j * NTS;
+                    if (p >= a1) continue;
                     T nb[8], s = 0;
                     int cnt = 0;
 #pragma unroll
@@ -151,6 +211,9 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
                     const T mn = (tau * rho * s + (yv[j] - beta) * isig) * FArith<T>::rcp(P);
                     const T xn = mn + zv[j] * FArith<T>::rsq(P);
                     xs[p] = xn;
+#pragma unroll
+                    for (int r = 1; r < CL; ++r)  // the other blocks' copies
+                        st_remote(remote_addr(xs + p, (rank + r) % CL), xn);
                     T e = 0;
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
@@ -174,17 +237,25 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
                     accR += r * r;
                     accA += r;
                     if (acc_now) {
-                        T mu = ms[p], mm = m2s[p];
+                        T mu = ms[ob + p], mm = m2s[ob + p];
                         const T delta = xn - mu;
                         mu += delta * inv_k;
                         mm += delta * (xn - mu);
-                        ms[p] = mu;
-                        m2s[p] = mm;
+                        ms[ob + p] = mu;
+                        m2s[ob + p] = mm;
                     }
                 }
-                if (c + 1 < K) asm volatile("bar.sync 1, %0;" ::"r"(NTS) : "memory");
+            }
+            // End of the colour step: the class is final in every copy.  (After the last step the
+            // barrier of the sums below serves.)
+            if (c + 1 < K) {
+                if (CL > 1 && early && c == 0) asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+                else if (CL > 1) cluster_sync();
+                else if (!drawer) asm volatile("bar.sync 1, %0;" ::"r"(NTS) : "memory");
             }
         }
+        // The sums: a shuffle tree per site warp, over the site warps, then over the blocks
+        // (block 0, in rank order), in precision T.
         if (!drawer) {
             for (int o = 16; o >= 1; o >>= 1) {
                 accS += __shfl_xor_sync(0xffffffffu, accS, o);
@@ -198,32 +269,65 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
             }
         }
         __syncthreads();
-        if (drawer) {
-            T v0 = lane < nsw ? red[lane][dw] : static_cast<T>(0);
-            T v1 = (dw == 1 && lane < nsw) ? red[lane][2] : static_cast<T>(0);
+        if (warp == nsw) {  // the first drawing warp of every block: this block's sums to block 0
+            T b0 = lane < nsw ? red[lane][0] : static_cast<T>(0);
+            T b1 = lane < nsw ? red[lane][1] : static_cast<T>(0);
+            T b2 = lane < nsw ? red[lane][2] : static_cast<T>(0);
             for (int o = 16; o >= 1; o >>= 1) {
-                v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-                v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+                b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+                b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+                b2 += __shfl_xor_sync(0xffffffffu, b2, o);
             }
-            if (lane == 0) dr.draw(h, v0, v1, beta, hs);
+            if (lane == 0) {
+                if (CL > 1) {
+                    st_remote(remote_addr(&red_cl[rank][0], 0), b0);
+                    st_remote(remote_addr(&red_cl[rank][1], 0), b1);
+                    st_remote(remote_addr(&red_cl[rank][2], 0), b2);
+                } else {
+                    red_cl[0][0] = b0;
+                    red_cl[0][1] = b1;
+                    red_cl[0][2] = b2;
+                }
+            }
+        }
+        if (CL > 1) cluster_sync();
+        else __syncthreads();
+        if (draws) {
+            T v0 = 0, v1 = 0;
+            for (int r = 0; r < CL; ++r) {
+                v0 += red_cl[r][dw];
+                if (dw == 1) v1 += red_cl[r][2];
+            }
+            dr.draw(h, v0, v1, beta, hs);
+            for (int r = 1; r < CL; ++r) {  // the new parameters into every block
+                if (dw == 0) {
+                    st_remote(remote_addr(&hs[0], r), hs[0]);
+                } else {
+                    st_remote(remote_addr(&hs[1], r), hs[1]);
+                    st_remote(remote_addr(&hs[2], r), hs[2]);
+                }
+            }
         }
         if (acc_now) ++acc;
         if (sw >= h.burn_in) thin_phase = (thin_phase + 1 == h.thin) ? 0 : thin_phase + 1;
         if (h.trace_cap > 0) slot = (slot + 1 == h.trace_cap) ? 0 : slot + 1;
-        __syncthreads();
+        if (CL > 1) cluster_sync();
+        else __syncthreads();
     }
-    if (drawer && lane == 0 && a.count > 0) dr.finish(h);
+    if (draws && a.count > 0) dr.finish(h);
     pdl_release();
 
     {
         T *X = static_cast<T *>(a.x) + f.slot0 * Cp + chain;
         T *MEAN = static_cast<T *>(a.mean) + f.slot0 * Cp + chain;
         T *M2 = static_cast<T *>(a.m2) + f.slot0 * Cp + chain;
-        for (int p = tid; p < n; p += NT) {
-            X[static_cast<int64_t>(p) * Cp] = xs[p];
-            MEAN[static_cast<int64_t>(p) * Cp] = ms[p];
-            M2[static_cast<int64_t>(p) * Cp] = m2s[p];
-        }
+        for (int c = 0; c < K; ++c)
+            for (int p = own_lo[c] + tid; p < own_hi[c]; p += NT) {
+                const int l = own_off[c] + p - own_lo[c];
+                X[static_cast<int64_t>(p) * Cp] = xs[p];
+                MEAN[static_cast<int64_t>(p) * Cp] = ms[l];
+                M2[static_cast<int64_t>(p) * Cp] = m2s[l];
+            }
     }
     __syncthreads();
     if (tid == 0) {
@@ -234,12 +338,13 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
             h.ctl->ticket = 0;
         }
     }
+    if (CL > 1) cluster_sync();  // no block leaves while another may still address its memory
 }
 
 }  // namespace
 
 int csr_resident_threads() { return kCsrThreads; }
-int csr_resident_max_positions() { return kCsrMaxPos * kCsrSiteThreads; }
+int csr_resident_max_positions() { return kCsrMaxPos * kCsrSiteThreads; }  // per block and class
 
 cudaError_t launch_pack_csr_records(int32_t n, const int32_t *rp, const int32_t *ci, uint4 *nbr, uint4 *nbr2,
                                     cudaStream_t stream)
@@ -248,17 +353,65 @@ cudaError_t launch_pack_csr_records(int32_t n, const int32_t *rp, const int32_t 
     return cudaGetLastError();
 }
 
-cudaError_t prepare_csr_resident(int precision, size_t smem)
+namespace {
+
+template <typename T, int CL>
+cudaError_t launch_cl(int chains, const ResCsrArgs &a, size_t smem, cudaStream_t stream)
 {
-    constexpr auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if (precision == 0) return cudaFuncSetAttribute(csr_resident_kernel<float>, attr, static_cast<int>(smem));
-    return cudaFuncSetAttribute(csr_resident_kernel<double>, attr, static_cast<int>(smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(chains * CL);
+    cfg.blockDim = dim3(kCsrThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = CL;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+    if (pdl_enabled()) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, csr_resident_kernel<T, CL>, a);
 }
 
-cudaError_t launch_csr_resident(int precision, int chains, const ResCsrArgs &a, size_t smem, cudaStream_t stream)
+template <typename T>
+cudaError_t prepare_t(size_t smem)
 {
-    if (precision == 0) return launch_sweep_kernel(csr_resident_kernel<float>, chains, kCsrThreads, smem, stream, a);
-    return launch_sweep_kernel(csr_resident_kernel<double>, chains, kCsrThreads, smem, stream, a);
+    constexpr auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(csr_resident_kernel<T, 1>, attr, static_cast<int>(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 2>, attr, static_cast<int>(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 4>, attr, static_cast<int>(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 8>, attr, static_cast<int>(smem));
+    return e;
+}
+
+template <typename T>
+cudaError_t launch_t(int cl, int chains, const ResCsrArgs &a, size_t smem, cudaStream_t stream)
+{
+    if (cl == 8) return launch_cl<T, 8>(chains, a, smem, stream);
+    if (cl == 4) return launch_cl<T, 4>(chains, a, smem, stream);
+    if (cl == 2) return launch_cl<T, 2>(chains, a, smem, stream);
+    return launch_cl<T, 1>(chains, a, smem, stream);
+}
+
+}  // namespace
+
+cudaError_t prepare_csr_resident(int precision, size_t smem)
+{
+    return precision == 0 ? prepare_t<float>(smem) : prepare_t<double>(smem);
+}
+
+cudaError_t launch_csr_resident(int precision, int cluster, int chains, const ResCsrArgs &a, size_t smem,
+                                cudaStream_t stream)
+{
+    return precision == 0 ? launch_t<float>(cluster, chains, a, smem, stream)
+                          : launch_t<double>(cluster, chains, a, smem, stream);
 }
 
 }  // namespace gmrf

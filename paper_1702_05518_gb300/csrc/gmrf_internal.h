@@ -137,6 +137,7 @@ struct ResCsrArgs {
     const int32_t *coff;  // colour offsets (ncolors + 1)
     int32_t ncolors;
     int32_t count, C;
+    int32_t own_max;      // positions a block of a chain's cluster owns (largest share)
     double rho;
     const void *zbuf;     // [count][C][n] normals by permuted position
 };
@@ -244,13 +245,15 @@ cudaError_t launch_lattice_resident(int precision, int kind, int NI, int threads
 // One thread per Philox block of the batch: `blocks_needed` = sweeps x groups x chain quadruples.
 cudaError_t launch_resident_normals(int precision, const ResNormArgs &a, int64_t blocks_needed, cudaStream_t stream);
 // Graph resident path: the neighbour records from the permuted CSR, the kernel's shared-memory
-// limit, and a launch (one block of csr_resident_threads() per chain).
+// limit, and a launch (one cluster of `cluster` (1, 2, 4 or 8) blocks of csr_resident_threads()
+// per chain).
 int csr_resident_threads();
 int csr_resident_max_positions();  // per site thread and colour class
 cudaError_t launch_pack_csr_records(int32_t n, const int32_t *rp, const int32_t *ci, uint4 *nbr, uint4 *nbr2,
                                     cudaStream_t stream);
 cudaError_t prepare_csr_resident(int precision, size_t smem);
-cudaError_t launch_csr_resident(int precision, int chains, const ResCsrArgs &a, size_t smem, cudaStream_t stream);
+cudaError_t launch_csr_resident(int precision, int cluster, int chains, const ResCsrArgs &a, size_t smem,
+                                cudaStream_t stream);
 
 // Chain diagnostics (diagnostics.cu): one parameter trace of every chain of one field.
 struct DiagArgs {

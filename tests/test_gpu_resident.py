@@ -211,14 +211,16 @@ def _wheels(nw, spokes, seed):
     return f
 
 
+# sizes for clusters of 1, 4 and 8 blocks per chain
 GRAPHS = [("delaunay_1500", lambda: _delaunay(1500, 21)), ("delaunay_9000", lambda: _delaunay(9000, 22)),
+          ("delaunay_20000", lambda: _delaunay(20000, 28)),
           ("wheels_16", lambda: _wheels(40, 16, 23)), ("wheels_9", lambda: _wheels(30, 9, 24)),
           ("delaunay_12", lambda: _delaunay(12, 25))]
 
 
 def test_graphs_which_take_it():
     small = _delaunay(2000, 1)
-    big = _delaunay(20000, 2)  # state, mean and M2 do not fit shared memory
+    big = _delaunay(40000, 2)  # positions do not fit 16 bits
 
     def res(fields, **kw):
         with g.Sampler(fields, seed=1, **kw) as s:
