@@ -142,6 +142,7 @@ struct gmrf_sampler {
     int resident = 0, res_NI = 0, res_NT = 0, res_batch = 0;  // resident: 1 lattice, 2 graph
     uint4 *res_nbr = nullptr, *res_nbr2 = nullptr;            // graph: neighbour records
     int res_cluster = 1, res_own_max = 0;                      // graph: blocks per chain, their share
+    int res_positions = 0;                                     // graph: 1 = one position per thread
     int32_t res_SR = 0, res_SC = 0;
     size_t res_smem = 0;
     void *res_z = nullptr;  // [res_batch][C][colours][NI][site threads] normals of a batch
@@ -544,11 +545,12 @@ cudaError_t plan_resident(gmrf_sampler *s, const std::vector<int32_t> &coff0)
         // A cluster of CL blocks per chain (at most 152 blocks in all): one block per 2048 sites.
         int cl = 1;
         while (cl < 8 && f.n >= 2048 * 2 * cl && s->C * 2 * cl <= 152) cl *= 2;
-        int own_max = 0;
+        int own_max = 0, share_max = 0;
         for (int c = 0; c < h.ncolors; ++c) {
             const int len = coff0[c + 1] - coff0[c], q = (len + cl - 1) / cl;
             if (q > csr_resident_max_positions()) return cudaSuccess;
             own_max += q;
+            share_max = std::max(share_max, q);
         }
         const size_t smem = (static_cast<size_t>(f.n) + 1 + 2 * static_cast<size_t>(own_max)) * tsize(s->precision);
         if (smem > 220 * 1024) return cudaSuccess;
@@ -563,6 +565,7 @@ cudaError_t plan_resident(gmrf_sampler *s, const std::vector<int32_t> &coff0)
         s->res_smem = smem;
         s->res_cluster = cl;
         s->res_own_max = own_max;
+        s->res_positions = share_max <= csr_resident_site_threads() ? 1 : 0;
         s->resident = 2;
         return cudaSuccess;
     }
@@ -747,8 +750,8 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int with_hyper, cudaStr
             if (draw || draw_beta) e = launch_pre(s, cnt, st);
             if (e == cudaSuccess) e = launch_res_normals(s, cnt, st);
             if (e == cudaSuccess && s->resident == 2)
-                e = launch_csr_resident(s->precision, s->res_cluster, s->C, csr_resident_args(s, cnt, draw, draw_beta),
-                                        s->res_smem, st);
+                e = launch_csr_resident(s->precision, s->res_cluster, s->res_positions, s->C,
+                                        csr_resident_args(s, cnt, draw, draw_beta), s->res_smem, st);
             else if (e == cudaSuccess)
                 e = launch_lattice_resident(s->precision, s->fd[0].kind, s->res_NI, s->res_NT, s->C,
                                             resident_args(s, cnt, draw, draw_beta), s->res_smem, st);

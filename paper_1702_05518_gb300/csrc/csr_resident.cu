@@ -87,7 +87,10 @@ __device__ __forceinline__ void cluster_sync()
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
-template <typename T, int CL>
+// MP: positions of a colour class per site thread, 1 or kCsrMaxPos.  With one, the loads of the
+// next colour step's position (its neighbour record, observation and normal) are issued before the
+// current step's update, so the step does not wait for L2.
+template <typename T, int CL, int MP>
 __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResCsrArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -155,6 +158,14 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
     const bool acc_on = h.acc_enabled != 0;
     int thin_phase = sweep0 >= h.burn_in ? static_cast<int>((sweep0 - h.burn_in) % h.thin) : 0;
     long long slot = h.trace_cap > 0 ? sweep0 % h.trace_cap : 0;
+    // MP == 1: the position of the first colour step, loaded ahead.
+    uint4 rn = make_uint4(0u, 0u, 0u, 0u);
+    T yn = 0, zn = 0;
+    if (MP == 1 && !drawer && K > 0 && a.count > 0 && own_lo[0] + tid < own_hi[0]) {
+        rn = a.nbr[own_lo[0] + tid];
+        yn = Y[own_lo[0] + tid];
+        zn = ZB[own_lo[0] + tid];
+    }
     // In a cluster the drawing warps arrive at the first colour barrier of a sweep before block
     // 0's drawing lanes do their part of the draws, so that work never holds the barrier.
     const bool early = CL > 1 && K > 1 && drawer;
@@ -167,82 +178,104 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
         const T inv_k = acc_now ? static_cast<T>(1) / static_cast<T>(acc + 1) : static_cast<T>(0);
         const T *Z = ZB + t * zstride;
         T accS = 0, accR = 0, accA = 0;
+        // One position of colour class c (first position lo; ob maps it into ms / m2s).
+        auto update = [&](int p, const uint4 &rc, T yv, T zv, int lo, int ob) {
+            T nb[8], s = 0;
+            int cnt = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int id = rec_id(rc, q);
+                nb[q] = xs[id];
+                s += nb[q];
+                cnt += id != n;
+            }
+            const bool more = (rc.x & 0x8000u) != 0;
+            uint4 r2 = make_uint4(0u, 0u, 0u, 0u);
+            if (more) {  // degree 9..16 (rare): the second record
+                r2 = a.nbr2[p];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int id = rec_entry(r2, q);
+                    s += xs[id];
+                    cnt += id != n;
+                }
+            }
+            const T d = static_cast<T>(cnt);
+            const T P = tau * d + isig;
+            const T mn = (tau * rho * s + (yv - beta) * isig) * FArith<T>::rcp(P);
+            const T xn = mn + zv * FArith<T>::rsq(P);
+            xs[p] = xn;
+#pragma unroll
+            for (int r = 1; r < CL; ++r)  // the other blocks' copies
+                st_remote(remote_addr(xs + p, (rank + r) % CL), xn);
+            T e = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (rec_id(rc, q) < lo) {  // lower colour (the pad n is never below lo)
+                    const T df = xn - nb[q];
+                    e += df * df;
+                }
+            }
+            if (more) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int id = rec_entry(r2, q);
+                    if (id < lo) {
+                        const T df = xn - xs[id];
+                        e += df * df;
+                    }
+                }
+            }
+            accS += (static_cast<T>(1) - rho) * d * xn * xn + rho * e;
+            const T r = (yv - beta) - xn;
+            accR += r * r;
+            accA += r;
+            if (acc_now) {
+                T mu = ms[ob + p], mm = m2s[ob + p];
+                const T delta = xn - mu;
+                mu += delta * inv_k;
+                mm += delta * (xn - mu);
+                ms[ob + p] = mu;
+                m2s[ob + p] = mm;
+            }
+        };
         for (int c = 0; c < K; ++c) {
             if (!drawer) {
                 const int lo = coffs[c], a0 = own_lo[c], a1 = own_hi[c], ob = own_off[c] - a0;
-                // Loads of all of this thread's positions of the share first (one round trip).
-                uint4 rec[kCsrMaxPos];
-                T yv[kCsrMaxPos], zv[kCsrMaxPos];
-#pragma unroll
-                for (int j = 0; j < kCsrMaxPos; ++j) {
-                    const int p = a0 + tid + j * NTS;
-                    if (p < a1) {
-                        rec[j] = a.nbr[p];
-                        yv[j] = Y[p];
-                        zv[j] = Z[p];
+                if constexpr (MP == 1) {
+                    // this step's position (loaded during the previous step), then the next one's loads
+                    const int p = a0 + tid;
+                    const uint4 rc = rn;
+                    const T yc = yn, zc = zn;
+                    int c2 = c + 1, t2 = t;
+                    if (c2 == K) {
+                        c2 = 0;
+                        ++t2;
                     }
-                }
-#pragma unroll
-                for (int j = 0; j < kCsrMaxPos; ++j) {
-                    const int p = a0 + tid + j * NTS;
-                    if (p >= a1) continue;
-                    T nb[8], s = 0;
-                    int cnt = 0;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int id = rec_id(rec[j], q);
-                        nb[q] = xs[id];
-                        s += nb[q];
-                        cnt += id != n;
+                    const int p2 = own_lo[c2] + tid;
+                    if (t2 < a.count && p2 < own_hi[c2]) {
+                        rn = a.nbr[p2];
+                        yn = Y[p2];
+                        zn = ZB[t2 * zstride + p2];
                     }
-                    const bool more = (rec[j].x & 0x8000u) != 0;
-                    uint4 r2 = make_uint4(0u, 0u, 0u, 0u);
-                    if (more) {  // degree 9..16 (rare): the second record
-                        r2 = a.nbr2[p];
+                    if (p < a1) update(p, rc, yc, zc, lo, ob);
+                } else {
+                    // Loads of all of this thread's positions of the share first (one round trip).
+                    uint4 rec[MP];
+                    T yv[MP], zv[MP];
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int id = rec_entry(r2, q);
-                            s += xs[id];
-                            cnt += id != n;
+                    for (int j = 0; j < MP; ++j) {
+                        const int p = a0 + tid + j * NTS;
+                        if (p < a1) {
+                            rec[j] = a.nbr[p];
+                            yv[j] = Y[p];
+                            zv[j] = Z[p];
                         }
                     }
-                    const T d = static_cast<T>(cnt);
-                    const T P = tau * d + isig;
-                    const T mn = (tau * rho * s + (yv[j] - beta) * isig) * FArith<T>::rcp(P);
-                    const T xn = mn + zv[j] * FArith<T>::rsq(P);
-                    xs[p] = xn;
 #pragma unroll
-                    for (int r = 1; r < CL; ++r)  // the other blocks' copies
-                        st_remote(remote_addr(xs + p, (rank + r) % CL), xn);
-                    T e = 0;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        if (rec_id(rec[j], q) < lo) {  // lower colour (the pad n is never below lo)
-                            const T df = xn - nb[q];
-                            e += df * df;
-                        }
-                    }
-                    if (more) {
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int id = rec_entry(r2, q);
-                            if (id < lo) {
-                                const T df = xn - xs[id];
-                                e += df * df;
-                            }
-                        }
-                    }
-                    accS += (static_cast<T>(1) - rho) * d * xn * xn + rho * e;
-                    const T r = (yv[j] - beta) - xn;
-                    accR += r * r;
-                    accA += r;
-                    if (acc_now) {
-                        T mu = ms[ob + p], mm = m2s[ob + p];
-                        const T delta = xn - mu;
-                        mu += delta * inv_k;
-                        mm += delta * (xn - mu);
-                        ms[ob + p] = mu;
-                        m2s[ob + p] = mm;
+                    for (int j = 0; j < MP; ++j) {
+                        const int p = a0 + tid + j * NTS;
+                        if (p < a1) update(p, rec[j], yv[j], zv[j], lo, ob);
                     }
                 }
             }
@@ -345,6 +378,7 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
 
 int csr_resident_threads() { return kCsrThreads; }
 int csr_resident_max_positions() { return kCsrMaxPos * kCsrSiteThreads; }  // per block and class
+int csr_resident_site_threads() { return kCsrSiteThreads; }
 
 cudaError_t launch_pack_csr_records(int32_t n, const int32_t *rp, const int32_t *ci, uint4 *nbr, uint4 *nbr2,
                                     cudaStream_t stream)
@@ -355,7 +389,7 @@ cudaError_t launch_pack_csr_records(int32_t n, const int32_t *rp, const int32_t 
 
 namespace {
 
-template <typename T, int CL>
+template <typename T, int CL, int MP>
 cudaError_t launch_cl(int chains, const ResCsrArgs &a, size_t smem, cudaStream_t stream)
 {
     cudaLaunchConfig_t cfg = {};
@@ -377,27 +411,40 @@ cudaError_t launch_cl(int chains, const ResCsrArgs &a, size_t smem, cudaStream_t
     }
     cfg.attrs = attr;
     cfg.numAttrs = na;
-    return cudaLaunchKernelEx(&cfg, csr_resident_kernel<T, CL>, a);
+    return cudaLaunchKernelEx(&cfg, csr_resident_kernel<T, CL, MP>, a);
+}
+
+template <typename T, int MP>
+cudaError_t prepare_mp(size_t smem)
+{
+    constexpr auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(csr_resident_kernel<T, 1, MP>, attr, static_cast<int>(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 2, MP>, attr, static_cast<int>(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 4, MP>, attr, static_cast<int>(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 8, MP>, attr, static_cast<int>(smem));
+    return e;
 }
 
 template <typename T>
 cudaError_t prepare_t(size_t smem)
 {
-    constexpr auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(csr_resident_kernel<T, 1>, attr, static_cast<int>(smem));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 2>, attr, static_cast<int>(smem));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 4>, attr, static_cast<int>(smem));
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 8>, attr, static_cast<int>(smem));
-    return e;
+    cudaError_t e = prepare_mp<T, 1>(smem);
+    return e == cudaSuccess ? prepare_mp<T, kCsrMaxPos>(smem) : e;
+}
+
+template <typename T, int MP>
+cudaError_t launch_mp(int cl, int chains, const ResCsrArgs &a, size_t smem, cudaStream_t stream)
+{
+    if (cl == 8) return launch_cl<T, 8, MP>(chains, a, smem, stream);
+    if (cl == 4) return launch_cl<T, 4, MP>(chains, a, smem, stream);
+    if (cl == 2) return launch_cl<T, 2, MP>(chains, a, smem, stream);
+    return launch_cl<T, 1, MP>(chains, a, smem, stream);
 }
 
 template <typename T>
-cudaError_t launch_t(int cl, int chains, const ResCsrArgs &a, size_t smem, cudaStream_t stream)
+cudaError_t launch_t(int cl, int mp, int chains, const ResCsrArgs &a, size_t smem, cudaStream_t stream)
 {
-    if (cl == 8) return launch_cl<T, 8>(chains, a, smem, stream);
-    if (cl == 4) return launch_cl<T, 4>(chains, a, smem, stream);
-    if (cl == 2) return launch_cl<T, 2>(chains, a, smem, stream);
-    return launch_cl<T, 1>(chains, a, smem, stream);
+    return mp == 1 ? launch_mp<T, 1>(cl, chains, a, smem, stream) : launch_mp<T, kCsrMaxPos>(cl, chains, a, smem, stream);
 }
 
 }  // namespace
@@ -407,11 +454,11 @@ cudaError_t prepare_csr_resident(int precision, size_t smem)
     return precision == 0 ? prepare_t<float>(smem) : prepare_t<double>(smem);
 }
 
-cudaError_t launch_csr_resident(int precision, int cluster, int chains, const ResCsrArgs &a, size_t smem,
-                                cudaStream_t stream)
+cudaError_t launch_csr_resident(int precision, int cluster, int positions, int chains, const ResCsrArgs &a,
+                                size_t smem, cudaStream_t stream)
 {
-    return precision == 0 ? launch_t<float>(cluster, chains, a, smem, stream)
-                          : launch_t<double>(cluster, chains, a, smem, stream);
+    return precision == 0 ? launch_t<float>(cluster, positions, chains, a, smem, stream)
+                          : launch_t<double>(cluster, positions, chains, a, smem, stream);
 }
 
 }  // namespace gmrf

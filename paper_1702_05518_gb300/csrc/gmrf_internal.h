@@ -252,8 +252,11 @@ int csr_resident_max_positions();  // per site thread and colour class
 cudaError_t launch_pack_csr_records(int32_t n, const int32_t *rp, const int32_t *ci, uint4 *nbr, uint4 *nbr2,
                                     cudaStream_t stream);
 cudaError_t prepare_csr_resident(int precision, size_t smem);
-cudaError_t launch_csr_resident(int precision, int cluster, int chains, const ResCsrArgs &a, size_t smem,
-                                cudaStream_t stream);
+int csr_resident_site_threads();
+// positions: 1 when every block's share of every class fits its site threads (then the next
+// step's loads are issued ahead), else csr_resident_max_positions() / csr_resident_site_threads().
+cudaError_t launch_csr_resident(int precision, int cluster, int positions, int chains, const ResCsrArgs &a,
+                                size_t smem, cudaStream_t stream);
 
 // Chain diagnostics (diagnostics.cu): one parameter trace of every chain of one field.
 struct DiagArgs {
