@@ -1064,8 +1064,6 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
         bool quad_ok = kind == GMRF_LATTICE2D_8 && s->Cp == 1 && s->precision == GMRF_FP32 && fused_kind[kind];
         for (auto &h : s->hf)
             if (h.kind == kind && h.dims[1] % 4 != 0) quad_ok = false;
-        if (const char *env = std::getenv("GMRF_FUSED_QUAD"))
-            if (env[0] == '0') quad_ok = false;
         if (s->tune.quad_config < 0) quad_ok = false;
         if (quad_ok) {
             // Configurations (quad columns, threads, quads per thread); tile TR x TC with
@@ -1147,20 +1145,6 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
                             s->fNT[kind] = nt;
                         }
                     }
-            }
-            // Tuning override: GMRF_FUSED_TILE="<rows>x<cols>[x<threads>]" (extents 8..256, made
-            // even so every staged region is aligned to the colour pattern; threads 512 or 1024).
-            if (const char *env = std::getenv("GMRF_FUSED_TILE")) {
-                int r = 0, c = 0, nt = 512;
-                const int got = std::sscanf(env, "%dx%dx%d", &r, &c, &nt);
-                r &= ~1;
-                c &= ~1;
-                if (got >= 2 && r >= 8 && c >= 8 && r <= 256 && c <= 256 && (nt == 512 || nt == 1024) &&
-                    lattice_fused_smem(s->precision, kind, s->Cp, r, c) <= 200 * 1024) {
-                    tr = r;
-                    tc = c;
-                    s->fNT[kind] = nt;
-                }
             }
             if (s->tune.fused_rows[kind]) {
                 const int r = s->tune.fused_rows[kind] & ~1, c = s->tune.fused_cols[kind] & ~1;

@@ -51,11 +51,10 @@ def test_quad_300_sweeps(dims):
     assert trace_relerr(r["sigma2_trace"], out["sigma2_trace"][0]) <= TOL_FP32_1000
 
 
-def test_quad_matches_general_fused_kernel(monkeypatch):
+def test_quad_matches_general_fused_kernel():
     f = wl.small_lattice(wl.LATTICE2D_8, (200, 176), 33)
     a, na = _run(f, 50)
-    monkeypatch.setenv("GMRF_FUSED_QUAD", "0")
-    b, nb = _run(f, 50)
+    b, nb = _run(f, 50, tuning={"quad_config": -1})
     assert na[0].startswith("fused quad sweep") and nb[0].startswith("fused sweep")
     assert relerr(a["x"], b["x"]) <= TOL_FP32_1000
     assert trace_relerr(a["tau_trace"], b["tau_trace"]) <= TOL_FP32_1000
