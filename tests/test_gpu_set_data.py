@@ -53,6 +53,10 @@ CASES = {
     "binomial_fp32": (lambda: [_binomial(1200, 9)], dict(precision=g.FP32, chains=2, **BINOM)),
     "binomial_fp64": (lambda: [_binomial(900, 10)], dict(precision=g.FP64, chains=1, **BINOM)),
     "plain_fp64": (lambda: [_delaunay(800, 11)], dict(precision=g.FP64, chains=2, algorithm=g.ALGO_PLAIN)),
+    # the resident paths (small single lattice, small single graph in clusters of 4 blocks)
+    "resident_lattice_fp32": (lambda: [wl.small_lattice(wl.LATTICE2D_8, (50, 50), 12)],
+                              dict(precision=g.FP32, chains=3, intercept=True)),
+    "resident_graph_fp32": (lambda: [_delaunay(9000, 13)], dict(precision=g.FP32, chains=2)),
 }
 
 
