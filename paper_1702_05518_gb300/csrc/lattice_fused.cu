@@ -569,7 +569,14 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4 && CP < 4) ? 
     stage(X, nullptr);
     __syncthreads();
 
-    // Phase B: colour steps; owned sites fold their terms of the hyperparameter sums.
+    // Phase B: colour steps.  An owned site is final after its own colour step: it is written
+    // back then (state and, on accumulated sweeps, the running mean / M2), so the stores overlap
+    // the remaining steps, and it folds its terms of the hyperparameter sums.
+    const bool acc = a.acc_enabled && sweep_accumulated(sweep_ll, a.burn_in, a.thin);
+    T inv_k = 0;
+    if (acc) inv_k = static_cast<T>(1) / static_cast<T>(a.ctl->acc_count + 1);
+    T *MEAN = static_cast<T *>(a.mean) + f.slot0 * CP;
+    T *M2 = static_cast<T *>(a.m2) + f.slot0 * CP;
     T accS[CP], accR[CP], accA[CP];
 #pragma unroll
     for (int v = 0; v < CP; ++v) {
@@ -619,20 +626,28 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4 && CP < 4) ? 
             const float rcp_nc = __frcp_rn(static_cast<float>(n_cols));
             for (int q = threadIdx.x; q < n_rows * n_cols; q += NT) {
                 const int ru = div_small(q, rcp_nc), w = q - ru * n_cols;
-                int i, j, idx, dp = 0;
+                int i, j, idx, sr, sv, dp = 0;
                 if (E8) {
-                    const int u = first_u + ru, v = first_v + w;
-                    i = gi0 + 2 * u + (c >> 1);
-                    j = gj0 + 2 * v + (c & 1);
-                    idx = (c * SR + u) * SC + v;
+                    sr = first_u + ru;
+                    sv = first_v + w;
+                    i = gi0 + 2 * sr + (c >> 1);
+                    j = gj0 + 2 * sv + (c & 1);
                 } else {
                     i = lo_i + ru;
                     const int p = (c + i) & 1;
-                    const int v = ((lo_j - gj0 - p + 1) >> 1) + w;
-                    j = gj0 + 2 * v + p;
+                    sr = i - gi0;
+                    sv = ((lo_j - gj0 - p + 1) >> 1) + w;
+                    j = gj0 + 2 * sv + p;
                     if (j >= hi_j) continue;
-                    idx = (c * SR + (i - gi0)) * SC + v;
                     dp = p;
+                }
+                idx = (c * SR + sr) * SC + sv;
+                const bool owned = i >= t.i0 && i < t.i0 + TR && j >= t.j0 && j < t.j0 + TC;
+                const int go = (c * gsub + (gu0 + sr) * gcols + gv0 + sv) * CP;
+                T mu[CP], mm[CP];
+                if (owned && acc) {
+                    Vec<T, CP>::ld(MEAN + go, mu);
+                    Vec<T, CP>::ld(M2 + go, mm);
                 }
                 T nb[ND][CP], s[CP];
 #pragma unroll
@@ -672,7 +687,18 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4 && CP < 4) ? 
                     xn[v] = m + z[v] * FArith<T>::rsq(P);
                 }
                 Vec<T, CP>::st(xs + idx * CP, xn);
-                if (i >= t.i0 && i < t.i0 + TR && j >= t.j0 && j < t.j0 + TC) {
+                if (owned) {
+                    Vec<T, CP>::st(XW + go, xn);
+                    if (acc) {
+#pragma unroll
+                        for (int v = 0; v < CP; ++v) {
+                            const T delta = xn[v] - mu[v];
+                            mu[v] += delta * inv_k;
+                            mm[v] += delta * (xn[v] - mu[v]);
+                        }
+                        Vec<T, CP>::st(MEAN + go, mu);
+                        Vec<T, CP>::st(M2 + go, mm);
+                    }
 #pragma unroll
                     for (int v = 0; v < CP; ++v) {
                         T e2 = 0;
@@ -690,46 +716,6 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4 && CP < 4) ? 
             }
         }
         __syncthreads();
-    }
-
-    // Write-back of the owned sites and the running mean / M2.
-    {
-        const bool acc = a.acc_enabled && sweep_accumulated(sweep_ll, a.burn_in, a.thin);
-        T inv_k = 0;
-        if (acc) inv_k = static_cast<T>(1) / static_cast<T>(a.ctl->acc_count + 1);
-        T *MEAN = static_cast<T *>(a.mean) + f.slot0 * CP;
-        T *M2 = static_cast<T *>(a.m2) + f.slot0 * CP;
-        const int orow = E8 ? (TR >> 1) : TR, tc2 = TC >> 1;
-        const int r0 = E8 ? (K >> 1) : K, v0 = K >> 1;
-        const bool tile_full = t.i0 + TR <= Hl && t.j0 + TC <= Wl;
-        const float rcp_tc2 = __frcp_rn(static_cast<float>(tc2)), rcp_orow = __frcp_rn(static_cast<float>(orow));
-        for (int q = threadIdx.x; q < NS * orow * tc2; q += NT) {
-            const int rr = div_small(q, rcp_tc2), w = q - rr * tc2;
-            const int sa = div_small(rr, rcp_orow), r = rr - sa * orow;
-            const int sr = r0 + r, v = v0 + w;
-            if (!tile_full) {
-                const int i = E8 ? gi0 + 2 * sr + (sa >> 1) : gi0 + sr;
-                const int j = gj0 + 2 * v + (E8 ? (sa & 1) : ((sa + i) & 1));
-                if (i >= Hl || j >= Wl) continue;
-            }
-            const int go = (sa * gsub + (gu0 + sr) * gcols + gv0 + v) * CP;
-            T xn[CP];
-            Vec<T, CP>::ld(xs + ((sa * SR + sr) * SC + v) * CP, xn);
-            Vec<T, CP>::st(XW + go, xn);
-            if (acc) {
-                T mu[CP], mm[CP];
-                Vec<T, CP>::ld(MEAN + go, mu);
-                Vec<T, CP>::ld(M2 + go, mm);
-#pragma unroll
-                for (int v2 = 0; v2 < CP; ++v2) {
-                    const T delta = xn[v2] - mu[v2];
-                    mu[v2] += delta * inv_k;
-                    mm[v2] += delta * (xn[v2] - mu[v2]);
-                }
-                Vec<T, CP>::st(MEAN + go, mu);
-                Vec<T, CP>::st(M2 + go, mm);
-            }
-        }
     }
 
     // Block reduction (all lanes hold the same chains): warp shuffle tree, then warps in order.
