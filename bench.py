@@ -475,8 +475,9 @@ def run_ours(args):
                                  "psrf": None if d["psrf"] != d["psrf"] else float(d["psrf"]),
                                  "ces_s": t_run / float(np.sum(d["ess"]))}
 
-    # Resident samplers (a small single 2-D lattice): a batch of sweeps is three launches (unit-
-    # rate Gamma variates, normals, the resident kernel); timed as whole batches.
+    # Resident samplers (a small single 2-D lattice, or a single graph below 32768 sites): a batch
+    # of sweeps is three launches (unit-rate Gamma variates, normals, the resident kernel); timed
+    # as whole batches.
     resident_batch = None
     if info["resident"]:
         G = spec["graph_sweeps"]
@@ -603,12 +604,15 @@ def run_ours(args):
         C = spec["chains"]
         res_bytes = 4 * (n * C * 6 + n + 2 * nb * n * C)
         ach = res_bytes / (resident_batch["us"] * 1e-6) / 1e9
+        graph = info["resident"] == 2
         roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                     "traffic": None, "peak_source": peak_note,
-                    "kernel": "resident batch: Gamma variates, normals, lattice_resident_kernel",
+                    "kernel": "resident batch: Gamma variates, normals, "
+                              + ("csr_resident_kernel" if graph else "lattice_resident_kernel"),
                     "algorithmic_bytes_per_launch": res_bytes, "avg_launch_us": resident_batch["us"],
                     "sweeps_per_launch": nb, "us_per_sweep": resident_batch["us"] / nb,
-                    "note": "latency-bound (whole sweeps in shared memory, one block per chain): the HBM "
+                    "note": "latency-bound (whole sweeps in shared memory, "
+                            + ("a cluster of blocks" if graph else "one block") + " per chain): the HBM "
                             "fraction only counts the batch's staging and normals",
                     "per_sweep_path_stages_us": {f"{st}:{name}": round(us, 3) for st, name, us in stages}}
 
