@@ -145,7 +145,7 @@ typedef struct {
     int32_t fused_cols[2];       /* and columns, 8..256 (made even); 0: automatic                    */
     int32_t fused_threads[2];    /* threads per block, 512 or 1024; 0: automatic                     */
     int32_t quad_config;         /* 8-neighbour lattices, one chain, FP32: quad kernel configuration  */
-                                 /* 1..4, -1 for the general fused kernel; 0: automatic               */
+                                 /* 1..5, -1 for the general fused kernel; 0: automatic               */
     int32_t quad_rows;           /* the quad kernel's tile rows (even, >= 8); 0: automatic            */
 } gmrf_tuning;
 

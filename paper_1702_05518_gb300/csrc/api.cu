@@ -325,7 +325,7 @@ gmrf_status check_opts(const gmrf_opts *o)
                 return fail(GMRF_E_INVALID, "tuning.fused_rows/cols must both be 0 or in 8..256");
             if (n != 0 && n != 512 && n != 1024) return fail(GMRF_E_INVALID, "tuning.fused_threads must be 0, 512 or 1024");
         }
-        if (t->quad_config < -1 || t->quad_config > 4) return fail(GMRF_E_INVALID, "tuning.quad_config must be in -1..4");
+        if (t->quad_config < -1 || t->quad_config > 5) return fail(GMRF_E_INVALID, "tuning.quad_config must be in -1..5");
         if (t->quad_rows != 0 && (t->quad_rows < 8 || (t->quad_rows & 1)))
             return fail(GMRF_E_INVALID, "tuning.quad_rows must be 0 or even and >= 8");
     }
@@ -1067,12 +1067,17 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
         if (s->tune.quad_config < 0) quad_ok = false;
         if (quad_ok) {
             // Configurations (quad columns, threads, quads per thread); tile TR x TC with
-            // TC = 2 qcs - 8 and (TR/2 + 4) qcs <= threads * quads per thread.  Cost: waves of
-            // one block per SM times quads per thread.
-            static const int cfg[4][3] = {{64, 768, 3}, {64, 1024, 2}, {32, 1024, 2}, {32, 512, 2}};
-            double best = 1e300;
+            // TC = 2 qcs - 8 and (TR/2 + 4) qcs <= threads * quads per thread (68 quad columns:
+            // TC = 128, eight tiles across a 1024-wide lattice).  Cost, compared in order (fitted
+            // to measured sweeps of 130 x 1000 to 2048 x 2048 lattices): tilings that fit in one
+            // wave (one block per SM) first; among those the fewest quads per thread (a thread's
+            // quads are its serial path through the latency-bound steps), then more threads per
+            // block, then fewer staged quads; with several waves, the fewest waves times staged
+            // quads per block (the work of the busiest SM).
+            static const int cfg[5][3] = {{64, 768, 3}, {64, 1024, 2}, {32, 1024, 2}, {32, 512, 2}, {68, 704, 3}};
+            double best[4] = {1e300, 0, 0, 0};
             int bq = 0, bn = 0, bm = 0, btr = 0;
-            for (int ci = 0; ci < 4; ++ci) {
+            for (int ci = 0; ci < 5; ++ci) {
                 if (s->tune.quad_config > 0 && ci != s->tune.quad_config - 1) continue;
                 const int *cf = cfg[ci];
                 const int qcs = cf[0], nt = cf[1], nq = cf[2];
@@ -1085,10 +1090,12 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
                     for (auto &h : s->hf)
                         if (h.kind == kind) tiles += static_cast<int64_t>((h.dims[0] + tr - 1) / tr) * ((h.dims[1] + tc - 1) / tc);
                     const int quads = (tr / 2 + 4) * qcs;
+                    const double waves = std::ceil(static_cast<double>(tiles) / 152.0);
                     const double per_thread = std::ceil(static_cast<double>(quads) / nt);
-                    const double cost = std::ceil(static_cast<double>(tiles) / 152.0) * per_thread;
-                    if (cost < best * 0.999) {
-                        best = cost;
+                    const double cost[4] = {waves > 1 ? 1.0 : 0.0, waves > 1 ? waves * quads : per_thread,
+                                            -static_cast<double>(nt), static_cast<double>(quads)};
+                    if (std::lexicographical_compare(cost, cost + 4, best, best + 4)) {
+                        std::copy(cost, cost + 4, best);
                         bq = qcs;
                         bn = nt;
                         bm = nq;

@@ -161,7 +161,7 @@ extern "C" gmrf_status gmrf_autotune(const gmrf_field_desc *fields, int32_t nfie
         }
     // 3. the quad kernel (one chain, FP32, 8-neighbour lattices)
     if (has_kind[GMRF_LATTICE2D_8] && cp == 1 && fp32) {
-        for (int q : {-1, 1, 2, 3, 4}) {
+        for (int q : {-1, 1, 2, 3, 4, 5}) {
             gmrf_tuning t = best;
             t.quad_config = q;
             t.quad_rows = 0;

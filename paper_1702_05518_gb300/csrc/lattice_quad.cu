@@ -352,6 +352,7 @@ cudaError_t prepare_lattice_quad(int qcs, int nt, int nq, size_t smem)
     GMRF_QUAD_CFG(64, 1024, 2)
     GMRF_QUAD_CFG(32, 1024, 2)
     GMRF_QUAD_CFG(32, 512, 2)
+    GMRF_QUAD_CFG(68, 704, 3)
 #undef GMRF_QUAD_CFG
     return cudaErrorInvalidValue;
 }
@@ -366,6 +367,7 @@ cudaError_t launch_lattice_quad(int qcs, int nt, int nq, const FusedArgs &a, siz
     GMRF_QUAD_CFG(64, 1024, 2)
     GMRF_QUAD_CFG(32, 1024, 2)
     GMRF_QUAD_CFG(32, 512, 2)
+    GMRF_QUAD_CFG(68, 704, 3)
 #undef GMRF_QUAD_CFG
     return cudaErrorInvalidValue;
 }

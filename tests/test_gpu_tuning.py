@@ -41,7 +41,7 @@ def _check(f, C, T, precision, tuning, seed=5, tol=None, **kw):
         assert trace_relerr(res[c]["tau_trace"], out["tau_trace"][c]) <= tol
 
 
-@pytest.mark.parametrize("quad", [(1, 0), (2, 0), (3, 0), (4, 0), (-1, 0), (1, 24), (3, 40)])
+@pytest.mark.parametrize("quad", [(1, 0), (2, 0), (3, 0), (4, 0), (5, 0), (-1, 0), (1, 24), (3, 40), (5, 54)])
 def test_quad_configurations(quad):
     f = wl.small_lattice(wl.LATTICE2D_8, (130, 200), 3)
     _check(f, 1, 1, g.FP32, {"quad_config": quad[0], "quad_rows": quad[1]})
@@ -73,7 +73,7 @@ def test_csr_fp64_tuned(v):
 
 @pytest.mark.parametrize("bad", [{"chains_per_thread": 3}, {"chains_per_thread": 4}, {"step_tile": 100},
                                  {"fused_rows": [16, 0], "fused_cols": [0, 0]}, {"fused_threads": [256, 0]},
-                                 {"quad_config": 5}, {"quad_rows": 13}, {"quad_config": 4, "quad_rows": 200},
+                                 {"quad_config": 6}, {"quad_rows": 13}, {"quad_config": 4, "quad_rows": 200},
                                  {"fused_rows": [0, 256], "fused_cols": [0, 256]}])
 def test_invalid_tunings(bad):
     # 2 chains: chains_per_thread 4 exceeds them; the 256 x 256 tile with FP64 state does not fit
