@@ -46,6 +46,38 @@ struct HostField {
     bool weighted = false;        // CSR: weights given
 };
 
+// Breadth-first order of a graph's vertices, each component from a pseudo-peripheral vertex (the
+// last one a breadth-first search from its lowest vertex reaches), neighbours in CSR order.  The
+// layout sorts each colour class in this order (the order inside a class is free, Sec. 2.3:
+// its sites are conditionally independent), so nearby sites get nearby positions.
+std::vector<int32_t> bfs_order(int32_t n, const int32_t *rp, const int32_t *ci)
+{
+    std::vector<int32_t> order, comp;
+    order.reserve(static_cast<size_t>(n));
+    std::vector<uint8_t> seen(static_cast<size_t>(n), 0);
+    auto search = [&](int32_t src, std::vector<int32_t> &out) {
+        size_t head = out.size();
+        out.push_back(src);
+        seen[src] = 1;
+        while (head < out.size()) {
+            const int32_t v = out[head++];
+            for (int32_t e = rp[v]; e < rp[v + 1]; ++e)
+                if (!seen[ci[e]]) {
+                    seen[ci[e]] = 1;
+                    out.push_back(ci[e]);
+                }
+        }
+    };
+    for (int32_t v0 = 0; v0 < n; ++v0) {
+        if (seen[v0]) continue;
+        comp.clear();
+        search(v0, comp);
+        for (int32_t v : comp) seen[v] = 0;
+        search(comp.back(), order);
+    }
+    return order;
+}
+
 }  // namespace
 
 bool gmrf::pdl_enabled()
@@ -985,7 +1017,14 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     }
     CK(s->alloc_t(&s->fields_dev, static_cast<size_t>(s->nfields), sizeof(FieldDev)));
 
-    // CSR fields: upload, colour (JP unless given), colour-permuted layout.
+    // CSR fields: upload, colour (JP unless given), colour-permuted layout.  Each colour class is
+    // ordered breadth-first (neighbouring sites in nearby positions: the per-colour kernels'
+    // gathers touch fewer sectors, measured 6 % faster on 15 K- and 50 K-site graphs), except for
+    // a single graph small enough for the resident kernel, which measured 3 % faster with the
+    // classes in natural order (its shared-memory gathers spread over the banks).
+    const bool natural_classes = s->nfields == 1 && s->hf[0].kind == GMRF_CSR && s->hf[0].n < 32768 &&
+                                 !binomial_model(s) && !(s->opts.flags & GMRF_FLAG_NO_RESIDENT) &&
+                                 (s->precision == GMRF_FP32 || (s->opts.flags & GMRF_FLAG_RESIDENT));
     std::vector<std::vector<int32_t>> coff_host(s->nfields);
     for (int fi = 0; fi < s->nfields; ++fi) {
         HostField &h = s->hf[fi];
@@ -1021,7 +1060,12 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
         CK(cudaMalloc(&scratch, layout_scratch_bytes(h.n, h.ncolors)));
         tmp.push_back(scratch);
         char *wbase = any_weights && f.weights ? static_cast<char *>(s->w) + d.nnz0 * T : nullptr;
-        CK(csr_layout(s->precision, h.n, h.ncolors, rp_d, ci_d, w_d, col_d, scratch, s->perm + d.csr0,
+        int32_t *order_d = nullptr;
+        if (!natural_classes && h.n > 0) {
+            const std::vector<int32_t> order = bfs_order(h.n, f.row_ptr, f.col_idx);
+            order_d = upload_t(order.data(), h.n, s->stream, tmp);
+        }
+        CK(csr_layout(s->precision, h.n, h.ncolors, rp_d, ci_d, w_d, col_d, order_d, scratch, s->perm + d.csr0,
                       s->perm_inv + d.csr0, s->coff + d.coff0, s->rp + d.rp0, s->ci + d.nnz0, wbase,
                       static_cast<char *>(s->deg) + d.csr0 * T, s->stream));
         coff_host[fi].resize(h.ncolors + 1);

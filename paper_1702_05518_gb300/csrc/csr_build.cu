@@ -93,12 +93,16 @@ __global__ void jp_assign_kernel(int32_t n, const int32_t *rp, const int32_t *ci
     if (localmax >= 0) atomicMax(maxcolor, localmax);
 }
 
-// Per block of kScanBlock vertices: count of each colour (colour-major [c][block]).
-__global__ void block_colour_counts_kernel(int32_t n, int32_t ncolors, const int32_t *colors, int32_t *counts,
-                                           int32_t nblocks)
+// The layout visits the vertices in the sequence order[0..n) (natural order when order is
+// null): element i of the sequence is vertex order[i].
+
+// Per block of kScanBlock elements of the sequence: count of each colour (colour-major
+// [c][block]).
+__global__ void block_colour_counts_kernel(int32_t n, int32_t ncolors, const int32_t *colors, const int32_t *order,
+                                           int32_t *counts, int32_t nblocks)
 {
-    const int64_t v = blockIdx.x * static_cast<int64_t>(kScanBlock) + threadIdx.x;
-    const int32_t cv = v < n ? colors[v] : -1;
+    const int64_t i = blockIdx.x * static_cast<int64_t>(kScanBlock) + threadIdx.x;
+    const int32_t cv = i < n ? colors[order ? order[i] : i] : -1;
     for (int32_t c = 0; c < ncolors; ++c) {
         const int cnt = __syncthreads_count(cv == c);
         if (threadIdx.x == 0) counts[static_cast<int64_t>(c) * nblocks + blockIdx.x] = cnt;
@@ -134,14 +138,16 @@ __global__ void colour_bases_kernel(int32_t ncolors, int32_t nblocks, const int3
         for (int32_t b = 0; b < nblocks; ++b) bases[static_cast<int64_t>(c) * nblocks + b] += coff[c];
 }
 
-// Stable scatter: position of v = base[colour][block] + rank of v among the block's vertices
-// of its colour (warp ballots, then warps in order).
-__global__ void colour_scatter_kernel(int32_t n, int32_t ncolors, const int32_t *colors, const int32_t *bases,
-                                      int32_t nblocks, int32_t *perm, int32_t *perm_inv)
+// Stable scatter: position of the sequence's element i (vertex v) = base[colour][block] + rank
+// of i among the block's elements of its colour (warp ballots, then warps in order), so each
+// colour class keeps the sequence order.
+__global__ void colour_scatter_kernel(int32_t n, int32_t ncolors, const int32_t *colors, const int32_t *order,
+                                      const int32_t *bases, int32_t nblocks, int32_t *perm, int32_t *perm_inv)
 {
     __shared__ int32_t wcount[kScanBlock / 32];
-    const int64_t v = blockIdx.x * static_cast<int64_t>(kScanBlock) + threadIdx.x;
-    const int32_t cv = v < n ? colors[v] : -1;
+    const int64_t i = blockIdx.x * static_cast<int64_t>(kScanBlock) + threadIdx.x;
+    const int64_t v = i < n ? (order ? order[i] : i) : -1;
+    const int32_t cv = i < n ? colors[v] : -1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int32_t c = 0; c < ncolors; ++c) {
         const unsigned mask = __ballot_sync(0xffffffffu, cv == c);
@@ -295,9 +301,9 @@ size_t layout_scratch_bytes(int32_t n, int32_t ncolors)
 }
 
 cudaError_t csr_layout(int precision, int32_t n, int32_t ncolors, const int32_t *rp, const int32_t *ci,
-                       const double *w, const int32_t *colors, void *scratch, int32_t *perm, int32_t *perm_inv,
-                       int32_t *coff, int32_t *rp_out, int32_t *ci_out, void *w_out, void *deg_out,
-                       cudaStream_t stream)
+                       const double *w, const int32_t *colors, const int32_t *order, void *scratch, int32_t *perm,
+                       int32_t *perm_inv, int32_t *coff, int32_t *rp_out, int32_t *ci_out, void *w_out,
+                       void *deg_out, cudaStream_t stream)
 {
     const int32_t nblocks = static_cast<int32_t>((static_cast<int64_t>(n) + kScanBlock - 1) / kScanBlock);
     const size_t nb = static_cast<size_t>(nblocks > 0 ? nblocks : 1);
@@ -312,9 +318,10 @@ cudaError_t csr_layout(int precision, int32_t n, int32_t ncolors, const int32_t 
         if (err != cudaSuccess) return err;
         return cudaMemsetAsync(rp_out, 0, sizeof(int32_t), stream);
     }
-    block_colour_counts_kernel<<<nblocks, kScanBlock, 0, stream>>>(n, ncolors, colors, counts, nblocks);
+    block_colour_counts_kernel<<<nblocks, kScanBlock, 0, stream>>>(n, ncolors, colors, order, counts, nblocks);
     colour_bases_kernel<<<1, 1024, 0, stream>>>(ncolors, nblocks, counts, bases, coff);
-    colour_scatter_kernel<<<nblocks, kScanBlock, 0, stream>>>(n, ncolors, colors, bases, nblocks, perm, perm_inv);
+    colour_scatter_kernel<<<nblocks, kScanBlock, 0, stream>>>(n, ncolors, colors, order, bases, nblocks, perm,
+                                                              perm_inv);
     if (precision == 0) {
         permuted_rows_kernel<float><<<grid_of(n, 256), 256, 0, stream>>>(n, rp, w, perm, len, static_cast<float *>(deg_out));
     } else {

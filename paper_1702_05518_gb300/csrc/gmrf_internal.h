@@ -300,12 +300,13 @@ size_t jp_scratch_bytes(int32_t n);
 cudaError_t jp_color(int32_t n, const int32_t *rp, const int32_t *ci, const uint32_t *prio,
                      uint64_t seed, int32_t *colors, void *scratch, int32_t *num_colors_host,
                      cudaStream_t stream);
-// Stable counting sort of the sites by colour and the permuted CSR (cols remapped, row order
-// kept), degrees and weights in precision T.  Outputs are device arrays of the field's block.
+// Stable counting sort by colour of the sites taken in the sequence `order` (device, n
+// vertices; null: natural order), and the permuted CSR (cols remapped, row order kept),
+// degrees and weights in precision T.  Outputs are device arrays of the field's block.
 size_t layout_scratch_bytes(int32_t n, int32_t ncolors);
 cudaError_t csr_layout(int precision, int32_t n, int32_t ncolors, const int32_t *rp, const int32_t *ci,
-                       const double *w, const int32_t *colors, void *scratch, int32_t *perm,
-                       int32_t *perm_inv, int32_t *coff, int32_t *rp_out, int32_t *ci_out,
+                       const double *w, const int32_t *colors, const int32_t *order, void *scratch,
+                       int32_t *perm, int32_t *perm_inv, int32_t *coff, int32_t *rp_out, int32_t *ci_out,
                        void *w_out, void *deg_out, cudaStream_t stream);
 
 // Plain FP64 baseline sweep (plain.cu): natural layout, one pass per colour over all sites.
