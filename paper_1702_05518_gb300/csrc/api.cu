@@ -534,6 +534,8 @@ HyperArgs hyper_args(gmrf_sampler *s, int draw, int draw_beta, int end_of_sweep)
     h.thin = s->opts.thin;
     h.acc_enabled = 1;
     h.gpre = s->gpre;
+    h.max_parts = 0;
+    for (int fi = 0; fi < s->nfields; ++fi) h.max_parts = std::max(h.max_parts, s->fd[fi].nparts);
     return h;
 }
 

@@ -90,6 +90,7 @@ struct HyperArgs {
     int32_t acc_enabled;
     const double *gpre;   // [batch][F * Cp][4]: unit-rate Gamma variates of tau and 1/sigma^2 and
                           // the intercept's standard normal, for the batch's sweeps
+    int32_t max_parts;    // the most tile partials of any field
 };
 
 // Arguments of one launch of the resident kernel (lattice_resident.cu): `count` whole sweeps of

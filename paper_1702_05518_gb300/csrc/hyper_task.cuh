@@ -97,7 +97,7 @@ __device__ __forceinline__ void hyper_draw(const HyperArgs &a, int which, int ch
 }
 
 // One task, run by all 32 lanes of the calling warp; `sweep` is the sweep being finished.
-template <typename T>
+template <typename T, bool BATCH>
 __device__ __forceinline__ void hyper_task(const HyperArgs &a, int task, long long sweep)
 {
     const int lane = threadIdx.x & 31;
@@ -132,27 +132,30 @@ __device__ __forceinline__ void hyper_task(const HyperArgs &a, int task, long lo
     const bool need_a = which && a.draw_beta;
     double S = 0.0, A = 0.0;
     if (need_sum) {
-        // Lane l adds partials l, l + 32, l + 64, ... in that order; eight loads are issued before
-        // their additions, so a warp waits for one L2 round trip per 256 partials, not per 32.
-        constexpr int U = 8;
-        const Part3 *P = a.partials + static_cast<int64_t>(part0) * a.Cp + chain;
+        // Lane l adds partials l, l + 32, l + 64, ... in that order.  BATCH (fields of many
+        // tiles): eight loads are issued before their additions, so a warp waits for one L2 round
+        // trip per 256 partials, not per 32; the sums are the same.
         int k = lane;
-        for (; k + 32 * (U - 1) < nparts; k += 32 * U) {
-            double vs[U], va[U];
+        if constexpr (BATCH) {
+            constexpr int U = 8;
+            const Part3 *P = a.partials + static_cast<int64_t>(part0) * a.Cp + chain;
+            for (; k + 32 * (U - 1) < nparts; k += 32 * U) {
+                double vs[U], va[U];
 #pragma unroll
-            for (int j = 0; j < U; ++j) {
-                const Part3 &p = P[static_cast<int64_t>(k + 32 * j) * a.Cp];
-                vs[j] = which ? p.R : p.S;
-                va[j] = need_a ? p.A : 0.0;
-            }
+                for (int j = 0; j < U; ++j) {
+                    const Part3 &p = P[static_cast<int64_t>(k + 32 * j) * a.Cp];
+                    vs[j] = which ? p.R : p.S;
+                    va[j] = need_a ? p.A : 0.0;
+                }
 #pragma unroll
-            for (int j = 0; j < U; ++j) {
-                S += vs[j];
-                if (need_a) A += va[j];
+                for (int j = 0; j < U; ++j) {
+                    S += vs[j];
+                    if (need_a) A += va[j];
+                }
             }
         }
         for (; k < nparts; k += 32) {
-            const Part3 p = P[static_cast<int64_t>(k) * a.Cp];
+            const Part3 p = a.partials[static_cast<int64_t>(part0 + k) * a.Cp + chain];
             S += which ? p.R : p.S;
             if (need_a) A += p.A;
         }

@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (KIND == kCsr ? 2 : 3
 // finish does (ticket counter; no block waits for another).
 constexpr int kHyperWarps = 8;
 
-template <typename T>
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(kHyperWarps * 32) hyper_kernel(const HyperArgs a)
 {
     // Let the next sweep kernel be scheduled now: it does its own early work (observations,
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(kHyperWarps * 32) hyper_kernel(const HyperArgs
     pdl_wait();
     const int task = blockIdx.x * kHyperWarps + (threadIdx.x >> 5);
     const long long sweep = a.ctl->sweep;
-    if (task < a.nfields * a.Cp * 2) hyper_task<T>(a, task, sweep);
+    if (task < a.nfields * a.Cp * 2) hyper_task<T, BATCH>(a, task, sweep);
     bool last = gridDim.x == 1;
     __syncthreads();
     if (!last && threadIdx.x == 0) {
@@ -701,8 +701,12 @@ cudaError_t launch_colour_step(int precision, int V, int kind, const StepArgs &a
 cudaError_t launch_hyper(int precision, const HyperArgs &a, cudaStream_t stream)
 {
     const int grid = (a.nfields * a.Cp * 2 + kHyperWarps - 1) / kHyperWarps;
-    if (precision == 0) return launch_sweep_kernel(hyper_kernel<float>, grid, kHyperWarps * 32, 0, stream, a);
-    return launch_sweep_kernel(hyper_kernel<double>, grid, kHyperWarps * 32, 0, stream, a);
+    if (a.max_parts >= 256) {  // batched partial-sum loads (fields of many tiles)
+        if (precision == 0) return launch_sweep_kernel(hyper_kernel<float, true>, grid, kHyperWarps * 32, 0, stream, a);
+        return launch_sweep_kernel(hyper_kernel<double, true>, grid, kHyperWarps * 32, 0, stream, a);
+    }
+    if (precision == 0) return launch_sweep_kernel(hyper_kernel<float, false>, grid, kHyperWarps * 32, 0, stream, a);
+    return launch_sweep_kernel(hyper_kernel<double, false>, grid, kHyperWarps * 32, 0, stream, a);
 }
 
 cudaError_t launch_pack(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx, int32_t C,
