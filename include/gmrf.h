@@ -59,7 +59,7 @@ typedef enum {
     GMRF_E_OOM = 3,         /* device allocation failed                                   */
     GMRF_E_STATE = 4,       /* sampler poisoned by an earlier error, or call out of order  */
     GMRF_E_TIMEOUT = 5,     /* a bounded device wait gave up (reserved; no kernel waits)   */
-    GMRF_E_UNSUPPORTED = 6  /* valid request that this build does not implement           */
+    GMRF_E_UNSUPPORTED = 6  /* valid request that the library does not implement          */
 } gmrf_status;
 
 typedef enum {
