@@ -369,7 +369,10 @@ gmrf_status gmrf_autotune(const gmrf_field_desc *fields, int32_t nfields, const 
  * Afterwards the sampler is in the state gmrf_sampler_create with these arrays followed by
  * gmrf_sampler_reset would give (all fields restart, as gmrf_sampler_reset does; the other
  * fields keep their data).  The host arrays are read before the call returns (it synchronises
- * the sampler's stream after its uploads); the rest is enqueued asynchronously.  The first call
+ * the sampler's stream after its uploads); the rest is enqueued asynchronously.  The restart
+ * itself is enqueued by the next call that uses the sampler's state (gmrf_sweep,
+ * gmrf_hyper_update, the fetch, diagnostic and stage calls, gmrf_sampler_info), so a set_data call
+ * per field restarts the chains once.  The first call
  * allocates a device staging buffer of (1 + chains) doubles (+ one int32 for binomial data) per
  * site of the largest field; later calls allocate nothing.
  * Errors: GMRF_E_INVALID (bad field index or data; nothing changes), GMRF_E_STATE, GMRF_E_OOM,

@@ -80,6 +80,7 @@ std::vector<int32_t> bfs_order(int32_t n, const int32_t *rp, const int32_t *ci)
 
 }  // namespace
 
+
 bool gmrf::pdl_enabled()
 {
     static const bool on = [] {
@@ -164,6 +165,7 @@ struct gmrf_sampler {
     std::vector<void *> allocs;
     int64_t bytes = 0;
     bool poisoned = false;
+    bool restart_pending = false;  // gmrf_sampler_set_data: restart before the state is next used
     int64_t launches_per_sweep = 0;
     // Resident path (lattice_resident.cu): whole sweeps of a small single 2-D lattice field in one
     // launch, one block per chain; 0 when the field takes the per-sweep stages.
@@ -1417,6 +1419,39 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
 // =============================================================================================
 // C ABI
 // =============================================================================================
+namespace {
+
+// The restart of gmrf_sampler_reset (stream-ordered): states from x_init, parameters from their
+// initial values, running moments and counters cleared.
+gmrf_status restart_state(gmrf_sampler *s)
+{
+    s->restart_pending = false;
+    try {
+        const bool plain = s->algorithm == GMRF_ALGO_PLAIN;
+        void *x = plain ? static_cast<void *>(s->plain.x) : s->x;
+        CK(cudaMemcpyAsync(x, s->x_init, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
+        if (s->x_alt) CK(cudaMemcpyAsync(s->x_alt, s->x_init, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
+        CK(cudaMemcpyAsync(s->tau, s->tau_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+        CK(cudaMemcpyAsync(s->sig2, s->sig2_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+        if (!plain) {
+            CK(cudaMemcpyAsync(s->beta, s->beta_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+            CK(cudaMemcpyAsync(s->hyp, s->hyp_init, s->hyp_bytes, cudaMemcpyDeviceToDevice, s->stream));
+            CK(cudaMemsetAsync(s->mean, 0, s->x_bytes, s->stream));
+            CK(cudaMemsetAsync(s->m2, 0, s->x_bytes, s->stream));
+        }
+        CK(launch_ctl_reset(s->ctl, s->opts.start_sweep, s->stream));
+    } catch (const CudaFail &f) {
+        s->poisoned = true;
+        return cuda_status(f);
+    }
+    return GMRF_OK;
+}
+
+// A restart requested by gmrf_sampler_set_data, before a call that uses the sampler's state.
+gmrf_status restart_if_pending(gmrf_sampler *s) { return s->restart_pending ? restart_state(s) : GMRF_OK; }
+
+}  // namespace
+
 extern "C" {
 
 const char *gmrf_last_error(void) { return g_last_error.c_str(); }
@@ -1562,6 +1597,7 @@ gmrf_status gmrf_sweep(gmrf_sampler *s, int32_t nsweeps, int32_t with_hyper)
     g_last_error.clear();
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (const gmrf_status r = restart_if_pending(s)) return r;
     if (nsweeps < 0) return fail(GMRF_E_INVALID, "nsweeps must be >= 0");
     const int wh = with_hyper ? 1 : 0;
     cudaError_t e = cudaSuccess;
@@ -1594,6 +1630,7 @@ gmrf_status gmrf_hyper_update(gmrf_sampler *s)
     g_last_error.clear();
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (const gmrf_status r = restart_if_pending(s)) return r;
     if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "hyper_update on the plain sweep");
     if (binomial_model(s)) return fail(GMRF_E_UNSUPPORTED, "hyper_update with the binomial likelihood");
     cudaError_t e = cudaSuccess;
@@ -1611,6 +1648,7 @@ gmrf_status gmrf_fetch_samples(gmrf_sampler *s, int32_t field, int32_t chain, do
     g_last_error.clear();
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (const gmrf_status r = restart_if_pending(s)) return r;
     if (field < 0 || field >= s->nfields || chain < 0 || chain >= s->C)
         return fail(GMRF_E_INVALID, "field or chain out of range");
     if (trace_cap < 0) return fail(GMRF_E_INVALID, "trace_cap must be >= 0");
@@ -1675,6 +1713,7 @@ gmrf_status gmrf_fetch_intercept(gmrf_sampler *s, int32_t field, int32_t chain, 
     g_last_error.clear();
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (const gmrf_status r = restart_if_pending(s)) return r;
     if (!has_beta(s)) return fail(GMRF_E_INVALID, "the model has no intercept");
     if (field < 0 || field >= s->nfields || chain < 0 || chain >= s->C)
         return fail(GMRF_E_INVALID, "field or chain out of range");
@@ -1709,6 +1748,7 @@ gmrf_status gmrf_trace_diagnostics(gmrf_sampler *s, int32_t field, int32_t param
     g_last_error.clear();
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (const gmrf_status r = restart_if_pending(s)) return r;
     if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "diagnostics of the plain sweep");
     if (field < 0 || field >= s->nfields) return fail(GMRF_E_INVALID, "field out of range");
     if (param < GMRF_PARAM_TAU2 || param > GMRF_PARAM_TAU) return fail(GMRF_E_INVALID, "param");
@@ -1756,6 +1796,7 @@ gmrf_status gmrf_site_psrf(gmrf_sampler *s, int32_t field, double *psrf, double 
     g_last_error.clear();
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (const gmrf_status r = restart_if_pending(s)) return r;
     if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "diagnostics of the plain sweep");
     if (field < 0 || field >= s->nfields) return fail(GMRF_E_INVALID, "field out of range");
     if (s->C < 2) return fail(GMRF_E_INVALID, "the PSRF needs at least 2 chains");
@@ -1790,25 +1831,7 @@ gmrf_status gmrf_sampler_reset(gmrf_sampler *s)
     g_last_error.clear();
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
-    try {
-        const bool plain = s->algorithm == GMRF_ALGO_PLAIN;
-        void *x = plain ? static_cast<void *>(s->plain.x) : s->x;
-        CK(cudaMemcpyAsync(x, s->x_init, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
-        if (s->x_alt) CK(cudaMemcpyAsync(s->x_alt, s->x_init, s->x_bytes, cudaMemcpyDeviceToDevice, s->stream));
-        CK(cudaMemcpyAsync(s->tau, s->tau_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
-        CK(cudaMemcpyAsync(s->sig2, s->sig2_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
-        if (!plain) {
-            CK(cudaMemcpyAsync(s->beta, s->beta_init, s->nh * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
-            CK(cudaMemcpyAsync(s->hyp, s->hyp_init, s->hyp_bytes, cudaMemcpyDeviceToDevice, s->stream));
-            CK(cudaMemsetAsync(s->mean, 0, s->x_bytes, s->stream));
-            CK(cudaMemsetAsync(s->m2, 0, s->x_bytes, s->stream));
-        }
-        CK(launch_ctl_reset(s->ctl, s->opts.start_sweep, s->stream));
-    } catch (const CudaFail &f) {
-        s->poisoned = true;
-        return cuda_status(f);
-    }
-    return GMRF_OK;
+    return restart_state(s);
 }
 
 gmrf_status gmrf_sampler_set_data(gmrf_sampler *s, int32_t field, const double *y, const int32_t *trials,
@@ -1875,7 +1898,10 @@ gmrf_status gmrf_sampler_set_data(gmrf_sampler *s, int32_t field, const double *
         s->poisoned = true;
         return cuda_status(f);
     }
-    return gmrf_sampler_reset(s);
+    // The restart runs once before the state is next used (a batch of set_data calls, one per
+    // field, restarts the chains once).
+    s->restart_pending = true;
+    return GMRF_OK;
 }
 
 gmrf_status gmrf_launch_stage(gmrf_sampler *s, int32_t stage, int32_t accumulate, const char **name)
@@ -1883,6 +1909,7 @@ gmrf_status gmrf_launch_stage(gmrf_sampler *s, int32_t stage, int32_t accumulate
     g_last_error.clear();
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (const gmrf_status r = restart_if_pending(s)) return r;
     if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "stages of the plain sweep");
     if (stage < 0 || stage >= static_cast<int32_t>(s->stages.size())) return fail(GMRF_E_INVALID, "stage out of range");
     static const char *kNames[4][4] = {
@@ -1920,6 +1947,7 @@ gmrf_status gmrf_sampler_info(gmrf_sampler *s, gmrf_info *out)
     g_last_error.clear();
     if (!s || !out) return fail(GMRF_E_INVALID, "sampler and out are required");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (const gmrf_status r = restart_if_pending(s)) return r;
     SweepCtl c{};
     cudaError_t e = cudaMemcpyAsync(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);

@@ -186,3 +186,27 @@ def test_fetch_mean_into_pinned_buffer():
         m = s.fetch_mean(0, 1, out=buf.numpy())
         np.testing.assert_array_equal(buf.numpy(), s.fetch(0, 1)["mean"])
         assert m is not None
+
+
+def test_set_data_on_every_field_restarts_once():
+    """set_data on each field of a sampler in turn, then the state: before any sweep it is the
+    restart state (x = the new y, no sweep done, empty moments); after sweeps it equals a sampler
+    created with all the new data."""
+    fields = [wl.small_lattice(wl.LATTICE2D_4, (48, 40), 19), _delaunay(800, 20),
+              wl.small_lattice(wl.LATTICE3D_6, (6, 7, 8), 21)]
+    news = [_new_data(f, 30 + i) for i, f in enumerate(fields)]
+    T = 4
+    with g.Sampler(fields, precision=g.FP32, chains=2, seed=12, burn_in=0) as a:
+        a.sweep(5)
+        for fi, nd in enumerate(news):
+            a.set_data(fi, nd["y"])
+        assert a.info()["sweeps_done"] == 0 and a.info()["accumulated"] == 0
+        for fi, nd in enumerate(news):
+            np.testing.assert_array_equal(a.fetch_x(fi, 1), nd["y"].astype(np.float32).astype(np.float64))
+        a.sweep(T)
+        got = _result(a, 3, 2, T)
+    with g.Sampler([dict(f, **nd) for f, nd in zip(fields, news)], precision=g.FP32, chains=2, seed=12,
+                   burn_in=0) as b:
+        b.sweep(T)
+        want = _result(b, 3, 2, T)
+    _same(got, want)
