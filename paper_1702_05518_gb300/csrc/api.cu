@@ -46,6 +46,24 @@ struct HostField {
     bool weighted = false;        // CSR: weights given
 };
 
+// Whether every value is finite: exponent bits not all ones, tested without a branch per value
+// (chunks of 4096, so a bad value ends the scan soon).
+bool all_finite(const double *v, int64_t n)
+{
+    constexpr uint64_t kExp = 0x7ff0000000000000ull;
+    for (int64_t i0 = 0; i0 < n; i0 += 4096) {
+        const int64_t i1 = std::min<int64_t>(n, i0 + 4096);
+        uint64_t bad = 0;
+        for (int64_t i = i0; i < i1; ++i) {
+            uint64_t b;
+            std::memcpy(&b, v + i, sizeof(b));
+            bad |= static_cast<uint64_t>((b & kExp) == kExp);
+        }
+        if (bad) return false;
+    }
+    return true;
+}
+
 // Breadth-first order of a graph's vertices, each component from a pseudo-peripheral vertex (the
 // last one a breadth-first search from its lowest vertex reaches), neighbours in CSR order.  The
 // layout sorts each colour class in this order (the order inside a class is free, Sec. 2.3:
@@ -1844,20 +1862,24 @@ gmrf_status gmrf_sampler_set_data(gmrf_sampler *s, int32_t field, const double *
     const int64_t n = s->hf[field].n;
     const bool binomial = binomial_model(s);
     if (!y) return fail(GMRF_E_INVALID, "y is required");
-    for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(y[i])) return fail(GMRF_E_INVALID, "y must be finite");
-    if (binomial) {
-        if (!trials) return fail(GMRF_E_INVALID, "binomial data need trials");
-        for (int64_t i = 0; i < n; ++i) {
-            if (trials[i] < 0 || trials[i] > 4095) return fail(GMRF_E_INVALID, "trials must be in 0..4095");
-            if (!(y[i] >= 0.0 && y[i] <= trials[i]))
-                return fail(GMRF_E_INVALID, "successes y must be in [0, trials]");
-        }
-    }
-    if (x0)
-        for (int64_t i = 0; i < n * s->C; ++i)
-            if (!std::isfinite(x0[i])) return fail(GMRF_E_INVALID, "x0 must be finite");
+    if (binomial && !trials) return fail(GMRF_E_INVALID, "binomial data need trials");
+    // The checks of the values (the caller's arrays, read on the host while the uploads into the
+    // staging buffer run; bad data leave the sampler unchanged).
+    auto check_data = [&]() -> gmrf_status {
+        if (!all_finite(y, n)) return fail(GMRF_E_INVALID, "y must be finite");
+        if (binomial)
+            for (int64_t i = 0; i < n; ++i) {
+                if (trials[i] < 0 || trials[i] > 4095) return fail(GMRF_E_INVALID, "trials must be in 0..4095");
+                if (!(y[i] >= 0.0 && y[i] <= trials[i]))
+                    return fail(GMRF_E_INVALID, "successes y must be in [0, trials]");
+            }
+        if (x0 && !all_finite(x0, n * s->C)) return fail(GMRF_E_INVALID, "x0 must be finite");
+        return GMRF_OK;
+    };
     const bool plain = s->algorithm == GMRF_ALGO_PLAIN;
+    if (plain) {
+        if (const gmrf_status r = check_data()) return r;
+    }
     if (!plain && !s->data_stage) {
         // One staging area for the largest field: y, then x0 (or its default) for every chain.
         int64_t max_n = 1;
@@ -1886,7 +1908,9 @@ gmrf_status gmrf_sampler_set_data(gmrf_sampler *s, int32_t field, const double *
             if (binomial)
                 CK(cudaMemcpyAsync(s->trials_stage, trials, sizeof(int32_t) * static_cast<size_t>(n),
                                    cudaMemcpyHostToDevice, s->stream));
+            const gmrf_status checked = check_data();
             CK(cudaStreamSynchronize(s->stream));  // the host arrays may be reused from here on
+            if (checked != GMRF_OK) return checked;  // only the staging buffer was written
             if (binomial)
                 CK(launch_pack_int(s->fields_dev, s->fd[field], field, s->trials_stage, s->perm_inv, s->trials,
                                    s->stream));
