@@ -58,7 +58,8 @@ typedef enum {
     GMRF_E_CUDA = 2,        /* a CUDA call failed; the sampler is poisoned                 */
     GMRF_E_OOM = 3,         /* device allocation failed                                   */
     GMRF_E_STATE = 4,       /* sampler poisoned by an earlier error, or call out of order  */
-    GMRF_E_TIMEOUT = 5,     /* a bounded device wait gave up (reserved; no kernel waits)   */
+    GMRF_E_TIMEOUT = 5,     /* a bounded device wait gave up (reserved; device waits that   */
+                            /* give up are counted in gmrf_info.wait_timeouts)              */
     GMRF_E_UNSUPPORTED = 6  /* valid request that the library does not implement          */
 } gmrf_status;
 
@@ -191,6 +192,7 @@ typedef struct {
     int64_t early_start_misses; /* sweep kernels that started before their predecessor ended */
                                 /* with a wrong sweep-number prediction (normals redrawn)    */
     int64_t resident;         /* sweeps run on the resident path: 1 lattice, 2 graph; 0 not  */
+    int64_t wait_timeouts;    /* bounded device waits that gave up (then results are invalid) */
 } gmrf_info;
 
 typedef struct gmrf_sampler gmrf_sampler;

@@ -1987,6 +1987,7 @@ gmrf_status gmrf_sampler_info(gmrf_sampler *s, gmrf_info *out)
     out->launches_per_sweep = s->launches_per_sweep;
     out->early_start_misses = c.fmiss;
     out->resident = s->resident;
+    out->wait_timeouts = static_cast<int64_t>(c.wait_timeouts);
     return GMRF_OK;
 }
 

@@ -87,6 +87,50 @@ __device__ __forceinline__ void cluster_sync()
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
+// Transaction barriers of the colour steps in a cluster: a block's new values go to the other
+// blocks' copies by asynchronous remote stores that complete on the receiving block's mbarrier
+// (complete_tx); the receiver expects the bytes of the other blocks' shares of the class and waits
+// for that phase.  No fence on the sending side.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void st_async(uint32_t addr, float v, uint32_t bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+                 "r"(__float_as_uint(v)), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr),
+                 "l"(__double_as_longlong(v)), "r"(bar)
+                 : "memory");
+}
+constexpr uint64_t kStepWaitNs = 1000000000ull;  // a colour step's wait gives up after 1 s
+
 // MP: positions of a colour class per site thread, 1 or kCsrMaxPos.  With one, the loads of the
 // next colour step's position (its neighbour record, observation and normal) are issued before the
 // current step's update, so the step does not wait for L2.
@@ -99,6 +143,8 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
     __shared__ T hs[3];         // tau, 1/sigma^2, beta0 of the current sweep
     __shared__ int coffs[kCsrMaxColours + 1];
     __shared__ int own_lo[kCsrMaxColours], own_hi[kCsrMaxColours], own_off[kCsrMaxColours];
+    __shared__ __align__(8) uint64_t sbar[2];  // cluster: the colour steps' barriers, by step parity
+    __shared__ int s_gave_up;                  // cluster: a step's wait ran out (no more waits)
 
     pdl_wait();
     const HyperArgs &h = a.h;
@@ -120,6 +166,12 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
     if (tid <= K) coffs[tid] = a.coff[tid];
     __syncthreads();
     if (tid == 0) {  // this block's share of every colour class and its place in ms / m2s
+        if (CL > 1) {
+            mbar_init(&sbar[0], 1);
+            mbar_init(&sbar[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        s_gave_up = 0;
         int off = 0;
         for (int c = 0; c < K; ++c) {
             const int lo = coffs[c], len = coffs[c + 1] - lo, q = (len + CL - 1) / CL;
@@ -166,12 +218,13 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
         yn = Y[own_lo[0] + tid];
         zn = ZB[own_lo[0] + tid];
     }
-    // In a cluster the drawing warps arrive at the first colour barrier of a sweep before block
-    // 0's drawing lanes do their part of the draws, so that work never holds the barrier.
-    const bool early = CL > 1 && K > 1 && drawer;
+    // Colour steps of this launch so far (cluster: step g uses barrier g & 1, phase parity
+    // (g >> 1) & 1; a block starts step g + 1 only when every other block's values of step g have
+    // arrived, i.e. after every block has read its neighbours of step g, so no copy is written
+    // while it is still read).
+    int g = 0;
     for (int t = 0; t < a.count; ++t) {
         const long long sw = sweep0 + t;
-        if (early) asm volatile("barrier.cluster.arrive.release;" ::: "memory");
         if (draws) dr.prep(h, sw, slot, t > 0, bbase, bcount, Cp);
         const T tau = hs[0], isig = hs[1], beta = hs[2];
         const bool acc_now = acc_on && sw >= h.burn_in && thin_phase == 0;
@@ -206,8 +259,10 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
             const T xn = mn + zv * FArith<T>::rsq(P);
             xs[p] = xn;
 #pragma unroll
-            for (int r = 1; r < CL; ++r)  // the other blocks' copies
-                st_remote(remote_addr(xs + p, (rank + r) % CL), xn);
+            for (int r = 1; r < CL; ++r) {  // the other blocks' copies
+                const uint32_t dst = (rank + r) % CL;
+                st_async(remote_addr(xs + p, dst), xn, remote_addr(&sbar[g & 1], dst));
+            }
             T e = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -239,7 +294,11 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
                 m2s[ob + p] = mm;
             }
         };
-        for (int c = 0; c < K; ++c) {
+        for (int c = 0; c < K; ++c, ++g) {
+            if (CL > 1 && tid == 0 && !s_gave_up) {  // this step's expected bytes: the other blocks' shares
+                const int others = (coffs[c + 1] - coffs[c]) - (own_hi[c] - own_lo[c]);
+                mbar_arrive_expect(&sbar[g & 1], static_cast<uint32_t>(others) * sizeof(T));
+            }
             if (!drawer) {
                 const int lo = coffs[c], a0 = own_lo[c], a1 = own_hi[c], ob = own_off[c] - a0;
                 if constexpr (MP == 1) {
@@ -279,12 +338,23 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
                     }
                 }
             }
-            // End of the colour step: the class is final in every copy.  (After the last step the
-            // barrier of the sums below serves.)
-            if (c + 1 < K) {
-                if (CL > 1 && early && c == 0) asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
-                else if (CL > 1) cluster_sync();
-                else if (!drawer) asm volatile("bar.sync 1, %0;" ::"r"(NTS) : "memory");
+            // End of the colour step: the class is final in this block's copy (the other blocks'
+            // values have arrived; the site threads' own ones after the named barrier).  With one
+            // block, after the last step the barrier of the sums below serves.
+            if (CL > 1 && !drawer) {
+                if (!s_gave_up && !mbar_try_wait(&sbar[g & 1], (g >> 1) & 1)) {
+                    const uint64_t t0 = global_ns();
+                    bool ok = false;
+                    while (!(ok = mbar_try_wait(&sbar[g & 1], (g >> 1) & 1)) && global_ns() - t0 < kStepWaitNs) {
+                    }
+                    if (!ok) {
+                        s_gave_up = 1;
+                        atomicAdd(&h.ctl->wait_timeouts, 1ull);
+                    }
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(NTS) : "memory");
+            } else if (CL == 1 && c + 1 < K && !drawer) {
+                asm volatile("bar.sync 1, %0;" ::"r"(NTS) : "memory");
             }
         }
         // The sums: a shuffle tree per site warp, over the site warps, then over the blocks

@@ -93,6 +93,7 @@ struct SweepCtl {
                            // last such kernel's sweep + 1); checked against `sweep` before use
     unsigned long long fticket;  // blocks of that kernel that have read fnext
     long long fmiss;       // launches whose prediction was wrong (their normals were redrawn)
+    unsigned long long wait_timeouts;  // bounded device waits that gave up (results invalid)
 };
 
 // Whether sweep number `sweep` is accumulated (burn-in, then every thin-th sweep).

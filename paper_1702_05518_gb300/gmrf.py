@@ -103,7 +103,7 @@ class Info(ctypes.Structure):
                 ("sweeps_done", ctypes.c_int64), ("accumulated", ctypes.c_int64),
                 ("hyper_fallbacks", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("launches_per_sweep", ctypes.c_int64), ("early_start_misses", ctypes.c_int64),
-                ("resident", ctypes.c_int64)]
+                ("resident", ctypes.c_int64), ("wait_timeouts", ctypes.c_int64)]
 
 
 _lock = threading.Lock()

@@ -242,6 +242,7 @@ def test_graph_fp64_parity(name, make, chains):
     res, info = _run([f], chains, 40, g.FP64, seed=7, flags=g.FLAG_RESIDENT, burn_in=10, graph_sweeps=16,
                      prior=g.PRIOR_PCAR, rho=0.95)
     assert info["resident"] == 2 and info["sweeps_done"] == 40 and info["accumulated"] == 30
+    assert info["wait_timeouts"] == 0
     _check_oracle(f, res, chains, 40, 7, TOL_FP64, burn_in=10, prior="pcar", rho=0.95)
 
 
@@ -256,7 +257,7 @@ def test_graph_fp32(name, make):
 def test_graph_fp32_1000_sweeps_and_intercept():
     f = _delaunay(4000, 26, shift=2.0)
     res, info = _run([f], 2, 1000, g.FP32, seed=11, burn_in=300, graph_sweeps=100, intercept=True)
-    assert info["resident"] == 2 and info["hyper_fallbacks"] == 0
+    assert info["resident"] == 2 and info["hyper_fallbacks"] == 0 and info["wait_timeouts"] == 0
     _check_oracle(f, res, 2, 1000, 11, TOL_FP32_1000, burn_in=300, intercept=True)
 
 
