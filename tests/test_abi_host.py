@@ -131,3 +131,33 @@ def test_null_arguments(L):
     assert L.gmrf_sampler_create(ctypes.byref(out), None, 0, None, None, None) == g.E_INVALID
     assert out.value is None
     L.gmrf_sampler_destroy(None)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the C structures' sizes and field offsets
+    (compiled from include/gmrf.h with the host C compiler)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    pairs = {"gmrf_field_desc": g.FieldDesc, "gmrf_model": g.Model, "gmrf_tuning": g.Tuning,
+             "gmrf_opts": g.Opts, "gmrf_info": g.Info}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "gmrf.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
