@@ -9,9 +9,11 @@
 // `count` sweeps of Algorithm 1 back to back.  A chain is shared by a cluster of CL blocks (on CL
 // SMs): every block keeps the chain's whole state in its shared memory and owns a contiguous share
 // of each colour class; after updating its share it stores the new values into the other blocks'
-// copies (distributed shared memory, st.shared::cluster), and a cluster barrier (release /
-// acquire) ends the colour step, so each block reads all neighbours locally.  The block sums go to
-// block 0, whose drawing warps draw and store the new parameters into every block.
+// copies (distributed shared memory) with asynchronous stores that complete on the receiving
+// block's mbarrier, and a colour step ends when the other blocks' values have arrived (a
+// transaction barrier per step, two alternating), so each block reads all neighbours locally.
+// The block sums go to block 0, whose drawing warps draw and store the new parameters into every
+// block, with cluster barriers (release / acquire) around that exchange.
 // What a sweep reads from L2 is the neighbour lists
 // -- re-packed for this kernel as one 16-byte record of eight 16-bit positions per site (a second
 // record for sites of degree 9 to 16), so a site's neighbours arrive in one load -- the
