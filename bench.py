@@ -164,8 +164,8 @@ MEASURED_TRAFFIC = {
                       sources={"lattice_quad.cu": "3e536b8a589e6c22b7f1aba7c5e3716f3208f0447ead67715aa4bb57c7f70589",
                                "gmrf_device.cuh": "39dd162e40198562e4f6096d6291842e9ce4389b3f5971fd3146620dcaa1a298",
                                "gmrf_internal.h:FusedArgs": "56db942c013e0b5fb3ff98aff46cecf959fbee26d7386333c58679d8093d2d9c"}),
-    "volume256": dict(kernel="colour_step_kernel<float, 4, 2, 0>", bytes=316_143_616 + 233_574_912,
-                      sources={"sweep_kernels.cu": "0f1e48d4f67ee7f979ef20d149556a2c3a75972a7672664d1ae82cb5cfb34537",
+    "volume256": dict(kernel="colour_step_kernel<float, 4, 2, 0>", bytes=316_079_104 + 234_375_936,
+                      sources={"sweep_kernels.cu": "95c871825e2a079b5a0bb4b0b74fbd7c65b21600f185e373b04275a78ad91a90",
                                "gmrf_device.cuh": "39dd162e40198562e4f6096d6291842e9ce4389b3f5971fd3146620dcaa1a298",
                                "gmrf_internal.h:StepArgs": "92f72ecd2bdcf4f1a8a8ea7c6a9e397d592dc5203447eb7e18789f620b4efb11"}),
 }
