@@ -162,11 +162,11 @@ def stage_algorithmic_bytes(spec, stage_name, colour, colourings, S=4):
 MEASURED_TRAFFIC = {
     "image1024": dict(kernel="lattice_quad_kernel<64, 768, 3>", bytes=8_453_120,
                       sources={"lattice_quad.cu": "3e536b8a589e6c22b7f1aba7c5e3716f3208f0447ead67715aa4bb57c7f70589",
-                               "gmrf_device.cuh": "39dd162e40198562e4f6096d6291842e9ce4389b3f5971fd3146620dcaa1a298",
+                               "gmrf_device.cuh": "a784a897b639feac1b61e7c197dbaf133ab26f487aff9ca2fd2e6c842752080e",
                                "gmrf_internal.h:FusedArgs": "56db942c013e0b5fb3ff98aff46cecf959fbee26d7386333c58679d8093d2d9c"}),
     "volume256": dict(kernel="colour_step_kernel<float, 4, 2, 0>", bytes=316_079_104 + 234_375_936,
                       sources={"sweep_kernels.cu": "95c871825e2a079b5a0bb4b0b74fbd7c65b21600f185e373b04275a78ad91a90",
-                               "gmrf_device.cuh": "39dd162e40198562e4f6096d6291842e9ce4389b3f5971fd3146620dcaa1a298",
+                               "gmrf_device.cuh": "a784a897b639feac1b61e7c197dbaf133ab26f487aff9ca2fd2e6c842752080e",
                                "gmrf_internal.h:StepArgs": "92f72ecd2bdcf4f1a8a8ea7c6a9e397d592dc5203447eb7e18789f620b4efb11"}),
 }
 
