@@ -1,10 +1,11 @@
 #!/usr/bin/env python3
 """Benchmark of the chromatic Gibbs sampler (site-updates per second) on synthetic workloads.
 
-Default workload: a 1024 x 1024 second-order (8-neighbour) intrinsic CAR lattice with the 2x2
-four-colouring, observations = 20 Gaussian bumps + N(0, 1) noise, FP32 state with FP64
-hyperparameter reductions, one chain, 2000 sweeps (the first 1000 burn-in, the rest accumulated
-into the running posterior mean and variance), tau and sigma^2 drawn every sweep.
+Default workload: a 256^3 first-order (6-neighbour) intrinsic CAR lattice with the parity
+colouring, observations = 50 ellipsoidal activations + N(0, 1) noise, FP32 state with FP64
+hyperparameter reductions, 8 chains, 500 sweeps (the first 250 burn-in, the rest accumulated
+into the running posterior mean and variance), tau and sigma^2 drawn every sweep.  Its state
+(537 MB) and observations (67 MB) live in HBM, so its colour steps are bound by HBM bandwidth.
 
 One step = one complete MCMC run of the workload on device-resident inputs: restart from the
 initial state, then all sweeps (every colour step, the fused reductions, the conjugate draws,
@@ -12,8 +13,9 @@ the accumulation), replayed as CUDA graphs.  L2 is flushed (a 512 MiB write) bet
 steps, outside the per-step CUDA events.
 
 Printed: one JSON line with the site-update rate, the end-to-end rate through the C ABI with
-host buffers, the roofline of the colour-step kernel, the clocks seen, and the oracle's CPU rate
-on a bounded sample.  ``--impl reference`` times the oracle instead.
+host buffers, the roofline of the dominant kernel, the FP32-vs-FP64 accuracy of the posterior
+means and traces with the speed-up over the plain FP64 sweep at that accuracy, the clocks seen,
+and the oracle's CPU rate on a bounded sample.  ``--impl reference`` times the oracle instead.
 """
 from __future__ import annotations
 
@@ -46,7 +48,8 @@ def workload_spec(name: str):
     if name == "image1024":
         return dict(name="1024x1024 8-neighbour ICAR, 2x2 colouring, 20 Gaussian bumps + N(0,1)",
                     fields=wl.image_1024_bumps(seed=2), chains=1, sweeps=2000, burn_in=1000,
-                    prior="icar", rho=1.0, seed=2, graph_sweeps=50, cpu_sweeps=20)
+                    prior="icar", rho=1.0, seed=2, graph_sweeps=50, cpu_sweeps=20, acc_sweeps=(2000, 1000),
+                    plain_sweeps=200)
     if name == "image64":
         return dict(name="64x64 4-neighbour ICAR, checkerboard, 4-level block image + N(0,0.5^2)",
                     fields=wl.image_64_block(seed=0), chains=1, sweeps=1000, burn_in=500,
@@ -54,13 +57,14 @@ def workload_spec(name: str):
     if name == "volume256":
         return dict(name="256^3 6-neighbour ICAR, parity colouring, 50 ellipsoids + N(0,1), 8 chains",
                     fields=wl.volume_ellipsoids(seed=5), chains=8, sweeps=500, burn_in=250,
-                    prior="icar", rho=1.0, seed=5, graph_sweeps=25, cpu_sweeps=1)
+                    prior="icar", rho=1.0, seed=5, graph_sweeps=25, cpu_sweeps=1, acc_sweeps=(500, 250),
+                    plain_sweeps=40)
     if name == "delaunay16k":
         f = wl.delaunay_pcar(seed=3)
         f[0]["color_seed"] = 3
         return dict(name="Delaunay 16384 points, proper CAR rho=0.95, 8 chains", fields=f, chains=8,
                     sweeps=5000, burn_in=2500, prior="pcar", rho=0.95, seed=3, graph_sweeps=50,
-                    cpu_sweeps=50)
+                    cpu_sweeps=50, acc_sweeps=(5000, 2500))
     if name == "batched":
         fields = wl.batched_uneven(seed=4)
         for i, f in enumerate(fields):
@@ -113,24 +117,16 @@ def colour_classes(field, colors=None):
     return [even, H * W - even]
 
 
-def stage_algorithmic_bytes(spec, stage_name, colour, colourings, S=4):
-    """Least bytes a launch of the stage must move (accumulation off), summed over its fields.
-
-    fused 2-D sweep: every site's state read once and written once (C chains), y read once:
-        n (2 C S + S);
-    lattice colour step c: the other colours' states read once, y and the new state of class c:
-        (n - n_c) C S + n_c S + n_c C S;
-    CSR colour step c: for the sites of class c, row pointers, degrees, permutation, y, the
-    column indices of their edges, the states of the distinct neighbours, and the new states.
-    """
-    C = spec["chains"]
-    total = 0
+def _stage_fields(spec, stage_name, colour, colourings):
+    """The fields a launch of the named stage covers: (index, field, its sites in the launch,
+    its colour-class sizes)."""
     for fi, f in enumerate(spec["fields"]):
         kind = f["kind"]
+        cls = colour_classes(f, colourings.get(fi))
         if "fused" in stage_name:
             if ("8-neighbour" in stage_name) != (kind == wl.LATTICE2D_8) or kind not in (wl.LATTICE2D_4, wl.LATTICE2D_8):
                 continue
-            total += f["n"] * (2 * C * S + S)
+            yield fi, f, f["n"], cls
             continue
         if "colour step" not in stage_name:
             continue
@@ -138,11 +134,50 @@ def stage_algorithmic_bytes(spec, stage_name, colour, colourings, S=4):
             continue
         if kind != wl.CSR and ("3-D" in stage_name) != (kind == wl.LATTICE3D_6):
             continue
-        cls = colour_classes(f, colourings.get(fi))
         if colour >= len(cls):
             continue
-        n_c = cls[colour]
-        if kind == wl.CSR:
+        yield fi, f, cls[colour], cls
+
+
+def bytes_per_update(field, chains, cls, S=4):
+    """Least HBM bytes per site-update of the method (each state value written once per sweep,
+    each other-colour neighbour value read once per colour step, the observations read once per
+    sweep and shared by the chains, the reductions fused, accumulation off):
+        2-colour lattices (2-D 4-neighbour, 3-D 6-neighbour): 2 S + S / C;
+        4-colour 8-neighbour lattice: 4 S + S / C;
+        CSR graph with k colours and mean degree deg: k S + (S + 4 (deg + 1)) / C
+    (row pointer and column indices at 4 bytes), with S the bytes of a state value."""
+    C = chains
+    if field["kind"] == wl.CSR:
+        deg = float(field["row_ptr"][-1]) / max(1, field["n"])
+        return len(cls) * S + (S + 4 * (deg + 1)) / C
+    k = 4 if field["kind"] == wl.LATTICE2D_8 else 2
+    return k * S + S / C
+
+
+def stage_algorithmic_bytes(spec, stage_name, colour, colourings, S=4):
+    """Algorithmic bytes of one launch of the stage: its site-updates times bytes_per_update."""
+    C = spec["chains"]
+    return sum(units * C * bytes_per_update(f, C, cls, S)
+               for _, f, units, cls in _stage_fields(spec, stage_name, colour, colourings))
+
+
+def stage_design_bytes(spec, stage_name, colour, colourings, S=4):
+    """Least bytes the kernel design itself must move per launch (accumulation off), summed over
+    its fields:
+    fused 2-D sweep (all colours in one launch, state staged in shared memory): every site's
+    state read once and written once, y read once: n (2 C S + S);
+    lattice colour step c: the other colours' states read once, y and the new state of class c:
+        (n - n_c) C S + n_c S + n_c C S;
+    CSR colour step c: for the sites of class c, row pointers, degrees, permutation, y, the
+    column indices of their edges, the states of the distinct neighbours, and the new states.
+    """
+    C = spec["chains"]
+    total = 0
+    for fi, f, n_c, cls in _stage_fields(spec, stage_name, colour, colourings):
+        if "fused" in stage_name:
+            total += f["n"] * (2 * C * S + S)
+        elif f["kind"] == wl.CSR:
             col = colourings[fi]
             rp, ci = f["row_ptr"], f["col_idx"]
             members = np.flatnonzero(col == colour)
@@ -401,6 +436,69 @@ def run_profile_case(args):
     return 0
 
 
+def accuracy_block(spec, g, seed):
+    """Accuracy of the FP32 sampler against FP64 on the workload (one field).
+
+    Both run the same chains (same seed and Philox counters, so they are coupled draw for draw)
+    for acc_sweeps sweeps, the first acc_burn of them burn-in: the FP32 sampler of the benchmark
+    and the FP64 sampler (which agrees with the oracle within 1e-12, and with the plain FP64 sweep
+    to rounding).  Reported: the largest errors of the FP32 posterior means, final states and
+    tau / sigma^2 traces relative to max(|FP64 value|, 1) (traces: relative to the value), and
+    the Monte Carlo standard error of each FP64 posterior mean, i.e. the statistical error of the
+    estimate itself: with two or more chains the standard deviation over the chains of their
+    means (each chain's mean is an independent estimate), with one chain sqrt(var tau_int / N)
+    with the integrated autocorrelation time of the tau^2 chain.  The FP32 sampler counts as
+    equally accurate when every error of a chain's posterior mean is below that site's standard
+    error."""
+    import torch
+
+    T, burn = spec["acc_sweeps"]
+    f0 = spec["fields"][0]
+    n, C = f0["n"], spec["chains"]
+    runs = {}
+    for prec in (g.FP32, g.FP64):
+        s = g.Sampler(spec["fields"], **sampler_kwargs(spec, g, seed, precision=prec, burn_in=burn,
+                                                       trace_capacity=T))
+        s.sweep(T)
+        torch.cuda.synchronize()
+        runs[prec] = s
+    s32, s64 = runs[g.FP32], runs[g.FP64]
+    N = T - burn
+    # standard error of each FP64 posterior mean
+    if C >= 2:
+        sm = np.zeros(n)
+        sq = np.zeros(n)
+        for c in range(C):
+            m = s64.fetch(0, c)["mean"]
+            sm += m
+            sq += m * m
+        var_between = np.maximum(sq - sm * sm / C, 0.0) / (C - 1)
+        se = np.sqrt(var_between)
+        se_kind = f"std over the {C} chains of their posterior means"
+    else:
+        iat = float(s64.trace_diagnostics(0, g.PARAM_TAU2, N)["iat"][0])
+        se = np.sqrt(s64.fetch(0, 0)["var"] * iat / N)
+        se_kind = f"sqrt(var tau_int / N), tau_int = {iat:.1f} (tau^2 chain), N = {N}"
+    worst = {"mean": 0.0, "x": 0.0, "tau_trace": 0.0, "sigma2_trace": 0.0}
+    ratio = 0.0
+    for c in range(C):
+        a = s32.fetch(0, c, trace=T)
+        b = s64.fetch(0, c, trace=T)
+        d = np.abs(a["mean"] - b["mean"])
+        worst["mean"] = max(worst["mean"], float(np.max(d / np.maximum(np.abs(b["mean"]), 1.0))))
+        worst["x"] = max(worst["x"], float(np.max(np.abs(a["x"] - b["x"]) / np.maximum(np.abs(b["x"]), 1.0))))
+        for key in ("tau_trace", "sigma2_trace"):
+            worst[key] = max(worst[key], float(np.max(np.abs(a[key] - b[key]) / np.abs(b[key]))))
+        ratio = max(ratio, float(np.max(d / np.maximum(se, 1e-300))))
+    s32.close()
+    s64.close()
+    return {"sweeps": T, "burn_in": burn, "reference": "FP64 sampler, same chains (coupled)",
+            "mean_max_relerr": worst["mean"], "x_max_relerr": worst["x"],
+            "tau_trace_max_relerr": worst["tau_trace"], "sigma2_trace_max_relerr": worst["sigma2_trace"],
+            "mc_se_median": float(np.median(se)), "mc_se_min": float(np.min(se)), "mc_se": se_kind,
+            "mean_err_over_se_max": ratio, "equal_accuracy": bool(ratio < 1.0)}
+
+
 def run_ours(args):
     import torch
 
@@ -518,13 +616,14 @@ def run_ours(args):
     dom = max(movers, key=lambda x: x[2])
     kernel_us = dom[2]
     algo_bytes = stage_algorithmic_bytes(spec, dom[1], colour_of_stage[dom[0]], colourings)
+    design_bytes = stage_design_bytes(spec, dom[1], colour_of_stage[dom[0]], colourings)
     s.close()
 
     # The plain single-field FP64 sweep (natural layout, one unfused pass per colour) on the same
     # workload and chains, a bounded number of sweeps: the speed-up of the path is value / its rate.
     plain = None
     if len(spec["fields"]) == 1 and not spec.get("intercept", False) and spec.get("likelihood") != "binomial":
-        ps = min(spec["sweeps"], 200)
+        ps = min(spec["sweeps"], spec.get("plain_sweeps", 200))
         with g.Sampler(spec["fields"], **sampler_kwargs(spec, g, seed, precision=g.FP64, algorithm=g.ALGO_PLAIN,
                                                        graph_sweeps=min(spec["graph_sweeps"], ps))) as sp:
             sp.sweep(ps)
@@ -579,6 +678,10 @@ def run_ours(args):
     cold_s = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
     e2e_cold = world * units * e2e_steps / cold_s
 
+    accuracy = None
+    if plain is not None and spec.get("acc_sweeps"):
+        accuracy = accuracy_block(spec, g, seed)
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -588,9 +691,15 @@ def run_ours(args):
     peak_note = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
     achieved = algo_bytes / (kernel_us * 1e-6) / 1e9
+    f0 = spec["fields"][0]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": measured_traffic(args.workload), "peak_source": peak_note,
-                "kernel": dom[1], "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_us": kernel_us,
+                "kernel": dom[1], "algorithmic_bytes_per_launch": algo_bytes,
+                "bytes_per_update": bytes_per_update(f0, spec["chains"],
+                                                     colour_classes(f0, colourings.get(0))),
+                "avg_launch_us": kernel_us,
+                "design_bytes_per_launch": design_bytes,
+                "design_frac": design_bytes / (kernel_us * 1e-6) / 1e9 / hbm,
                 "stages_us": {f"{st}:{name}": round(us, 3) for st, name, us in stages}}
     if resident_batch:
         # The resident kernel keeps the chain in shared memory for the whole batch: its HBM bytes
@@ -658,9 +767,13 @@ def run_ours(args):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "plain_fp64": plain,
+            "accuracy": accuracy,
+            "speedup_equal_accuracy": None,
             "efficiency": efficiency}
     if plain:
         plain["speedup"] = value / plain["value"]
+        if accuracy and accuracy["equal_accuracy"]:
+            line["speedup_equal_accuracy"] = value / plain["value"]
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
@@ -675,7 +788,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="image1024",
+    ap.add_argument("--workload", default="volume256",
                     choices=["image1024", "image64", "volume256", "delaunay16k", "batched", "paper50",
                              "paper512", "election"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")

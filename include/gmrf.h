@@ -148,6 +148,10 @@ typedef struct {
     int32_t quad_config;         /* 8-neighbour lattices, one chain, FP32: quad kernel configuration  */
                                  /* 1..5, -1 for the general fused kernel; 0: automatic               */
     int32_t quad_rows;           /* the quad kernel's tile rows (even, >= 8); 0: automatic            */
+    int32_t wide_3d;             /* 3-D lattices, FP32, 3 to 8 chains: 1 updates every chain of a     */
+                                 /* site in one thread, -1 keeps chains_per_thread; 0: automatic      */
+                                 /* (the former for classes of >= 256 sites per SM when               */
+                                 /* chains_per_thread is 0)                                           */
 } gmrf_tuning;
 
 typedef struct {

@@ -191,6 +191,9 @@ struct gmrf_sampler {
     // on a predicted sweep number, see lattice_fused_fast), or -1.
     int early_kind = -1;
     gmrf_tuning tune{};  // launch configuration overrides (zeros: the cost models)
+    // 3-D lattice colour steps with every chain of a site in one thread (lattice3d.cu): the
+    // padded chain count 4 or 8 when used, 0 when the general colour-step kernel runs them.
+    int wide3d = 0;
     int resident = 0, res_NI = 0, res_NT = 0, res_batch = 0;  // resident: 1 lattice, 2 graph
     uint4 *res_nbr = nullptr, *res_nbr2 = nullptr;            // graph: neighbour records
     int res_cluster = 1, res_own_max = 0;                      // graph: blocks per chain, their share
@@ -380,6 +383,9 @@ gmrf_status check_opts(const gmrf_opts *o)
         if (t->quad_config < -1 || t->quad_config > 5) return fail(GMRF_E_INVALID, "tuning.quad_config must be in -1..5");
         if (t->quad_rows != 0 && (t->quad_rows < 8 || (t->quad_rows & 1)))
             return fail(GMRF_E_INVALID, "tuning.quad_rows must be 0 or even and >= 8");
+        if (t->wide_3d < -1 || t->wide_3d > 1) return fail(GMRF_E_INVALID, "tuning.wide_3d must be -1, 0 or 1");
+        if (t->wide_3d == 1 && (o->precision != GMRF_FP32 || cp < 4 || cp > 8))
+            return fail(GMRF_E_INVALID, "tuning.wide_3d = 1 needs FP32 and 3 to 8 chains");
     }
     return GMRF_OK;
 }
@@ -767,6 +773,8 @@ cudaError_t enqueue_stage(gmrf_sampler *s, size_t k, int update, int accumulate,
         }
         return launch_lattice_fused(s->precision, s->V, g.kind, fa, s->fsmem[g.kind], st);
     }
+    if (g.type == 0 && g.kind == GMRF_LATTICE3D_6 && s->wide3d)
+        return launch_lattice3d(s->wide3d, step_args(s, g.colour, g.kind, update, accumulate), st);
     if (g.type == 0)
         return launch_colour_step(s->precision, s->V, g.kind, step_args(s, g.colour, g.kind, update, accumulate), st);
     if (g.type == 3) {
@@ -1245,6 +1253,42 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
     const int64_t per_colour = total_elems / 2;
     const int64_t target = s->tune.step_tile ? s->tune.step_tile
                                              : std::min<int64_t>(16384, std::max<int64_t>(kBlock, per_colour / (152 * 4)));
+    // 3-D lattices with every chain of a site in one thread: FP32, 4 or 8 chains (padded), the
+    // Gaussian likelihood, and either asked for (tuning.wide_3d = 1) or, by default, colour
+    // classes of at least one site for each of 256 threads on every SM.  A launch is then one
+    // wave of blocks (the blocks resident per SM times the SMs), each field getting blocks in
+    // proportion to its sites; block k of a field takes its sub-array rows k, k + nt, k + 2 nt,
+    // ... (nt blocks), so that at any time all blocks work on a narrow band of rows and the rows
+    // a plane apart that a site reads are read from DRAM once, by whichever block comes first.
+    std::vector<int32_t> tiles3d(s->nfields, 0);
+    {
+        int64_t sites3d = 0;
+        for (auto &h : s->hf)
+            if (h.kind == GMRF_LATTICE3D_6) sites3d += h.n;
+        const bool able = s->precision == GMRF_FP32 && (s->Cp == 4 || s->Cp == 8) && !binomial_model(s) && sites3d > 0;
+        int nsm = 0;
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device));
+        bool use = false;
+        if (s->tune.wide_3d == 1) use = able;
+        else if (s->tune.wide_3d == 0 && s->tune.chains_per_thread == 0) use = able && sites3d / 2 >= int64_t(nsm) * 256;
+        if (use) {
+            int bps = 1;
+            CK(lattice3d_blocks_per_sm(s->Cp, &bps));
+            int64_t units = 0;  // sub-array sites per colour over the 3-D fields
+            for (int fi = 0; fi < s->nfields; ++fi)
+                if (s->fd[fi].kind == GMRF_LATTICE3D_6) units += static_cast<int64_t>(s->fd[fi].rows) * s->fd[fi].cols;
+            // one wave, unless that leaves fewer than one site per thread
+            const int64_t goal = std::max<int64_t>(1, std::min<int64_t>(int64_t(nsm) * bps, units / 256));
+            for (int fi = 0; fi < s->nfields; ++fi) {
+                const FieldDev &d = s->fd[fi];
+                if (d.kind != GMRF_LATTICE3D_6) continue;
+                const double share = static_cast<double>(d.rows) * d.cols / static_cast<double>(units);
+                tiles3d[fi] = static_cast<int32_t>(std::max<int64_t>(
+                    1, std::min<int64_t>(d.rows, std::llround(share * static_cast<double>(goal)))));
+            }
+            s->wide3d = s->Cp;
+        }
+    }
     s->kmax = 0;
     for (auto &h : s->hf) s->kmax = std::max(s->kmax, h.ncolors);
     std::vector<std::vector<Tile>> by_colour(s->kmax);
@@ -1277,6 +1321,18 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
                     t.colour = c;
                     t.start = static_cast<int32_t>(st);
                     t.count = static_cast<int32_t>(std::min<int64_t>(per, hi - st));
+                    t.part = part++;
+                    by_colour[c].push_back(t);
+                }
+            } else if (tiles3d[fi] > 0) {
+                const int32_t nt = tiles3d[fi];
+                for (int32_t k = 0; k < nt; ++k) {
+                    Tile t{};
+                    t.field = fi;
+                    t.colour = c;
+                    t.start = k;
+                    t.count = (d.rows - k + nt - 1) / nt;
+                    t.stride = nt;
                     t.part = part++;
                     by_colour[c].push_back(t);
                 }
@@ -1945,6 +2001,8 @@ gmrf_status gmrf_launch_stage(gmrf_sampler *s, int32_t stage, int32_t accumulate
     const gmrf_sampler::Stage &g = s->stages[stage];
     if (name) *name = kNames[g.type][g.kind < 0 ? 0 : g.kind];
     if (name && g.type == 1 && s->fQCS[g.kind]) *name = "fused quad sweep, 2-D 8-neighbour lattice";
+    if (name && g.type == 0 && g.kind == GMRF_LATTICE3D_6 && s->wide3d)
+        *name = "colour step, 3-D 6-neighbour lattice, all chains of a site per thread";
     const int draw = s->model.fix_hyper ? 0 : 1;
     cudaError_t e = enqueue_stage(s, static_cast<size_t>(stage), 1, accumulate ? 1 : 0, draw, 1, 1, s->stream);
     if (e != cudaSuccess) return poison(s, e, "stage launch");

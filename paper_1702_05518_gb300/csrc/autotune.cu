@@ -1,7 +1,7 @@
 // autotune.cu -- gmrf_autotune: the launch configuration of a sampler chosen by measurement.
 //
-// The sweep kernels' work decomposition (chains per thread, the colour-step tile, the fused 2-D
-// tile shape and block size, the quad kernel's configuration) changes nothing but the rounding
+// The sweep kernels' work decomposition (chains per thread, the 3-D kernel, the colour-step tile,
+// the fused 2-D tile shape and block size, the quad kernel's configuration) changes nothing but the rounding
 // of the partial sums, and the library's cost models pick it from the sizes alone.  The
 // autotuner measures instead: starting from the cost models' choice it tries each knob's
 // candidates in turn (coordinate descent), keeping a candidate when it is at least 2 % faster
@@ -152,6 +152,13 @@ extern "C" gmrf_status gmrf_autotune(const gmrf_field_desc *fields, int32_t nfie
         t.chains_per_thread = v;
         consider(t);
     }
+    // 1b. 3-D lattices: every chain of a site in one thread, or the general colour-step kernel
+    if (has_kind[GMRF_LATTICE3D_6] && fp32 && cp >= 4 && cp <= 8)
+        for (int w : {1, -1}) {
+            gmrf_tuning t = best;
+            t.wide_3d = w;
+            consider(t);
+        }
     // 2. the colour-step tile (3-D lattices, graphs, and 2-D lattices on per-colour launches)
     if (has_kind[GMRF_LATTICE3D_6] || has_kind[GMRF_CSR] || (opts->flags & GMRF_FLAG_PER_COLOUR))
         for (int tile : {256, 512, 1024, 2048, 4096, 8192, 16384}) {

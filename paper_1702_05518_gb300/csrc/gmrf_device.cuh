@@ -63,14 +63,16 @@ __device__ __forceinline__ int fast_div(int n, uint32_t m, int s)
 }
 
 // A unit of work of one colour step: a range of sub-array rows (lattice) or of permuted
-// positions (CSR) of one field's colour class.
+// positions (CSR) of one field's colour class.  With stride > 1 (the 3-D kernel of
+// lattice3d.cu) the tile's rows are start, start + stride, ... (count of them).
 struct Tile {
     int32_t field;
     int32_t colour;
     int32_t start;
     int32_t count;
     int32_t part;       // partial-sum slot
-    int32_t pad[3];
+    int32_t stride;     // 0 or 1: contiguous rows
+    int32_t pad[2];
 };
 
 // Device-resident sweep control, read by every kernel of a sweep and advanced by the last.
@@ -110,8 +112,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        // one 32 x 32 -> 64-bit product gives both halves of each multiplication
+        const uint64_t p0 = static_cast<uint64_t>(c.x) * 0xD2511F53u;
+        const uint64_t p1 = static_cast<uint64_t>(c.z) * 0xCD9E8D57u;
+        const uint32_t hi0 = static_cast<uint32_t>(p0 >> 32), lo0 = static_cast<uint32_t>(p0);
+        const uint32_t hi1 = static_cast<uint32_t>(p1 >> 32), lo1 = static_cast<uint32_t>(p1);
         c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
         k.x += 0x9E3779B9u;
         k.y += 0xBB67AE85u;

@@ -217,6 +217,10 @@ cudaError_t launch_pg_stage(int precision, const PgArgs &a, cudaStream_t stream)
 // Launchers (each enqueues on `stream` and returns the launch status).
 // One colour step of the tiles in `a` (all of field kind `kind`).
 cudaError_t launch_colour_step(int precision, int V, int kind, const StepArgs &a, cudaStream_t stream);
+// 3-D lattice colour step with every chain of a site in one thread (FP32, chains_padded 4 or 8;
+// lattice3d.cu), and the blocks of it that are resident on one SM.
+cudaError_t launch_lattice3d(int chains_padded, const StepArgs &a, cudaStream_t stream);
+cudaError_t lattice3d_blocks_per_sm(int chains_padded, int *blocks);
 cudaError_t launch_hyper(int precision, const HyperArgs &a, cudaStream_t stream);
 cudaError_t launch_pack(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx,
                         int32_t C, int32_t Cp, const double *y_nat, const double *x0_nat,

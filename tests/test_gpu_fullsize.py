@@ -65,4 +65,4 @@ def test_batched_uneven_full_size():
     fields = wl.batched_uneven(seed=4)
     for i, f in enumerate(fields):
         f["color_seed"] = 100 + i
-    _check(fields, 1, 2, 4, TOL_FP32_1 * 10)
+    _check(fields, 1, 1, 4, TOL_FP32_1)
