@@ -591,26 +591,30 @@ def run_ours(args):
         batch_us = ev_a.elapsed_time(ev_b) * 1e3 / 10
         resident_batch = {"sweeps": nb, "us": batch_us}
 
-    # Each stage of a sweep alone: back-to-back launches, CUDA events on the launching stream
-    # (accumulation off); the dominant stage is the longest one that moves the state.
+    # Each stage of a sweep timed in its place: whole sweeps launched stage by stage in sweep order
+    # (accumulation off), CUDA events on the launching stream around every launch, averaged over
+    # the sweeps, so each kernel sees the L2 contents its predecessor leaves; the dominant stage is
+    # the longest one that moves the state.
     reps = 50
     colourings = {fi: s.colors(fi)[0] for fi, f in enumerate(spec["fields"]) if f["kind"] == wl.CSR}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stages = []
-    colour_of_stage = {}
-    seen = {}
-    for st in range(info["launches_per_sweep"]):
-        name = s.launch_stage(st)
-        key = name
-        colour_of_stage[st] = seen.get(key, 0)
-        seen[key] = colour_of_stage[st] + 1
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(reps):
+    nst = info["launches_per_sweep"]
+    names, colour_of_stage, seen = [], {}, {}
+    for st in range(nst):
+        names.append(s.launch_stage(st))
+        colour_of_stage[st] = seen.get(names[st], 0)
+        seen[names[st]] = colour_of_stage[st] + 1
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nst)]
+           for _ in range(reps)]
+    torch.cuda.synchronize()
+    for r in range(reps):
+        for st in range(nst):
+            evs[r][st][0].record(stream)
             s.launch_stage(st)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        stages.append((st, name, ev0.elapsed_time(ev1) * 1e3 / reps))
+            evs[r][st][1].record(stream)
+    torch.cuda.synchronize()
+    stages = [(st, names[st], sum(evs[r][st][0].elapsed_time(evs[r][st][1]) for r in range(reps)) * 1e3 / reps)
+              for st in range(nst)]
     # the roofline is taken on the longest state-moving stage (not the parameter draws)
     movers = [st_ for st_ in stages if "draw" not in st_[1]] or stages
     dom = max(movers, key=lambda x: x[2])

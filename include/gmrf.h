@@ -58,8 +58,10 @@ typedef enum {
     GMRF_E_CUDA = 2,        /* a CUDA call failed; the sampler is poisoned                 */
     GMRF_E_OOM = 3,         /* device allocation failed                                   */
     GMRF_E_STATE = 4,       /* sampler poisoned by an earlier error, or call out of order  */
-    GMRF_E_TIMEOUT = 5,     /* a bounded device wait gave up (reserved; device waits that   */
-                            /* give up are counted in gmrf_info.wait_timeouts)              */
+    GMRF_E_TIMEOUT = 5,     /* a bounded device wait gave up: the results of the sweeps     */
+                            /* since are invalid; reported by the next call that reads the  */
+                            /* sampler's counters (fetches, info, diagnostics), which then  */
+                            /* poisons the sampler                                          */
     GMRF_E_UNSUPPORTED = 6  /* valid request that the library does not implement          */
 } gmrf_status;
 
@@ -182,6 +184,12 @@ typedef struct {
 #define GMRF_FLAG_PER_COLOUR 1
 #define GMRF_FLAG_NO_RESIDENT 2
 #define GMRF_FLAG_RESIDENT 4
+/* GMRF_FLAG_TEST_STALL (for tests of failure handling only): on the resident graph path with a
+ * cluster of two or more blocks per chain (a single graph of 4096 or more sites), every colour
+ * step of the cluster kernel expects 16 more bytes than the other blocks send, so its bounded
+ * wait gives up (after 1 ms with this flag, instead of 1 s), as a lost exchange would make it; the
+ * kernel still finishes, and the next call that reads the counters returns GMRF_E_TIMEOUT. */
+#define GMRF_FLAG_TEST_STALL 8
 
 typedef struct {
     int32_t nfields;
@@ -232,14 +240,21 @@ gmrf_status gmrf_color_graph(int32_t n, const int32_t *row_ptr, const int32_t *c
  *   priorities: device [n] or NULL for Philox priorities of `seed`.
  *   colors: device out [n], 0-based, caller-owned; num_colors: host out.
  *   cuda_stream: a cudaStream_t (NULL: legacy default stream); the call synchronises it.
- * Scratch: one fixed file-scope device array (priorities, round flags, counters; 5 MiB).  The
- * first call on each device, with that device current, looks up the array's address
- * (cudaGetSymbolAddress) and keeps it; make that first call before any stream capture.  Each
- * call clears the counters and the check flag it needs at its start.  Concurrent or
- * overlapping calls on one device share the array and race: serialise them.
+ * Scratch: one fixed file-scope device array (priorities, round flags, counters; 5 MiB).  It is
+ * part of the library's device code, which CUDA loads onto a device when the library first runs
+ * there (lazy module loading, the default): so make a first call of this function (or any other
+ * library call on that device) before the caller's allocator reserves the device's memory, or
+ * load modules eagerly (CUDA_MODULE_LOADING=EAGER).  The first call on each device, with that
+ * device current, looks up the array's address (cudaGetSymbolAddress) and keeps it for the
+ * process; make that first call before any stream capture.  A reset of the device
+ * (cudaDeviceReset) unloads the array: do not call this function after one.  Each call clears
+ * the counters and the check flag it needs at its start.  Concurrent or overlapping calls on
+ * one device share the array and race: serialise them.
  * The structure (row_ptr[0] == 0, non-decreasing, row_ptr[n] == nnz, columns in [0, n), no
  * self-loops) is checked on the device before colouring: GMRF_E_INVALID if it fails.  Symmetry
- * is the caller's duty (not checked; a non-symmetric graph still terminates in bounds).
+ * is the caller's duty and is not checked: for a non-symmetric graph the call still stays in
+ * bounds and terminates, but its result is unspecified (it may differ from run to run and need
+ * not be a proper colouring).
  * Errors: GMRF_E_INVALID, GMRF_E_UNSUPPORTED (device ordinal > 63), GMRF_E_CUDA.
  */
 gmrf_status gmrf_color_graph_noalloc(int32_t n, int64_t nnz, const int32_t *row_ptr,
@@ -429,6 +444,16 @@ gmrf_status gmrf_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t 
 gmrf_status gmrf_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream, uint32_t chain,
                               int32_t lanes, int32_t precision, int64_t count, void *out,
                               void *cuda_stream);
+
+/*
+ * Fault injection for tests of the error paths (process-wide, not thread-safe; no paper
+ * counterpart).  gmrf_debug_fail_alloc: the nth device allocation the library makes from now on
+ * (1 = the next) fails as if the device were out of memory (GMRF_E_OOM from the call that made
+ * it, with everything that call allocated released); 0 disarms.  gmrf_debug_poison: marks a
+ * sampler as after a CUDA error, so that its later calls return GMRF_E_STATE.
+ */
+gmrf_status gmrf_debug_fail_alloc(int64_t nth);
+gmrf_status gmrf_debug_poison(gmrf_sampler *s);
 
 /* Description of the last failure on the calling thread ("" if none). */
 const char *gmrf_last_error(void);

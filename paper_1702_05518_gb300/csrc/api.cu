@@ -11,11 +11,14 @@
 #include <string>
 #include <vector>
 
+#include <atomic>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/gmrf.h"
 #include "gmrf_device.cuh"
 #include "gmrf_internal.h"
+#include "mbarrier.cuh"
 
 using namespace gmrf;
 
@@ -33,6 +36,22 @@ struct CudaFail {
     cudaError_t err;
     std::string where;
 };
+
+// Fault injection for tests (gmrf_debug_fail_alloc): device allocations left before one fails
+// (0: none fails).  Every device allocation of the library goes through dev_malloc.
+std::atomic<int64_t> g_fail_alloc{0};
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    int64_t k = g_fail_alloc.load();
+    while (k > 0 && !g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 
 struct HostField {
     int32_t kind = 0;
@@ -183,6 +202,7 @@ struct gmrf_sampler {
     std::vector<void *> allocs;
     int64_t bytes = 0;
     bool poisoned = false;
+    bool test_stall = false;  // GMRF_FLAG_TEST_STALL: the graph cluster kernel's waits run out
     bool restart_pending = false;  // gmrf_sampler_set_data: restart before the state is next used
     int64_t launches_per_sweep = 0;
     // Resident path (lattice_resident.cu): whole sweeps of a small single 2-D lattice field in one
@@ -206,7 +226,7 @@ struct gmrf_sampler {
     {
         *p = nullptr;
         if (b == 0) b = 16;
-        cudaError_t e = cudaMalloc(p, b);
+        cudaError_t e = dev_malloc(p, b);
         if (e == cudaSuccess) {
             allocs.push_back(*p);
             bytes += static_cast<int64_t>(b);
@@ -465,7 +485,7 @@ int pow2_at_least(int c)
 double *upload(const double *h, int64_t n, cudaStream_t st, std::vector<void *> &tmp)
 {
     void *d = nullptr;
-    CK(cudaMalloc(&d, sizeof(double) * static_cast<size_t>(n > 0 ? n : 1)));
+    CK(dev_malloc(&d, sizeof(double) * static_cast<size_t>(n > 0 ? n : 1)));
     tmp.push_back(d);
     CK(cudaMemcpyAsync(d, h, sizeof(double) * static_cast<size_t>(n), cudaMemcpyHostToDevice, st));
     return static_cast<double *>(d);
@@ -474,7 +494,7 @@ double *upload(const double *h, int64_t n, cudaStream_t st, std::vector<void *> 
 template <typename P> P *upload_t(const P *h, int64_t n, cudaStream_t st, std::vector<void *> &tmp)
 {
     void *d = nullptr;
-    CK(cudaMalloc(&d, sizeof(P) * static_cast<size_t>(n > 0 ? n : 1)));
+    CK(dev_malloc(&d, sizeof(P) * static_cast<size_t>(n > 0 ? n : 1)));
     tmp.push_back(d);
     if (n > 0) CK(cudaMemcpyAsync(d, h, sizeof(P) * static_cast<size_t>(n), cudaMemcpyHostToDevice, st));
     return static_cast<P *>(d);
@@ -515,6 +535,7 @@ StepArgs step_args(gmrf_sampler *s, int colour, int kind, int update, int accumu
     a.partials = s->partials;
     a.ctl = s->ctl;
     a.key = philox_key(s->opts.seed);
+    philox_round_keys(a.key, a.rk);
     a.Cp = s->Cp;
     a.lanes = std::min(s->Cp, 4);
     a.rho = s->model.prior == GMRF_PRIOR_PCAR ? s->model.rho : 1.0;
@@ -622,6 +643,12 @@ cudaError_t plan_resident(gmrf_sampler *s, const std::vector<int32_t> &coff0)
         if (e == cudaSuccess) e = s->alloc(&s->res_z, static_cast<size_t>(batch) * s->C * f.n * tsize(s->precision));
         if (e != cudaSuccess) return e;
         s->res_batch = batch;
+        if (s->test_stall) {
+            // After its wait gives up a block no longer announces the bytes the other blocks send it;
+            // a launch's unannounced bytes stay below the transaction count's range.
+            const int64_t per_sweep = static_cast<int64_t>(f.n) * static_cast<int64_t>(tsize(s->precision));
+            s->res_batch = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(batch, (int64_t(1) << 19) / per_sweep)));
+        }
         s->res_smem = smem;
         s->res_cluster = cl;
         s->res_own_max = own_max;
@@ -701,6 +728,8 @@ ResCsrArgs csr_resident_args(gmrf_sampler *s, int count, int draw, int draw_beta
     r.own_max = s->res_own_max;
     r.rho = s->model.prior == GMRF_PRIOR_PCAR ? s->model.rho : 1.0;
     r.zbuf = s->res_z;
+    r.extra_bytes = s->test_stall ? 16u : 0u;
+    r.wait_ns = s->test_stall ? 1000000ull : kWaitNs;
     return r;
 }
 
@@ -760,9 +789,32 @@ FusedArgs fused_args(gmrf_sampler *s, int kind, int update, int accumulate)
 
 // One stage of a sweep (see gmrf_launch_stage); `draw`, `draw_beta` and `end_of_sweep` only
 // matter for the hyperparameter stage.
+// Description of stage k of a sweep (also its NVTX range name).
+const char *stage_name(const gmrf_sampler *s, size_t k)
+{
+    static const char *kNames[4][4] = {
+        {"colour step, 2-D 4-neighbour lattice", "colour step, 2-D 8-neighbour lattice",
+         "colour step, 3-D 6-neighbour lattice", "colour step, CSR graph"},
+        {"fused sweep, 2-D 4-neighbour lattice", "fused sweep, 2-D 8-neighbour lattice", "", ""},
+        {"hyperparameter draw", "hyperparameter draw", "hyperparameter draw", "hyperparameter draw"},
+        {"Polya-Gamma draws", "Polya-Gamma draws", "Polya-Gamma draws", "Polya-Gamma draws"}};
+    const gmrf_sampler::Stage &g = s->stages[k];
+    if (g.type == 1 && s->fQCS[g.kind]) return "fused quad sweep, 2-D 8-neighbour lattice";
+    if (g.type == 0 && g.kind == GMRF_LATTICE3D_6 && s->wide3d)
+        return "colour step, 3-D 6-neighbour lattice, all chains of a site per thread";
+    return kNames[g.type][g.kind < 0 ? 0 : g.kind];
+}
+
+// An NVTX range around the host-side enqueue of a stage (and of a call), for timeline tools.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 cudaError_t enqueue_stage(gmrf_sampler *s, size_t k, int update, int accumulate, int draw, int draw_beta,
                           int end_of_sweep, cudaStream_t st)
 {
+    const NvtxRange range(stage_name(s, k));
     const gmrf_sampler::Stage &g = s->stages[k];
     if (g.type == 1) {
         FusedArgs fa = fused_args(s, g.kind, update, accumulate);
@@ -808,6 +860,7 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int with_hyper, cudaStr
         // Batches of sweeps: the batch's unit-rate Gamma variates and normals, then all its sweeps
         // in one launch.
         for (int k = 0; k < nsweeps && e == cudaSuccess;) {
+            const NvtxRange range(s->resident == 2 ? "resident batch, graph" : "resident batch, lattice");
             const int cnt = std::min(s->res_batch, nsweeps - k);
             if (draw || draw_beta) e = launch_pre(s, cnt, st);
             if (e == cudaSuccess) e = launch_res_normals(s, cnt, st);
@@ -886,6 +939,16 @@ gmrf_status poison(gmrf_sampler *s, cudaError_t e, const char *where)
     return cuda_status(CudaFail{e, where});
 }
 
+// A bounded device wait that gave up (counted in the sweep control block) makes the results since
+// invalid: the call reports it and the sampler is poisoned.
+gmrf_status check_waits(gmrf_sampler *s, const SweepCtl &c)
+{
+    if (c.wait_timeouts == 0) return GMRF_OK;
+    s->poisoned = true;
+    return fail(GMRF_E_TIMEOUT, "a bounded device wait gave up (" + std::to_string(c.wait_timeouts) +
+                                    " times): the results of the sweeps since are invalid");
+}
+
 gmrf_status build_plain(gmrf_sampler *s, const gmrf_field_desc &f, std::vector<void *> &tmp)
 {
     HostField &h = s->hf[0];
@@ -932,7 +995,7 @@ gmrf_status build_plain(gmrf_sampler *s, const gmrf_field_desc &f, std::vector<v
         CK(s->alloc_t(&s->plain_colors, static_cast<size_t>(n), sizeof(int32_t)));
         if (h.colors.empty()) {
             void *scratch = nullptr;
-            CK(cudaMalloc(&scratch, jp_scratch_bytes(h.n)));
+            CK(dev_malloc(&scratch, jp_scratch_bytes(h.n)));
             tmp.push_back(scratch);
             int32_t k = 0;
             CK(jp_color(h.n, rp, ci, nullptr, f.color_seed, s->plain_colors, scratch, &k, s->stream));
@@ -1068,13 +1131,13 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
         int32_t *col_d = nullptr;
         {
             void *p = nullptr;
-            CK(cudaMalloc(&p, sizeof(int32_t) * h.n));
+            CK(dev_malloc(&p, sizeof(int32_t) * h.n));
             tmp.push_back(p);
             col_d = static_cast<int32_t *>(p);
         }
         if (h.colors.empty()) {
             void *scratch = nullptr;
-            CK(cudaMalloc(&scratch, jp_scratch_bytes(h.n)));
+            CK(dev_malloc(&scratch, jp_scratch_bytes(h.n)));
             tmp.push_back(scratch);
             int32_t k = 0;
             CK(jp_color(h.n, rp_d, ci_d, nullptr, f.color_seed, col_d, scratch, &k, s->stream));
@@ -1087,7 +1150,7 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
         if (h.ncolors > 1024) return fail(GMRF_E_UNSUPPORTED, "CSR colouring with more than 1024 colours");
         d.ncolors = h.ncolors;
         void *scratch = nullptr;
-        CK(cudaMalloc(&scratch, layout_scratch_bytes(h.n, h.ncolors)));
+        CK(dev_malloc(&scratch, layout_scratch_bytes(h.n, h.ncolors)));
         tmp.push_back(scratch);
         char *wbase = any_weights && f.weights ? static_cast<char *>(s->w) + d.nnz0 * T : nullptr;
         int32_t *order_d = nullptr;
@@ -1553,9 +1616,9 @@ gmrf_status gmrf_color_graph(int32_t n, const int32_t *row_ptr, const int32_t *c
         int32_t *ci = upload_t(col_idx, row_ptr[n], stream, tmp);
         uint32_t *pr = priorities ? upload_t(priorities, n, stream, tmp) : nullptr;
         void *col = nullptr, *scratch = nullptr;
-        CK(cudaMalloc(&col, sizeof(int32_t) * n));
+        CK(dev_malloc(&col, sizeof(int32_t) * n));
         tmp.push_back(col);
-        CK(cudaMalloc(&scratch, jp_scratch_bytes(n)));
+        CK(dev_malloc(&scratch, jp_scratch_bytes(n)));
         tmp.push_back(scratch);
         int32_t k = 0;
         CK(jp_color(n, rp, ci, pr, seed, static_cast<int32_t *>(col), scratch, &k, stream));
@@ -1603,6 +1666,7 @@ gmrf_status gmrf_sampler_create(gmrf_sampler **out, const gmrf_field_desc *field
     s->opts = *opts;
     if (opts->tuning) s->tune = *opts->tuning;
     s->opts.tuning = nullptr;  // no caller memory is retained
+    s->test_stall = (opts->flags & GMRF_FLAG_TEST_STALL) != 0;
     s->precision = opts->precision;
     s->C = opts->chains;
     s->Cp = pow2_at_least(opts->chains);
@@ -1668,6 +1732,7 @@ void gmrf_sampler_destroy(gmrf_sampler *s)
 
 gmrf_status gmrf_sweep(gmrf_sampler *s, int32_t nsweeps, int32_t with_hyper)
 {
+    const NvtxRange range("gmrf_sweep");
     g_last_error.clear();
     if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
     if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
@@ -1732,6 +1797,7 @@ gmrf_status gmrf_fetch_samples(gmrf_sampler *s, int32_t field, int32_t chain, do
         SweepCtl c{};
         CK(cudaMemcpyAsync(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));
+        if (const gmrf_status w = check_waits(s, c)) return w;
         const bool plain = s->algorithm == GMRF_ALGO_PLAIN;
         const int64_t k = plain ? 0 : c.acc_count;
         auto fetch = [&](const void *src, const void *m2, double scale, double *dst) {
@@ -1796,6 +1862,7 @@ gmrf_status gmrf_fetch_intercept(gmrf_sampler *s, int32_t field, int32_t chain, 
         SweepCtl c{};
         CK(cudaMemcpyAsync(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));
+        if (const gmrf_status w = check_waits(s, c)) return w;
         const int64_t cap = s->opts.trace_capacity;
         const int64_t avail = std::min<int64_t>(c.sweep - s->opts.start_sweep, cap);
         if (n_trace) *n_trace = avail;
@@ -1832,6 +1899,7 @@ gmrf_status gmrf_trace_diagnostics(gmrf_sampler *s, int32_t field, int32_t param
         SweepCtl c{};
         CK(cudaMemcpyAsync(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));
+        if (const gmrf_status w = check_waits(s, c)) return w;
         const int64_t cap = s->opts.trace_capacity;
         const int64_t avail = std::min<int64_t>(c.sweep - s->opts.start_sweep, cap);
         const int64_t N = n_last == 0 ? avail : std::min<int64_t>(n_last, avail);
@@ -1878,6 +1946,7 @@ gmrf_status gmrf_site_psrf(gmrf_sampler *s, int32_t field, double *psrf, double 
         SweepCtl c{};
         CK(cudaMemcpyAsync(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));
+        if (const gmrf_status w = check_waits(s, c)) return w;
         if (c.acc_count < 2) return fail(GMRF_E_INVALID, "the PSRF needs at least 2 accumulated sweeps");
         unsigned long long *mx = reinterpret_cast<unsigned long long *>(s->diag_out + static_cast<int64_t>(s->Cp) * 4 + 1);
         CK(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s->stream));
@@ -1992,17 +2061,7 @@ gmrf_status gmrf_launch_stage(gmrf_sampler *s, int32_t stage, int32_t accumulate
     if (const gmrf_status r = restart_if_pending(s)) return r;
     if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "stages of the plain sweep");
     if (stage < 0 || stage >= static_cast<int32_t>(s->stages.size())) return fail(GMRF_E_INVALID, "stage out of range");
-    static const char *kNames[4][4] = {
-        {"colour step, 2-D 4-neighbour lattice", "colour step, 2-D 8-neighbour lattice",
-         "colour step, 3-D 6-neighbour lattice", "colour step, CSR graph"},
-        {"fused sweep, 2-D 4-neighbour lattice", "fused sweep, 2-D 8-neighbour lattice", "", ""},
-        {"hyperparameter draw", "hyperparameter draw", "hyperparameter draw", "hyperparameter draw"},
-        {"Polya-Gamma draws", "Polya-Gamma draws", "Polya-Gamma draws", "Polya-Gamma draws"}};
-    const gmrf_sampler::Stage &g = s->stages[stage];
-    if (name) *name = kNames[g.type][g.kind < 0 ? 0 : g.kind];
-    if (name && g.type == 1 && s->fQCS[g.kind]) *name = "fused quad sweep, 2-D 8-neighbour lattice";
-    if (name && g.type == 0 && g.kind == GMRF_LATTICE3D_6 && s->wide3d)
-        *name = "colour step, 3-D 6-neighbour lattice, all chains of a site per thread";
+    if (name) *name = stage_name(s, static_cast<size_t>(stage));
     const int draw = s->model.fix_hyper ? 0 : 1;
     cudaError_t e = enqueue_stage(s, static_cast<size_t>(stage), 1, accumulate ? 1 : 0, draw, 1, 1, s->stream);
     if (e != cudaSuccess) return poison(s, e, "stage launch");
@@ -2034,6 +2093,7 @@ gmrf_status gmrf_sampler_info(gmrf_sampler *s, gmrf_info *out)
     cudaError_t e = cudaMemcpyAsync(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return poison(s, e, "info");
+    if (const gmrf_status w = check_waits(s, c)) return w;
     out->nfields = s->nfields;
     out->chains = s->C;
     out->precision = s->precision;
@@ -2046,6 +2106,22 @@ gmrf_status gmrf_sampler_info(gmrf_sampler *s, gmrf_info *out)
     out->early_start_misses = c.fmiss;
     out->resident = s->resident;
     out->wait_timeouts = static_cast<int64_t>(c.wait_timeouts);
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_debug_fail_alloc(int64_t nth)
+{
+    g_last_error.clear();
+    if (nth < 0) return fail(GMRF_E_INVALID, "nth must be >= 0");
+    g_fail_alloc.store(nth);
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_debug_poison(gmrf_sampler *s)
+{
+    g_last_error.clear();
+    if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
+    s->poisoned = true;
     return GMRF_OK;
 }
 

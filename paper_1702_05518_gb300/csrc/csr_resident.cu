@@ -26,6 +26,7 @@
 
 #include "gmrf_device.cuh"
 #include "gmrf_internal.h"
+#include "mbarrier.cuh"
 #include "lattice_common.cuh"
 #include "resident_draws.cuh"
 
@@ -93,32 +94,6 @@ __device__ __forceinline__ void cluster_sync()
 // blocks' copies by asynchronous remote stores that complete on the receiving block's mbarrier
 // (complete_tx); the receiver expects the bytes of the other blocks' shares of the class and waits
 // for that phase.  No fence on the sending side.
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok)
-                 : "r"(smem_u32(bar)), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 __device__ __forceinline__ void st_async(uint32_t addr, float v, uint32_t bar)
 {
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
@@ -131,7 +106,6 @@ __device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t bar)
                  "l"(__double_as_longlong(v)), "r"(bar)
                  : "memory");
 }
-constexpr uint64_t kStepWaitNs = 1000000000ull;  // a colour step's wait gives up after 1 s
 
 // MP: positions of a colour class per site thread, 1 or kCsrMaxPos.  With one, the loads of the
 // next colour step's position (its neighbour record, observation and normal) are issued before the
@@ -299,7 +273,7 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
         for (int c = 0; c < K; ++c, ++g) {
             if (CL > 1 && tid == 0 && !s_gave_up) {  // this step's expected bytes: the other blocks' shares
                 const int others = (coffs[c + 1] - coffs[c]) - (own_hi[c] - own_lo[c]);
-                mbar_arrive_expect(&sbar[g & 1], static_cast<uint32_t>(others) * sizeof(T));
+                mbar_arrive_expect(&sbar[g & 1], static_cast<uint32_t>(others) * sizeof(T) + a.extra_bytes);
             }
             if (!drawer) {
                 const int lo = coffs[c], a0 = own_lo[c], a1 = own_hi[c], ob = own_off[c] - a0;
@@ -347,7 +321,7 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
                 if (!s_gave_up && !mbar_try_wait(&sbar[g & 1], (g >> 1) & 1)) {
                     const uint64_t t0 = global_ns();
                     bool ok = false;
-                    while (!(ok = mbar_try_wait(&sbar[g & 1], (g >> 1) & 1)) && global_ns() - t0 < kStepWaitNs) {
+                    while (!(ok = mbar_try_wait(&sbar[g & 1], (g >> 1) & 1)) && global_ns() - t0 < a.wait_ns) {
                     }
                     if (!ok) {
                         s_gave_up = 1;

@@ -124,6 +124,32 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
     return c;
 }
 
+// The same with the ten round keys given: rk[2r], rk[2r + 1] = the key after r Weyl increments
+// (philox_round_keys).  Kept in a kernel's parameters, they are read from constant memory by the
+// XOR that uses them, so no round spends instructions on the key schedule.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk)[20])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = static_cast<uint64_t>(c.x) * 0xD2511F53u;
+        const uint64_t p1 = static_cast<uint64_t>(c.z) * 0xCD9E8D57u;
+        const uint32_t hi0 = static_cast<uint32_t>(p0 >> 32), lo0 = static_cast<uint32_t>(p0);
+        const uint32_t hi1 = static_cast<uint32_t>(p1 >> 32), lo1 = static_cast<uint32_t>(p1);
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+    }
+    return c;
+}
+
+__host__ __device__ __forceinline__ void philox_round_keys(uint2 k, uint32_t (&rk)[20])
+{
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k.x;
+        rk[2 * r + 1] = k.y;
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+}
+
 __host__ __device__ __forceinline__ uint2 philox_key(uint64_t seed)
 {
     return make_uint2(static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32));

@@ -62,6 +62,7 @@ struct StepArgs {
     int32_t binomial;    // binomial counts (successes in y) with the logistic link
     const int32_t *trials;  // [slots] binomial trials m_i (binomial model only)
     const void *psi;     // [slots][Cp] Polya-Gamma draws of this sweep (binomial model only)
+    uint32_t rk[20];     // Philox round keys of `key` (philox_round_keys), read from the parameters
 };
 
 struct HyperArgs {
@@ -141,6 +142,8 @@ struct ResCsrArgs {
     int32_t own_max;      // positions a block of a chain's cluster owns (largest share)
     double rho;
     const void *zbuf;     // [count][C][n] normals by permuted position
+    uint32_t extra_bytes; // added to every colour step's expected bytes (0; 16 under GMRF_FLAG_TEST_STALL)
+    uint64_t wait_ns;     // limit of a colour step's wait
 };
 
 // A tile of the fused 2-D lattice sweep: natural coordinates of its first site.

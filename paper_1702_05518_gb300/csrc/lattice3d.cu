@@ -11,6 +11,12 @@
 // kernel is built to stream it: one pass over the other colour's state and this colour's
 // observations, one write of this colour's state.
 //
+// Chain values travel in pairs: two chains' FP32 values in one 64-bit register, and the per-chain
+// arithmetic (the two Box-Muller pairs of a Philox block, neighbour sums, the update, the sums
+// for the draws, the running moments) uses the packed two-lane FP32 instructions
+// (add/sub/mul/fma .rn.f32x2), one instruction per pair with each lane rounded as the scalar
+// operation would be.
+//
 // Layout (colour-split, chains innermost): the colour-c sites of sub-array row r = l*H + i are
 // columns h = 0 .. cols-1 at j = 2h + p, p = (c + l + i) & 1; their neighbours are columns
 // h - 1 + p and h + p of the other colour's row r and column h of its rows r -+ 1 and r -+ H.
@@ -19,9 +25,12 @@
 // launch is one wave, so at any time all blocks work on a band of about nt rows, and each row
 // of the other colour, which six sites of three rows and two planes read, comes from DRAM once.
 // Colour 1 walks the rows from the end, so each colour step starts on the rows the previous
-// step wrote last, which are still in L2.  A warp whose sites are all interior (six
+// step wrote last, which are still in L2.  In colour 0 a thread takes a site's neighbour sums,
+// issues the loads of its next site, and then draws the site, so the loads arrive while it does;
+// colour 1 keeps a site's neighbour values for its edge sums and loads them at the site's start.
+// A warp whose sites are all interior (six
 // neighbours) takes a path without boundary masks, with m_i = a s_i + b (y_i - beta0) and
-// a = tau rho / P, b = (1/sigma^2) / P, 1/sqrt(P) computed once per thread for d = 6; other
+// a = tau rho / P, b = (1/sigma^2) / P, 1/sqrt(P) computed once per launch for d = 6; other
 // warps compute them per site by the same operations, so a site's result does not depend on
 // the path its warp took.
 //
@@ -41,18 +50,116 @@ namespace {
 
 constexpr int k3Block = 256;
 
-__device__ __forceinline__ void ld4(const float *p, float *v)
+// Two FP32 values (low half: the even chain) in one 64-bit register.
+using f2 = unsigned long long;
+
+__device__ __forceinline__ f2 pk(float lo, float hi)
 {
-    const float4 t = *reinterpret_cast<const float4 *>(p);
-    v[0] = t.x;
-    v[1] = t.y;
-    v[2] = t.z;
-    v[3] = t.w;
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// a * b + c, rounded once per lane
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
 }
 
-__device__ __forceinline__ void st4(float *p, const float *v)
+// Four chain values (two pairs) at p, 16-byte aligned.
+__device__ __forceinline__ void ld2x2(const float *p, f2 &a, f2 &b)
 {
-    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(p);
+    a = t.x;
+    b = t.y;
+}
+__device__ __forceinline__ void st2x2(float *p, f2 a, f2 b) { *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(a, b); }
+
+__device__ __forceinline__ f2 splat(float v) { return pk(v, v); }
+__device__ __forceinline__ f2 lanes_f(uint32_t a, uint32_t b) { return pk(static_cast<float>(a), static_cast<float>(b)); }
+
+// The two Box-Muller pairs of one Philox block, (w.x, w.y) in the low lanes and (w.z, w.w) in
+// the high lanes, with the operations of box_muller_f32 lane by lane (so the normals are those of
+// the scalar routine, bit for bit): -2 ln u from the base-2 logarithm for u < 3/4 and from the
+// atanh series in v = 1 - u above, r = that times its reciprocal square root, and the angle
+// reduced on the word to a quadrant and a Taylor-series sine and cosine.  Returns the normals of
+// chains (0, 1) and (2, 3) of the block as pairs.
+__device__ __forceinline__ void box_muller_block_f32x2(uint4 w, f2 &z01, f2 &z23)
+{
+    const f2 k32 = splat(0x1p-32f), k33 = splat(0x1p-33f);
+    const f2 ua = fma2(lanes_f(w.x, w.z), k32, k33);
+    float ua0, ua1;
+    upk(ua, ua0, ua1);
+    const f2 l1 = mul2(pk(lg2_approx(ua0), lg2_approx(ua1)), splat(-1.3862943611198906f));
+    const f2 v = fma2(lanes_f(~w.x, ~w.z), k32, k33);
+    float d0, d1;
+    upk(sub2(splat(2.0f), v), d0, d1);
+    const f2 t = mul2(v, pk(rcp_approx(d0), rcp_approx(d1)));
+    const f2 t2 = mul2(t, t);
+    const f2 p = fma2(fma2(fma2(fma2(splat(1.0f / 9.0f), t2, splat(1.0f / 7.0f)), t2, splat(1.0f / 5.0f)), t2,
+                           splat(1.0f / 3.0f)),
+                      t2, splat(1.0f));
+    const f2 l2 = mul2(mul2(splat(4.0f), t), p);
+    float l1a, l1b, l2a, l2b;
+    upk(l1, l1a, l1b);
+    upk(l2, l2a, l2b);
+    const float q0 = w.x >= 0xC0000000u ? l2a : l1a, q1 = w.z >= 0xC0000000u ? l2b : l1b;
+    const f2 q2 = pk(q0, q1);
+    const f2 r = mul2(q2, pk(rsqrt_approx(q0), rsqrt_approx(q1)));
+    const uint32_t s0 = w.y + 0x20000000u, s1 = w.w + 0x20000000u;
+    const f2 dd = add2(sub2(pk(__uint_as_float(0x3F800000u | ((s0 >> 7) & 0x7FFFFFu)),
+                               __uint_as_float(0x3F800000u | ((s1 >> 7) & 0x7FFFFFu))),
+                            splat(1.5f)),
+                       splat(0x1p-24f));
+    const f2 dsq = mul2(dd, dd);
+    const f2 ps = fma2(fma2(fma2(fma2(splat(1.6044118478735982e-4f), dsq, splat(-4.6817541353186881e-3f)), dsq,
+                                 splat(7.9692626246167046e-2f)),
+                            dsq, splat(-6.4596409750624625e-1f)),
+                       dsq, splat(1.5707963267948966f));
+    float sn[2], cs[2];
+    upk(mul2(dd, ps), sn[0], sn[1]);
+    upk(fma2(fma2(fma2(fma2(splat(9.1926027483942659e-4f), dsq, splat(-2.0863480763352961e-2f)), dsq,
+                       splat(2.5366950790104802e-1f)),
+                  dsq, splat(-1.2337005501361697f)),
+             dsq, splat(1.0f)),
+        cs[0], cs[1]);
+    const uint32_t quad[2] = {s0 >> 30, s1 >> 30};
+    float cq[2], sq[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        cq[h] = (quad[h] & 1u) ? -sn[h] : cs[h];
+        sq[h] = (quad[h] & 1u) ? cs[h] : sn[h];
+        if (quad[h] & 2u) {
+            cq[h] = -cq[h];
+            sq[h] = -sq[h];
+        }
+    }
+    const f2 zc = mul2(r, pk(cq[0], cq[1])), zs = mul2(r, pk(sq[0], sq[1]));
+    float c0, c1, n0, n1;
+    upk(zc, c0, c1);
+    upk(zs, n0, n1);
+    z01 = pk(c0, n0);
+    z23 = pk(c1, n1);
 }
 
 // Per chain parameters of the launch, in shared memory: tau, tau rho, 1/sigma^2, beta0, and the
@@ -63,111 +170,151 @@ struct alignas(16) Params3 {
     float ca[NC], cb[NC], crs[NC];
 };
 
-// Per-thread partial sums.
 template <int NC>
+__device__ __forceinline__ f2 pair_of(const float (&v)[NC], int u)
+{
+    return *reinterpret_cast<const f2 *>(&v[2 * u]);
+}
+
+// Per-thread partial sums, by chain pair.
+template <int NP>
 struct Acc3 {
-    float S[NC], R[NC], A[NC];
+    f2 S[NP], R[NP], A[NP];
 };
 
 struct Site3 {
-    const float *xo;   // the other colour's slot of this site's column in row r
-    float *xs, *ms, *qs;
-    int64_t noff[6];   // neighbour offsets from xo (floats)
-    uint32_t valid;    // neighbours present (bit k: noff[k])
-    uint32_t site;     // natural site index
+    int64_t rb;           // slot of the site in its colour's sub-array (and of its column in the
+                          // other colour's)
+    uint32_t valid;       // neighbours present: bit k for j - 1, j + 1, i - 1, i + 1, l - 1, l + 1
+    uint32_t site;        // natural site index
     float y, d;
+    int p;                // column parity of the site's row
+    bool ok, interior;    // a site of the lattice; every site of the warp has six neighbours
 };
 
-// Update chain groups G0 .. G0 + GN - 1 (four chains each) of one site.
-template <int NC, int G0, int GN, bool ODD, bool ICPT, bool PCAR, bool INTERIOR>
-__device__ __forceinline__ void site_groups(const StepArgs &a, const Params3<NC> &pp, Acc3<NC> &ac, const Site3 &st,
-                                            uint32_t sweep, uint32_t stream, bool update, bool acc, float inv_k,
-                                            float rho, float om)
+// Offsets of the six neighbours' chain vectors from the other colour's slot rb (in floats).
+struct NbrOff {
+    int64_t row, plane;
+};
+
+// The neighbours' values of a site (zeros for missing ones); XO: the other colour's sub-array.
+template <int NG, bool INTERIOR>
+__device__ __forceinline__ void load_neighbours(const float *XO, const NbrOff &no, const Site3 &st, f2 (&nb)[6][2 * NG])
 {
-    constexpr int M = 4 * GN;
-    float nb[6][M];
+    constexpr int NC = 4 * NG;
+    const float *xo = XO + st.rb * NC;
+    const float *nbp[6] = {xo + (st.p - 1) * NC, xo + st.p * NC, xo - no.row, xo + no.row, xo - no.plane, xo + no.plane};
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         if (INTERIOR || ((st.valid >> k) & 1u)) {
 #pragma unroll
-            for (int g = 0; g < GN; ++g) ld4(st.xo + st.noff[k] + 4 * (G0 + g), &nb[k][4 * g]);
+            for (int g = 0; g < NG; ++g) ld2x2(nbp[k] + 4 * g, nb[k][2 * g], nb[k][2 * g + 1]);
         } else {
 #pragma unroll
-            for (int v = 0; v < M; ++v) nb[k][v] = 0.0f;
+            for (int u = 0; u < 2 * NG; ++u) nb[k][u] = 0ull;
         }
     }
-    float x[M];
+}
+
+// The neighbour sums of a site, per chain pair.
+template <int NG>
+__device__ __forceinline__ void sum_neighbours(const f2 (&nb)[6][2 * NG], f2 (&s)[2 * NG])
+{
+#pragma unroll
+    for (int u = 0; u < 2 * NG; ++u) {
+        s[u] = add2(nb[0][u], nb[1][u]);
+#pragma unroll
+        for (int k = 2; k < 6; ++k) s[u] = add2(s[u], nb[k][u]);
+    }
+}
+
+// Draw the NC = 4 NG chains of one site from its neighbour sums s and add its terms to the sums
+// (colour 1's edge terms from the neighbour values nb).
+template <int NG, bool ODD, bool ICPT, bool PCAR, bool INTERIOR>
+__device__ __forceinline__ void site_update(const StepArgs &a, const Params3<4 * NG> &pp, Acc3<2 * NG> &ac,
+                                            const Site3 &st, const f2 (&s)[2 * NG], const f2 (&nb)[6][2 * NG],
+                                            float *XS, float *MS, float *QS, uint32_t sweep, uint32_t stream,
+                                            bool update, bool acc, f2 invk2, f2 rho2, float om)
+{
+    constexpr int NC = 4 * NG, NP = 2 * NG;
+    float *xs = XS + st.rb * NC;
+    const f2 yy = pk(st.y, st.y);
+    f2 x[NP];
     if (update) {
-        float z[M];
+        f2 z[NP];
 #pragma unroll
-        for (int g = 0; g < GN; ++g) {
-            const uint4 w = philox4x32_10(make_uint4(st.site, sweep, stream, (kTagX << 24) | (G0 + g)), a.key);
-            box_muller_f32(w.x, w.y, z[4 * g], z[4 * g + 1]);
-            box_muller_f32(w.z, w.w, z[4 * g + 2], z[4 * g + 3]);
+        for (int g = 0; g < NG; ++g) {
+            const uint4 w = philox4x32_10_rk(make_uint4(st.site, sweep, stream, (kTagX << 24) | g), a.rk);
+            box_muller_block_f32x2(w, z[2 * g], z[2 * g + 1]);
         }
 #pragma unroll
-        for (int u = 0; u < M; ++u) {
-            const int v = 4 * G0 + u;
-            float s = nb[0][u];
-#pragma unroll
-            for (int k = 1; k < 6; ++k) s += nb[k][u];
-            float ca, cb, crs;
+        for (int u = 0; u < NP; ++u) {
+            f2 ca, cb, crs;
             if (INTERIOR) {
-                ca = pp.ca[v];
-                cb = pp.cb[v];
-                crs = pp.crs[v];
+                ca = pair_of<NC>(pp.ca, u);
+                cb = pair_of<NC>(pp.cb, u);
+                crs = pair_of<NC>(pp.crs, u);
             } else {
-                const float P = fmaf(pp.tau[v], st.d, pp.isig[v]);
-                const float rP = rcp_approx(P);
-                ca = pp.tr[v] * rP;
-                cb = pp.isig[v] * rP;
-                crs = rsqrt_approx(P);
+                float c[3][2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int v = 2 * u + h;
+                    const float P = fmaf(pp.tau[v], st.d, pp.isig[v]);
+                    const float rP = rcp_approx(P);
+                    c[0][h] = pp.tr[v] * rP;
+                    c[1][h] = pp.isig[v] * rP;
+                    c[2][h] = rsqrt_approx(P);
+                }
+                ca = pk(c[0][0], c[0][1]);
+                cb = pk(c[1][0], c[1][1]);
+                crs = pk(c[2][0], c[2][1]);
             }
-            const float yb = ICPT ? st.y - pp.beta[v] : st.y;
-            x[u] = fmaf(z[u], crs, fmaf(ca, s, yb * cb));
+            const f2 yb = ICPT ? sub2(yy, pair_of<NC>(pp.beta, u)) : yy;
+            x[u] = fma2(z[u], crs, fma2(ca, s[u], mul2(yb, cb)));
         }
 #pragma unroll
-        for (int g = 0; g < GN; ++g) st4(st.xs + 4 * (G0 + g), &x[4 * g]);
+        for (int g = 0; g < NG; ++g) st2x2(xs + 4 * g, x[2 * g], x[2 * g + 1]);
     } else {
 #pragma unroll
-        for (int g = 0; g < GN; ++g) ld4(st.xs + 4 * (G0 + g), &x[4 * g]);
+        for (int g = 0; g < NG; ++g) ld2x2(xs + 4 * g, x[2 * g], x[2 * g + 1]);
     }
+    const f2 omd2 = pk(om * st.d, om * st.d);
 #pragma unroll
-    for (int u = 0; u < M; ++u) {
-        const int v = 4 * G0 + u;
-        float sv = 0.0f;
+    for (int u = 0; u < NP; ++u) {
+        f2 sv = 0ull;
         if (ODD) {
-            float ev = 0.0f;
+            f2 ev = 0ull;
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 if (INTERIOR || ((st.valid >> k) & 1u)) {
-                    const float df = x[u] - nb[k][u];
-                    ev = fmaf(df, df, ev);
+                    const f2 df = sub2(x[u], nb[k][u]);
+                    ev = fma2(df, df, ev);
                 }
             }
-            sv = PCAR ? rho * ev : ev;
+            sv = PCAR ? mul2(rho2, ev) : ev;
         }
-        if (PCAR) sv = fmaf(om * st.d * x[u], x[u], sv);
-        if (ODD || PCAR) ac.S[v] += sv;
-        const float res = (ICPT ? st.y - pp.beta[v] : st.y) - x[u];
-        ac.R[v] = fmaf(res, res, ac.R[v]);
-        if (ICPT) ac.A[v] += res;
+        if (PCAR) sv = fma2(mul2(omd2, x[u]), x[u], sv);
+        if (ODD || PCAR) ac.S[u] = add2(ac.S[u], sv);
+        const f2 res = sub2(ICPT ? sub2(yy, pair_of<NC>(pp.beta, u)) : yy, x[u]);
+        ac.R[u] = fma2(res, res, ac.R[u]);
+        if (ICPT) ac.A[u] = add2(ac.A[u], res);
     }
     if (acc) {
+        float *ms = MS + st.rb * NC, *qs = QS + st.rb * NC;
 #pragma unroll
-        for (int g = 0; g < GN; ++g) {
-            float mu[4], mm[4];
-            ld4(st.ms + 4 * (G0 + g), mu);
-            ld4(st.qs + 4 * (G0 + g), mm);
+        for (int g = 0; g < NG; ++g) {
+            f2 mu[2], mm[2];
+            ld2x2(ms + 4 * g, mu[0], mu[1]);
+            ld2x2(qs + 4 * g, mm[0], mm[1]);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float xv = x[4 * g + u];
-                const float delta = xv - mu[u];
-                mu[u] = fmaf(delta, inv_k, mu[u]);
-                mm[u] = fmaf(delta, xv - mu[u], mm[u]);
+            for (int h = 0; h < 2; ++h) {
+                const f2 xv = x[2 * g + h];
+                const f2 delta = sub2(xv, mu[h]);
+                mu[h] = fma2(delta, invk2, mu[h]);
+                mm[h] = fma2(delta, sub2(xv, mu[h]), mm[h]);
             }
-            st4(st.ms + 4 * (G0 + g), mu);
-            st4(st.qs + 4 * (G0 + g), mm);
+            st2x2(ms + 4 * g, mu[0], mu[1]);
+            st2x2(qs + 4 * g, mm[0], mm[1]);
         }
     }
 }
@@ -177,7 +324,7 @@ __device__ __forceinline__ void site_groups(const StepArgs &a, const Params3<NC>
 template <int NG, bool ODD, bool ICPT, bool PCAR>
 __global__ void __launch_bounds__(k3Block, 2) lattice3d_kernel(const StepArgs a)
 {
-    constexpr int NC = 4 * NG;
+    constexpr int NC = 4 * NG, NP = 2 * NG;
     __shared__ Params3<NC> pp;
     __shared__ float red[k3Block / 32][NC][3];
     pdl_wait_then_release();
@@ -202,12 +349,12 @@ __global__ void __launch_bounds__(k3Block, 2) lattice3d_kernel(const StepArgs a)
         pp.crs[v] = rsqrt_approx(P);
     }
     __syncthreads();
-    Acc3<NC> ac;
+    Acc3<NP> ac;
 #pragma unroll
-    for (int v = 0; v < NC; ++v) {
-        ac.S[v] = 0.0f;
-        ac.R[v] = 0.0f;
-        ac.A[v] = 0.0f;
+    for (int u = 0; u < NP; ++u) {
+        ac.S[u] = 0ull;
+        ac.R[u] = 0ull;
+        ac.A[u] = 0ull;
     }
     const bool update = a.update != 0;
     bool acc = false;
@@ -216,6 +363,7 @@ __global__ void __launch_bounds__(k3Block, 2) lattice3d_kernel(const StepArgs a)
         acc = true;
         inv_k = 1.0f / static_cast<float>(a.ctl->acc_count + 1);
     }
+    const f2 invk2 = pk(inv_k, inv_k), rho2 = pk(rho, rho);
 
     const int L = f.dims[0], H = f.dims[1], W = f.dims[2];
     const int cols = f.cols;
@@ -231,58 +379,102 @@ __global__ void __launch_bounds__(k3Block, 2) lattice3d_kernel(const StepArgs a)
     const int stride = t.stride > 1 ? t.stride : 1;
     const int nelem = t.count * cols;
 
-    for (int q = threadIdx.x; q < nelem; q += k3Block) {
+    const NbrOff no{off_row, off_plane};
+    // Site of element q (in processing order) and its masks; its observation load is issued here.
+    auto site_at = [&](int q, Site3 &st) {
         const int e = ODD ? nelem - 1 - q : q;
         const int m = fast_div(e, f.cols_m, f.cols_s);
         const int h = e - m * cols;
         const int r = t.start + m * stride;
         const int l = fast_div(r, f.h_m, f.h_s);
         const int i = r - l * H;
-        const int p = (c + l + i) & 1;
-        const int j = 2 * h + p;
-        const bool ok = j < W;
-        const uint32_t valid = (j > 0 ? 1u : 0u) | (j + 1 < W ? 2u : 0u) | (i > 0 ? 4u : 0u) |
-                               (i + 1 < H ? 8u : 0u) | (l > 0 ? 16u : 0u) | (l + 1 < L ? 32u : 0u);
-        const bool interior = __all_sync(__activemask(), valid == 63u || !ok);
-        if (!ok)
-            continue;
-        Site3 st;
-        const int64_t rb = static_cast<int64_t>(r) * cols + h;
-        st.xo = XO + rb * NC;
-        st.xs = XS + rb * NC;
-        st.ms = MS + rb * NC;
-        st.qs = QS + rb * NC;
-        st.noff[0] = static_cast<int64_t>(p - 1) * NC;
-        st.noff[1] = static_cast<int64_t>(p) * NC;
-        st.noff[2] = -off_row;
-        st.noff[3] = off_row;
-        st.noff[4] = -off_plane;
-        st.noff[5] = off_plane;
-        st.valid = valid;
+        st.p = (c + l + i) & 1;
+        const int j = 2 * h + st.p;
+        st.ok = j < W;
+        st.valid = (j > 0 ? 1u : 0u) | (j + 1 < W ? 2u : 0u) | (i > 0 ? 4u : 0u) | (i + 1 < H ? 8u : 0u) |
+                   (l > 0 ? 16u : 0u) | (l + 1 < L ? 32u : 0u);
+        st.interior = __all_sync(__activemask(), st.valid == 63u || !st.ok);
+        st.rb = static_cast<int64_t>(r) * cols + h;
         st.site = static_cast<uint32_t>(r) * static_cast<uint32_t>(W) + static_cast<uint32_t>(j);
-        st.y = YS[rb];
-        st.d = static_cast<float>(__popc(valid));
-        if (interior)
-            site_groups<NC, 0, NG, ODD, ICPT, PCAR, true>(a, pp, ac, st, sweep, f.stream, update, acc, inv_k, rho, om);
-        else
-            site_groups<NC, 0, NG, ODD, ICPT, PCAR, false>(a, pp, ac, st, sweep, f.stream, update, acc, inv_k, rho, om);
+        st.y = st.ok ? YS[st.rb] : 0.0f;
+        st.d = static_cast<float>(__popc(st.valid));
+    };
+    auto start_loads = [&](const Site3 &st, f2 (&nb)[6][NP]) {
+        if (st.ok) {
+            if (st.interior) load_neighbours<NG, true>(XO, no, st, nb);
+            else load_neighbours<NG, false>(XO, no, st, nb);
+        }
+    };
+    f2 nb[6][NP];
+    if (!ODD) {
+        // Colour 0: a site's neighbour sums are taken first (freeing `nb`), then the loads of the
+        // thread's next site are issued, then the site is drawn and updated while they arrive.
+        Site3 cur;
+        int q = threadIdx.x;
+        if (q < nelem) {
+            site_at(q, cur);
+            start_loads(cur, nb);
+        }
+        for (; q < nelem; q += k3Block) {
+            f2 s[NP];
+            if (cur.ok) sum_neighbours<NG>(nb, s);
+            Site3 nxt;
+            nxt.ok = false;
+            if (q + k3Block < nelem) {
+                site_at(q + k3Block, nxt);
+                start_loads(nxt, nb);
+            }
+            if (cur.ok) {
+                if (cur.interior)
+                    site_update<NG, ODD, ICPT, PCAR, true>(a, pp, ac, cur, s, nb, XS, MS, QS, sweep, f.stream, update,
+                                                           acc, invk2, rho2, om);
+                else
+                    site_update<NG, ODD, ICPT, PCAR, false>(a, pp, ac, cur, s, nb, XS, MS, QS, sweep, f.stream, update,
+                                                            acc, invk2, rho2, om);
+            }
+            cur = nxt;
+        }
+    } else {
+        // Colour 1: the neighbour values are kept for the edge sums, so a site's loads are issued
+        // at its own start (before its random numbers).
+        for (int q = threadIdx.x; q < nelem; q += k3Block) {
+            Site3 cur;
+            site_at(q, cur);
+            if (!cur.ok)
+                continue;
+            f2 s[NP];
+            start_loads(cur, nb);
+            sum_neighbours<NG>(nb, s);
+            if (cur.interior)
+                site_update<NG, ODD, ICPT, PCAR, true>(a, pp, ac, cur, s, nb, XS, MS, QS, sweep, f.stream, update, acc,
+                                                       invk2, rho2, om);
+            else
+                site_update<NG, ODD, ICPT, PCAR, false>(a, pp, ac, cur, s, nb, XS, MS, QS, sweep, f.stream, update, acc,
+                                                        invk2, rho2, om);
+        }
     }
 
     // Block sums per chain: a shuffle tree over the warp's lanes, then the warps in order.
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int v = 0; v < NC; ++v) {
-        float sS = ac.S[v], sR = ac.R[v], sA = ac.A[v];
+    for (int u = 0; u < NP; ++u) {
+        float sS[2], sR[2], sA[2];
+        upk(ac.S[u], sS[0], sS[1]);
+        upk(ac.R[u], sR[0], sR[1]);
+        upk(ac.A[u], sA[0], sA[1]);
 #pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-            if (ODD || PCAR) sS += __shfl_xor_sync(0xffffffffu, sS, off);
-            sR += __shfl_xor_sync(0xffffffffu, sR, off);
-            if (ICPT) sA += __shfl_xor_sync(0xffffffffu, sA, off);
-        }
-        if (lane == 0) {
-            red[warp][v][0] = sS;
-            red[warp][v][1] = sR;
-            red[warp][v][2] = sA;
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                if (ODD || PCAR) sS[h] += __shfl_xor_sync(0xffffffffu, sS[h], off);
+                sR[h] += __shfl_xor_sync(0xffffffffu, sR[h], off);
+                if (ICPT) sA[h] += __shfl_xor_sync(0xffffffffu, sA[h], off);
+            }
+            if (lane == 0) {
+                red[warp][2 * u + h][0] = sS[h];
+                red[warp][2 * u + h][1] = sR[h];
+                red[warp][2 * u + h][2] = sA[h];
+            }
         }
     }
     __syncthreads();

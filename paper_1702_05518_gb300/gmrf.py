@@ -23,6 +23,7 @@ ALGO_CHROMATIC, ALGO_PLAIN = 0, 1
 FLAG_PER_COLOUR = 1
 FLAG_NO_RESIDENT = 2
 FLAG_RESIDENT = 4
+FLAG_TEST_STALL = 8
 PARAM_TAU2, PARAM_SIGMA2, PARAM_BETA0, PARAM_TAU = range(4)
 LIKELIHOOD_GAUSSIAN, LIKELIHOOD_BINOMIAL = 0, 1
 
@@ -30,8 +31,8 @@ EXPORTED = ["gmrf_color_graph", "gmrf_color_graph_noalloc", "gmrf_sampler_create
             "gmrf_hyper_update", "gmrf_fetch_samples", "gmrf_field_colors", "gmrf_sampler_info",
             "gmrf_sampler_reset", "gmrf_sampler_set_data", "gmrf_launch_stage", "gmrf_fetch_intercept",
             "gmrf_trace_diagnostics", "gmrf_site_psrf", "gmrf_autotune",
-            "gmrf_validate_csr", "gmrf_philox_words", "gmrf_site_normals", "gmrf_last_error",
-            "gmrf_version"]
+            "gmrf_validate_csr", "gmrf_philox_words", "gmrf_site_normals", "gmrf_debug_fail_alloc",
+            "gmrf_debug_poison", "gmrf_last_error", "gmrf_version"]
 
 
 class GmrfError(RuntimeError):
@@ -170,6 +171,10 @@ def lib() -> ctypes.CDLL:
                                             ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int64, vp, vp]
             L.gmrf_site_normals.restype = st
+            L.gmrf_debug_fail_alloc.argtypes = [ctypes.c_int64]
+            L.gmrf_debug_fail_alloc.restype = st
+            L.gmrf_debug_poison.argtypes = [vp]
+            L.gmrf_debug_poison.restype = st
             L.gmrf_last_error.argtypes = []
             L.gmrf_last_error.restype = ctypes.c_char_p
             L.gmrf_version.argtypes = []
@@ -231,8 +236,29 @@ def color_graph(row_ptr, col_idx, seed=0, priorities=None):
 
 def color_graph_noalloc(row_ptr, col_idx, colors, priorities=None, seed=0):
     """gmrf_color_graph_noalloc on device tensors (int32 row_ptr [n+1], col_idx [nnz], colors
-    [n] out; optional int32/uint32 priorities [n]) on the current stream -> number of colours."""
+    [n] out; optional int32/uint32 priorities [n]) on the current stream -> number of colours.
+    Raises ValueError, before any call, unless every tensor is contiguous, of those types and
+    sizes, and on the current CUDA device (the library reads and writes them as device arrays)."""
+    import torch
+
     n = int(row_ptr.numel()) - 1
+    named = [("row_ptr", row_ptr, (torch.int32,), None), ("col_idx", col_idx, (torch.int32,), None),
+             ("colors", colors, (torch.int32,), n)]
+    if priorities is not None:
+        named.append(("priorities", priorities, (torch.int32, torch.uint32), n))
+    for name, t, dtypes, size in named:
+        if t.dtype not in dtypes:
+            raise ValueError(f"{name} must be {' or '.join(str(d) for d in dtypes)}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if size is not None and int(t.numel()) != size:
+            raise ValueError(f"{name} has {t.numel()} elements, expected n = {size}")
+    if n < 0:
+        raise ValueError("row_ptr must have n + 1 >= 1 elements")
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+    for name, t, _, _ in named:
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{name} must be on the current CUDA device")
     k = ctypes.c_int32(0)
     pr = None if priorities is None else ctypes.c_void_p(priorities.data_ptr())
     _check(lib().gmrf_color_graph_noalloc(n, int(col_idx.numel()), ctypes.c_void_p(row_ptr.data_ptr()),
@@ -240,6 +266,11 @@ def color_graph_noalloc(row_ptr, col_idx, colors, priorities=None, seed=0):
                                           ctypes.c_void_p(colors.data_ptr()), ctypes.byref(k),
                                           current_stream()))
     return k.value
+
+
+def debug_fail_alloc(nth):
+    """Make the nth device allocation of the library from now on fail as out of memory (0: off)."""
+    _check(lib().gmrf_debug_fail_alloc(int(nth)))
 
 
 def philox_words(seed, c1, c2, c3, count):
@@ -382,6 +413,10 @@ class Sampler:
         name = ctypes.c_char_p()
         _check(lib().gmrf_launch_stage(self._h, int(stage), 1 if accumulate else 0, ctypes.byref(name)))
         return name.value.decode()
+
+    def debug_poison(self):
+        """Mark the sampler as after a CUDA error (later calls raise with GMRF_E_STATE)."""
+        _check(lib().gmrf_debug_poison(self._h))
 
     def hyper_update(self):
         _check(lib().gmrf_hyper_update(self._h))

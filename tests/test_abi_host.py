@@ -161,3 +161,26 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_noalloc_wrapper_checks_tensors_before_any_call():
+    # a colors tensor shorter than n (or the wrong type) is refused on the host: the library would
+    # write n entries through its pointer
+    torch = pytest.importorskip("torch")
+    rp, ci = wl.cycle_graph(6)
+    rpt = torch.from_numpy(rp.astype(np.int32))
+    cit = torch.from_numpy(ci.astype(np.int32))
+    with pytest.raises(ValueError, match="colors has 5 elements"):
+        g.color_graph_noalloc(rpt, cit, torch.empty(5, dtype=torch.int32))
+    with pytest.raises(ValueError, match="colors must be"):
+        g.color_graph_noalloc(rpt, cit, torch.empty(6, dtype=torch.int64))
+    with pytest.raises(ValueError, match="priorities has 3 elements"):
+        g.color_graph_noalloc(rpt, cit, torch.empty(6, dtype=torch.int32), priorities=torch.zeros(3, dtype=torch.int32))
+    with pytest.raises(ValueError, match="current CUDA device"):  # host tensors are not device arrays
+        g.color_graph_noalloc(rpt, cit, torch.empty(6, dtype=torch.int32))
+
+
+def test_debug_hooks_reject_bad_arguments(L):
+    assert L.gmrf_debug_fail_alloc(-1) == g.E_INVALID
+    assert L.gmrf_debug_fail_alloc(0) == g.OK
+    assert L.gmrf_debug_poison(None) == g.E_INVALID

@@ -19,6 +19,7 @@ from paper_1702_05518_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 WIDE = {"wide_3d": 1}
+GENERAL = {"wide_3d": -1}
 NAME = "colour step, 3-D 6-neighbour lattice, all chains of a site per thread"
 
 
@@ -124,8 +125,8 @@ def test_graph_replay_equals_direct_launches():
 
 def test_general_kernel_agrees_and_selection():
     f = wl.small_lattice(wl.LATTICE3D_6, (12, 40, 41), 10)
-    a, _ = _run(f, 8, 10, tuning={"wide_3d": 1})
-    b, _ = _run(f, 8, 10, tuning={"wide_3d": -1})
+    a, _ = _run(f, 8, 10, tuning=WIDE)
+    b, _ = _run(f, 8, 10, tuning=GENERAL)
     for c in range(8):
         assert relerr(a[c]["x"], b[c]["x"]) <= 2 * TOL_FP32_1000
     with g.Sampler([f], precision=g.FP32, chains=8, seed=1, tuning=WIDE, graph_sweeps=0) as s:

@@ -52,6 +52,23 @@ def test_noalloc_matches_colour_graph_twice(name):
         assert np.array_equal(col.cpu().numpy(), want)
 
 
+def test_noalloc_keeps_device_memory_unchanged():
+    # the defining property: after a first call (which loads the library's device code), a call
+    # takes no device memory
+    import torch
+
+    rp, ci = GRAPHS["delaunay20k"]
+    rp_d, ci_d = _dev(rp), _dev(ci)
+    col = torch.empty(len(rp) - 1, dtype=torch.int32, device="cuda")
+    g.color_graph_noalloc(rp_d, ci_d, col, seed=3)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        g.color_graph_noalloc(rp_d, ci_d, col, seed=3)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
 def test_noalloc_given_priorities():
     import torch
 
