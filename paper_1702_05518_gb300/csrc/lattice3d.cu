@@ -25,9 +25,10 @@
 // launch is one wave, so at any time all blocks work on a band of about nt rows, and each row
 // of the other colour, which six sites of three rows and two planes read, comes from DRAM once.
 // Colour 1 walks the rows from the end, so each colour step starts on the rows the previous
-// step wrote last, which are still in L2.  In colour 0 a thread takes a site's neighbour sums,
-// issues the loads of its next site, and then draws the site, so the loads arrive while it does;
-// colour 1 keeps a site's neighbour values for its edge sums and loads them at the site's start.
+// step wrote last, which are still in L2.  A thread's loads of its next site's neighbours are in
+// flight while it computes: in colour 0 they are issued once the current site's neighbour sums
+// are taken, before its draw; colour 1 keeps a site's neighbour values for its edge sums, so it
+// issues them after those and then draws the next site's normals while they arrive.
 // A warp whose sites are all interior (six
 // neighbours) takes a path without boundary masks, with m_i = a s_i + b (y_i - beta0) and
 // a = tau rho / P, b = (1/sigma^2) / P, 1/sqrt(P) computed once per launch for d = 6; other
@@ -230,23 +231,28 @@ __device__ __forceinline__ void sum_neighbours(const f2 (&nb)[6][2 * NG], f2 (&s
 
 // Draw the NC = 4 NG chains of one site from its neighbour sums s and add its terms to the sums
 // (colour 1's edge terms from the neighbour values nb).
+template <int NG>
+__device__ __forceinline__ void draw_normals(const StepArgs &a, const Site3 &st, uint32_t sweep, uint32_t stream,
+                                             f2 (&z)[2 * NG])
+{
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const uint4 w = philox4x32_10_rk(make_uint4(st.site, sweep, stream, (kTagX << 24) | g), a.rk);
+        box_muller_block_f32x2(w, z[2 * g], z[2 * g + 1]);
+    }
+}
+
 template <int NG, bool ODD, bool ICPT, bool PCAR, bool INTERIOR>
 __device__ __forceinline__ void site_update(const StepArgs &a, const Params3<4 * NG> &pp, Acc3<2 * NG> &ac,
                                             const Site3 &st, const f2 (&s)[2 * NG], const f2 (&nb)[6][2 * NG],
-                                            float *XS, float *MS, float *QS, uint32_t sweep, uint32_t stream,
-                                            bool update, bool acc, f2 invk2, f2 rho2, float om)
+                                            const f2 (&z)[2 * NG], float *XS, float *MS, float *QS, bool update,
+                                            bool acc, f2 invk2, f2 rho2, float om)
 {
     constexpr int NC = 4 * NG, NP = 2 * NG;
     float *xs = XS + st.rb * NC;
     const f2 yy = pk(st.y, st.y);
     f2 x[NP];
     if (update) {
-        f2 z[NP];
-#pragma unroll
-        for (int g = 0; g < NG; ++g) {
-            const uint4 w = philox4x32_10_rk(make_uint4(st.site, sweep, stream, (kTagX << 24) | g), a.rk);
-            box_muller_block_f32x2(w, z[2 * g], z[2 * g + 1]);
-        }
 #pragma unroll
         for (int u = 0; u < NP; ++u) {
             f2 ca, cb, crs;
@@ -416,7 +422,7 @@ __global__ void __launch_bounds__(k3Block, 2) lattice3d_kernel(const StepArgs a)
             start_loads(cur, nb);
         }
         for (; q < nelem; q += k3Block) {
-            f2 s[NP];
+            f2 s[NP], z[NP];
             if (cur.ok) sum_neighbours<NG>(nb, s);
             Site3 nxt;
             nxt.ok = false;
@@ -425,32 +431,46 @@ __global__ void __launch_bounds__(k3Block, 2) lattice3d_kernel(const StepArgs a)
                 start_loads(nxt, nb);
             }
             if (cur.ok) {
+                if (update) draw_normals<NG>(a, cur, sweep, f.stream, z);
                 if (cur.interior)
-                    site_update<NG, ODD, ICPT, PCAR, true>(a, pp, ac, cur, s, nb, XS, MS, QS, sweep, f.stream, update,
-                                                           acc, invk2, rho2, om);
+                    site_update<NG, ODD, ICPT, PCAR, true>(a, pp, ac, cur, s, nb, z, XS, MS, QS, update, acc, invk2,
+                                                           rho2, om);
                 else
-                    site_update<NG, ODD, ICPT, PCAR, false>(a, pp, ac, cur, s, nb, XS, MS, QS, sweep, f.stream, update,
-                                                            acc, invk2, rho2, om);
+                    site_update<NG, ODD, ICPT, PCAR, false>(a, pp, ac, cur, s, nb, z, XS, MS, QS, update, acc, invk2,
+                                                            rho2, om);
             }
             cur = nxt;
         }
     } else {
-        // Colour 1: the neighbour values are kept for the edge sums, so a site's loads are issued
-        // at its own start (before its random numbers).
-        for (int q = threadIdx.x; q < nelem; q += k3Block) {
-            Site3 cur;
+        // Colour 1 keeps a site's neighbour values until its edge sums: after those, the loads of
+        // the thread's next site are issued and that site's normals drawn while they arrive.
+        Site3 cur;
+        f2 z[NP];
+        int q = threadIdx.x;
+        if (q < nelem) {
             site_at(q, cur);
-            if (!cur.ok)
-                continue;
-            f2 s[NP];
             start_loads(cur, nb);
-            sum_neighbours<NG>(nb, s);
-            if (cur.interior)
-                site_update<NG, ODD, ICPT, PCAR, true>(a, pp, ac, cur, s, nb, XS, MS, QS, sweep, f.stream, update, acc,
-                                                       invk2, rho2, om);
-            else
-                site_update<NG, ODD, ICPT, PCAR, false>(a, pp, ac, cur, s, nb, XS, MS, QS, sweep, f.stream, update, acc,
-                                                        invk2, rho2, om);
+            if (cur.ok && update) draw_normals<NG>(a, cur, sweep, f.stream, z);
+        }
+        for (; q < nelem; q += k3Block) {
+            if (cur.ok) {
+                f2 s[NP];
+                sum_neighbours<NG>(nb, s);
+                if (cur.interior)
+                    site_update<NG, ODD, ICPT, PCAR, true>(a, pp, ac, cur, s, nb, z, XS, MS, QS, update, acc, invk2,
+                                                           rho2, om);
+                else
+                    site_update<NG, ODD, ICPT, PCAR, false>(a, pp, ac, cur, s, nb, z, XS, MS, QS, update, acc, invk2,
+                                                            rho2, om);
+            }
+            Site3 nxt;
+            nxt.ok = false;
+            if (q + k3Block < nelem) {
+                site_at(q + k3Block, nxt);
+                start_loads(nxt, nb);
+                if (nxt.ok && update) draw_normals<NG>(a, nxt, sweep, f.stream, z);
+            }
+            cur = nxt;
         }
     }
 
