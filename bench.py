@@ -622,6 +622,12 @@ def run_ours(args):
     algo_bytes = stage_algorithmic_bytes(spec, dom[1], colour_of_stage[dom[0]], colourings)
     design_bytes = stage_design_bytes(spec, dom[1], colour_of_stage[dom[0]], colourings)
     s.close()
+    # The random numbers alone of the dominant 3-D colour step (same counters and arithmetic, no
+    # state traffic): a floor under the kernel's time like the HBM roofline's.
+    rng_only = None
+    if "3-D" in dom[1] and "all chains" in dom[1]:
+        n_c = sum(units for _, _, units, _ in _stage_fields(spec, dom[1], colour_of_stage[dom[0]], colourings))
+        rng_only = g.normals_timing(seed, n_c, spec["chains"], reps=20)
 
     # The plain single-field FP64 sweep (natural layout, one unfused pass per colour) on the same
     # workload and chains, a bounded number of sweeps: the speed-up of the path is value / its rate.
@@ -704,6 +710,8 @@ def run_ours(args):
                 "avg_launch_us": kernel_us,
                 "design_bytes_per_launch": design_bytes,
                 "design_frac": design_bytes / (kernel_us * 1e-6) / 1e9 / hbm,
+                "normals_only_us": rng_only,
+                "normals_only_frac": None if rng_only is None else algo_bytes / (rng_only * 1e-6) / 1e9 / hbm,
                 "stages_us": {f"{st}:{name}": round(us, 3) for st, name, us in stages}}
     if resident_batch:
         # The resident kernel keeps the chain in shared memory for the whole batch: its HBM bytes

@@ -446,6 +446,18 @@ gmrf_status gmrf_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream, ui
                               void *cuda_stream);
 
 /*
+ * Diagnostic: the time of the random numbers of one 3-D lattice colour step alone -- for each
+ * of `sites` sites the normals of all its chains (chains <= 4: one Philox4x32-10 block and two
+ * Box-Muller pairs; 5..8: two of each), with the counters and arithmetic of the sweep kernel,
+ * summed per thread with no state traffic -- on the sweep kernel's grid.  `reps` timed launches
+ * (CUDA events on cuda_stream, after 3 untimed ones); *us_per_launch receives their mean.  It
+ * bounds the colour step from below the way the HBM roofline does.  Synchronises the stream.
+ * Errors: GMRF_E_INVALID, GMRF_E_CUDA, GMRF_E_OOM.
+ */
+gmrf_status gmrf_normals_timing(uint64_t seed, int64_t sites, int32_t chains, int32_t reps, void *cuda_stream,
+                                double *us_per_launch);
+
+/*
  * Fault injection for tests of the error paths (process-wide, not thread-safe; no paper
  * counterpart).  gmrf_debug_fail_alloc: the nth device allocation the library makes from now on
  * (1 = the next) fails as if the device were out of memory (GMRF_E_OOM from the call that made

@@ -2109,6 +2109,25 @@ gmrf_status gmrf_sampler_info(gmrf_sampler *s, gmrf_info *out)
     return GMRF_OK;
 }
 
+gmrf_status gmrf_normals_timing(uint64_t seed, int64_t sites, int32_t chains, int32_t reps, void *cuda_stream,
+                                double *us_per_launch)
+{
+    g_last_error.clear();
+    if (sites < 1 || sites > (int64_t(1) << 31) || chains < 1 || chains > 8 || reps < 1 || !us_per_launch)
+        return fail(GMRF_E_INVALID, "sites in 1..2^31, chains in 1..8, reps >= 1 and us_per_launch are required");
+    const int cp = chains <= 4 ? 4 : 8;
+    const int threads = normals_only_threads(cp);
+    if (threads < 1) return cuda_status(CudaFail{cudaErrorInvalidConfiguration, "normals timing grid"});
+    void *out = nullptr;
+    cudaError_t e = dev_malloc(&out, sizeof(unsigned long long) * static_cast<size_t>(threads));
+    if (e == cudaSuccess)
+        e = time_normals_only(seed, sites, cp, reps, static_cast<unsigned long long *>(out),
+                              static_cast<cudaStream_t>(cuda_stream), us_per_launch);
+    if (out) cudaFree(out);
+    if (e != cudaSuccess) return cuda_status(CudaFail{e, "normals timing"});
+    return GMRF_OK;
+}
+
 gmrf_status gmrf_debug_fail_alloc(int64_t nth)
 {
     g_last_error.clear();

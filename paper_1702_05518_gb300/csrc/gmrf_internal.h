@@ -224,6 +224,12 @@ cudaError_t launch_colour_step(int precision, int V, int kind, const StepArgs &a
 // lattice3d.cu), and the blocks of it that are resident on one SM.
 cudaError_t launch_lattice3d(int chains_padded, const StepArgs &a, cudaStream_t stream);
 cudaError_t lattice3d_blocks_per_sm(int chains_padded, int *blocks);
+// Time (CUDA events, `reps` launches after 3 untimed ones) of the 3-D kernel's normals alone for
+// `sites` sites and chains_padded (4 or 8) chains, on the kernel's grid.
+// (`out`: one 8-byte word per thread of that grid, normals_only_threads).
+int normals_only_threads(int chains_padded);
+cudaError_t time_normals_only(uint64_t seed, int64_t sites, int chains_padded, int reps, unsigned long long *out,
+                              cudaStream_t stream, double *us_per_launch);
 cudaError_t launch_hyper(int precision, const HyperArgs &a, cudaStream_t stream);
 cudaError_t launch_pack(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx,
                         int32_t C, int32_t Cp, const double *y_nat, const double *x0_nat,

@@ -536,7 +536,72 @@ cudaError_t occupancy(int *blocks)
     return e;
 }
 
+// The normals of one colour step alone: for each of `sites` sites, the NG Philox blocks and
+// packed Box-Muller pairs of the kernel above (same counters, same arithmetic), summed per
+// thread and written once per thread, so the launch moves no state: its time is the random
+// numbers' share of a colour step.
+template <int NG>
+__global__ void __launch_bounds__(k3Block, 2) normals_only_kernel(const StepArgs a, int64_t sites, uint32_t sweep,
+                                                                  unsigned long long *out)
+{
+    constexpr int NP = 2 * NG;
+    f2 acc[NP];
+#pragma unroll
+    for (int u = 0; u < NP; ++u) acc[u] = 0ull;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(k3Block) + threadIdx.x; i < sites;
+         i += static_cast<int64_t>(gridDim.x) * k3Block) {
+        Site3 st;
+        st.site = static_cast<uint32_t>(i);
+        f2 z[NP];
+        draw_normals<NG>(a, st, sweep, 0u, z);
+#pragma unroll
+        for (int u = 0; u < NP; ++u) acc[u] = add2(acc[u], z[u]);
+    }
+    f2 t = acc[0];
+#pragma unroll
+    for (int u = 1; u < NP; ++u) t = add2(t, acc[u]);
+    out[blockIdx.x * static_cast<int64_t>(k3Block) + threadIdx.x] = t;
+}
+
 }  // namespace
+
+int normals_only_threads(int chains_padded)
+{
+    int bps = 1, nsm = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        lattice3d_blocks_per_sm(chains_padded, &bps) != cudaSuccess)
+        return 0;
+    return nsm * bps * k3Block;
+}
+
+cudaError_t time_normals_only(uint64_t seed, int64_t sites, int chains_padded, int reps, unsigned long long *out,
+                              cudaStream_t stream, double *us_per_launch)
+{
+    StepArgs a{};
+    a.key = philox_key(seed);
+    philox_round_keys(a.key, a.rk);
+    const int grid = normals_only_threads(chains_padded) / k3Block;
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    auto launch = [&](uint32_t sweep) {
+        if (chains_padded == 8) normals_only_kernel<2><<<grid, k3Block, 0, stream>>>(a, sites, sweep, out);
+        else normals_only_kernel<1><<<grid, k3Block, 0, stream>>>(a, sites, sweep, out);
+        return cudaGetLastError();
+    };
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch(static_cast<uint32_t>(r));
+    if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch(static_cast<uint32_t>(r + 3));
+    if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) *us_per_launch = 1e3 * ms / reps;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return e;
+}
 
 cudaError_t launch_lattice3d(int chains_padded, const StepArgs &a, cudaStream_t stream)
 {

@@ -31,7 +31,7 @@ EXPORTED = ["gmrf_color_graph", "gmrf_color_graph_noalloc", "gmrf_sampler_create
             "gmrf_hyper_update", "gmrf_fetch_samples", "gmrf_field_colors", "gmrf_sampler_info",
             "gmrf_sampler_reset", "gmrf_sampler_set_data", "gmrf_launch_stage", "gmrf_fetch_intercept",
             "gmrf_trace_diagnostics", "gmrf_site_psrf", "gmrf_autotune",
-            "gmrf_validate_csr", "gmrf_philox_words", "gmrf_site_normals", "gmrf_debug_fail_alloc",
+            "gmrf_validate_csr", "gmrf_philox_words", "gmrf_site_normals", "gmrf_normals_timing", "gmrf_debug_fail_alloc",
             "gmrf_debug_poison", "gmrf_last_error", "gmrf_version"]
 
 
@@ -171,6 +171,9 @@ def lib() -> ctypes.CDLL:
                                             ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_int64, vp, vp]
             L.gmrf_site_normals.restype = st
+            L.gmrf_normals_timing.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, vp,
+                                              f64p]
+            L.gmrf_normals_timing.restype = st
             L.gmrf_debug_fail_alloc.argtypes = [ctypes.c_int64]
             L.gmrf_debug_fail_alloc.restype = st
             L.gmrf_debug_poison.argtypes = [vp]
@@ -266,6 +269,13 @@ def color_graph_noalloc(row_ptr, col_idx, colors, priorities=None, seed=0):
                                           ctypes.c_void_p(colors.data_ptr()), ctypes.byref(k),
                                           current_stream()))
     return k.value
+
+
+def normals_timing(seed, sites, chains, reps=20):
+    """Microseconds per launch of the 3-D colour step's normals alone (sites x chains normals)."""
+    us = ctypes.c_double(0)
+    _check(lib().gmrf_normals_timing(int(seed), int(sites), int(chains), int(reps), current_stream(), ctypes.byref(us)))
+    return us.value
 
 
 def debug_fail_alloc(nth):

@@ -146,3 +146,15 @@ def test_invalid_wide_tuning(bad):
         g.Sampler([f], precision=g.FP32, chains=2, seed=1, tuning=WIDE)
     with pytest.raises(g.GmrfError):
         g.Sampler([f], precision=g.FP64, chains=8, seed=1, tuning=WIDE)
+
+
+def test_normals_timing_diagnostic():
+    # the random numbers of a 256^3 colour step with 8 chains alone: a few tens of microseconds,
+    # and about half that for 4 chains (one Philox block per site instead of two)
+    t8 = g.normals_timing(5, 1 << 23, 8, reps=5)
+    t4 = g.normals_timing(5, 1 << 23, 4, reps=5)
+    assert 5.0 < t8 < 5000.0 and 0.3 * t8 < t4 < 0.9 * t8
+    with pytest.raises(g.GmrfError):
+        g.normals_timing(5, 0, 8)
+    with pytest.raises(g.GmrfError):
+        g.normals_timing(5, 100, 9)
