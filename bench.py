@@ -199,10 +199,10 @@ MEASURED_TRAFFIC = {
                       sources={"lattice_quad.cu": "3e536b8a589e6c22b7f1aba7c5e3716f3208f0447ead67715aa4bb57c7f70589",
                                "gmrf_device.cuh": "a784a897b639feac1b61e7c197dbaf133ab26f487aff9ca2fd2e6c842752080e",
                                "gmrf_internal.h:FusedArgs": "56db942c013e0b5fb3ff98aff46cecf959fbee26d7386333c58679d8093d2d9c"}),
-    "volume256": dict(kernel="colour_step_kernel<float, 4, 2, 0>", bytes=316_079_104 + 234_375_936,
-                      sources={"sweep_kernels.cu": "95c871825e2a079b5a0bb4b0b74fbd7c65b21600f185e373b04275a78ad91a90",
-                               "gmrf_device.cuh": "a784a897b639feac1b61e7c197dbaf133ab26f487aff9ca2fd2e6c842752080e",
-                               "gmrf_internal.h:StepArgs": "92f72ecd2bdcf4f1a8a8ea7c6a9e397d592dc5203447eb7e18789f620b4efb11"}),
+    "volume256": dict(kernel="lattice3d_kernel<2, 1, 0, 0>", bytes=350_960_640 + 235_669_504,
+                      sources={"lattice3d.cu": "1b9b9bbdb5dcf3267b9a7f9a8a2a88ac56def6d9dc87df30936602f3aad29cd5",
+                               "gmrf_device.cuh": "f89a8dbebb7e5d110437f0659ea10631a854d30ca2b8499c136050457bdca206",
+                               "gmrf_internal.h:StepArgs": "f1074e9506e5570bccaa0fa63d2106830a8bbbd7d9a256d2de0630bbe74378c7"}),
 }
 
 
