@@ -154,6 +154,10 @@ typedef struct {
                                  /* site in one thread, -1 keeps chains_per_thread; 0: automatic      */
                                  /* (the former for classes of >= 256 sites per SM when               */
                                  /* chains_per_thread is 0)                                           */
+    int32_t graph_cluster;       /* resident graph path: blocks sharing a chain, 1, 2, 4 or 8 (times  */
+                                 /* the chains at most 152); a class share that does not fit the      */
+                                 /* blocks keeps the per-colour path; 0: automatic (one block per     */
+                                 /* 2048 sites, at most 8)                                            */
 } gmrf_tuning;
 
 typedef struct {

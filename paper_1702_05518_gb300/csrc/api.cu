@@ -404,6 +404,10 @@ gmrf_status check_opts(const gmrf_opts *o)
         if (t->quad_rows != 0 && (t->quad_rows < 8 || (t->quad_rows & 1)))
             return fail(GMRF_E_INVALID, "tuning.quad_rows must be 0 or even and >= 8");
         if (t->wide_3d < -1 || t->wide_3d > 1) return fail(GMRF_E_INVALID, "tuning.wide_3d must be -1, 0 or 1");
+        if (t->graph_cluster != 0 && t->graph_cluster != 1 && t->graph_cluster != 2 && t->graph_cluster != 4 &&
+            t->graph_cluster != 8 && t->graph_cluster != 16)
+            return fail(GMRF_E_INVALID, "tuning.graph_cluster must be 0, 1, 2, 4, 8 or 16");
+        if (t->graph_cluster * o->chains > 152) return fail(GMRF_E_INVALID, "tuning.graph_cluster x chains exceeds 152 blocks");
         if (t->wide_3d == 1 && (o->precision != GMRF_FP32 || cp < 4 || cp > 8))
             return fail(GMRF_E_INVALID, "tuning.wide_3d = 1 needs FP32 and 3 to 8 chains");
     }
@@ -626,6 +630,7 @@ cudaError_t plan_resident(gmrf_sampler *s, const std::vector<int32_t> &coff0)
         // A cluster of CL blocks per chain (at most 152 blocks in all): one block per 2048 sites.
         int cl = 1;
         while (cl < 8 && f.n >= 2048 * 2 * cl && s->C * 2 * cl <= 152) cl *= 2;
+        if (s->tune.graph_cluster) cl = s->tune.graph_cluster;
         int own_max = 0, share_max = 0;
         for (int c = 0; c < h.ncolors; ++c) {
             const int len = coff0[c + 1] - coff0[c], q = (len + cl - 1) / cl;

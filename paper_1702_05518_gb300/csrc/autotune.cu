@@ -159,6 +159,14 @@ extern "C" gmrf_status gmrf_autotune(const gmrf_field_desc *fields, int32_t nfie
             t.wide_3d = w;
             consider(t);
         }
+    // 1c. a single graph on the resident path: blocks per chain's cluster
+    if (nfields == 1 && has_kind[GMRF_CSR])
+        for (int cl : {1, 2, 4, 8, 16}) {
+            if (cl * opts->chains > 152) continue;
+            gmrf_tuning t = best;
+            t.graph_cluster = cl;
+            consider(t);
+        }
     // 2. the colour-step tile (3-D lattices, graphs, and 2-D lattices on per-colour launches)
     if (has_kind[GMRF_LATTICE3D_6] || has_kind[GMRF_CSR] || (opts->flags & GMRF_FLAG_PER_COLOUR))
         for (int tile : {256, 512, 1024, 2048, 4096, 8192, 16384}) {

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T red[kCsrThreads / 32][3];
-    __shared__ T red_cl[8][3];  // block 0: the blocks' sums
+    __shared__ T red_cl[CL > 8 ? CL : 8][3];  // block 0: the blocks' sums
     __shared__ T hs[3];         // tau, 1/sigma^2, beta0 of the current sweep
     __shared__ int coffs[kCsrMaxColours + 1];
     __shared__ int own_lo[kCsrMaxColours], own_hi[kCsrMaxColours], own_off[kCsrMaxColours];
@@ -468,6 +468,10 @@ cudaError_t prepare_mp(size_t smem)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 2, MP>, attr, static_cast<int>(smem));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 4, MP>, attr, static_cast<int>(smem));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 8, MP>, attr, static_cast<int>(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(csr_resident_kernel<T, 16, MP>, attr, static_cast<int>(smem));
+    // clusters of 16 blocks exceed the portable size of 8
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(csr_resident_kernel<T, 16, MP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
 
@@ -481,6 +485,7 @@ cudaError_t prepare_t(size_t smem)
 template <typename T, int MP>
 cudaError_t launch_mp(int cl, int chains, const ResCsrArgs &a, size_t smem, cudaStream_t stream)
 {
+    if (cl == 16) return launch_cl<T, 16, MP>(chains, a, smem, stream);
     if (cl == 8) return launch_cl<T, 8, MP>(chains, a, smem, stream);
     if (cl == 4) return launch_cl<T, 4, MP>(chains, a, smem, stream);
     if (cl == 2) return launch_cl<T, 2, MP>(chains, a, smem, stream);

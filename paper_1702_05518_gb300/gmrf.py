@@ -67,7 +67,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("chains_per_thread", ctypes.c_int32), ("step_tile", ctypes.c_int32),
                 ("fused_rows", ctypes.c_int32 * 2), ("fused_cols", ctypes.c_int32 * 2),
                 ("fused_threads", ctypes.c_int32 * 2), ("quad_config", ctypes.c_int32),
-                ("quad_rows", ctypes.c_int32), ("wide_3d", ctypes.c_int32)]
+                ("quad_rows", ctypes.c_int32), ("wide_3d", ctypes.c_int32), ("graph_cluster", ctypes.c_int32)]
 
     @classmethod
     def from_dict(cls, d):

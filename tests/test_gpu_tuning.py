@@ -105,3 +105,26 @@ def test_autotune_returns_a_cached_configuration():
         st, _ = run_oracle(f, 2, 1, seed=9, stream=fi)
         for c in range(2):
             assert relerr(res[fi * 2 + c]["x"], st.x[c]) <= TOL_FP32_1
+
+
+@pytest.mark.parametrize("cl", [1, 2, 4, 8, 16])
+def test_graph_cluster_sizes(cl):
+    # the resident graph kernel with a chosen number of blocks per chain (1 keeps 5000 sites in one
+    # block's shares); every size samples as the oracle does
+    f = _delaunay(5000, 21)
+    with g.Sampler([f], precision=g.FP32, chains=4, seed=9, tuning={"graph_cluster": cl}, graph_sweeps=10) as s:
+        s.sweep(20)
+        res = [s.fetch(0, c, trace=20) for c in range(4)]
+        info = s.info()
+    st, out = run_oracle(f, 4, 20, seed=9, stream=0)
+    for c in range(4):
+        assert relerr(res[c]["x"], st.x[c]) <= 1e-4
+        assert trace_relerr(res[c]["tau_trace"], out["tau_trace"][c]) <= 1e-4
+    assert info["wait_timeouts"] == 0
+
+
+@pytest.mark.parametrize("bad", [{"graph_cluster": 3}, {"graph_cluster": 32}])
+def test_invalid_graph_cluster(bad):
+    f = _delaunay(1000, 22)
+    with pytest.raises(g.GmrfError):
+        g.Sampler([f], precision=g.FP32, chains=2, seed=1, tuning=bad)
