@@ -25,8 +25,9 @@
 // launch is one wave, so at any time all blocks work on a band of about nt rows, and each row
 // of the other colour, which six sites of three rows and two planes read, comes from DRAM once.
 // Colour 1 walks the rows from the end, so each colour step starts on the rows the previous
-// step wrote last, which are still in L2.  A thread's loads of its next site's neighbours are in
-// flight while it computes: in colour 0 they are issued once the current site's neighbour sums
+// step wrote last, which are still in L2.  In accumulating sweeps a site's running mean and M2
+// (read after its draw) are prefetched into L2 when its neighbours are loaded.  A thread's loads
+// of its next site's neighbours are in flight while it computes: in colour 0 they are issued once the current site's neighbour sums
 // are taken, before its draw; colour 1 keeps a site's neighbour values for its edge sums, so it
 // issues them after those and then draws the next site's normals while they arrive.
 // A warp whose sites are all interior (six
@@ -406,6 +407,11 @@ __global__ void __launch_bounds__(k3Block, 2) lattice3d_kernel(const StepArgs a)
         st.d = static_cast<float>(__popc(st.valid));
     };
     auto start_loads = [&](const Site3 &st, f2 (&nb)[6][NP]) {
+        if (st.ok && acc) {
+            // the site's running moments, read after its draw: on their way to L2 from now
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(MS + st.rb * NC));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(QS + st.rb * NC));
+        }
         if (st.ok) {
             if (st.interior) load_neighbours<NG, true>(XO, no, st, nb);
             else load_neighbours<NG, false>(XO, no, st, nb);
