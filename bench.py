@@ -199,8 +199,8 @@ MEASURED_TRAFFIC = {
                       sources={"lattice_quad.cu": "3e536b8a589e6c22b7f1aba7c5e3716f3208f0447ead67715aa4bb57c7f70589",
                                "gmrf_device.cuh": "a784a897b639feac1b61e7c197dbaf133ab26f487aff9ca2fd2e6c842752080e",
                                "gmrf_internal.h:FusedArgs": "56db942c013e0b5fb3ff98aff46cecf959fbee26d7386333c58679d8093d2d9c"}),
-    "volume256": dict(kernel="lattice3d_kernel<2, 1, 0, 0>", bytes=350_960_640 + 235_669_504,
-                      sources={"lattice3d.cu": "1b9b9bbdb5dcf3267b9a7f9a8a2a88ac56def6d9dc87df30936602f3aad29cd5",
+    "volume256": dict(kernel="lattice3d_kernel<2, 1, 0, 0>", bytes=325_104_128 + 234_769_664,
+                      sources={"lattice3d.cu": "d2717661e24e1327713d0fc46a2cb9f3d7ac22a5aac69fe2de1121caee971b14",
                                "gmrf_device.cuh": "f89a8dbebb7e5d110437f0659ea10631a854d30ca2b8499c136050457bdca206",
                                "gmrf_internal.h:StepArgs": "f1074e9506e5570bccaa0fa63d2106830a8bbbd7d9a256d2de0630bbe74378c7"}),
 }
@@ -665,27 +665,27 @@ def run_ours(args):
 
     # End to end through the C ABI with host buffers.  Serving: one sampler built for the graph
     # (outside the timed region); per step the observations (and trials) go up from pinned host
-    # memory (gmrf_sampler_set_data, which also restarts the chains), all sweeps run, and every
-    # chain's posterior mean comes back into pinned host memory.  Cold: the same plus creating and
-    # destroying the sampler (colouring, layout, tiles, graph capture) inside every step.
+    # memory (gmrf_sampler_set_data, which also restarts the chains), all sweeps run, and the
+    # posterior mean and variance pooled over the chains come back into pinned host memory.  Cold:
+    # the same plus creating and destroying the sampler (colouring, layout, tiles, graph capture)
+    # inside every step.
     e2e_steps = max(1, min(3, args.steps))
     n_total = sum(f["n"] for f in spec["fields"])
     binom = spec.get("likelihood") == "binomial"
     host_y = [torch.from_numpy(np.ascontiguousarray(f["y"], np.float64)).pin_memory() for f in spec["fields"]]
     host_m = [torch.from_numpy(np.ascontiguousarray(f["trials"], np.int32)).pin_memory() if binom else None
               for f in spec["fields"]]
-    host_mean = [[torch.empty(f["n"], dtype=torch.float64, pin_memory=True) for _ in range(spec["chains"])]
-                 for f in spec["fields"]]
+    host_mean = [torch.empty(f["n"], dtype=torch.float64, pin_memory=True) for f in spec["fields"]]
+    host_var = [torch.empty(f["n"], dtype=torch.float64, pin_memory=True) for f in spec["fields"]]
     h2d = (8 + (4 if binom else 0)) * n_total
-    d2h = 8 * n_total * spec["chains"]
+    d2h = 16 * n_total
 
     def e2e_step(sampler):
         for fi in range(len(spec["fields"])):
             sampler.set_data(fi, host_y[fi].numpy(), None if host_m[fi] is None else host_m[fi].numpy())
         sampler.sweep(spec["sweeps"])
         for fi in range(len(spec["fields"])):
-            for c in range(spec["chains"]):
-                sampler.fetch_mean(fi, c, out=host_mean[fi][c].numpy())
+            sampler.fetch_pooled(fi, mean=host_mean[fi].numpy(), var=host_var[fi].numpy())
 
     with g.Sampler(spec["fields"], **kw) as s2:
         e2e_step(s2)  # warm-up
@@ -788,8 +788,8 @@ def run_ours(args):
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps,
-                    "per_step": "observations H2D (pinned) + restart, all sweeps, posterior means D2H (pinned); "
-                                "sampler built once outside the timed region",
+                    "per_step": "observations H2D (pinned) + restart, all sweeps, posterior mean and variance "
+                                "pooled over the chains D2H (pinned); sampler built once outside the timed region",
                     "cold_value": e2e_cold,
                     "cold_per_step": "the same with sampler creation and destruction inside every step"},
             "gpu_launches": launches,

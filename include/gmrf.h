@@ -450,6 +450,18 @@ gmrf_status gmrf_site_normals(uint64_t seed, uint32_t sweep, uint32_t stream, ui
                               void *cuda_stream);
 
 /*
+ * The posterior mean and variance of one field pooled over its chains (natural site order, host
+ * out [n] each, either may be NULL): mean = the chains' running means averaged; var = the
+ * variance of all C k accumulated draws, (sum over chains of M2_c + k (mean_c - mean)^2) / (C k - 1)
+ * with k draws per chain (Chan et al.'s pairwise combination of Welford's moments), in FP64 on
+ * the device.  The multi-chain estimate of the posterior (Sec. 3.1 runs three chains) in one
+ * read-back instead of one per chain.  Synchronises; before any accumulated sweep mean is 0
+ * and var NaN.  Errors: GMRF_E_INVALID, GMRF_E_UNSUPPORTED (plain algorithm), GMRF_E_STATE,
+ * GMRF_E_TIMEOUT, GMRF_E_CUDA.
+ */
+gmrf_status gmrf_fetch_pooled(gmrf_sampler *s, int32_t field, double *mean, double *var);
+
+/*
  * Diagnostic: the time of the random numbers of one 3-D lattice colour step alone -- for each
  * of `sites` sites the normals of all its chains (chains <= 4: one Philox4x32-10 block and two
  * Box-Muller pairs; 5..8: two of each), with the counters and arithmetic of the sweep kernel,

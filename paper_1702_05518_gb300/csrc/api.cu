@@ -186,6 +186,7 @@ struct gmrf_sampler {
     double *gpre = nullptr;     // [gpre_batch][F * Cp][4] precomputed variates of a batch
     int32_t gpre_batch = 0;     // sweeps per batch of precomputed variates
     double *staging = nullptr;  // [max_n] doubles for fetch
+    double *pool_stage = nullptr;  // [max_n] doubles: the pooled variance of gmrf_fetch_pooled
     double *data_stage = nullptr;    // [max_n][1 + C] doubles: uploads of gmrf_sampler_set_data
     int32_t *trials_stage = nullptr; // [max_n] trials uploaded by gmrf_sampler_set_data
     double *diag_work = nullptr;  // [Cp][trace_capacity] scratch of the trace diagnostics
@@ -1709,6 +1710,8 @@ gmrf_status gmrf_sampler_create(gmrf_sampler **out, const gmrf_field_desc *field
             s->max_n = 0;
             for (auto &h : s->hf) s->max_n = std::max<int64_t>(s->max_n, h.n);
             CK(s->alloc_t(&s->staging, static_cast<size_t>(s->max_n), sizeof(double)));
+            if (s->algorithm != GMRF_ALGO_PLAIN)
+                CK(s->alloc_t(&s->pool_stage, static_cast<size_t>(s->max_n), sizeof(double)));
             CK(cudaStreamSynchronize(s->stream));
         }
     } catch (const CudaFail &f) {
@@ -1845,6 +1848,39 @@ gmrf_status gmrf_fetch_samples(gmrf_sampler *s, int32_t field, int32_t chain, do
         if (tau_now) CK(cudaMemcpyAsync(tau_now, s->tau + hc, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
         if (sigma2_now) CK(cudaMemcpyAsync(sigma2_now, s->sig2 + hc, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));
+    } catch (const CudaFail &f) {
+        s->poisoned = true;
+        return cuda_status(f);
+    }
+    return GMRF_OK;
+}
+
+gmrf_status gmrf_fetch_pooled(gmrf_sampler *s, int32_t field, double *mean, double *var)
+{
+    g_last_error.clear();
+    if (!s) return fail(GMRF_E_INVALID, "sampler is NULL");
+    if (s->poisoned) return fail(GMRF_E_STATE, "sampler is poisoned by an earlier CUDA error");
+    if (const gmrf_status r = restart_if_pending(s)) return r;
+    if (field < 0 || field >= s->nfields) return fail(GMRF_E_INVALID, "field out of range");
+    if (s->algorithm == GMRF_ALGO_PLAIN) return fail(GMRF_E_UNSUPPORTED, "the plain sweep keeps no running moments");
+    const int64_t n = s->hf[field].n;
+    try {
+        SweepCtl c{};
+        CK(cudaMemcpyAsync(&c, s->ctl, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        if (const gmrf_status w = check_waits(s, c)) return w;
+        const int64_t k = c.acc_count;
+        if (mean && k < 1) std::fill(mean, mean + n, 0.0);
+        if (var && s->C * k < 2) std::fill(var, var + n, NAN);
+        double *dm = (mean && k >= 1) ? s->staging : nullptr;
+        double *dv = (var && s->C * k >= 2) ? s->pool_stage : nullptr;
+        if (dm || dv) {
+            CK(launch_pool(s->precision, s->fields_dev, s->fd[field], field, s->Cp, s->C, k, s->mean, s->m2,
+                           s->perm_inv, dm, dv, s->stream));
+            if (dm) CK(cudaMemcpyAsync(mean, dm, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+            if (dv) CK(cudaMemcpyAsync(var, dv, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+        }
     } catch (const CudaFail &f) {
         s->poisoned = true;
         return cuda_status(f);

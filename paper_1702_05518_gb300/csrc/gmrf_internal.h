@@ -237,6 +237,10 @@ cudaError_t launch_pack(int precision, const FieldDev *fields_dev, const FieldDe
 cudaError_t launch_unpack(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx,
                           int32_t Cp, int32_t chain, const void *src, const void *m2, double inv_km1,
                           const int32_t *perm_inv, double *out, cudaStream_t stream);
+// Moments pooled over the chains (natural order, FP64; out_var needs C k >= 2, either output may be null).
+cudaError_t launch_pool(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx, int32_t Cp,
+                        int32_t C, int64_t k, const void *mean, const void *m2, const int32_t *perm_inv,
+                        double *out_mean, double *out_var, cudaStream_t stream);
 cudaError_t launch_pack_int(const FieldDev *fields_dev, const FieldDev &f, int32_t fidx, const int32_t *v_nat,
                             const int32_t *perm_inv, int32_t *v, cudaStream_t stream);
 cudaError_t launch_ctl_reset(SweepCtl *ctl, long long start_sweep, cudaStream_t stream);

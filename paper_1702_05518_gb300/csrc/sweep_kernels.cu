@@ -591,6 +591,32 @@ __global__ void unpack_kernel(const FieldDev *fields, int32_t fidx, int32_t Cp, 
     }
 }
 
+// Running moments pooled over the C chains of one field, natural order, FP64: mean = the chains'
+// means averaged; var = the sum over chains of M2_c + k (mean_c - mean)^2, over C k - 1 (the
+// variance of all C k draws).  k >= 1 accumulated draws per chain.
+template <typename T>
+__global__ void pool_kernel(const FieldDev *fields, int32_t fidx, int32_t Cp, int32_t C, int64_t k, const T *mean,
+                            const T *m2, const int32_t *perm_inv, double *out_mean, double *out_var)
+{
+    const FieldDev f = fields[fidx];
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < f.n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t slot = f.slot0 + (f.kind == kCsr ? perm_inv[f.csr0 + i] : lattice_slot_of_site(f, i));
+        double mu = 0.0;
+        for (int c = 0; c < C; ++c) mu += static_cast<double>(mean[slot * Cp + c]);
+        mu /= static_cast<double>(C);
+        if (out_mean) out_mean[i] = mu;
+        if (out_var) {
+            double ss = 0.0;
+            for (int c = 0; c < C; ++c) {
+                const double d = static_cast<double>(mean[slot * Cp + c]) - mu;
+                ss += static_cast<double>(m2[slot * Cp + c]) + static_cast<double>(k) * d * d;
+            }
+            out_var[i] = ss / static_cast<double>(C * k - 1);
+        }
+    }
+}
+
 __global__ void philox_words_kernel(uint2 key, uint32_t c1, uint32_t c2, uint32_t c3, int64_t count, uint4 *out)
 {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < count;
@@ -751,6 +777,20 @@ cudaError_t launch_unpack(int precision, const FieldDev *fields_dev, const Field
     else
         unpack_kernel<double><<<grid, 256, 0, stream>>>(fields_dev, fidx, Cp, chain, static_cast<const double *>(src),
                                                         static_cast<const double *>(m2), inv_km1, perm_inv, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pool(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx, int32_t Cp,
+                        int32_t C, int64_t k, const void *mean, const void *m2, const int32_t *perm_inv,
+                        double *out_mean, double *out_var, cudaStream_t stream)
+{
+    const int grid = grid_for(f.n, 256);
+    if (precision == 0)
+        pool_kernel<float><<<grid, 256, 0, stream>>>(fields_dev, fidx, Cp, C, k, static_cast<const float *>(mean),
+                                                     static_cast<const float *>(m2), perm_inv, out_mean, out_var);
+    else
+        pool_kernel<double><<<grid, 256, 0, stream>>>(fields_dev, fidx, Cp, C, k, static_cast<const double *>(mean),
+                                                      static_cast<const double *>(m2), perm_inv, out_mean, out_var);
     return cudaGetLastError();
 }
 

@@ -31,7 +31,8 @@ EXPORTED = ["gmrf_color_graph", "gmrf_color_graph_noalloc", "gmrf_sampler_create
             "gmrf_hyper_update", "gmrf_fetch_samples", "gmrf_field_colors", "gmrf_sampler_info",
             "gmrf_sampler_reset", "gmrf_sampler_set_data", "gmrf_launch_stage", "gmrf_fetch_intercept",
             "gmrf_trace_diagnostics", "gmrf_site_psrf", "gmrf_autotune",
-            "gmrf_validate_csr", "gmrf_philox_words", "gmrf_site_normals", "gmrf_normals_timing", "gmrf_debug_fail_alloc",
+            "gmrf_validate_csr", "gmrf_philox_words", "gmrf_site_normals", "gmrf_normals_timing", "gmrf_fetch_pooled",
+            "gmrf_debug_fail_alloc",
             "gmrf_debug_poison", "gmrf_last_error", "gmrf_version"]
 
 
@@ -174,6 +175,8 @@ def lib() -> ctypes.CDLL:
             L.gmrf_normals_timing.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, vp,
                                               f64p]
             L.gmrf_normals_timing.restype = st
+            L.gmrf_fetch_pooled.argtypes = [vp, ctypes.c_int32, f64p, f64p]
+            L.gmrf_fetch_pooled.restype = st
             L.gmrf_debug_fail_alloc.argtypes = [ctypes.c_int64]
             L.gmrf_debug_fail_alloc.restype = st
             L.gmrf_debug_poison.argtypes = [vp]
@@ -493,6 +496,19 @@ class Sampler:
         _check(lib().gmrf_fetch_samples(self._h, field, chain, None, _p(m, ctypes.c_double), None,
                                         0, None, None, None, None, None))
         return m
+
+    def fetch_pooled(self, field=0, mean=None, var=None, want_var=True):
+        """Posterior mean and variance of one field pooled over its chains, natural order, into
+        `mean` / `var` (contiguous float64 host arrays of n, e.g. pinned tensors' numpy views) or
+        new arrays; var is None when want_var is false."""
+        n = int(self.fields[field]["n"])
+        m = np.zeros(n) if mean is None else mean
+        v = (np.zeros(n) if var is None else var) if want_var else None
+        for a in (m, v):
+            if a is not None and (a.dtype != np.float64 or a.shape != (n,) or not a.flags["C_CONTIGUOUS"]):
+                raise ValueError(f"outputs must be contiguous float64 arrays of {n}")
+        _check(lib().gmrf_fetch_pooled(self._h, field, _p(m, ctypes.c_double), _p(v, ctypes.c_double)))
+        return m, v
 
     def set_data(self, field, y, trials=None, x0=None):
         """Replace one field's observations (and binomial trials, initial states) and restart

@@ -7,7 +7,7 @@ the new data.
 import numpy as np
 import pytest
 
-from gmrf_testutil import TOL_FP64, relerr, run_oracle, trace_relerr
+from gmrf_testutil import TOL_FP32_1000, TOL_FP64, relerr, run_oracle, trace_relerr
 from paper_1702_05518_gb300 import gmrf as g
 from paper_1702_05518_gb300 import workloads as wl
 
@@ -210,3 +210,49 @@ def test_set_data_on_every_field_restarts_once():
         b.sweep(T)
         want = _result(b, 3, 2, T)
     _same(got, want)
+
+
+# --------------------------------------------------------------------------------------------
+# Moments pooled over the chains (gmrf_fetch_pooled)
+# --------------------------------------------------------------------------------------------
+def _pooled(means, m2s, k):
+    means, m2s = np.asarray(means), np.asarray(m2s)
+    mu = means.mean(axis=0)
+    var = (m2s + k * (means - mu) ** 2).sum(axis=0) / (means.shape[0] * k - 1)
+    return mu, var
+
+
+@pytest.mark.parametrize("kind", ["3d_c5", "2d8_c3", "csr_c4"])
+def test_fetch_pooled_equals_chains_combined(kind):
+    if kind == "3d_c5":
+        f, C = wl.small_lattice(wl.LATTICE3D_6, (9, 14, 23), 3), 5
+    elif kind == "2d8_c3":
+        f, C = wl.small_lattice(wl.LATTICE2D_8, (37, 41), 4), 3
+    else:
+        rp, ci, _ = wl.delaunay_graph(1200, wl.rng(5))
+        f, C = wl.graph_field(rp, ci, seed=6), 4
+        f["color_seed"] = 5
+    T, burn = 40, 15
+    with g.Sampler([f], precision=g.FP64, chains=C, seed=19, burn_in=burn, flags=g.FLAG_NO_RESIDENT) as s:
+        m0, v0 = s.fetch_pooled(0)
+        assert np.all(m0 == 0) and np.all(np.isnan(v0))  # nothing accumulated yet
+        s.sweep(T)
+        mean, var = s.fetch_pooled(0)
+        per = [s.fetch(0, c) for c in range(C)]
+    k = T - burn
+    mu, vv = _pooled([p["mean"] for p in per], [p["var"] * (k - 1) for p in per], k)
+    assert relerr(mean, mu) <= 1e-12 and relerr(var, vv) <= 1e-10
+    # and against the oracle's chains pooled the same way
+    st, _ = run_oracle(f, C, T, seed=19, stream=0, burn_in=burn)
+    mo, vo = _pooled(st.mean, st.m2, st.count)
+    assert relerr(mean, mo) <= 1e-12 and relerr(var, vo) <= 1e-10
+
+
+def test_fetch_pooled_fp32_volume():
+    f = wl.small_lattice(wl.LATTICE3D_6, (40, 40, 48), 8)
+    with g.Sampler([f], precision=g.FP32, chains=8, seed=23, burn_in=10, graph_sweeps=10) as s:
+        s.sweep(50)
+        mean, var = s.fetch_pooled(0)
+    st, _ = run_oracle(f, 8, 50, seed=23, stream=0, burn_in=10)
+    mo, vo = _pooled(st.mean, st.m2, st.count)
+    assert relerr(mean, mo) <= TOL_FP32_1000 and relerr(var, vo) <= 1e-3
