@@ -730,7 +730,25 @@ def run_ours(args):
                 "normals_only_us": rng_only,
                 "normals_only_frac": None if rng_only is None else algo_bytes / (rng_only * 1e-6) / 1e9 / hbm,
                 "stages_us": {f"{st}:{name}": round(us, 3) for st, name, us in stages}}
-    if resident_batch:
+    if resident_batch and info["resident"] == 3:
+        # The quad kernel's tiles kept in shared memory for a batch of sweeps (one cooperative
+        # launch, a grid barrier per sweep): the method's least bytes per sweep (bytes_per_update
+        # per site-update, every sweep) over the batch's time, Gamma-variate launch included.
+        nb = resident_batch["sweeps"]
+        q_bytes = algo_bytes * nb
+        ach = q_bytes / (resident_batch["us"] * 1e-6) / 1e9
+        roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": None, "peak_source": peak_note,
+                    "kernel": "resident batch: Gamma variates, lattice_quad_resident_kernel (cooperative, one "
+                              "block per tile)",
+                    "algorithmic_bytes_per_launch": q_bytes,
+                    "bytes_per_update": bytes_per_update(f0, spec["chains"], colour_classes(f0)),
+                    "avg_launch_us": resident_batch["us"], "sweeps_per_launch": nb,
+                    "us_per_sweep": resident_batch["us"] / nb,
+                    "note": "the state stays in shared memory and L2 between sweeps, so the bound is the "
+                            "latency of a sweep (colour steps, grid barrier, draws), not HBM",
+                    "per_sweep_path_stages_us": {f"{st}:{name}": round(us, 3) for st, name, us in stages}}
+    elif resident_batch:
         # The resident kernel keeps the chain in shared memory for the whole batch: its HBM bytes
         # per batch are one read and one write of state, mean and M2, one read of y, and the
         # batch's normals (written by their producer, read once), so the bound is the latency of
@@ -775,7 +793,8 @@ def run_ours(args):
         rb = min(128, max(64, G))
         full, rem = divmod(spec["sweeps"], G) if G > 0 else (0, spec["sweeps"])
         chunks = full * -(-G // rb) + (rem if G > 0 else -(-rem // rb))
-        launches = args.steps * (3 * chunks + 1)
+        # quad tiles: the Gamma variates and the cooperative kernel (its blocks draw the normals)
+        launches = args.steps * ((2 if info["resident"] == 3 else 3) * chunks + 1)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

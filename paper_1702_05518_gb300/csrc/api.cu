@@ -215,7 +215,9 @@ struct gmrf_sampler {
     // 3-D lattice colour steps with every chain of a site in one thread (lattice3d.cu): the
     // padded chain count 4 or 8 when used, 0 when the general colour-step kernel runs them.
     int wide3d = 0;
-    int resident = 0, res_NI = 0, res_NT = 0, res_batch = 0;  // resident: 1 lattice, 2 graph
+    // resident: 1 small lattice (one block per chain), 2 graph (a cluster per chain), 3 the quad
+    // lattice kernel's tiles kept resident (one cooperative launch per batch)
+    int resident = 0, res_NI = 0, res_NT = 0, res_batch = 0;
     uint4 *res_nbr = nullptr, *res_nbr2 = nullptr;            // graph: neighbour records
     int res_cluster = 1, res_own_max = 0;                      // graph: blocks per chain, their share
     int res_positions = 0;                                     // graph: 1 = one position per thread
@@ -607,12 +609,27 @@ cudaError_t launch_pre(gmrf_sampler *s, int count, cudaStream_t st)
     return launch_gamma_pre(g, st);
 }
 
+// The resident form of the quad kernel: a single-chain FP32 8-neighbour field on the quad kernel
+// whose tiles can all be resident at once (one block each).
+cudaError_t plan_quad_resident(gmrf_sampler *s)
+{
+    const int kind = GMRF_LATTICE2D_8;
+    if (s->fd[0].kind != kind || !s->fQCS[kind]) return cudaSuccess;
+    bool fits = false;
+    const cudaError_t e = lattice_quad_resident_fits(s->fQCS[kind], s->fNT[kind], s->fNQ[kind], s->fsmem[kind],
+                                                     s->ftile_cnt[kind], &fits);
+    if (e != cudaSuccess || !fits) return e;
+    s->res_batch = std::min(128, std::max(64, s->opts.graph_sweeps));
+    s->resident = 3;
+    return cudaSuccess;
+}
+
 // The resident path applies to a single fused 2-D lattice field with the Gaussian likelihood whose
 // chain fits in shared memory (state, observations, mean and M2 with a ring of zeros: cells below
 // 2^16, sites below 2^16) and whose colour classes have at most 2 x 576 (8-neighbour) or 4 x 576
-// (4-neighbour) positions.  It is the
-// default for FP32 samplers; GMRF_FLAG_RESIDENT asks for it in FP64 too and GMRF_FLAG_NO_RESIDENT
-// switches it off.
+// (4-neighbour) positions; a larger single-chain FP32 8-neighbour field takes the resident quad
+// kernel when its tiles fit in one wave.  It is the default for FP32 samplers; GMRF_FLAG_RESIDENT
+// asks for the small-lattice form in FP64 too and GMRF_FLAG_NO_RESIDENT switches both off.
 cudaError_t plan_resident(gmrf_sampler *s, const std::vector<int32_t> &coff0)
 {
     s->resident = 0;
@@ -675,11 +692,11 @@ cudaError_t plan_resident(gmrf_sampler *s, const std::vector<int32_t> &coff0)
     int NI = 0;
     for (int ni : {1, 2, 4})
         if (!NI && (ni < 4 || !e8) && (maxq + ni - 1) / ni <= (ni == 1 ? 640 : 576)) NI = ni;
-    if (!NI || cells >= 65536 || f.n >= 65536) return cudaSuccess;
+    if (!NI || cells >= 65536 || f.n >= 65536) return plan_quad_resident(s);
     int NTS = static_cast<int>((maxq + NI - 1) / NI);
     NTS = (NTS + 31) / 32 * 32;
     const size_t smem = 4 * static_cast<size_t>(cells) * tsize(s->precision) + 8 * static_cast<size_t>(K) * NI * NTS;
-    if (smem > 220 * 1024) return cudaSuccess;  // with the static reduction scratch, under 227 KiB
+    if (smem > 220 * 1024) return plan_quad_resident(s);  // with the static reduction scratch, under 227 KiB
     const int NT = NTS + 64;  // and the two drawing warps
     cudaError_t e = prepare_lattice_resident(s->precision, f.kind, NI, smem);
     if (e != cudaSuccess) return e;
@@ -793,6 +810,17 @@ FusedArgs fused_args(gmrf_sampler *s, int kind, int update, int accumulate)
     return a;
 }
 
+QuadResArgs quad_resident_args(gmrf_sampler *s, int count, int draw, int draw_beta)
+{
+    QuadResArgs r{};
+    r.f = fused_args(s, GMRF_LATTICE2D_8, 1, 1);
+    r.h = hyper_args(s, draw, draw_beta, 1);
+    r.count = count;
+    r.extra_arrivals = s->test_stall ? 1u : 0u;
+    r.wait_ns = s->test_stall ? 1000000ull : kWaitNs;
+    return r;
+}
+
 // One stage of a sweep (see gmrf_launch_stage); `draw`, `draw_beta` and `end_of_sweep` only
 // matter for the hyperparameter stage.
 // Description of stage k of a sweep (also its NVTX range name).
@@ -865,10 +893,21 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int with_hyper, cudaStr
     if (s->resident) {
         // Batches of sweeps: the batch's unit-rate Gamma variates and normals, then all its sweeps
         // in one launch.
+        static const char *kBatch[4] = {"", "resident batch, lattice", "resident batch, graph",
+                                        "resident batch, quad lattice"};
         for (int k = 0; k < nsweeps && e == cudaSuccess;) {
-            const NvtxRange range(s->resident == 2 ? "resident batch, graph" : "resident batch, lattice");
+            const NvtxRange range(kBatch[s->resident]);
             const int cnt = std::min(s->res_batch, nsweeps - k);
             if (draw || draw_beta) e = launch_pre(s, cnt, st);
+            if (s->resident == 3) {
+                // the quad kernel's tiles draw their own normals
+                const int kd = GMRF_LATTICE2D_8;
+                if (e == cudaSuccess)
+                    e = launch_lattice_quad_resident(s->fQCS[kd], s->fNT[kd], s->fNQ[kd],
+                                                     quad_resident_args(s, cnt, draw, draw_beta), s->fsmem[kd], st);
+                k += cnt;
+                continue;
+            }
             if (e == cudaSuccess) e = launch_res_normals(s, cnt, st);
             if (e == cudaSuccess && s->resident == 2)
                 e = launch_csr_resident(s->precision, s->res_cluster, s->res_positions, s->C,

@@ -7,6 +7,7 @@
 // in include/gmrf.h, so every draw is a pure function of (seed, counter).
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -96,7 +97,13 @@ struct SweepCtl {
     unsigned long long fticket;  // blocks of that kernel that have read fnext
     long long fmiss;       // launches whose prediction was wrong (their normals were redrawn)
     unsigned long long wait_timeouts;  // bounded device waits that gave up (results invalid)
+    unsigned long long pad0;
+    // The resident quad kernel's grid barrier (16-byte aligned, read as one vector): arrivals
+    // (0 between launches), and a flag set when a block gave up waiting (the others stop too).
+    unsigned long long gbar;
+    unsigned long long gabort;
 };
+static_assert(offsetof(SweepCtl, gbar) % 16 == 0, "the grid barrier's two words are read as one 16-byte vector");
 
 // Whether sweep number `sweep` is accumulated (burn-in, then every thin-th sweep).
 __host__ __device__ __forceinline__ bool sweep_accumulated(long long sweep, long long burn_in, int thin)

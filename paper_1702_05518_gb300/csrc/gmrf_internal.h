@@ -303,6 +303,18 @@ int record_error(int st, const char *msg);
 size_t lattice_quad_smem(int qcs, int TR);
 cudaError_t prepare_lattice_quad(int qcs, int nt, int nq, size_t smem);
 cudaError_t launch_lattice_quad(int qcs, int nt, int nq, const FusedArgs &a, size_t smem, cudaStream_t stream);
+// Its resident form: `count` whole sweeps of the single field in one cooperative launch, one block
+// per tile, every block resident at once.
+struct QuadResArgs {
+    FusedArgs f;              // the tiling and buffers of the per-sweep kernel (update 1)
+    HyperArgs h;              // the conjugate draws at the end of each sweep (end_of_sweep 1)
+    int32_t count;            // sweeps of the launch
+    uint32_t extra_arrivals;  // 0; 1 under GMRF_FLAG_TEST_STALL (no grid barrier completes)
+    uint64_t wait_ns;         // limit of a wait at the grid barrier
+};
+cudaError_t lattice_quad_resident_fits(int qcs, int nt, int nq, size_t smem, int ntiles, bool *fits);
+cudaError_t launch_lattice_quad_resident(int qcs, int nt, int nq, const QuadResArgs &ra, size_t smem,
+                                         cudaStream_t stream);
 
 // Jones-Plassmann colouring and colour-permuted CSR layout (csr_build.cu).
 struct CsrBuild {

@@ -29,14 +29,15 @@ namespace gmrf {
 
 // The draw of one task given its sums, by one thread (see hyper_task): `cur` is the current value
 // of the parameter drawn (tau, or sigma^2), `s2old` the current sigma^2, `b` the beta0 copy the
-// sweep used, gpv and zb the precomputed Gamma variate and normal when `pre`.  Writes the FP64
-// values, the precision-T copies and the traces; returns the parameter's new value (tau or
-// sigma^2) in val and, for task 1, beta0 in bval.
+// sweep used, gpv and zb the precomputed Gamma variate and normal when `pre`.  With `rec`, writes
+// the FP64 values, the precision-T copies and the traces (without it the caller only takes the
+// results: the blocks of the resident quad kernel that draw redundantly); returns the parameter's
+// new value (tau or sigma^2) in val and, for task 1, beta0 in bval.
 template <typename T>
 __device__ __forceinline__ void hyper_draw(const HyperArgs &a, int which, int chain, int64_t hc, long long sweep,
                                            double S, double A, double cur, double s2old, double b, double gpv,
                                            double zb, bool pre, long long extra, uint32_t fstream, int32_t fn,
-                                           int32_t frank, double &val_out, double &bval_out)
+                                           int32_t frank, double &val_out, double &bval_out, bool rec = true)
 {
     T *hyp = static_cast<T *>(a.hyp);
     const uint32_t word1 = static_cast<uint32_t>(a.end_of_sweep ? sweep : extra);
@@ -59,8 +60,10 @@ __device__ __forceinline__ void hyper_draw(const HyperArgs &a, int which, int ch
             bval = b + delta;
             S = S - 2.0 * delta * A + fn * (delta * delta);
         }
-        a.beta[hc] = bval;
-        hyp[hc * kHypStride + 2] = static_cast<T>(bval);
+        if (rec) {
+            a.beta[hc] = bval;
+            hyp[hc * kHypStride + 2] = static_cast<T>(bval);
+        }
     } else if (which && a.trace_beta) {
         bval = a.beta[hc];
     }
@@ -79,21 +82,89 @@ __device__ __forceinline__ void hyper_draw(const HyperArgs &a, int which, int ch
             // The sweep kernels use 1/sigma^2 recomputed from sigma^2, so a run resumed
             // from a fetched sigma^2 continues bit for bit.
             val = rate / G;
-            a.sig2[hc] = val;
-            hyp[hc * kHypStride + 1] = static_cast<T>(1.0 / val);
+            if (rec) {
+                a.sig2[hc] = val;
+                hyp[hc * kHypStride + 1] = static_cast<T>(1.0 / val);
+            }
         } else {
             val = G / rate;
-            a.tau[hc] = val;
-            hyp[hc * kHypStride] = static_cast<T>(val);
+            if (rec) {
+                a.tau[hc] = val;
+                hyp[hc * kHypStride] = static_cast<T>(val);
+            }
         }
     }
-    if (a.end_of_sweep && a.trace_cap > 0) {
+    if (rec && a.end_of_sweep && a.trace_cap > 0) {
         const int64_t slot = hc * a.trace_cap + (sweep % a.trace_cap);
         (which ? a.trace_sig : a.trace_tau)[slot] = val;
         if (which && a.trace_beta) a.trace_beta[slot] = bval;
     }
     val_out = val;
     bval_out = bval;
+}
+
+// The values task `which` needs of one tile partial: S (which 0) or R, and A when need_a.  CG:
+// loaded through L2 only, field by field.
+template <bool CG>
+__device__ __forceinline__ void part_values(const Part3 *p, int which, bool need_a, double &v, double &va)
+{
+    if constexpr (CG) {
+        v = __ldcg(which ? &p->R : &p->S);
+        va = need_a ? __ldcg(&p->A) : 0.0;
+    } else {
+        const Part3 q = *p;
+        v = which ? q.R : q.S;
+        va = need_a ? q.A : 0.0;
+    }
+}
+
+// The sums of task `which` over the field's tile partials, by all 32 lanes of the calling warp,
+// in a fixed order: lane l adds partials l, l + 32, l + 64, ... in that order, then a shuffle
+// tree.  S: the S (which 0) or R (which 1) sums; A: the intercept's sums when need_a.  U loads
+// are issued before their additions, so a warp waits for one L2 round trip per 32 U partials,
+// not per 32 (the sums are those of one load at a time).  BATCH (fields of many tiles): whole
+// rounds of U first; the last round, or every round of a smaller field, is predicated.  CG: the
+// partials are loaded through L2 only (the resident quad kernel reads partials that other blocks
+// of the same launch rewrite every sweep).
+template <bool BATCH, bool CG, int U = 8>
+__device__ __forceinline__ void hyper_sums(const HyperArgs &a, int which, bool need_a, int chain, int32_t part0,
+                                           int32_t nparts, double &S, double &A)
+{
+    const int lane = threadIdx.x & 31;
+    const Part3 *P = a.partials + static_cast<int64_t>(part0) * a.Cp + chain;
+    int k = lane;
+    if constexpr (BATCH) {
+        for (; k + 32 * (U - 1) < nparts; k += 32 * U) {
+            double vs[U], va[U];
+#pragma unroll
+            for (int j = 0; j < U; ++j) part_values<CG>(P + static_cast<int64_t>(k + 32 * j) * a.Cp, which, need_a, vs[j], va[j]);
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                S += vs[j];
+                if (need_a) A += va[j];
+            }
+        }
+    }
+    for (; k < nparts; k += 32 * U) {
+        double vs[U], va[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            vs[j] = 0.0;
+            va[j] = 0.0;
+            if (k + 32 * j < nparts)
+                part_values<CG>(P + static_cast<int64_t>(k + 32 * j) * a.Cp, which, need_a, vs[j], va[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (k + 32 * j < nparts) {
+                S += vs[j];
+                if (need_a) A += va[j];
+            }
+        }
+    }
+    for (int off = 16; off >= 1; off >>= 1) S += __shfl_xor_sync(0xffffffffu, S, off);
+    if (need_a)
+        for (int off = 16; off >= 1; off >>= 1) A += __shfl_xor_sync(0xffffffffu, A, off);
 }
 
 // One task, run by all 32 lanes of the calling warp; `sweep` is the sweep being finished.
@@ -131,38 +202,7 @@ __device__ __forceinline__ void hyper_task(const HyperArgs &a, int task, long lo
     const bool need_sum = which ? (a.draw || a.draw_beta) : a.draw;
     const bool need_a = which && a.draw_beta;
     double S = 0.0, A = 0.0;
-    if (need_sum) {
-        // Lane l adds partials l, l + 32, l + 64, ... in that order.  BATCH (fields of many
-        // tiles): eight loads are issued before their additions, so a warp waits for one L2 round
-        // trip per 256 partials, not per 32; the sums are the same.
-        int k = lane;
-        if constexpr (BATCH) {
-            constexpr int U = 8;
-            const Part3 *P = a.partials + static_cast<int64_t>(part0) * a.Cp + chain;
-            for (; k + 32 * (U - 1) < nparts; k += 32 * U) {
-                double vs[U], va[U];
-#pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    const Part3 &p = P[static_cast<int64_t>(k + 32 * j) * a.Cp];
-                    vs[j] = which ? p.R : p.S;
-                    va[j] = need_a ? p.A : 0.0;
-                }
-#pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    S += vs[j];
-                    if (need_a) A += va[j];
-                }
-            }
-        }
-        for (; k < nparts; k += 32) {
-            const Part3 p = a.partials[static_cast<int64_t>(part0 + k) * a.Cp + chain];
-            S += which ? p.R : p.S;
-            if (need_a) A += p.A;
-        }
-        for (int off = 16; off >= 1; off >>= 1) S += __shfl_xor_sync(0xffffffffu, S, off);
-        if (need_a)
-            for (int off = 16; off >= 1; off >>= 1) A += __shfl_xor_sync(0xffffffffu, A, off);
-    }
+    if (need_sum) hyper_sums<BATCH, false>(a, which, need_a, chain, part0, nparts, S, A);
     if (lane == 0) {
         double val, bval;
         hyper_draw<T>(a, which, chain, hc, sweep, S, A, cur, s2old, b, gpv, zb, pre, extra, fstream, fn, frank, val,

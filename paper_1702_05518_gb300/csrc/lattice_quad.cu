@@ -29,6 +29,8 @@
 
 #include "gmrf_device.cuh"
 #include "gmrf_internal.h"
+#include "hyper_task.cuh"
+#include "mbarrier.cuh"
 
 namespace gmrf {
 namespace {
@@ -48,14 +50,15 @@ struct QuadCtx {
     // the next sweep and, in accumulated sweeps, the running mean and M2 (Welford, from the
     // shared-memory copies ms, m2s).
     float *XW, *MEAN, *M2;
-    const float *ms, *m2s;
+    float *ms, *m2s;
     int gsub, gcols, gu0, gv0;
     bool acc;
     float inv_k;
 };
 
-// Colour step C for the thread's quads.
-template <int C, int QCS, int NQ, int NT>
+// Colour step C for the thread's quads.  RES (the resident kernel): the running moments stay in
+// shared memory (ms, m2s) instead of going to global memory.
+template <int C, int QCS, int NQ, int NT, bool RES = false>
 __device__ __forceinline__ void quad_colour_step(float *xs, const float *ys, int SUB, const float (&z)[NQ][4],
                                                  int gi0, int gj0, int Hl, int Wl, int lo_i, int hi_i, int lo_j,
                                                  int hi_j, int own_i0, int own_i1, int own_j0, int own_j1,
@@ -114,15 +117,19 @@ __device__ __forceinline__ void quad_colour_step(float *xs, const float *ys, int
                 const float mu = cx.ms[C * SUB + base], mm = cx.m2s[C * SUB + base];
                 const float delta = x - mu;
                 const float m1 = mu + delta * cx.inv_k;
-                cx.MEAN[go] = m1;
-                cx.M2[go] = mm + delta * (x - m1);
+                const float m2 = mm + delta * (x - m1);
+                if (RES) {
+                    cx.ms[C * SUB + base] = m1;
+                    cx.m2s[C * SUB + base] = m2;
+                } else {
+                    cx.MEAN[go] = m1;
+                    cx.M2[go] = m2;
+                }
             }
         }
     }
 }
 
-// Normals of the thread's quads for sweep `sweep` (z[k][c]: the colour-c site of quad k).  Every
-// lane of the warp takes part (the lane pairs exchange words), whether or not its quads exist.
 // Whether site s (sub-array s = 2a + b) of staged quad (u, v) is owned by the tile and on the
 // lattice.
 __device__ __forceinline__ bool quad_owned_site(int u, int v, int s, int QR, int TC, int gu0, int gv0, int Hl, int Wl)
@@ -131,6 +138,8 @@ __device__ __forceinline__ bool quad_owned_site(int u, int v, int s, int QR, int
     return 2 * (gu0 + u) + (s >> 1) < Hl && 2 * (gv0 + v) + (s & 1) < Wl;
 }
 
+// Normals of the thread's quads for sweep `sweep` (z[k][c]: the colour-c site of quad k).  Every
+// lane of the warp takes part (the lane pairs exchange words), whether or not its quads exist.
 template <int QCS, int NT, int NQ>
 __device__ __forceinline__ void quad_normals(float (&z)[NQ][4], uint2 key, uint32_t sweep, uint32_t stream,
                                              uint32_t blocks_per_row, int gu0, int gv0)
@@ -336,6 +345,296 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
     }
 }
 
+constexpr int kQuadResGpre = 128;
+
+// The barrier's arrival count and abort flag in one load (ctl->gbar, ctl->gabort; 16-byte aligned).
+__device__ __forceinline__ void ld_barrier(const unsigned long long *p, unsigned long long &arrivals,
+                                           unsigned long long &abort)
+{
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(arrivals), "=l"(abort) : "l"(p) : "memory");
+}
+
+// The resident form of the quad sweep: `count` whole sweeps of the single field in one
+// cooperative launch (every block resident at once), the tile of each block kept in shared
+// memory from sweep to sweep.  Per sweep:
+//   * the four colour steps as in lattice_quad_kernel (the owned sites go to the next sweep's
+//     state buffer right after their step; the running moments of accumulated sweeps stay in
+//     shared memory until the end of the launch);
+//   * the block's sums (as in lattice_quad_kernel) to its tile partial, then a grid barrier: one
+//     arrival per block on a counter in the sweep control block; while the other blocks finish,
+//     the threads draw their normals of the next sweep;
+//   * every block then draws tau | x (warp 0) and beta0, sigma^2 (warp 1) from all the tile
+//     partials, summed in the order of the hyperparameter kernel and drawn by hyper_draw with the
+//     batch's precomputed variates, so each block holds the values the per-sweep path would have;
+//     block 0 alone stores them and the traces;
+//   * the halo (the two quad rows and columns around the tile), which the neighbouring tiles
+//     have just written, is staged again from global memory through L2.
+// The state buffers alternate by sweep number as on the per-sweep path, so a block that writes
+// sweep t + 1's state never overwrites what a slower block may still read for sweep t.  A wait at
+// the barrier gives up after `wait_ns`: the block counts it in ctl->wait_timeouts and sets
+// ctl->gabort, at which every block leaves its sweep loop.
+template <int QCS, int NT, int NQ>
+__global__ void __launch_bounds__(NT, 1) lattice_quad_resident_kernel(const QuadResArgs ra)
+{
+    constexpr int NW = NT / 32;
+    const FusedArgs &a = ra.f;
+    const HyperArgs &h = ra.h;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float red[NW][3];
+    __shared__ float hs[3];        // tau, 1/sigma^2, beta0 of the current sweep (FP32 copies)
+    __shared__ double dcur[2];     // tau and sigma^2 (FP64) as last drawn
+    __shared__ int s_abort;
+    // the precomputed variates of the launch's first kQuadResGpre sweeps: tau's and 1/sigma^2's
+    // unit-rate Gamma variates and the intercept's normal
+    __shared__ double gsh[kQuadResGpre][3];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const TileXY t = a.tiles[blockIdx.x];
+    const FieldDev f = a.fields[t.field];
+    const int Hl = f.dims[0], Wl = f.dims[1];
+    const int TR = a.TR, TC = a.TC;
+    const int QR = TR / 2 + 4;
+    const int SUB = QR * QCS;
+    const int nquads = SUB;
+    float *xs = reinterpret_cast<float *>(smem_raw);
+    float *ys = xs + 4 * SUB;
+    float *ms = ys + 4 * SUB;
+    float *m2s = ms + 4 * SUB;
+    const int gi0 = t.i0 - 4, gj0 = t.j0 - 4;
+    const int gu0 = gi0 >> 1, gv0 = gj0 >> 1;
+    const bool interior = gi0 >= 0 && gj0 >= 0 && gi0 + 2 * QR <= Hl && gj0 + 2 * QCS <= Wl;
+    const int gsub = f.rows * f.cols, gcols = f.cols;
+    SweepCtl *ctl = a.ctl;
+    const long long sweep0 = ctl->sweep;
+    long long acc_count = ctl->acc_count;
+    const long long bbase = ctl->batch_base, bcount = ctl->batch_count;
+    const float *Y = static_cast<const float *>(a.y) + f.slot0;
+    const float *X0 = static_cast<const float *>((sweep0 & 1) ? a.x_alt : a.x) + f.slot0;
+    float *MEAN = static_cast<float *>(a.mean) + f.slot0;
+    float *M2 = static_cast<float *>(a.m2) + f.slot0;
+
+    // Stage the observations, the state and (owned sites) the running moments once.
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        const int q = tid + k * NT;
+        if (q >= nquads) break;
+        const int u = q / QCS, v = q % QCS;
+        const int gu = gu0 + u, gv = gv0 + v;
+        const int go = gu * gcols + gv;
+        float yv[4], xv[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int i = 2 * gu + (s >> 1), j = 2 * gv + (s & 1);
+            const bool ok = interior || (gu >= 0 && gv >= 0 && i < Hl && j < Wl);
+            yv[s] = ok ? Y[s * gsub + go] : 0.0f;
+            xv[s] = ok ? X0[s * gsub + go] : 0.0f;
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            ys[s * SUB + q] = yv[s];
+            xs[s * SUB + q] = xv[s];
+            if (a.acc_enabled && quad_owned_site(u, v, s, QR, TC, gu0, gv0, Hl, Wl)) {
+                ms[s * SUB + q] = MEAN[s * gsub + go];
+                m2s[s * SUB + q] = M2[s * gsub + go];
+            }
+        }
+    }
+    if (tid < 3) hs[tid] = static_cast<const float *>(a.hyp)[static_cast<int64_t>(t.field) * kHypStride + tid];
+    for (int q = tid; q < 3 * min(ra.count, kQuadResGpre); q += NT) {
+        const long long kb = sweep0 + q / 3 - bbase;
+        gsh[q / 3][q % 3] = (h.gpre && kb >= 0 && kb < bcount) ? h.gpre[kb * h.nfields * h.Cp * 4 + q % 3] : 0.0;
+    }
+    if (tid == 0) {
+        dcur[0] = h.tau[0];
+        dcur[1] = h.sig2[0];
+        s_abort = 0;
+    }
+    float z[NQ][4];
+    quad_normals<QCS, NT, NQ>(z, a.key, static_cast<uint32_t>(sweep0), f.stream, static_cast<uint32_t>(Wl) >> 2, gu0,
+                              gv0);
+    const int own_i0 = t.i0, own_i1 = min(Hl, t.i0 + TR), own_j0 = t.j0, own_j1 = min(Wl, t.j0 + TC);
+    const unsigned long long nblk = gridDim.x;
+
+    for (int it = 0; it < ra.count; ++it) {
+        const long long sw = sweep0 + it;
+        __syncthreads();  // the staged state (halo) and the sweep's parameters
+        QuadCtx cx;
+        cx.tau = hs[0];
+        cx.isig = hs[1];
+        cx.beta = hs[2];
+        cx.rho = static_cast<float>(a.rho);
+        cx.accS = 0.0f;
+        cx.accR = 0.0f;
+        cx.accA = 0.0f;
+        float *XW = static_cast<float *>((sw & 1) ? a.x : a.x_alt) + f.slot0;
+        cx.XW = XW;
+        cx.MEAN = MEAN;
+        cx.M2 = M2;
+        cx.ms = ms;
+        cx.m2s = m2s;
+        cx.gsub = gsub;
+        cx.gcols = gcols;
+        cx.gu0 = gu0;
+        cx.gv0 = gv0;
+        cx.acc = a.acc_enabled && sweep_accumulated(sw, a.burn_in, a.thin);
+        cx.inv_k = cx.acc ? 1.0f / static_cast<float>(acc_count + 1) : 0.0f;
+#define GMRF_QUAD_STEP(C)                                                                                        \
+    quad_colour_step<C, QCS, NQ, NT, true>(xs, ys, SUB, z, gi0, gj0, Hl, Wl, max(0, t.i0 - (3 - C)),          \
+                                           min(Hl, t.i0 + TR + (3 - C)), max(0, t.j0 - (3 - C)),               \
+                                           min(Wl, t.j0 + TC + (3 - C)), own_i0, own_i1, own_j0, own_j1,       \
+                                           interior, nquads, cx);                                               \
+    __syncthreads();
+        GMRF_QUAD_STEP(0)
+        GMRF_QUAD_STEP(1)
+        GMRF_QUAD_STEP(2)
+        GMRF_QUAD_STEP(3)
+#undef GMRF_QUAD_STEP
+        if (cx.acc) ++acc_count;
+
+        // The tile's sums, in the order of lattice_quad_kernel.
+        float sS = cx.accS, sR = cx.accR, sA = cx.accA;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            sS += __shfl_xor_sync(0xffffffffu, sS, o);
+            sR += __shfl_xor_sync(0xffffffffu, sR, o);
+            sA += __shfl_xor_sync(0xffffffffu, sA, o);
+        }
+        if (lane == 0) {
+            red[warp][0] = sS;
+            red[warp][1] = sR;
+            red[warp][2] = sA;
+        }
+        __syncthreads();
+        if (tid < 3) {
+            float sum = 0.0f;
+            for (int w = 0; w < NW; ++w) sum += red[w][tid];
+            reinterpret_cast<double *>(a.partials + t.part)[tid] = static_cast<double>(sum);
+        }
+        __syncthreads();  // the partial and every owned site of the sweep are stored
+
+        // Grid barrier: arrive, draw the next sweep's normals, then wait (bounded).
+        if (tid == 0)  // release: this block's stores, ordered before by the barrier above
+            asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(&ctl->gbar) : "memory");
+        if (it + 1 < ra.count)
+            quad_normals<QCS, NT, NQ>(z, a.key, static_cast<uint32_t>(sw + 1), f.stream, static_cast<uint32_t>(Wl) >> 2,
+                                      gu0, gv0);
+        if (tid == 0) {
+            const unsigned long long target = (static_cast<unsigned long long>(it) + 1) * nblk + ra.extra_arrivals;
+            unsigned long long arrived, aborted;
+            ld_barrier(&ctl->gbar, arrived, aborted);
+            const uint64_t t0 = global_ns();
+            for (uint32_t spin = 1; arrived < target; ++spin) {
+                if (aborted != 0) {
+                    s_abort = 1;
+                    break;
+                }
+                if ((spin & 15u) == 0 && global_ns() - t0 >= ra.wait_ns) {
+                    atomicAdd(&ctl->wait_timeouts, 1ull);
+                    atomicExch(&ctl->gabort, 1ull);
+                    s_abort = 1;
+                    break;
+                }
+                ld_barrier(&ctl->gbar, arrived, aborted);
+            }
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");  // acquire: the stores before every arrival
+        }
+        __syncthreads();
+        if (s_abort) break;
+
+        // The halo of the next sweep (its state buffer is XW), through L2, by the threads of the
+        // warps that do not draw (one halo quad each: the two quad rows above and below the tile,
+        // then the two quad columns on each side), while warps 0 and 1 draw.
+        if (warp >= 2) {
+            const int nhalo = 4 * QCS + 4 * (QR - 4);
+            for (int hq = tid - 64; hq < nhalo; hq += NT - 64) {
+                int u, v;
+                if (hq < 4 * QCS) {
+                    const int r = hq / QCS;
+                    u = r < 2 ? r : QR - 4 + r;
+                    v = hq - r * QCS;
+                } else {
+                    const int r = hq - 4 * QCS, c = r & 3;
+                    u = 2 + (r >> 2);
+                    v = c < 2 ? c : QCS - 4 + c;
+                }
+                const int q = u * QCS + v;
+                const int gu = gu0 + u, gv = gv0 + v;
+                const int go = gu * gcols + gv;
+                float hv[4];
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    const int i = 2 * gu + (s >> 1), j = 2 * gv + (s & 1);
+                    const bool ok = interior || (gu >= 0 && gv >= 0 && i < Hl && j < Wl);
+                    hv[s] = ok ? __ldcg(XW + s * gsub + go) : 0.0f;
+                }
+#pragma unroll
+                for (int s = 0; s < 4; ++s) xs[s * SUB + q] = hv[s];
+            }
+        }
+
+        // The conjugate draws at the end of sweep sw (warp 0: tau; warp 1: beta0, then sigma^2).
+        if (warp < 2) {
+            const int which = warp;
+            const bool need_sum = which ? (h.draw || h.draw_beta) : h.draw;
+            const bool need_a = which && h.draw_beta;
+            double S = 0.0, A = 0.0;
+            if (need_sum) hyper_sums<false, true, 5>(h, which, need_a, 0, f.part0, f.nparts, S, A);
+            if (lane == 0) {
+                const long long kb = sw - bbase;
+                const bool pre = h.gpre && kb >= 0 && kb < bcount;
+                double gpv = 0.0, zb = 0.0;
+                if (pre) {
+                    const double *gp = it < kQuadResGpre ? gsh[it] : h.gpre + kb * h.nfields * h.Cp * 4;
+                    gpv = gp[which];
+                    zb = gp[2];
+                }
+                // (warp 0's draw reads neither sigma^2 nor beta0, which warp 1 replaces meanwhile)
+                const double cur = dcur[which], s2old = which ? dcur[1] : 0.0;
+                const double b = which ? static_cast<double>(hs[2]) : 0.0;
+                double val, bval;
+                hyper_draw<float>(h, which, 0, 0, sw, S, A, cur, s2old, b, gpv, zb, pre, 0, f.stream, f.n, f.rank, val,
+                                  bval, blockIdx.x == 0);
+                if (which == 0) {
+                    if (h.draw) hs[0] = static_cast<float>(val);
+                } else {
+                    if (h.draw_beta) hs[2] = static_cast<float>(bval);
+                    if (h.draw) hs[1] = static_cast<float>(1.0 / val);
+                }
+                dcur[which] = val;
+            }
+        }
+    }
+
+    // The running moments of the owned sites back to global memory.
+    if (a.acc_enabled) {
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const int q = tid + k * NT;
+            if (q >= nquads) break;
+            const int u = q / QCS, v = q % QCS;
+            const int go = (gu0 + u) * gcols + gv0 + v;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                if (!quad_owned_site(u, v, s, QR, TC, gu0, gv0, Hl, Wl)) continue;
+                MEAN[s * gsub + go] = ms[s * SUB + q];
+                M2[s * gsub + go] = m2s[s * SUB + q];
+            }
+        }
+    }
+    // The last block to finish advances the counters and clears the barrier for the next launch.
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl->ticket, 1ull) == nblk - 1) {
+            ctl->sweep = sweep0 + ra.count;
+            ctl->fnext = sweep0 + ra.count;
+            ctl->acc_count = acc_count;
+            ctl->ticket = 0;
+            ctl->gbar = 0;
+            ctl->gabort = 0;
+        }
+    }
+}
+
 }  // namespace
 
 // Configurations: (quad columns per staged row, threads, quads per thread).
@@ -363,6 +662,59 @@ cudaError_t launch_lattice_quad(int qcs, int nt, int nq, const FusedArgs &a, siz
     if (qcs == Q && nt == N && nq == M) {                                              \
         return launch_sweep_kernel(lattice_quad_kernel<Q, N, M>, a.ntiles, N, smem, stream, a); \
     }
+    GMRF_QUAD_CFG(64, 768, 3)
+    GMRF_QUAD_CFG(64, 1024, 2)
+    GMRF_QUAD_CFG(32, 1024, 2)
+    GMRF_QUAD_CFG(32, 512, 2)
+    GMRF_QUAD_CFG(68, 704, 3)
+#undef GMRF_QUAD_CFG
+    return cudaErrorInvalidValue;
+}
+
+// The resident form: whether every tile's block can be resident at once (one wave), and the
+// cooperative launch of `ra.count` sweeps.
+cudaError_t lattice_quad_resident_fits(int qcs, int nt, int nq, size_t smem, int ntiles, bool *fits)
+{
+    *fits = false;
+    int dev = 0, sms = 0, coop = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e != cudaSuccess) return e;
+#define GMRF_QUAD_CFG(Q, N, M)                                                                                   \
+    if (qcs == Q && nt == N && nq == M) {                                                                     \
+        e = cudaFuncSetAttribute(lattice_quad_resident_kernel<Q, N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 static_cast<int>(smem));                                                     \
+        if (e == cudaSuccess)                                                                                 \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lattice_quad_resident_kernel<Q, N, M>, N, smem); \
+        if (e != cudaSuccess) return e;                                                                       \
+        *fits = coop != 0 && static_cast<int64_t>(per_sm) * sms >= ntiles;                                   \
+        return cudaSuccess;                                                                                   \
+    }
+    GMRF_QUAD_CFG(64, 768, 3)
+    GMRF_QUAD_CFG(64, 1024, 2)
+    GMRF_QUAD_CFG(32, 1024, 2)
+    GMRF_QUAD_CFG(32, 512, 2)
+    GMRF_QUAD_CFG(68, 704, 3)
+#undef GMRF_QUAD_CFG
+    return cudaSuccess;
+}
+
+cudaError_t launch_lattice_quad_resident(int qcs, int nt, int nq, const QuadResArgs &ra, size_t smem,
+                                         cudaStream_t stream)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ra.f.ntiles);
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+#define GMRF_QUAD_CFG(Q, N, M) \
+    if (qcs == Q && nt == N && nq == M) return cudaLaunchKernelEx(&cfg, lattice_quad_resident_kernel<Q, N, M>, ra);
     GMRF_QUAD_CFG(64, 768, 3)
     GMRF_QUAD_CFG(64, 1024, 2)
     GMRF_QUAD_CFG(32, 1024, 2)
