@@ -30,11 +30,12 @@
 // of its next site's neighbours are in flight while it computes: in colour 0 they are issued once the current site's neighbour sums
 // are taken, before its draw; colour 1 keeps a site's neighbour values for its edge sums, so it
 // issues them after those and then draws the next site's normals while they arrive.
-// A warp whose sites are all interior (six
-// neighbours) takes a path without boundary masks, with m_i = a s_i + b (y_i - beta0) and
-// a = tau rho / P, b = (1/sigma^2) / P, 1/sqrt(P) computed once per launch for d = 6; other
-// warps compute them per site by the same operations, so a site's result does not depend on
-// the path its warp took.
+// Every site takes m_i = a s_i + b (y_i - beta0) and x_i = m_i + c z_i with a = tau rho / P,
+// b = (1/sigma^2) / P, c = 1/sqrt(P), computed once per launch for each degree d = 0 .. 6 (a
+// row's first and last sites are boundary sites, so at 256^3 half the warps hold one); a warp
+// whose sites all have six neighbours takes a path without boundary masks, one whose sites all
+// have their four off-row neighbours (at 256^3 nearly every other warp) tests only the two in-row
+// ones, and a site's result does not depend on the path its warp took.
 //
 // Sums for the conjugate draws, per chain: colour 1 adds rho sum_k (x_i - x_k)^2 over its
 // neighbours (all of lower colour, final by then), both colours add (1 - rho) d_i x_i^2 (proper
@@ -156,20 +157,20 @@ __device__ __forceinline__ void box_muller_block_f32x2(uint4 w, f2 &z01, f2 &z23
             sq[h] = -sq[h];
         }
     }
-    const f2 zc = mul2(r, pk(cq[0], cq[1])), zs = mul2(r, pk(sq[0], sq[1]));
-    float c0, c1, n0, n1;
-    upk(zc, c0, c1);
-    upk(zs, n0, n1);
-    z01 = pk(c0, n0);
-    z23 = pk(c1, n1);
+    // each pair's radius times its (cos, sin): the chains' order, with no transposition
+    float r0, r1;
+    upk(r, r0, r1);
+    z01 = mul2(splat(r0), pk(cq[0], sq[0]));
+    z23 = mul2(splat(r1), pk(cq[1], sq[1]));
 }
 
-// Per chain parameters of the launch, in shared memory: tau, tau rho, 1/sigma^2, beta0, and the
-// interior coefficients (d = 6) tau rho / P, (1/sigma^2) / P, 1/sqrt(P).
+// Per chain parameters of the launch, in shared memory: tau, tau rho, 1/sigma^2, beta0, and for
+// every degree d = 0 .. 6 the coefficients tau rho / P, (1/sigma^2) / P, 1/sqrt(P) with
+// P = tau d + 1/sigma^2 (a boundary site reads those of its degree instead of computing them).
 template <int NC>
 struct alignas(16) Params3 {
     float tau[NC], tr[NC], isig[NC], beta[NC];
-    float ca[NC], cb[NC], crs[NC];
+    float ca[7][NC], cb[7][NC], crs[7][NC];
 };
 
 template <int NC>
@@ -189,9 +190,12 @@ struct Site3 {
                           // other colour's)
     uint32_t valid;       // neighbours present: bit k for j - 1, j + 1, i - 1, i + 1, l - 1, l + 1
     uint32_t site;        // natural site index
-    float y, d;
+    float y, d;           // observation, degree
+    int dg;               // degree
     int p;                // column parity of the site's row
-    bool ok, interior;    // a site of the lattice; every site of the warp has six neighbours
+    bool ok;              // a site of the lattice
+    int mode;             // kMaskNone: every site of the warp has six neighbours; kMaskRow: every
+                          // site of the warp has its four off-row neighbours; kMaskAll: neither
 };
 
 // Offsets of the six neighbours' chain vectors from the other colour's slot rb (in floats).
@@ -200,7 +204,11 @@ struct NbrOff {
 };
 
 // The neighbours' values of a site (zeros for missing ones); XO: the other colour's sub-array.
-template <int NG, bool INTERIOR>
+// Which neighbours a warp's sites must test before use (see Site3::mode).
+constexpr int kMaskAll = 0, kMaskRow = 1, kMaskNone = 2;
+__host__ __device__ constexpr bool always_present(int mode, int k) { return mode == kMaskNone || (mode == kMaskRow && k >= 2); }
+
+template <int NG, int MODE>
 __device__ __forceinline__ void load_neighbours(const float *XO, const NbrOff &no, const Site3 &st, f2 (&nb)[6][2 * NG])
 {
     constexpr int NC = 4 * NG;
@@ -208,7 +216,7 @@ __device__ __forceinline__ void load_neighbours(const float *XO, const NbrOff &n
     const float *nbp[6] = {xo + (st.p - 1) * NC, xo + st.p * NC, xo - no.row, xo + no.row, xo - no.plane, xo + no.plane};
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        if (INTERIOR || ((st.valid >> k) & 1u)) {
+        if (always_present(MODE, k) || ((st.valid >> k) & 1u)) {
 #pragma unroll
             for (int g = 0; g < NG; ++g) ld2x2(nbp[k] + 4 * g, nb[k][2 * g], nb[k][2 * g + 1]);
         } else {
@@ -243,7 +251,7 @@ __device__ __forceinline__ void draw_normals(const StepArgs &a, const Site3 &st,
     }
 }
 
-template <int NG, bool ODD, bool ICPT, bool PCAR, bool INTERIOR>
+template <int NG, bool ODD, bool ICPT, bool PCAR, int MODE>
 __device__ __forceinline__ void site_update(const StepArgs &a, const Params3<4 * NG> &pp, Acc3<2 * NG> &ac,
                                             const Site3 &st, const f2 (&s)[2 * NG], const f2 (&nb)[6][2 * NG],
                                             const f2 (&z)[2 * NG], float *XS, float *MS, float *QS, bool update,
@@ -254,28 +262,10 @@ __device__ __forceinline__ void site_update(const StepArgs &a, const Params3<4 *
     const f2 yy = pk(st.y, st.y);
     f2 x[NP];
     if (update) {
+        const int dg = MODE == kMaskNone ? 6 : st.dg;
 #pragma unroll
         for (int u = 0; u < NP; ++u) {
-            f2 ca, cb, crs;
-            if (INTERIOR) {
-                ca = pair_of<NC>(pp.ca, u);
-                cb = pair_of<NC>(pp.cb, u);
-                crs = pair_of<NC>(pp.crs, u);
-            } else {
-                float c[3][2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int v = 2 * u + h;
-                    const float P = fmaf(pp.tau[v], st.d, pp.isig[v]);
-                    const float rP = rcp_approx(P);
-                    c[0][h] = pp.tr[v] * rP;
-                    c[1][h] = pp.isig[v] * rP;
-                    c[2][h] = rsqrt_approx(P);
-                }
-                ca = pk(c[0][0], c[0][1]);
-                cb = pk(c[1][0], c[1][1]);
-                crs = pk(c[2][0], c[2][1]);
-            }
+            const f2 ca = pair_of<NC>(pp.ca[dg], u), cb = pair_of<NC>(pp.cb[dg], u), crs = pair_of<NC>(pp.crs[dg], u);
             const f2 yb = ICPT ? sub2(yy, pair_of<NC>(pp.beta, u)) : yy;
             x[u] = fma2(z[u], crs, fma2(ca, s[u], mul2(yb, cb)));
         }
@@ -293,7 +283,7 @@ __device__ __forceinline__ void site_update(const StepArgs &a, const Params3<4 *
             f2 ev = 0ull;
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
-                if (INTERIOR || ((st.valid >> k) & 1u)) {
+                if (always_present(MODE, k) || ((st.valid >> k) & 1u)) {
                     const f2 df = sub2(x[u], nb[k][u]);
                     ev = fma2(df, df, ev);
                 }
@@ -348,12 +338,15 @@ __global__ void __launch_bounds__(k3Block, 2) lattice3d_kernel(const StepArgs a)
         pp.tr[v] = PCAR ? hyp[0] * rho : hyp[0];
         pp.isig[v] = hyp[1];
         pp.beta[v] = ICPT ? hyp[2] : 0.0f;
-        // the operations of the boundary path at d = 6
-        const float P = fmaf(pp.tau[v], 6.0f, pp.isig[v]);
+    }
+    __syncthreads();
+    if (threadIdx.x < 7 * NC) {
+        const int d = threadIdx.x / NC, v = threadIdx.x - d * NC;
+        const float P = fmaf(pp.tau[v], static_cast<float>(d), pp.isig[v]);
         const float rP = rcp_approx(P);
-        pp.ca[v] = pp.tr[v] * rP;
-        pp.cb[v] = pp.isig[v] * rP;
-        pp.crs[v] = rsqrt_approx(P);
+        pp.ca[d][v] = pp.tr[v] * rP;
+        pp.cb[d][v] = pp.isig[v] * rP;
+        pp.crs[d][v] = rsqrt_approx(P);
     }
     __syncthreads();
     Acc3<NP> ac;
@@ -398,13 +391,25 @@ __global__ void __launch_bounds__(k3Block, 2) lattice3d_kernel(const StepArgs a)
         st.p = (c + l + i) & 1;
         const int j = 2 * h + st.p;
         st.ok = j < W;
-        st.valid = (j > 0 ? 1u : 0u) | (j + 1 < W ? 2u : 0u) | (i > 0 ? 4u : 0u) | (i + 1 < H ? 8u : 0u) |
-                   (l > 0 ? 16u : 0u) | (l + 1 < L ? 32u : 0u);
-        st.interior = __all_sync(__activemask(), st.valid == 63u || !st.ok);
+        // 0 < j < W - 1 and the same for i, l (unsigned comparisons; false for extents below 3)
+        const bool jin = static_cast<unsigned>(j - 1) < static_cast<unsigned>(W - 2);
+        const bool rin = static_cast<unsigned>(i - 1) < static_cast<unsigned>(H - 2) &&
+                         static_cast<unsigned>(l - 1) < static_cast<unsigned>(L - 2);
+        const unsigned act = __activemask();
+        st.mode = __all_sync(act, (jin && rin) || !st.ok) ? kMaskNone
+                                                          : (__all_sync(act, rin || !st.ok) ? kMaskRow : kMaskAll);
+        if (st.mode == kMaskNone)
+            st.valid = 63u;
+        else if (st.mode == kMaskRow)
+            st.valid = 60u | (j > 0 ? 1u : 0u) | (j + 1 < W ? 2u : 0u);
+        else
+            st.valid = (j > 0 ? 1u : 0u) | (j + 1 < W ? 2u : 0u) | (i > 0 ? 4u : 0u) | (i + 1 < H ? 8u : 0u) |
+                       (l > 0 ? 16u : 0u) | (l + 1 < L ? 32u : 0u);
         st.rb = static_cast<int64_t>(r) * cols + h;
         st.site = static_cast<uint32_t>(r) * static_cast<uint32_t>(W) + static_cast<uint32_t>(j);
         st.y = st.ok ? YS[st.rb] : 0.0f;
-        st.d = static_cast<float>(__popc(st.valid));
+        st.dg = __popc(st.valid);
+        st.d = static_cast<float>(st.dg);
     };
     auto start_loads = [&](const Site3 &st, f2 (&nb)[6][NP]) {
         if (st.ok && acc) {
@@ -413,11 +418,20 @@ __global__ void __launch_bounds__(k3Block, 2) lattice3d_kernel(const StepArgs a)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(QS + st.rb * NC));
         }
         if (st.ok) {
-            if (st.interior) load_neighbours<NG, true>(XO, no, st, nb);
-            else load_neighbours<NG, false>(XO, no, st, nb);
+            if (st.mode == kMaskNone) load_neighbours<NG, kMaskNone>(XO, no, st, nb);
+            else if (st.mode == kMaskRow) load_neighbours<NG, kMaskRow>(XO, no, st, nb);
+            else load_neighbours<NG, kMaskAll>(XO, no, st, nb);
         }
     };
     f2 nb[6][NP];
+    auto update_site = [&](const Site3 &st, const f2 (&s)[NP], const f2 (&z)[NP]) {
+        if (st.mode == kMaskNone)
+            site_update<NG, ODD, ICPT, PCAR, kMaskNone>(a, pp, ac, st, s, nb, z, XS, MS, QS, update, acc, invk2, rho2, om);
+        else if (st.mode == kMaskRow)
+            site_update<NG, ODD, ICPT, PCAR, kMaskRow>(a, pp, ac, st, s, nb, z, XS, MS, QS, update, acc, invk2, rho2, om);
+        else
+            site_update<NG, ODD, ICPT, PCAR, kMaskAll>(a, pp, ac, st, s, nb, z, XS, MS, QS, update, acc, invk2, rho2, om);
+    };
     if (!ODD) {
         // Colour 0: a site's neighbour sums are taken first (freeing `nb`), then the loads of the
         // thread's next site are issued, then the site is drawn and updated while they arrive.
@@ -438,12 +452,7 @@ __global__ void __launch_bounds__(k3Block, 2) lattice3d_kernel(const StepArgs a)
             }
             if (cur.ok) {
                 if (update) draw_normals<NG>(a, cur, sweep, f.stream, z);
-                if (cur.interior)
-                    site_update<NG, ODD, ICPT, PCAR, true>(a, pp, ac, cur, s, nb, z, XS, MS, QS, update, acc, invk2,
-                                                           rho2, om);
-                else
-                    site_update<NG, ODD, ICPT, PCAR, false>(a, pp, ac, cur, s, nb, z, XS, MS, QS, update, acc, invk2,
-                                                            rho2, om);
+                update_site(cur, s, z);
             }
             cur = nxt;
         }
@@ -462,12 +471,7 @@ __global__ void __launch_bounds__(k3Block, 2) lattice3d_kernel(const StepArgs a)
             if (cur.ok) {
                 f2 s[NP];
                 sum_neighbours<NG>(nb, s);
-                if (cur.interior)
-                    site_update<NG, ODD, ICPT, PCAR, true>(a, pp, ac, cur, s, nb, z, XS, MS, QS, update, acc, invk2,
-                                                           rho2, om);
-                else
-                    site_update<NG, ODD, ICPT, PCAR, false>(a, pp, ac, cur, s, nb, z, XS, MS, QS, update, acc, invk2,
-                                                            rho2, om);
+                update_site(cur, s, z);
             }
             Site3 nxt;
             nxt.ok = false;
