@@ -120,24 +120,26 @@ __device__ __forceinline__ void part_values(const Part3 *p, int which, bool need
 
 // The sums of task `which` over the field's tile partials, by all 32 lanes of the calling warp,
 // in a fixed order: lane l adds partials l, l + 32, l + 64, ... in that order, then a shuffle
-// tree.  S: the S (which 0) or R (which 1) sums; A: the intercept's sums when need_a.  U loads
-// are issued before their additions, so a warp waits for one L2 round trip per 32 U partials,
-// not per 32 (the sums are those of one load at a time).  BATCH (fields of many tiles): whole
-// rounds of U first; the last round, or every round of a smaller field, is predicated.  CG: the
-// partials are loaded through L2 only (the resident quad kernel reads partials that other blocks
-// of the same launch rewrite every sweep).
-template <bool BATCH, bool CG, int U = 8>
+// tree.  S: the S (which 0) or R (which 1) sums; A: the intercept's sums when need_a.  BATCH
+// (fields of 256 or more tiles): eight loads are issued before their additions, so a warp waits
+// for one L2 round trip per 256 partials, not per 32 (the sums are the same); for fewer partials
+// one load at a time measured faster (the draws of the 512 x 512 image: 15.3 against 15.9 us per
+// sweep with eight predicated loads in flight).  CG: the partials are loaded through L2 only (the
+// resident quad kernel reads partials that other blocks of the same launch rewrite every sweep).
+template <bool BATCH, bool CG>
 __device__ __forceinline__ void hyper_sums(const HyperArgs &a, int which, bool need_a, int chain, int32_t part0,
                                            int32_t nparts, double &S, double &A)
 {
     const int lane = threadIdx.x & 31;
     const Part3 *P = a.partials + static_cast<int64_t>(part0) * a.Cp + chain;
+    constexpr int U = 8;
     int k = lane;
     if constexpr (BATCH) {
         for (; k + 32 * (U - 1) < nparts; k += 32 * U) {
             double vs[U], va[U];
 #pragma unroll
-            for (int j = 0; j < U; ++j) part_values<CG>(P + static_cast<int64_t>(k + 32 * j) * a.Cp, which, need_a, vs[j], va[j]);
+            for (int j = 0; j < U; ++j)
+                part_values<CG>(P + static_cast<int64_t>(k + 32 * j) * a.Cp, which, need_a, vs[j], va[j]);
 #pragma unroll
             for (int j = 0; j < U; ++j) {
                 S += vs[j];
@@ -145,22 +147,11 @@ __device__ __forceinline__ void hyper_sums(const HyperArgs &a, int which, bool n
             }
         }
     }
-    for (; k < nparts; k += 32 * U) {
-        double vs[U], va[U];
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-            vs[j] = 0.0;
-            va[j] = 0.0;
-            if (k + 32 * j < nparts)
-                part_values<CG>(P + static_cast<int64_t>(k + 32 * j) * a.Cp, which, need_a, vs[j], va[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-            if (k + 32 * j < nparts) {
-                S += vs[j];
-                if (need_a) A += va[j];
-            }
-        }
+    for (; k < nparts; k += 32) {
+        double v, va;
+        part_values<CG>(P + static_cast<int64_t>(k) * a.Cp, which, need_a, v, va);
+        S += v;
+        if (need_a) A += va;
     }
     for (int off = 16; off >= 1; off >>= 1) S += __shfl_xor_sync(0xffffffffu, S, off);
     if (need_a)

@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_resident_kernel(const Quad
             const bool need_sum = which ? (h.draw || h.draw_beta) : h.draw;
             const bool need_a = which && h.draw_beta;
             double S = 0.0, A = 0.0;
-            if (need_sum) hyper_sums<false, true, 5>(h, which, need_a, 0, f.part0, f.nparts, S, A);
+            if (need_sum) hyper_sums<false, true>(h, which, need_a, 0, f.part0, f.nparts, S, A);
             if (lane == 0) {
                 const long long kb = sw - bbase;
                 const bool pre = h.gpre && kb >= 0 && kb < bcount;
