@@ -584,9 +584,10 @@ def run_ours(args):
                                  "psrf": None if d["psrf"] != d["psrf"] else float(d["psrf"]),
                                  "ces_s": t_run / float(np.sum(d["ess"]))}
 
-    # Resident samplers (a small single 2-D lattice, or a single graph below 32768 sites): a batch
-    # of sweeps is three launches (unit-rate Gamma variates, normals, the resident kernel); timed
-    # as whole batches.
+    # Resident samplers (a small single 2-D lattice, a single graph below 32768 sites, or the quad
+    # lattice's tiles in one wave): a batch of sweeps is two launches (the unit-rate Gamma variates,
+    # with the batch's normals where the resident kernel does not draw its own, then the resident
+    # kernel); timed as whole batches.
     resident_batch = None
     if info["resident"]:
         G = spec["graph_sweeps"]
@@ -780,7 +781,7 @@ def run_ours(args):
                "sample": f"{spec['cpu_sweeps']} sweeps of the full workload ({u} site-updates, {dt:.1f} s); "
                          f"CPU: {cpu_model()}"}
     # per step: every stage of every sweep, one Gamma-variate batch per 64 (or graph_sweeps)
-    # sweeps, and the restart kernel; resident samplers: three launches per batch of sweeps (a
+    # sweeps, and the restart kernel; resident samplers: two launches per batch of sweeps (a
     # graph of graph_sweeps sweeps holds ceil(graph_sweeps / batch) batches, a left-over sweep one)
     batch = max(64, spec["graph_sweeps"])
     launches = args.steps * (spec["sweeps"] * info["launches_per_sweep"] + -(-spec["sweeps"] // batch) + 1)
@@ -789,8 +790,9 @@ def run_ours(args):
         rb = min(128, max(64, G))
         full, rem = divmod(spec["sweeps"], G) if G > 0 else (0, spec["sweeps"])
         chunks = full * -(-G // rb) + (rem if G > 0 else -(-rem // rb))
-        # quad tiles: the Gamma variates and the cooperative kernel (its blocks draw the normals)
-        launches = args.steps * ((2 if info["resident"] == 3 else 3) * chunks + 1)
+        # two launches per batch: the Gamma variates (with the batch's normals, except for quad
+        # tiles, whose blocks draw their own) and the resident kernel
+        launches = args.steps * (2 * chunks + 1)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

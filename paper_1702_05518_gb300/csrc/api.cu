@@ -593,7 +593,7 @@ HyperArgs hyper_args(gmrf_sampler *s, int draw, int draw_beta, int end_of_sweep)
     return h;
 }
 
-cudaError_t launch_pre(gmrf_sampler *s, int count, cudaStream_t st)
+GammaPreArgs gamma_pre_args(gmrf_sampler *s, int count)
 {
     GammaPreArgs g{};
     g.fields = s->fields_dev;
@@ -606,7 +606,12 @@ cudaError_t launch_pre(gmrf_sampler *s, int count, cudaStream_t st)
     g.count = count;
     g.intercept = has_beta(s) ? 1 : 0;
     g.gpre = s->gpre;
-    return launch_gamma_pre(g, st);
+    return g;
+}
+
+cudaError_t launch_pre(gmrf_sampler *s, int count, cudaStream_t st)
+{
+    return launch_gamma_pre(gamma_pre_args(s, count), st);
 }
 
 // The resident form of the quad kernel: a single-chain FP32 8-neighbour field on the quad kernel
@@ -756,9 +761,14 @@ ResCsrArgs csr_resident_args(gmrf_sampler *s, int count, int draw, int draw_beta
     return r;
 }
 
-cudaError_t launch_res_normals(gmrf_sampler *s, int count, cudaStream_t st)
+// The batch's normals for the resident kernels and, with `gamma`, its Gamma variates (one launch).
+cudaError_t launch_res_normals(gmrf_sampler *s, int count, bool gamma, cudaStream_t st)
 {
     ResNormArgs r{};
+    if (gamma) {
+        r.g = gamma_pre_args(s, count);
+        r.gamma_blocks = (count * s->nfields * s->Cp * 4 + 63) / 64;
+    }
     r.fields = s->fields_dev;
     r.ctl = s->ctl;
     r.key = philox_key(s->opts.seed);
@@ -898,8 +908,8 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int with_hyper, cudaStr
         for (int k = 0; k < nsweeps && e == cudaSuccess;) {
             const NvtxRange range(kBatch[s->resident]);
             const int cnt = std::min(s->res_batch, nsweeps - k);
-            if (draw || draw_beta) e = launch_pre(s, cnt, st);
             if (s->resident == 3) {
+                if (draw || draw_beta) e = launch_pre(s, cnt, st);
                 // the quad kernel's tiles draw their own normals
                 const int kd = GMRF_LATTICE2D_8;
                 if (e == cudaSuccess)
@@ -908,7 +918,8 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int with_hyper, cudaStr
                 k += cnt;
                 continue;
             }
-            if (e == cudaSuccess) e = launch_res_normals(s, cnt, st);
+            // the batch's normals and, when drawn, its Gamma variates
+            e = launch_res_normals(s, cnt, draw || draw_beta, st);
             if (e == cudaSuccess && s->resident == 2)
                 e = launch_csr_resident(s->precision, s->res_cluster, s->res_positions, s->C,
                                         csr_resident_args(s, cnt, draw, draw_beta), s->res_smem, st);

@@ -122,7 +122,9 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
     __shared__ __align__(8) uint64_t sbar[2];  // cluster: the colour steps' barriers, by step parity
     __shared__ int s_gave_up;                  // cluster: a step's wait ran out (no more waits)
 
-    pdl_wait();
+    // Everything up to the first normals depends only on the previous batch's kernel (complete
+    // before this launch's predecessor, the batch's normals, let this one start), so the chain is
+    // staged while the normals are still being drawn; pdl_wait comes before their first use.
     const HyperArgs &h = a.h;
     const uint32_t rank = CL > 1 ? cluster_rank() : 0u;
     const int chain = blockIdx.x / CL, tid = threadIdx.x, NT = blockDim.x, NTS = kCsrSiteThreads;
@@ -137,7 +139,6 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
 
     const long long sweep0 = h.ctl->sweep;
     long long acc = h.ctl->acc_count;
-    const long long bbase = h.ctl->batch_base, bcount = h.ctl->batch_count;
     if (tid < 3) hs[tid] = static_cast<const T *>(h.hyp)[static_cast<int64_t>(chain) * kHypStride + tid];
     if (tid <= K) coffs[tid] = a.coff[tid];
     __syncthreads();
@@ -178,6 +179,8 @@ __global__ void __launch_bounds__(kCsrThreads, 1) csr_resident_kernel(const ResC
     }
     __syncthreads();
     if (CL > 1) cluster_sync();  // every block of the cluster has its copy before any store into it
+    pdl_wait();                  // the batch's normals and Gamma variates
+    const long long bbase = h.ctl->batch_base, bcount = h.ctl->batch_count;
 
     const T *Y = static_cast<const T *>(a.y) + f.slot0;
     const T *ZB = static_cast<const T *>(a.zbuf) + static_cast<int64_t>(chain) * n;

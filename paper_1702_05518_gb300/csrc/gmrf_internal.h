@@ -94,6 +94,20 @@ struct HyperArgs {
     int32_t max_parts;    // the most tile partials of any field
 };
 
+// Unit-rate Gamma variates (tau and 1/sigma^2 of every field and chain) for sweeps
+// ctl->sweep .. ctl->sweep + count - 1, one thread each; records the batch in ctl.
+struct GammaPreArgs {
+    const FieldDev *fields;
+    int32_t nfields;
+    int32_t Cp;
+    SweepCtl *ctl;
+    uint2 key;
+    double a_tau, a_sig;
+    int32_t count;
+    int32_t intercept;   // 1: also the standard normals of the intercept draws
+    double *gpre;
+};
+
 // Arguments of one launch of the resident kernel (lattice_resident.cu): `count` whole sweeps of
 // the single 2-D lattice field 0, one block per chain, the chain in shared memory.
 struct ResidentArgs {
@@ -122,6 +136,8 @@ struct ResNormArgs {
     int32_t NI, NTS;      // lattice: positions per thread and class, site threads
     const int32_t *perm_inv;  // graph: natural site -> permuted position (then out is [count][C][n])
     void *out;
+    GammaPreArgs g;           // the batch's Gamma variates, drawn by the first gamma_blocks blocks
+    int32_t gamma_blocks;     // (64 threads of each); 0: none
 };
 
 // Arguments of one launch of the graph resident kernel (csr_resident.cu): `count` whole sweeps
@@ -184,19 +200,6 @@ struct FusedArgs {
 };
 
 
-// Unit-rate Gamma variates (tau and 1/sigma^2 of every field and chain) for sweeps
-// ctl->sweep .. ctl->sweep + count - 1, one thread each; records the batch in ctl.
-struct GammaPreArgs {
-    const FieldDev *fields;
-    int32_t nfields;
-    int32_t Cp;
-    SweepCtl *ctl;
-    uint2 key;
-    double a_tau, a_sig;
-    int32_t count;
-    int32_t intercept;   // 1: also the standard normals of the intercept draws
-    double *gpre;
-};
 cudaError_t launch_gamma_pre(const GammaPreArgs &a, cudaStream_t stream);
 
 // Polya-Gamma stage of the binomial model (sweep_kernels.cu): psi[slot][chain] ~ PG(m_i, beta0 +

@@ -26,6 +26,7 @@
 
 #include "gmrf_device.cuh"
 #include "gmrf_internal.h"
+#include "gamma_pre.cuh"
 #include "lattice_common.cuh"
 #include "resident_draws.cuh"
 
@@ -53,7 +54,9 @@ __global__ void __launch_bounds__(res_threads<NI>(), 1) lattice_resident_kernel(
     __shared__ T red[kResMaxThreads / 32][3];
     __shared__ T hs[3];  // tau, 1/sigma^2, beta0 of the current sweep, precision T
 
-    pdl_wait();
+    // Everything up to the first normals depends only on the previous batch's kernel (complete
+    // before this launch's predecessor, the batch's normals, let this one start), so the chain is
+    // staged while the normals are still being drawn; pdl_wait comes before their first use.
     const HyperArgs &h = a.h;
     const int chain = blockIdx.x, NT = blockDim.x, tid = threadIdx.x;
     const int NTS = NT - 64;  // site threads; the last two warps draw the hyperparameters
@@ -73,7 +76,6 @@ __global__ void __launch_bounds__(res_threads<NI>(), 1) lattice_resident_kernel(
 
     const long long sweep0 = h.ctl->sweep;
     long long acc = h.ctl->acc_count;
-    const long long bbase = h.ctl->batch_base, bcount = h.ctl->batch_count;
     if (tid < 3) hs[tid] = static_cast<const T *>(h.hyp)[static_cast<int64_t>(chain) * kHypStride + tid];
     // The drawing lanes' state lives in shared memory (no thread keeps registers for it).
     __shared__ ResidentDraws<T> drs[2];
@@ -152,6 +154,8 @@ __global__ void __launch_bounds__(res_threads<NI>(), 1) lattice_resident_kernel(
     const int64_t zstride = static_cast<int64_t>(a.C) * K * NI * NTS;  // per sweep
     const T *ZB = static_cast<const T *>(a.zbuf) + static_cast<int64_t>(chain) * K * NI * NTS + tid;
     T z[K][NI], zn[K][NI];
+    pdl_wait();  // the batch's normals and Gamma variates
+    const long long bbase = h.ctl->batch_base, bcount = h.ctl->batch_count;
     __syncthreads();
     if (!drawer) {
 #pragma unroll
@@ -323,11 +327,22 @@ __global__ void __launch_bounds__(res_threads<NI>(), 1) lattice_resident_kernel(
 // [sweep][chain][position]; one thread per Philox block (a group of G = 4 / lanes
 // sites and a quadruple of chains, as in site_normals), whose four normals go to the positions of
 // their (site, chain) pairs.  Position q of colour class c belongs to site thread q mod NTS, slot
-// q / NTS; the class positions are those of lattice_resident_kernel.
+// q / NTS; the class positions are those of lattice_resident_kernel.  The first gamma_blocks
+// blocks instead draw the batch's Gamma variates (gamma_pre.cuh) with 64 threads each, so those
+// long FP64 draws spread over as many SMs and run beside the normals.
 template <typename T>
 __global__ void resident_normals_kernel(const ResNormArgs a)
 {
     pdl_wait_then_release();
+    if (static_cast<int>(blockIdx.x) < a.gamma_blocks) {
+        const long long gbase = a.ctl->sweep;
+        const int total = gamma_pre_tasks(a.g);
+        if (threadIdx.x < 64)
+            for (int q = blockIdx.x * 64 + threadIdx.x; q < total; q += a.gamma_blocks * 64) gamma_pre_task(a.g, q, gbase);
+        if (blockIdx.x == 0 && threadIdx.x == 0) gamma_pre_record(a.g, gbase);
+        return;
+    }
+    const int bid = blockIdx.x - a.gamma_blocks, nblk = gridDim.x - a.gamma_blocks;
     const FieldDev f = a.fields[0];
     const int Wl = f.dims[1], n = f.n;
     const bool e8 = f.kind == kLat2D8;
@@ -339,8 +354,8 @@ __global__ void resident_normals_kernel(const ResNormArgs a)
     const int64_t per_sweep = ngroups * nquads;
     const int64_t total = per_sweep * a.count;
     T *out = static_cast<T *>(a.out);
-    for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
-         q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int64_t q = bid * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
+         q += static_cast<int64_t>(nblk) * blockDim.x) {
         const int64_t t = q / per_sweep, r0 = q - t * per_sweep;
         const int cq = static_cast<int>(r0 / ngroups);
         const int64_t g = r0 - static_cast<int64_t>(cq) * ngroups;
@@ -405,6 +420,7 @@ cudaError_t launch_resident_normals(int precision, const ResNormArgs &a, int64_t
     int64_t blocks = (blocks_needed + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
+    blocks += a.gamma_blocks;
     if (precision == 0)
         return launch_sweep_kernel(resident_normals_kernel<float>, static_cast<int>(blocks), 256, 0, stream, a);
     return launch_sweep_kernel(resident_normals_kernel<double>, static_cast<int>(blocks), 256, 0, stream, a);

@@ -22,6 +22,7 @@
 
 #include "gmrf_device.cuh"
 #include "gmrf_internal.h"
+#include "gamma_pre.cuh"
 #include "hyper_task.cuh"
 #include "pg.cuh"
 
@@ -644,34 +645,9 @@ __global__ void gamma_pre_kernel(const GammaPreArgs a)
 {
     pdl_wait_then_release();
     const long long base = a.ctl->sweep;
-    const int npairs = a.nfields * a.Cp;
-    const int total = a.count * npairs * 4;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-        const int which = q & 3, pidx = (q >> 2) % npairs, k = (q >> 2) / npairs;
-        const int fi = pidx / a.Cp, chain = pidx - fi * a.Cp;
-        const FieldDev &f = a.fields[fi];
-        const uint32_t word1 = static_cast<uint32_t>(base + k);
-        if (which == 3) continue;
-        if (which == 2) {
-            double zb = 0.0, unused;
-            if (a.intercept) {
-                const uint4 w = philox4x32_10(
-                    make_uint4(0u, word1, f.stream, (kTagBeta << 24) | static_cast<uint32_t>(chain)), a.key);
-                box_muller_f64(w.x, w.y, zb, unused);
-            }
-            a.gpre[q] = zb;
-            continue;
-        }
-        const double shape = which ? a.a_sig + 0.5 * f.n : a.a_tau + 0.5 * f.rank;
-        const uint32_t tag = which ? kTagSig : kTagTau;
-        int fb = 0;
-        a.gpre[q] = gamma_mt(shape, 1.0, a.key, word1, f.stream, (tag << 24) | static_cast<uint32_t>(chain), fb);
-        if (fb) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctl->fallbacks), 1ull);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.ctl->batch_base = base;
-        a.ctl->batch_count = a.count;
-    }
+    const int total = gamma_pre_tasks(a);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) gamma_pre_task(a, q, base);
+    if (blockIdx.x == 0 && threadIdx.x == 0) gamma_pre_record(a, base);
 }
 
 __global__ void ctl_reset_kernel(SweepCtl *ctl, long long start_sweep)
