@@ -244,6 +244,10 @@ cudaError_t launch_unpack(int precision, const FieldDev *fields_dev, const Field
 cudaError_t launch_pool(int precision, const FieldDev *fields_dev, const FieldDev &f, int32_t fidx, int32_t Cp,
                         int32_t C, int64_t k, const void *mean, const void *m2, const int32_t *perm_inv,
                         double *out_mean, double *out_var, cudaStream_t stream);
+// Device checks of data staged by gmrf_sampler_set_data (bits of *flag: 1 y not finite, 2 trials
+// outside 0..4095, 4 successes outside [0, trials], 8 x0 not finite); trials, x0 may be null.
+cudaError_t launch_check_data(const double *y, const int32_t *trials, const double *x0, int64_t n, int64_t nx0,
+                              unsigned int *flag, cudaStream_t stream);
 cudaError_t launch_pack_int(const FieldDev *fields_dev, const FieldDev &f, int32_t fidx, const int32_t *v_nat,
                             const int32_t *perm_inv, int32_t *v, cudaStream_t stream);
 cudaError_t launch_ctl_reset(SweepCtl *ctl, long long start_sweep, cudaStream_t stream);

@@ -735,6 +735,43 @@ cudaError_t launch_pg_stage(int precision, const PgArgs &a, cudaStream_t stream)
     return launch_sweep_kernel(pg_stage_kernel<double>, static_cast<int>(blocks), 256, 0, stream, a);
 }
 
+namespace {
+
+// The checks of data uploaded for gmrf_sampler_set_data, on the device: bit 0 of *flag when a y
+// is not finite, bit 1 a trials count outside 0..4095, bit 2 a success count outside
+// [0, trials], bit 3 an x0 not finite (x0 may be null; trials null unless binomial).
+__global__ void check_data_kernel(const double *y, const int32_t *trials, const double *x0, int64_t n, int64_t nx0,
+                                  unsigned int *flag)
+{
+    unsigned int bad = 0;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+        const double v = y[i];
+        if (!isfinite(v)) bad |= 1u;
+        if (trials) {
+            const int32_t m = trials[i];
+            if (m < 0 || m > 4095) bad |= 2u;
+            if (!(v >= 0.0 && v <= static_cast<double>(m))) bad |= 4u;
+        }
+    }
+    if (x0)
+        for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < nx0; i += stride)
+            if (!isfinite(x0[i])) bad |= 8u;
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (bad && (threadIdx.x & 31) == 0) atomicOr(flag, bad);
+}
+
+}  // namespace
+
+cudaError_t launch_check_data(const double *y, const int32_t *trials, const double *x0, int64_t n, int64_t nx0,
+                              unsigned int *flag, cudaStream_t stream)
+{
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(unsigned int), stream);
+    if (e != cudaSuccess) return e;
+    check_data_kernel<<<grid_for(n > nx0 ? n : nx0, 256), 256, 0, stream>>>(y, trials, x0, n, nx0, flag);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_int(const FieldDev *fields_dev, const FieldDev &f, int32_t fidx, const int32_t *v_nat,
                             const int32_t *perm_inv, int32_t *v, cudaStream_t stream)
 {

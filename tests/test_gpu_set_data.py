@@ -148,14 +148,20 @@ def test_set_data_rejects_bad_data():
     with g.Sampler([f], precision=g.FP32, chains=1, seed=4) as s:
         s.sweep(3)
         before = s.fetch_x(0, 0)
-        bad = f["y"].copy()
-        bad[17] = np.nan
-        with pytest.raises(g.GmrfError) as e:
-            s.set_data(0, bad)
-        assert e.value.status == g.E_INVALID
-        with pytest.raises(g.GmrfError) as e:
+        # checked on the device after the upload: any position, the last one included
+        for i, v in ((17, np.nan), (f["n"] - 1, np.inf), (0, -np.inf)):
+            bad = f["y"].copy()
+            bad[i] = v
+            with pytest.raises(g.GmrfError, match="y must be finite") as e:
+                s.set_data(0, bad)
+            assert e.value.status == g.E_INVALID
+        with pytest.raises(g.GmrfError, match="x0 must be finite") as e:
             s.set_data(0, f["y"], x0=np.full(f["n"], np.inf))
         assert e.value.status == g.E_INVALID
+        x0 = np.tile(f["y"], (1, 1))
+        x0[0, -1] = np.nan
+        with pytest.raises(g.GmrfError, match="x0 must be finite"):
+            s.set_data(0, f["y"], x0=x0)
         with pytest.raises(g.GmrfError) as e:
             s.set_data(1, f["y"])
         assert e.value.status == g.E_INVALID
@@ -170,9 +176,14 @@ def test_set_data_rejects_bad_data():
         m = fb["trials"].copy()
         y = fb["y"].copy()
         y[np.argmax(m)] = m.max() + 1
-        with pytest.raises(g.GmrfError) as e:
+        with pytest.raises(g.GmrfError, match=r"successes y must be in \[0, trials\]") as e:
             s.set_data(0, y, m)
         assert e.value.status == g.E_INVALID
+        for bad_m in (-1, 4096):
+            m2 = m.copy()
+            m2[-1] = bad_m
+            with pytest.raises(g.GmrfError, match="trials must be in 0..4095"):
+                s.set_data(0, np.minimum(fb["y"], np.maximum(m2, 0)), m2)
         s.sweep(2)
 
 
