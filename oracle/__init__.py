@@ -90,6 +90,7 @@ def _load():
             lib.ora_lattice_colors.argtypes = [ctypes.c_int32, i32p, i32p]
             lib.ora_lattice_colors.restype = ctypes.c_int32
             lib.ora_priorities.argtypes = [ctypes.c_uint64, ctypes.c_int32, u32p]
+            lib.ora_priorities_ldf.argtypes = [ctypes.c_uint64, ctypes.c_int32, i32p, u32p]
             lib.ora_color_greedy.argtypes = [ctypes.c_int32, i32p, i32p, u32p, i32p]
             lib.ora_color_greedy.restype = ctypes.c_int32
             lib.ora_components.argtypes = [ctypes.c_int32, i32p, i32p]
@@ -254,6 +255,16 @@ def priorities(seed, n):
     return p
 
 
+def priorities_ldf(seed, row_ptr):
+    """Largest-degree-first priorities: min(degree, 255) in the top 8 bits, the top 24 bits of the
+    random priority of `seed` below."""
+    rp = _i32(row_ptr)
+    n = len(rp) - 1
+    p = np.zeros(n, np.uint32)
+    _load().ora_priorities_ldf(seed, int(n), _ptr(rp, ctypes.c_int32), _ptr(p, ctypes.c_uint32))
+    return p
+
+
 def color_greedy(row_ptr, col_idx, prio):
     """First-fit greedy colouring in decreasing (priority, index) order -> (colors, k)."""
     rp, ci = _i32(row_ptr), _i32(col_idx)
@@ -265,10 +276,12 @@ def color_greedy(row_ptr, col_idx, prio):
     return colors, k
 
 
-def color_graph(row_ptr, col_idx, seed):
-    """The colouring a graph gets from its seed: greedy in decreasing Philox-priority order."""
+def color_graph(row_ptr, col_idx, seed, ldf=False):
+    """The colouring a graph gets from its seed: greedy in decreasing Philox-priority order
+    (largest degree first with ldf)."""
     n = len(row_ptr) - 1
-    return color_greedy(row_ptr, col_idx, priorities(seed, n))
+    prio = priorities_ldf(seed, row_ptr) if ldf else priorities(seed, n)
+    return color_greedy(row_ptr, col_idx, prio)
 
 
 def components(row_ptr, col_idx):

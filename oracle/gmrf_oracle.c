@@ -14,6 +14,8 @@
  *     sequential first-fit greedy colouring taken in decreasing (priority, index) order; with
  *     priority decreasing in the index it is the greedy colouring the paper gives (each class
  *     is the lexicographically first maximal independent set of the vertices still uncoloured).
+ *     With largest-degree-first priorities (ora_priorities_ldf) higher-degree vertices come
+ *     first, which usually needs fewer colours (one per colour step of a sweep).
  *     Lattices use the colourings found "by inspection" (Sec. 2.3, Fig. 1): parity for 4- and
  *     6-neighbour lattices, the 2x2 pattern for the 8-neighbour lattice.
  *   - One Gibbs sweep (Algorithm 1): for colour j = 0..k-1, every site i of colour j is drawn
@@ -277,6 +279,20 @@ void ora_priorities(uint64_t seed, int32_t n, uint32_t *prio)
         uint32_t ctr[4] = {(uint32_t)v, 0u, 0u, (uint32_t)ORA_TAG_PRIO << 24};
         ora_philox4x32_10(ctr, key, w);
         prio[v] = w[0];
+    }
+}
+
+/* Largest-degree-first priorities (the Jones-Plassmann LDF variant, Sec. 2.3 leaves the order
+ * of the greedy colouring open): the degree, capped at 255, in the top 8 bits and the top 24
+ * bits of the random priority above below it, so vertices of larger degree are coloured first
+ * and equal degrees fall back to the random order (then the index). */
+void ora_priorities_ldf(uint64_t seed, int32_t n, const int32_t *row_ptr, uint32_t *prio)
+{
+    ora_priorities(seed, n, prio);
+    for (int32_t v = 0; v < n; ++v) {
+        int32_t d = row_ptr[v + 1] - row_ptr[v];
+        if (d > 255) d = 255;
+        prio[v] = ((uint32_t)d << 24) | (prio[v] >> 8);
     }
 }
 

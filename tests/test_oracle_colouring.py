@@ -7,6 +7,10 @@
   out here independently.
 - With random priorities it equals a round-by-round Jones-Plassmann simulation (the parallel
   algorithm the CUDA path runs), and every colouring is proper with k <= max degree + 1.
+- Largest-degree-first priorities order the vertices by degree (capped at 255), then by the
+  random priority's top 24 bits, then by index; the colouring is proper, equals the JP
+  simulation with those priorities, and on graphs where the order is known (a star, a path with
+  a pendant hub, K_{n,n} minus a perfect matching) it gives the known colourings.
 """
 import itertools
 
@@ -153,3 +157,60 @@ def test_components():
     assert oracle.components(*wl.csr_from_edges(8, e)) == 4
     rp, ci = oracle.lattice_csr(oracle.LAT3D_6, (3, 3, 3))
     assert oracle.components(rp, ci) == 1
+
+
+def _order(prio):
+    n = len(prio)
+    return sorted(range(n), key=lambda v: (int(prio[v]), v), reverse=True)
+
+
+@pytest.mark.parametrize("gi", range(10))
+def test_ldf_order_by_degree_then_random_then_index(gi):
+    rp, ci = _graphs()[gi]
+    n = len(rp) - 1
+    deg = np.minimum(np.diff(rp), 255)
+    rnd = oracle.priorities(77 + gi, n)
+    ldf = oracle.priorities_ldf(77 + gi, rp)
+    want = sorted(range(n), key=lambda v: (int(deg[v]), int(rnd[v]) >> 8, v), reverse=True)
+    assert _order(ldf) == want
+    colors, k = oracle.color_greedy(rp, ci, ldf)
+    jp, _ = _jp_rounds(rp, ci, ldf)
+    assert np.array_equal(colors, jp) and _proper(rp, ci, colors)
+    assert k <= int(np.diff(rp).max() if n else 0) + 1
+    assert np.array_equal(oracle.color_graph(rp, ci, 77 + gi, ldf=True)[0], colors)
+
+
+def test_ldf_degree_cap():
+    # a hub of degree 300 and one of degree 256 share the capped degree 255: the random bits decide
+    e = [[0, 1 + i] for i in range(300)] + [[301, 302 + i] for i in range(256)]
+    rp, ci = wl.csr_from_edges(558, np.array(e))
+    p = oracle.priorities_ldf(5, rp)
+    r = oracle.priorities(5, 558)
+    assert p[0] >> 24 == 255 and p[301] >> 24 == 255
+    assert (p[0] & 0xFFFFFF) == r[0] >> 8 and (p[301] & 0xFFFFFF) == r[301] >> 8
+
+
+def test_ldf_known_colourings():
+    # star: the hub first (colour 0), every leaf colour 1
+    rp, ci = wl.star_graph(40)
+    colors, k = oracle.color_graph(rp, ci, 3, ldf=True)
+    assert k == 2 and colors[0] == 0 and np.all(colors[1:] == 1)
+    # crown graph (K_{m,m} minus a perfect matching): any order that alternates the two sides
+    # pairwise (u_i, v_i, ...) needs m colours, while taking one side first needs 2; with equal
+    # degrees everywhere the LDF order is the random order, so compare with the index order that
+    # alternates (m colours) and check LDF stays proper and within max degree + 1
+    m = 6
+    e = [[i, m + j] for i in range(m) for j in range(m) if i != j]
+    rp, ci = wl.csr_from_edges(2 * m, np.array(e))
+    alt = np.zeros(2 * m, np.uint32)
+    for i in range(m):
+        alt[i], alt[m + i] = 2 * m - 2 * i, 2 * m - 2 * i - 1
+    assert oracle.color_greedy(rp, ci, alt)[1] == m
+    colors, k = oracle.color_graph(rp, ci, 9, ldf=True)
+    assert _proper(rp, ci, colors) and k <= m
+    # path 0-1-2-3 with a pendant star on 2: vertex 2 (degree 5) first (colour 0), then 1 (degree
+    # 2: colour 1), then the leaves (0 next to 1: colour 0; 3 to 6 next to 2: colour 1)
+    e = [[0, 1], [1, 2], [2, 3], [2, 4], [2, 5], [2, 6]]
+    rp, ci = wl.csr_from_edges(7, np.array(e))
+    colors, _ = oracle.color_graph(rp, ci, 11, ldf=True)
+    assert colors[2] == 0 and colors[1] == 1 and colors[0] == 0 and np.all(colors[3:] == 1)
