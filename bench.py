@@ -302,7 +302,7 @@ def oracle_rate(spec, sweeps):
     for i, f in enumerate(spec["fields"]):
         if f["kind"] == CSR:
             graph = (f["row_ptr"], f["col_idx"])
-            colors = oracle.color_graph(f["row_ptr"], f["col_idx"], f.get("color_seed", 0))[0]
+            colors = oracle.color_graph(f["row_ptr"], f["col_idx"], f.get("color_seed", 0), ldf=True)[0]
         else:
             graph = oracle.lattice_csr(kinds[f["kind"]], f["dims"])
             colors = oracle.lattice_colors(kinds[f["kind"]], f["dims"])[0]

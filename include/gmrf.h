@@ -98,7 +98,7 @@ typedef struct {
     const int32_t *col_idx;   /* CSR only                                                   */
     const double *weights;    /* CSR only, may be NULL                                      */
     const int32_t *colors;    /* CSR only, may be NULL                                      */
-    uint64_t color_seed;      /* CSR with colors == NULL: priority seed                     */
+    uint64_t color_seed;      /* CSR with colors == NULL: priority seed (see GMRF_FLAG_COLOR_RANDOM) */
     const double *y;          /* [n] observations, natural order (host)                     */
     const double *x0;         /* [chains][n] initial states (host) or NULL: x0 = y          */
     const double *tau0;       /* [chains] initial tau or NULL: model.tau0                   */
@@ -199,6 +199,14 @@ typedef struct {
  * wait gives up (after 1 ms with this flag, instead of 1 s), as a lost exchange would make it; the
  * kernel still finishes, and the next call that reads the counters returns GMRF_E_TIMEOUT. */
 #define GMRF_FLAG_TEST_STALL 8
+/* Graphs that a sampler colours itself (colors == NULL) take Jones-Plassmann with
+ * largest-degree-first priorities: min(degree, 255) in the top 8 bits, the top 24 bits of the
+ * random priority of color_seed (the priority gmrf_color_graph uses for that seed) below, so
+ * vertices of larger degree are coloured first; the colouring equals the greedy colouring in
+ * that priority order and usually needs fewer colours, i.e. fewer colour steps per sweep (the
+ * 16,384-site Delaunay graph: 6 against 7).  GMRF_FLAG_COLOR_RANDOM takes the random priorities
+ * alone, as gmrf_color_graph with that seed does. */
+#define GMRF_FLAG_COLOR_RANDOM 16
 
 typedef struct {
     int32_t nfields;

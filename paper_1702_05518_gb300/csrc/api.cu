@@ -1055,7 +1055,8 @@ gmrf_status build_plain(gmrf_sampler *s, const gmrf_field_desc &f, std::vector<v
             CK(dev_malloc(&scratch, jp_scratch_bytes(h.n)));
             tmp.push_back(scratch);
             int32_t k = 0;
-            CK(jp_color(h.n, rp, ci, nullptr, f.color_seed, s->plain_colors, scratch, &k, s->stream));
+            CK(jp_color(h.n, rp, ci, nullptr, f.color_seed, s->plain_colors, scratch, &k, s->stream,
+                        (s->opts.flags & GMRF_FLAG_COLOR_RANDOM) == 0));
             h.ncolors = k;
             a.ncolors = k;
             h.colors.resize(static_cast<size_t>(n));
@@ -1197,7 +1198,8 @@ gmrf_status build_chromatic(gmrf_sampler *s, const gmrf_field_desc *fields, std:
             CK(dev_malloc(&scratch, jp_scratch_bytes(h.n)));
             tmp.push_back(scratch);
             int32_t k = 0;
-            CK(jp_color(h.n, rp_d, ci_d, nullptr, f.color_seed, col_d, scratch, &k, s->stream));
+            CK(jp_color(h.n, rp_d, ci_d, nullptr, f.color_seed, col_d, scratch, &k, s->stream,
+                        (s->opts.flags & GMRF_FLAG_COLOR_RANDOM) == 0));
             h.ncolors = k;
             h.colors.resize(h.n);
             CK(cudaMemcpyAsync(h.colors.data(), col_d, sizeof(int32_t) * h.n, cudaMemcpyDeviceToHost, s->stream));

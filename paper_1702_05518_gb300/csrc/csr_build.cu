@@ -30,6 +30,19 @@ __global__ void jp_priorities_kernel(int32_t n, uint2 key, uint32_t *prio)
         prio[v] = philox4x32_10(make_uint4(static_cast<uint32_t>(v), 0u, 0u, kTagPrio << 24), key).x;
 }
 
+// Largest-degree-first priorities: min(degree, 255) in the top 8 bits, the top 24 bits of the
+// random priority below (vertices of larger degree are coloured first; equal degrees in the
+// random order, then by index).
+__global__ void jp_priorities_ldf_kernel(int32_t n, uint2 key, const int32_t *rp, uint32_t *prio)
+{
+    for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < n;
+         v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t w = philox4x32_10(make_uint4(static_cast<uint32_t>(v), 0u, 0u, kTagPrio << 24), key).x;
+        const int32_t d = min(rp[v + 1] - rp[v], 255);
+        prio[v] = (static_cast<uint32_t>(d) << 24) | (w >> 8);
+    }
+}
+
 __global__ void fill_kernel(int32_t *p, int64_t n, int32_t value)
 {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
@@ -245,7 +258,7 @@ size_t jp_scratch_bytes(int32_t n)
 }
 
 cudaError_t jp_color(int32_t n, const int32_t *rp, const int32_t *ci, const uint32_t *prio_in, uint64_t seed,
-                     int32_t *colors, void *scratch, int32_t *num_colors_host, cudaStream_t stream)
+                     int32_t *colors, void *scratch, int32_t *num_colors_host, cudaStream_t stream, bool ldf)
 {
     char *sp = static_cast<char *>(scratch);
     uint32_t *prio = reinterpret_cast<uint32_t *>(sp);
@@ -262,6 +275,8 @@ cudaError_t jp_color(int32_t n, const int32_t *rp, const int32_t *ci, const uint
     if (prio_in) {
         err = cudaMemcpyAsync(prio, prio_in, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, stream);
         if (err != cudaSuccess) return err;
+    } else if (ldf) {
+        jp_priorities_ldf_kernel<<<grid_of(n, 256), 256, 0, stream>>>(n, philox_key(seed), rp, prio);
     } else {
         jp_priorities_kernel<<<grid_of(n, 256), 256, 0, stream>>>(n, philox_key(seed), prio);
     }

@@ -334,9 +334,10 @@ struct CsrBuild {
 // JP colouring on the device; priorities: device [n] or nullptr for Philox(seed).
 // Scratch (`scratch_bytes` from jp_scratch_bytes) is caller-provided device memory.
 size_t jp_scratch_bytes(int32_t n);
+// ldf (with prio == nullptr): largest-degree-first priorities of `seed` instead of the random ones.
 cudaError_t jp_color(int32_t n, const int32_t *rp, const int32_t *ci, const uint32_t *prio,
                      uint64_t seed, int32_t *colors, void *scratch, int32_t *num_colors_host,
-                     cudaStream_t stream);
+                     cudaStream_t stream, bool ldf = false);
 // Stable counting sort by colour of the sites taken in the sequence `order` (device, n
 // vertices; null: natural order), and the permuted CSR (cols remapped, row order kept),
 // degrees and weights in precision T.  Outputs are device arrays of the field's block.

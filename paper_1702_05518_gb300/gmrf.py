@@ -24,6 +24,7 @@ FLAG_PER_COLOUR = 1
 FLAG_NO_RESIDENT = 2
 FLAG_RESIDENT = 4
 FLAG_TEST_STALL = 8
+FLAG_COLOR_RANDOM = 16
 PARAM_TAU2, PARAM_SIGMA2, PARAM_BETA0, PARAM_TAU = range(4)
 LIKELIHOOD_GAUSSIAN, LIKELIHOOD_BINOMIAL = 0, 1
 

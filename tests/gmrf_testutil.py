@@ -25,7 +25,10 @@ def oracle_colors(field):
     if field["kind"] == wl.CSR:
         if field.get("colors") is not None:
             return np.asarray(field["colors"], np.int32)
-        return oracle.color_graph(field["row_ptr"], field["col_idx"], field.get("color_seed", 0))[0]
+        # the sampler's own colouring: largest degree first unless the field asks for random
+        # priorities (sampled with GMRF_FLAG_COLOR_RANDOM)
+        return oracle.color_graph(field["row_ptr"], field["col_idx"], field.get("color_seed", 0),
+                                  ldf=not field.get("color_random", False))[0]
     return oracle.lattice_colors(KIND_TO_ORACLE[field["kind"]], field["dims"])[0]
 
 

@@ -4,7 +4,8 @@
 - The update normals agree with the oracle's FP64 Box-Muller: to rounding in FP64, within the
   single-precision error budget in FP32.
 - The GPU's JP colouring equals the oracle's sequential greedy colouring in decreasing
-  (priority, index) order, exactly; with priority = n - 1 - index it is the paper's greedy.
+  (priority, index) order, exactly; with priority = n - 1 - index it is the paper's greedy; a
+  sampler's own colouring (largest-degree-first priorities, or the random ones on request) too.
 """
 import numpy as np
 import pytest
@@ -105,3 +106,51 @@ def test_jp_all_equal_priorities_break_ties_by_index():
 def test_single_vertex_graph():
     colors, k = g.color_graph(np.array([0, 0]), np.zeros(0, np.int32), seed=3)
     assert k == 1 and colors.tolist() == [0]
+
+
+@pytest.mark.parametrize("name", ["er_sparse", "er_dense", "star", "k40", "isolated", "delaunay16k"])
+@pytest.mark.parametrize("random", [False, True])
+def test_sampler_colouring_bit_exact(name, random):
+    # a sampler's own JP colouring: largest-degree-first priorities by default, the random ones
+    # under GMRF_FLAG_COLOR_RANDOM; equal to the oracle's greedy colouring in that order, exactly
+    rp, ci = GRAPHS[name]
+    f = dict(wl.graph_field(rp, ci, seed=4), color_seed=9)
+    flags = g.FLAG_COLOR_RANDOM if random else 0
+    with g.Sampler([f], precision=g.FP32, chains=1, seed=1, flags=flags) as s:
+        colors, k = s.colors(0)
+    want, kw = oracle.color_graph(rp, ci, 9, ldf=not random)
+    assert np.array_equal(colors, want) and k == kw
+
+
+def test_ldf_takes_fewer_colours_on_the_delaunay_benchmark_graph():
+    rp, ci = GRAPHS["delaunay16k"]
+    f = dict(wl.graph_field(rp, ci, seed=4), color_seed=3)
+    ks = []
+    for flags in (g.FLAG_COLOR_RANDOM, 0):
+        with g.Sampler([f], precision=g.FP32, chains=8, seed=1, flags=flags) as s:
+            ks.append(s.colors(0)[1])
+    assert ks == [7, 6]
+
+
+@pytest.mark.parametrize("resident", [True, False])
+@pytest.mark.parametrize("random", [False, True])
+def test_sampler_colouring_parity(resident, random):
+    # sweeps over either colouring (graph resident kernel, or the per-colour path) against the
+    # oracle run on the same colouring
+    from gmrf_testutil import TOL_FP32_1000, relerr, run_oracle, trace_relerr
+
+    rp, ci, _ = wl.delaunay_graph(3000, wl.rng(12))
+    f = dict(wl.graph_field(rp, ci, seed=13), color_seed=14, color_random=random)
+    flags = (g.FLAG_COLOR_RANDOM if random else 0) | (0 if resident else g.FLAG_NO_RESIDENT)
+    with g.Sampler([f], precision=g.FP32, chains=2, seed=15, flags=flags, burn_in=20) as s:
+        s.sweep(60)
+        assert (s.info()["resident"] == 2) == resident
+        res = [s.fetch(0, c, trace=60) for c in range(2)]
+        colors, _ = s.colors(0)
+    want, _ = oracle.color_graph(rp, ci, 14, ldf=not random)
+    assert np.array_equal(colors, want)
+    st, out = run_oracle(f, 2, 60, seed=15, stream=0, burn_in=20)
+    for c in range(2):
+        assert relerr(res[c]["x"], st.x[c]) <= TOL_FP32_1000
+        assert relerr(res[c]["mean"], st.mean[c]) <= TOL_FP32_1000
+        assert trace_relerr(res[c]["tau_trace"], out["tau_trace"][c]) <= TOL_FP32_1000
