@@ -666,7 +666,7 @@ def run_ours(args):
     # posterior mean and variance pooled over the chains come back into pinned host memory.  Cold:
     # the same plus creating and destroying the sampler (colouring, layout, tiles, graph capture)
     # inside every step.
-    e2e_steps = max(1, min(3, args.steps))
+    e2e_steps = max(1, min(5, args.steps))
     n_total = sum(f["n"] for f in spec["fields"])
     binom = spec.get("likelihood") == "binomial"
     host_y = [torch.from_numpy(np.ascontiguousarray(f["y"], np.float64)).pin_memory() for f in spec["fields"]]
@@ -688,8 +688,11 @@ def run_ours(args):
         e2e_step(s2)  # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        e2e_step_ms = []
         for _ in range(e2e_steps):
-            e2e_step(s2)
+            t1 = time.perf_counter()
+            e2e_step(s2)  # ends with the pooled read-back, which synchronises the stream
+            e2e_step_ms.append(1e3 * (time.perf_counter() - t1))
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
     e2e_value = world * units * e2e_steps / e2e_s
@@ -805,6 +808,8 @@ def run_ours(args):
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps,
+                    "step_ms": [round(v, 3) for v in e2e_step_ms],
+                    "step_spread": (max(e2e_step_ms) - min(e2e_step_ms)) / (sum(e2e_step_ms) / len(e2e_step_ms)),
                     "per_step": "observations H2D (pinned) + restart, all sweeps, posterior mean and variance "
                                 "pooled over the chains D2H (pinned); sampler built once outside the timed region",
                     "cold_value": e2e_cold,
