@@ -730,8 +730,8 @@ def run_ours(args):
                 "normals_only_us": rng_only,
                 "normals_only_frac": None if rng_only is None else algo_bytes / (rng_only * 1e-6) / 1e9 / hbm,
                 "stages_us": {f"{st}:{name}": round(us, 3) for st, name, us in stages}}
-    if resident_batch and info["resident"] == 3:
-        # The quad kernel's tiles kept in shared memory for a batch of sweeps (one cooperative
+    if resident_batch and info["resident"] in (3, 4):
+        # The quad kernel's or the fused sweep's tiles kept in shared memory for a batch of sweeps (one cooperative
         # launch, a grid barrier per sweep): the method's least bytes per sweep (bytes_per_update
         # per site-update, every sweep) over the batch's time, Gamma-variate launch included.
         nb = resident_batch["sweeps"]
@@ -739,8 +739,9 @@ def run_ours(args):
         ach = q_bytes / (resident_batch["us"] * 1e-6) / 1e9
         roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                     "traffic": None, "peak_source": peak_note,
-                    "kernel": "resident batch: Gamma variates, lattice_quad_resident_kernel (cooperative, one "
-                              "block per tile)",
+                    "kernel": "resident batch: Gamma variates, "
+                              + ("lattice_quad_resident_kernel" if info["resident"] == 3 else "lattice_fused_resident")
+                              + " (cooperative, one block per tile)",
                     "algorithmic_bytes_per_launch": q_bytes,
                     "bytes_per_update": bytes_per_update(f0, spec["chains"], colour_classes(f0)),
                     "avg_launch_us": resident_batch["us"], "sweeps_per_launch": nb,

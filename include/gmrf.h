@@ -182,12 +182,14 @@ typedef struct {
  * 4-neighbour one), or of one small graph (unit weights, Gaussian likelihood, fewer than 32768
  * sites with state, mean and M2 in shared memory, at most 16 neighbours, 64 colours and 4096
  * sites per colour class), runs a batch of whole sweeps per launch, one block per chain (same
- * draws and counters, results equal up to rounding).  A larger single-chain FP32 8-neighbour
- * field on the quad kernel whose tiles can all be resident at once (1024 x 1024 takes 144 blocks)
- * also runs a batch of sweeps per launch: one cooperative launch, a block per tile keeping it in
- * shared memory, a grid barrier (bounded wait) per sweep, results bit for bit those of the
- * per-sweep launches.  On by default in FP32; GMRF_FLAG_RESIDENT asks for the small-lattice form
- * in FP64 as well, GMRF_FLAG_NO_RESIDENT keeps the per-sweep launches.
+ * draws and counters, results equal up to rounding).  A larger FP32 2-D lattice field whose
+ * per-sweep kernel's tiles can all be resident at once also runs a batch of sweeps per launch:
+ * one cooperative launch, a block per tile keeping it in shared memory, a grid barrier (bounded
+ * wait) per sweep, results bit for bit those of the per-sweep launches -- the quad kernel's tiles
+ * for single-chain 8-neighbour fields (1024 x 1024 takes 144 blocks), else the fused sweep's when
+ * every thread holds all chains (1, 2 or 4 in the layout; with the intercept only on request).  On
+ * by default in FP32; GMRF_FLAG_RESIDENT asks for the small-lattice form in FP64 as well and for
+ * the fused tiles' form with the intercept, GMRF_FLAG_NO_RESIDENT keeps the per-sweep launches.
  * gmrf_info.resident tells which path a sampler took. */
 #define GMRF_FLAG_PER_COLOUR 1
 #define GMRF_FLAG_NO_RESIDENT 2
@@ -195,7 +197,7 @@ typedef struct {
 /* GMRF_FLAG_TEST_STALL (for tests of failure handling only): on the resident graph path with a
  * cluster of two or more blocks per chain (a single graph of 4096 or more sites), every colour
  * step of the cluster kernel expects 16 more bytes than the other blocks send, and on the resident
- * quad path every grid barrier expects one arrival more than there are blocks, so the bounded
+ * tile paths every grid barrier expects one arrival more than there are blocks, so the bounded
  * wait gives up (after 1 ms with this flag, instead of 1 s), as a lost exchange would make it; the
  * kernel still finishes, and the next call that reads the counters returns GMRF_E_TIMEOUT. */
 #define GMRF_FLAG_TEST_STALL 8
@@ -221,7 +223,7 @@ typedef struct {
     int64_t early_start_misses; /* sweep kernels that started before their predecessor ended */
                                 /* with a wrong sweep-number prediction (normals redrawn)    */
     int64_t resident;         /* sweeps run on the resident path: 1 small lattice, 2 graph,   */
-                              /* 3 quad lattice tiles; 0 not                                 */
+                              /* 3 quad lattice tiles, 4 fused lattice tiles; 0 not          */
     int64_t wait_timeouts;    /* bounded device waits that gave up (then results are invalid) */
 } gmrf_info;
 

@@ -217,7 +217,8 @@ struct gmrf_sampler {
     // padded chain count 4 or 8 when used, 0 when the general colour-step kernel runs them.
     int wide3d = 0;
     // resident: 1 small lattice (one block per chain), 2 graph (a cluster per chain), 3 the quad
-    // lattice kernel's tiles kept resident (one cooperative launch per batch)
+    // lattice kernel's tiles kept resident, 4 the fused lattice sweep's tiles kept resident (3, 4:
+    // one cooperative launch per batch)
     int resident = 0, res_NI = 0, res_NT = 0, res_batch = 0;
     uint4 *res_nbr = nullptr, *res_nbr2 = nullptr;            // graph: neighbour records
     int res_cluster = 1, res_own_max = 0;                      // graph: blocks per chain, their share
@@ -615,27 +616,42 @@ cudaError_t launch_pre(gmrf_sampler *s, int count, cudaStream_t st)
     return launch_gamma_pre(gamma_pre_args(s, count), st);
 }
 
-// The resident form of the quad kernel: a single-chain FP32 8-neighbour field on the quad kernel
-// whose tiles can all be resident at once (one block each).
-cudaError_t plan_quad_resident(gmrf_sampler *s)
+// The resident tile forms, for a single 2-D lattice field whose per-sweep kernel's tiles can all be
+// resident at once (one block each): the quad kernel's (single-chain FP32 8-neighbour fields), else
+// the fused sweep's when it runs the fast form (FP32, every thread holding all chains).
+cudaError_t plan_tile_resident(gmrf_sampler *s)
 {
-    const int kind = GMRF_LATTICE2D_8;
-    if (s->fd[0].kind != kind || !s->fQCS[kind]) return cudaSuccess;
+    const int kind = s->fd[0].kind;
+    if (kind != GMRF_LATTICE2D_4 && kind != GMRF_LATTICE2D_8) return cudaSuccess;
     bool fits = false;
-    const cudaError_t e = lattice_quad_resident_fits(s->fQCS[kind], s->fNT[kind], s->fNQ[kind], s->fsmem[kind],
-                                                     s->ftile_cnt[kind], &fits);
+    if (s->fQCS[kind]) {
+        const cudaError_t e = lattice_quad_resident_fits(s->fQCS[kind], s->fNT[kind], s->fNQ[kind], s->fsmem[kind],
+                                                         s->ftile_cnt[kind], &fits);
+        if (e != cudaSuccess || !fits) return e;
+        s->res_batch = std::min(128, std::max(64, s->opts.graph_sweeps));
+        s->resident = 3;
+        return cudaSuccess;
+    }
+    if (s->precision != GMRF_FP32 || s->V != s->Cp || (s->Cp != 1 && s->Cp != 2 && s->Cp != 4)) return cudaSuccess;
+    // With the intercept every block would repeat the serial FP64 chain of beta0 and sigma^2 after
+    // each barrier, which the per-sweep path hides behind the next sweep's normals (the 512 x 512
+    // image with 3 chains: 16.8 against 16.2 us per sweep); GMRF_FLAG_RESIDENT asks for it anyway.
+    if (has_beta(s) && !(s->opts.flags & GMRF_FLAG_RESIDENT)) return cudaSuccess;
+    const cudaError_t e = lattice_fused_resident_fits(kind, s->fNT[kind], s->Cp, s->fsmem[kind], s->ftile_cnt[kind],
+                                                      &fits);
     if (e != cudaSuccess || !fits) return e;
     s->res_batch = std::min(128, std::max(64, s->opts.graph_sweeps));
-    s->resident = 3;
+    s->resident = 4;
     return cudaSuccess;
 }
 
 // The resident path applies to a single fused 2-D lattice field with the Gaussian likelihood whose
 // chain fits in shared memory (state, observations, mean and M2 with a ring of zeros: cells below
 // 2^16, sites below 2^16) and whose colour classes have at most 2 x 576 (8-neighbour) or 4 x 576
-// (4-neighbour) positions; a larger single-chain FP32 8-neighbour field takes the resident quad
-// kernel when its tiles fit in one wave.  It is the default for FP32 samplers; GMRF_FLAG_RESIDENT
-// asks for the small-lattice form in FP64 too and GMRF_FLAG_NO_RESIDENT switches both off.
+// (4-neighbour) positions; a larger FP32 field takes the resident form of its per-sweep kernel (the
+// quad kernel, or the fused sweep's fast form without the intercept) when its tiles fit in one
+// wave.  It is the default for FP32 samplers; GMRF_FLAG_RESIDENT asks for the small-lattice form in
+// FP64 too and for the fused tiles with the intercept; GMRF_FLAG_NO_RESIDENT switches all off.
 cudaError_t plan_resident(gmrf_sampler *s, const std::vector<int32_t> &coff0)
 {
     s->resident = 0;
@@ -698,11 +714,11 @@ cudaError_t plan_resident(gmrf_sampler *s, const std::vector<int32_t> &coff0)
     int NI = 0;
     for (int ni : {1, 2, 4})
         if (!NI && (ni < 4 || !e8) && (maxq + ni - 1) / ni <= (ni == 1 ? 640 : 576)) NI = ni;
-    if (!NI || cells >= 65536 || f.n >= 65536) return plan_quad_resident(s);
+    if (!NI || cells >= 65536 || f.n >= 65536) return plan_tile_resident(s);
     int NTS = static_cast<int>((maxq + NI - 1) / NI);
     NTS = (NTS + 31) / 32 * 32;
     const size_t smem = 4 * static_cast<size_t>(cells) * tsize(s->precision) + 8 * static_cast<size_t>(K) * NI * NTS;
-    if (smem > 220 * 1024) return plan_quad_resident(s);  // with the static reduction scratch, under 227 KiB
+    if (smem > 220 * 1024) return plan_tile_resident(s);  // with the static reduction scratch, under 227 KiB
     const int NT = NTS + 64;  // and the two drawing warps
     cudaError_t e = prepare_lattice_resident(s->precision, f.kind, NI, smem);
     if (e != cudaSuccess) return e;
@@ -821,10 +837,10 @@ FusedArgs fused_args(gmrf_sampler *s, int kind, int update, int accumulate)
     return a;
 }
 
-QuadResArgs quad_resident_args(gmrf_sampler *s, int count, int draw, int draw_beta)
+TileResArgs tile_resident_args(gmrf_sampler *s, int count, int draw, int draw_beta)
 {
-    QuadResArgs r{};
-    r.f = fused_args(s, GMRF_LATTICE2D_8, 1, 1);
+    TileResArgs r{};
+    r.f = fused_args(s, s->fd[0].kind, 1, 1);
     r.h = hyper_args(s, draw, draw_beta, 1);
     r.count = count;
     r.extra_arrivals = s->test_stall ? 1u : 0u;
@@ -904,18 +920,20 @@ cudaError_t enqueue_sweeps(gmrf_sampler *s, int nsweeps, int with_hyper, cudaStr
     if (s->resident) {
         // Batches of sweeps: the batch's unit-rate Gamma variates and normals, then all its sweeps
         // in one launch.
-        static const char *kBatch[4] = {"", "resident batch, lattice", "resident batch, graph",
-                                        "resident batch, quad lattice"};
+        static const char *kBatch[5] = {"", "resident batch, lattice", "resident batch, graph",
+                                        "resident batch, quad lattice", "resident batch, fused lattice"};
         for (int k = 0; k < nsweeps && e == cudaSuccess;) {
             const NvtxRange range(kBatch[s->resident]);
             const int cnt = std::min(s->res_batch, nsweeps - k);
-            if (s->resident == 3) {
+            if (s->resident >= 3) {
+                // the tile kernels draw their own normals
                 if (draw || draw_beta) e = launch_pre(s, cnt, st);
-                // the quad kernel's tiles draw their own normals
-                const int kd = GMRF_LATTICE2D_8;
-                if (e == cudaSuccess)
-                    e = launch_lattice_quad_resident(s->fQCS[kd], s->fNT[kd], s->fNQ[kd],
-                                                     quad_resident_args(s, cnt, draw, draw_beta), s->fsmem[kd], st);
+                const int kd = s->fd[0].kind;
+                const TileResArgs ra = tile_resident_args(s, cnt, draw, draw_beta);
+                if (e == cudaSuccess && s->resident == 3)
+                    e = launch_lattice_quad_resident(s->fQCS[kd], s->fNT[kd], s->fNQ[kd], ra, s->fsmem[kd], st);
+                else if (e == cudaSuccess)
+                    e = launch_lattice_fused_resident(kd, s->fNT[kd], s->Cp, ra, s->fsmem[kd], st);
                 k += cnt;
                 continue;
             }

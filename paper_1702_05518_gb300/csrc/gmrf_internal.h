@@ -310,9 +310,10 @@ int record_error(int st, const char *msg);
 size_t lattice_quad_smem(int qcs, int TR);
 cudaError_t prepare_lattice_quad(int qcs, int nt, int nq, size_t smem);
 cudaError_t launch_lattice_quad(int qcs, int nt, int nq, const FusedArgs &a, size_t smem, cudaStream_t stream);
-// Its resident form: `count` whole sweeps of the single field in one cooperative launch, one block
-// per tile, every block resident at once.
-struct QuadResArgs {
+// The resident tile kernels (the quad kernel's and the fused 2-D sweep's resident forms): `count`
+// whole sweeps of the single field in one cooperative launch, one block per tile, every block
+// resident at once.
+struct TileResArgs {
     FusedArgs f;              // the tiling and buffers of the per-sweep kernel (update 1)
     HyperArgs h;              // the conjugate draws at the end of each sweep (end_of_sweep 1)
     int32_t count;            // sweeps of the launch
@@ -320,7 +321,12 @@ struct QuadResArgs {
     uint64_t wait_ns;         // limit of a wait at the grid barrier
 };
 cudaError_t lattice_quad_resident_fits(int qcs, int nt, int nq, size_t smem, int ntiles, bool *fits);
-cudaError_t launch_lattice_quad_resident(int qcs, int nt, int nq, const QuadResArgs &ra, size_t smem,
+// The fused sweep's resident form (lattice_fused_resident.cu; FP32, every thread holding all Cp
+// chains as lattice_fused_fast): whether the tiles fit in one wave, and the launch.
+cudaError_t lattice_fused_resident_fits(int kind, int threads, int Cp, size_t smem, int ntiles, bool *fits);
+cudaError_t launch_lattice_fused_resident(int kind, int threads, int Cp, const TileResArgs &ra, size_t smem,
+                                          cudaStream_t stream);
+cudaError_t launch_lattice_quad_resident(int qcs, int nt, int nq, const TileResArgs &ra, size_t smem,
                                          cudaStream_t stream);
 
 // Jones-Plassmann colouring and colour-permuted CSR layout (csr_build.cu).

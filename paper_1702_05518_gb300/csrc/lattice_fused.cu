@@ -23,29 +23,6 @@
 namespace gmrf {
 namespace {
 
-// Shared memory holds the staged region (natural rows gi0 .. gi0+RR-1, columns gj0 .. gj0+RC-1,
-// gi0 and gj0 even) in the same colour-split layout as the state in global memory:
-//   8-neighbour lattice: sub-array s = 2 (i & 1) + (j & 1), row (i - gi0) / 2, column (j - gj0) / 2;
-//   4-neighbour lattice: sub-array s = (i + j) & 1,           row  i - gi0,     column (j - gj0) / 2;
-// each sub-array SR x SC sites with Cp chains innermost.  A colour class is one sub-array, so a
-// warp walking a class reads consecutive addresses, and staging and write-back copy rows of
-// the global sub-arrays.
-template <int KIND>
-__device__ __forceinline__ int sm_index(int i, int j, int gi0, int gj0, int SR, int SC)
-{
-    if (KIND == kLat2D8) return ((2 * (i & 1) + (j & 1)) * SR + ((i - gi0) >> 1)) * SC + ((j - gj0) >> 1);
-    return (((i + j) & 1) * SR + (i - gi0)) * SC + ((j - gj0) >> 1);
-}
-
-
-// q / d for 0 <= q < 2^16 and d >= 1 by one single-precision multiply: (q + 1/2) / d is at least
-// 1/(2d) away from an integer and the two roundings err by less than 2^-7 / d, so the floor is
-// exact.
-__device__ __forceinline__ int div_small(int q, float rcp_d)
-{
-    return static_cast<int>((static_cast<float>(q) + 0.5f) * rcp_d);
-}
-
 template <typename T, int V, int KIND, int kFusedBlock>
 __global__ void __launch_bounds__(kFusedBlock, (kFusedBlock == 512 && sizeof(T) == 4 && V <= 2) ? 2 : 1)
     lattice_fused_kernel(const FusedArgs a)

@@ -30,7 +30,7 @@
 #include "gmrf_device.cuh"
 #include "gmrf_internal.h"
 #include "hyper_task.cuh"
-#include "mbarrier.cuh"
+#include "grid_barrier.cuh"
 
 namespace gmrf {
 namespace {
@@ -347,13 +347,6 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_kernel(const FusedArgs a)
 
 constexpr int kQuadResGpre = 128;
 
-// The barrier's arrival count and abort flag in one load (ctl->gbar, ctl->gabort; 16-byte aligned).
-__device__ __forceinline__ void ld_barrier(const unsigned long long *p, unsigned long long &arrivals,
-                                           unsigned long long &abort)
-{
-    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(arrivals), "=l"(abort) : "l"(p) : "memory");
-}
-
 // The resident form of the quad sweep: `count` whole sweeps of the single field in one
 // cooperative launch (every block resident at once), the tile of each block kept in shared
 // memory from sweep to sweep.  Per sweep:
@@ -374,7 +367,7 @@ __device__ __forceinline__ void ld_barrier(const unsigned long long *p, unsigned
 // the barrier gives up after `wait_ns`: the block counts it in ctl->wait_timeouts and sets
 // ctl->gabort, at which every block leaves its sweep loop.
 template <int QCS, int NT, int NQ>
-__global__ void __launch_bounds__(NT, 1) lattice_quad_resident_kernel(const QuadResArgs ra)
+__global__ void __launch_bounds__(NT, 1) lattice_quad_resident_kernel(const TileResArgs ra)
 {
     constexpr int NW = NT / 32;
     const FusedArgs &a = ra.f;
@@ -512,30 +505,13 @@ __global__ void __launch_bounds__(NT, 1) lattice_quad_resident_kernel(const Quad
         __syncthreads();  // the partial and every owned site of the sweep are stored
 
         // Grid barrier: arrive, draw the next sweep's normals, then wait (bounded).
-        if (tid == 0)  // release: this block's stores, ordered before by the barrier above
-            asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(&ctl->gbar) : "memory");
+        if (tid == 0) grid_arrive(ctl);  // release: this block's stores, ordered before by the barrier above
         if (it + 1 < ra.count)
             quad_normals<QCS, NT, NQ>(z, a.key, static_cast<uint32_t>(sw + 1), f.stream, static_cast<uint32_t>(Wl) >> 2,
                                       gu0, gv0);
         if (tid == 0) {
             const unsigned long long target = (static_cast<unsigned long long>(it) + 1) * nblk + ra.extra_arrivals;
-            unsigned long long arrived, aborted;
-            ld_barrier(&ctl->gbar, arrived, aborted);
-            const uint64_t t0 = global_ns();
-            for (uint32_t spin = 1; arrived < target; ++spin) {
-                if (aborted != 0) {
-                    s_abort = 1;
-                    break;
-                }
-                if ((spin & 15u) == 0 && global_ns() - t0 >= ra.wait_ns) {
-                    atomicAdd(&ctl->wait_timeouts, 1ull);
-                    atomicExch(&ctl->gabort, 1ull);
-                    s_abort = 1;
-                    break;
-                }
-                ld_barrier(&ctl->gbar, arrived, aborted);
-            }
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");  // acquire: the stores before every arrival
+            if (grid_wait(ctl, target, ra.wait_ns)) s_abort = 1;
         }
         __syncthreads();
         if (s_abort) break;
@@ -700,7 +676,7 @@ cudaError_t lattice_quad_resident_fits(int qcs, int nt, int nq, size_t smem, int
     return cudaSuccess;
 }
 
-cudaError_t launch_lattice_quad_resident(int qcs, int nt, int nq, const QuadResArgs &ra, size_t smem,
+cudaError_t launch_lattice_quad_resident(int qcs, int nt, int nq, const TileResArgs &ra, size_t smem,
                                          cudaStream_t stream)
 {
     cudaLaunchConfig_t cfg = {};
