@@ -59,12 +59,16 @@ def workload_spec(name: str):
                     fields=wl.volume_ellipsoids(seed=5), chains=8, sweeps=500, burn_in=250,
                     prior="icar", rho=1.0, seed=5, graph_sweeps=25, cpu_sweeps=1, acc_sweeps=(500, 250),
                     plain_sweeps=40)
-    if name == "delaunay16k":
+    if name in ("delaunay16k", "delaunay16k_ldf"):
+        # Jones-Plassmann with random 32-bit priorities, as the workload is stated; the _ldf
+        # variant takes the sampler's default order (largest degree first, 6 colours against 7)
         f = wl.delaunay_pcar(seed=3)
         f[0]["color_seed"] = 3
-        return dict(name="Delaunay 16384 points, proper CAR rho=0.95, 8 chains", fields=f, chains=8,
+        ldf = name.endswith("_ldf")
+        return dict(name="Delaunay 16384 points, proper CAR rho=0.95, 8 chains, JP colouring with "
+                    + ("largest-degree-first" if ldf else "random 32-bit") + " priorities", fields=f, chains=8,
                     sweeps=5000, burn_in=2500, prior="pcar", rho=0.95, seed=3, graph_sweeps=50,
-                    cpu_sweeps=50, acc_sweeps=(5000, 2500))
+                    cpu_sweeps=50, acc_sweeps=(5000, 2500), color_random=not ldf)
     if name == "batched":
         fields = wl.batched_uneven(seed=4)
         for i, f in enumerate(fields):
@@ -302,7 +306,8 @@ def oracle_rate(spec, sweeps):
     for i, f in enumerate(spec["fields"]):
         if f["kind"] == CSR:
             graph = (f["row_ptr"], f["col_idx"])
-            colors = oracle.color_graph(f["row_ptr"], f["col_idx"], f.get("color_seed", 0), ldf=True)[0]
+            colors = oracle.color_graph(f["row_ptr"], f["col_idx"], f.get("color_seed", 0),
+                                        ldf=not spec.get("color_random", False))[0]
         else:
             graph = oracle.lattice_csr(kinds[f["kind"]], f["dims"])
             colors = oracle.lattice_colors(kinds[f["kind"]], f["dims"])[0]
@@ -425,6 +430,8 @@ def sampler_kwargs(spec, g, seed, **over):
               intercept=spec.get("intercept", False), **spec.get("hyper", {}))
     if spec.get("likelihood") == "binomial":
         kw["likelihood"] = g.LIKELIHOOD_BINOMIAL
+    if spec.get("color_random"):
+        kw["flags"] = g.FLAG_COLOR_RANDOM
     kw.update(over)
     return kw
 
@@ -841,7 +848,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="volume256",
-                    choices=["image1024", "image64", "volume256", "delaunay16k", "batched", "paper50",
+                    choices=["image1024", "image64", "volume256", "delaunay16k", "delaunay16k_ldf", "batched", "paper50",
                              "paper512", "election"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--tune", action="store_true",

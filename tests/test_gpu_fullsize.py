@@ -3,7 +3,8 @@ benchmark times (CUDA graphs of several sweeps), compared with the oracle elemen
 
 - 1024 x 1024 8-neighbour ICAR, 2x2 colouring, 20 Gaussian bumps + N(0,1), FP32, 1 chain.
 - 256^3 6-neighbour ICAR, parity colouring, 50 ellipsoids + N(0,1), FP32, 8 chains.
-- Delaunay graph of 16384 points, proper CAR rho = 0.95, prior-drawn truth, FP32, 8 chains.
+- Delaunay graph of 16384 points, proper CAR rho = 0.95, prior-drawn truth, FP32, 8 chains (coloured
+  with random priorities, and largest degree first).
 - 224 lattices + 32 Delaunay graphs of uneven sizes in one batched sampler, FP32.
 """
 import numpy as np
@@ -54,11 +55,15 @@ def test_volume_256_ellipsoids_full_size():
     _check(f, 8, 1, 5, TOL_FP32_1)
 
 
-def test_delaunay_16k_pcar_full_size():
+@pytest.mark.parametrize("random", [True, False], ids=["random_priorities", "largest_degree_first"])
+def test_delaunay_16k_pcar_full_size(random):
+    # the workload's colouring (Jones-Plassmann, random 32-bit priorities) and the sampler's default
     f = wl.delaunay_pcar(seed=3)
     f[0]["color_seed"] = 3
-    _check(f, 8, 1, 3, TOL_FP32_1, prior=g.PRIOR_PCAR, rho=0.95)
-    _check(f, 8, 200, 3, TOL_FP32_1000, prior=g.PRIOR_PCAR, rho=0.95)
+    f[0]["color_random"] = random
+    flags = g.FLAG_COLOR_RANDOM if random else 0
+    _check(f, 8, 1, 3, TOL_FP32_1, prior=g.PRIOR_PCAR, rho=0.95, flags=flags)
+    _check(f, 8, 200, 3, TOL_FP32_1000, prior=g.PRIOR_PCAR, rho=0.95, flags=flags)
 
 
 def test_batched_uneven_full_size():
