@@ -187,9 +187,9 @@ typedef struct {
  * one cooperative launch, a block per tile keeping it in shared memory, a grid barrier (bounded
  * wait) per sweep, results bit for bit those of the per-sweep launches -- the quad kernel's tiles
  * for single-chain 8-neighbour fields (1024 x 1024 takes 144 blocks), else the fused sweep's when
- * every thread holds all chains (1, 2 or 4 in the layout; with the intercept only on request).  On
- * by default in FP32; GMRF_FLAG_RESIDENT asks for the small-lattice form in FP64 as well and for
- * the fused tiles' form with the intercept, GMRF_FLAG_NO_RESIDENT keeps the per-sweep launches.
+ * every thread holds all chains (1, 2 or 4 in the layout).  On by default in FP32;
+ * GMRF_FLAG_RESIDENT asks for the small-lattice form in FP64 as well, GMRF_FLAG_NO_RESIDENT keeps
+ * the per-sweep launches.
  * gmrf_info.resident tells which path a sampler took. */
 #define GMRF_FLAG_PER_COLOUR 1
 #define GMRF_FLAG_NO_RESIDENT 2

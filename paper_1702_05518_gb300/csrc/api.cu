@@ -226,6 +226,7 @@ struct gmrf_sampler {
     int32_t res_SR = 0, res_SC = 0;
     size_t res_smem = 0;
     void *res_z = nullptr;  // [res_batch][C][colours][NI][site threads] normals of a batch
+    double *res_pm = nullptr;  // fused resident tiles, Cp = 4: the tile partials by field (TileResArgs)
 
     cudaError_t alloc(void **p, size_t b)
     {
@@ -633,13 +634,13 @@ cudaError_t plan_tile_resident(gmrf_sampler *s)
         return cudaSuccess;
     }
     if (s->precision != GMRF_FP32 || s->V != s->Cp || (s->Cp != 1 && s->Cp != 2 && s->Cp != 4)) return cudaSuccess;
-    // With the intercept every block would repeat the serial FP64 chain of beta0 and sigma^2 after
-    // each barrier, which the per-sweep path hides behind the next sweep's normals (the 512 x 512
-    // image with 3 chains: 16.8 against 16.2 us per sweep); GMRF_FLAG_RESIDENT asks for it anyway.
-    if (has_beta(s) && !(s->opts.flags & GMRF_FLAG_RESIDENT)) return cudaSuccess;
     const cudaError_t e = lattice_fused_resident_fits(kind, s->fNT[kind], s->Cp, s->fsmem[kind], s->ftile_cnt[kind],
                                                       &fits);
     if (e != cudaSuccess || !fits) return e;
+    if (s->Cp == 4) {
+        const cudaError_t ea = s->alloc_t(&s->res_pm, static_cast<size_t>(3) * s->Cp * s->ftile_cnt[kind], sizeof(double));
+        if (ea != cudaSuccess) return ea;
+    }
     s->res_batch = std::min(128, std::max(64, s->opts.graph_sweeps));
     s->resident = 4;
     return cudaSuccess;
@@ -649,9 +650,9 @@ cudaError_t plan_tile_resident(gmrf_sampler *s)
 // chain fits in shared memory (state, observations, mean and M2 with a ring of zeros: cells below
 // 2^16, sites below 2^16) and whose colour classes have at most 2 x 576 (8-neighbour) or 4 x 576
 // (4-neighbour) positions; a larger FP32 field takes the resident form of its per-sweep kernel (the
-// quad kernel, or the fused sweep's fast form without the intercept) when its tiles fit in one
-// wave.  It is the default for FP32 samplers; GMRF_FLAG_RESIDENT asks for the small-lattice form in
-// FP64 too and for the fused tiles with the intercept; GMRF_FLAG_NO_RESIDENT switches all off.
+// quad kernel, or the fused sweep's fast form) when its tiles fit in one wave.  It is the default
+// for FP32 samplers; GMRF_FLAG_RESIDENT asks for the small-lattice form in FP64 too and
+// GMRF_FLAG_NO_RESIDENT switches all off.
 cudaError_t plan_resident(gmrf_sampler *s, const std::vector<int32_t> &coff0)
 {
     s->resident = 0;
@@ -843,6 +844,7 @@ TileResArgs tile_resident_args(gmrf_sampler *s, int count, int draw, int draw_be
     r.f = fused_args(s, s->fd[0].kind, 1, 1);
     r.h = hyper_args(s, draw, draw_beta, 1);
     r.count = count;
+    r.pm = s->res_pm;
     r.extra_arrivals = s->test_stall ? 1u : 0u;
     r.wait_ns = s->test_stall ? 1000000ull : kWaitNs;
     return r;

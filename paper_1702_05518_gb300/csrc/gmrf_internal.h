@@ -317,6 +317,10 @@ struct TileResArgs {
     FusedArgs f;              // the tiling and buffers of the per-sweep kernel (update 1)
     HyperArgs h;              // the conjugate draws at the end of each sweep (end_of_sweep 1)
     int32_t count;            // sweeps of the launch
+    double *pm;               // fused tiles with four chains per thread: the tile partials again,
+                              // [Cp][S, R, A][tile of the field], so that a warp's reads of one
+                              // value over 32 tiles cover consecutive doubles (in the partial
+                              // records they fall in 32 lines); null otherwise
     uint32_t extra_arrivals;  // 0; 1 under GMRF_FLAG_TEST_STALL (no grid barrier completes)
     uint64_t wait_ns;         // limit of a wait at the grid barrier
 };

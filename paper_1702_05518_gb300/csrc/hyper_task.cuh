@@ -158,6 +158,37 @@ __device__ __forceinline__ void hyper_sums(const HyperArgs &a, int which, bool n
         for (int off = 16; off >= 1; off >>= 1) A += __shfl_xor_sync(0xffffffffu, A, off);
 }
 
+// The sums of hyper_sums<*, true> from a copy of the partials laid out by field: sv[k] is the
+// S (which 0) or R (which 1) value of partial k and av[k] its A value, so a warp's loads cover
+// consecutive doubles (the partial records put 32 lanes' loads in 32 sectors).  Each lane issues
+// up to eight loads through L2 before adding them, in the order of hyper_sums (lane l: partials
+// l, l + 32, ...; the same shuffle tree), so the sums are bit for bit those of hyper_sums.
+__device__ __forceinline__ void hyper_sums_by_field(const double *sv, const double *av, bool need_a,
+                                                    int32_t nparts, double &S, double &A)
+{
+    const int lane = threadIdx.x & 31;
+    constexpr int U = 8;
+    for (int k0 = lane; k0 < nparts; k0 += 32 * U) {
+        double vs[U], va[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            const int k = k0 + 32 * j;
+            vs[j] = k < nparts ? __ldcg(sv + k) : 0.0;
+            va[j] = (need_a && k < nparts) ? __ldcg(av + k) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (k0 + 32 * j < nparts) {
+                S += vs[j];
+                if (need_a) A += va[j];
+            }
+        }
+    }
+    for (int off = 16; off >= 1; off >>= 1) S += __shfl_xor_sync(0xffffffffu, S, off);
+    if (need_a)
+        for (int off = 16; off >= 1; off >>= 1) A += __shfl_xor_sync(0xffffffffu, A, off);
+}
+
 // One task, run by all 32 lanes of the calling warp; `sweep` is the sweep being finished.
 template <typename T, bool BATCH>
 __device__ __forceinline__ void hyper_task(const HyperArgs &a, int task, long long sweep)

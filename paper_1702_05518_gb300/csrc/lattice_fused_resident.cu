@@ -368,6 +368,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 && CP < 4) ? 2 : 1) lattice_fus
             T sum = 0;
             for (int w = 0; w < NW; ++w) sum += red[(w * CP + chain) * 3 + k];
             reinterpret_cast<double *>(a.partials + static_cast<int64_t>(t.part) * CP + chain)[k] = static_cast<double>(sum);
+            if (CP == 4) ra.pm[(chain * 3 + k) * f.nparts + (t.part - f.part0)] = static_cast<double>(sum);
         }
         __syncthreads();  // the partial and every owned site of the sweep are stored; `red` is free
 
@@ -382,15 +383,27 @@ __global__ void __launch_bounds__(NT, (NT == 512 && CP < 4) ? 2 : 1) lattice_fus
         if (s_abort) break;
 
         if (warp >= 2 * CP) {
-            // The halo for the next sweep (its state buffer is XW), through L2.
-            for (int q = tid - 64 * CP; q < NS * SUB; q += NT - 64 * CP) {
-                int i, j, sa, r, v;
-                site_of(q, i, j, sa, r, v);
-                if (i >= t.i0 && i < t.i0 + TR && j >= t.j0 && j < t.j0 + TC) continue;  // owned
-                if (!interior && (i < 0 || i >= Hl || j < 0 || j >= Wl)) continue;      // stays 0
+            // The halo for the next sweep (its state buffer is XW), through L2: the K rows above
+            // and below the tile (RC sites each), then the K columns left and right of its rows.
+            const int HB = 2 * K * RC, HN = HB + 2 * K * TR;
+            const float rcp_rc = __frcp_rn(static_cast<float>(RC));
+            for (int q = tid - 64 * CP; q < HN; q += NT - 64 * CP) {
+                int i, j;
+                if (q < HB) {
+                    const int b = div_small(q, rcp_rc);
+                    i = gi0 + (b < K ? b : TR + b);
+                    j = gj0 + (q - b * RC);
+                } else {
+                    const int r2 = static_cast<int>(static_cast<unsigned>(q - HB) / (2u * K)), k = q - HB - r2 * (2 * K);
+                    i = t.i0 + r2;
+                    j = gj0 + (k < K ? k : TC + k);
+                }
+                if (!interior && (i < 0 || i >= Hl || j < 0 || j >= Wl)) continue;  // stays 0
+                const int sa = E8 ? 2 * (i & 1) + (j & 1) : ((i + j) & 1);
+                const int r = E8 ? (i - gi0) >> 1 : i - gi0, v = (j - gj0) >> 1;
                 T val[CP];
                 LdCg<CP>::ld(XW + (sa * gsub + (gu0 + r) * gcols + gv0 + v) * CP, val);
-                Vec<T, CP>::st(xs + q * CP, val);
+                Vec<T, CP>::st(xs + ((sa * SR + r) * SC + v) * CP, val);
             }
         } else {
             // The conjugate draws at the end of sweep sw: warp 2 v draws tau of chain v, warp
@@ -400,8 +413,17 @@ __global__ void __launch_bounds__(NT, (NT == 512 && CP < 4) ? 2 : 1) lattice_fus
             const bool need_a = which && h.draw_beta;
             double S = 0.0, A = 0.0;
             if (need_sum) {
-                if (h.max_parts >= 256) hyper_sums<true, true>(h, which, need_a, chain, f.part0, f.nparts, S, A);
-                else hyper_sums<false, true>(h, which, need_a, chain, f.part0, f.nparts, S, A);
+                // four chains per thread: from the copy by field (measured 16.1 -> 14.1 us per
+                // sweep of the 512 x 512 image with the intercept; with one or two chains the
+                // records' reads measured faster)
+                if (CP == 4) {
+                    const double *pc = ra.pm + chain * 3 * f.nparts;
+                    hyper_sums_by_field(pc + which * f.nparts, pc + 2 * f.nparts, need_a, f.nparts, S, A);
+                } else if (h.max_parts >= 256) {
+                    hyper_sums<true, true>(h, which, need_a, chain, f.part0, f.nparts, S, A);
+                } else {
+                    hyper_sums<false, true>(h, which, need_a, chain, f.part0, f.nparts, S, A);
+                }
             }
             if (lane == 0) {
                 const long long kb = sw - bbase;

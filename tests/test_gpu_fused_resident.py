@@ -71,8 +71,7 @@ def test_fused_resident_equals_per_sweep_path(case):
     if kw.get("intercept"):
         f = dict(f, y=f["y"] + 2.0)
     calls = [37, 70, 1, 92]  # batch boundaries, a single sweep and a batch cut short
-    # with the intercept the resident form is taken only on request
-    a, ia, aa = _run(f, C, calls, flags=g.FLAG_RESIDENT if kw.get("intercept") else 0, **kw)
+    a, ia, aa = _run(f, C, calls, **kw)
     b, ib, _ = _run(f, C, calls, flags=g.FLAG_NO_RESIDENT, **kw)
     assert ia["resident"] == 4 and ib["resident"] == 0
     _same(a, b, intercept=kw.get("intercept", False))
@@ -124,9 +123,9 @@ def test_fused_resident_300_sweeps_oracle():
         assert trace_relerr(r[c]["sigma2_trace"], out["sigma2_trace"][c]) <= TOL_FP32_1000
 
 
-def test_fused_resident_intercept_only_on_request():
+def test_fused_resident_taken_with_the_intercept():
     f = wl.small_lattice(wl.LATTICE2D_8, (300, 244), 59)
-    for flags, want in ((0, 0), (g.FLAG_RESIDENT, 4)):
+    for flags, want in ((0, 4), (g.FLAG_RESIDENT, 4), (g.FLAG_NO_RESIDENT, 0)):
         with g.Sampler([f], precision=g.FP32, chains=2, seed=1, intercept=True, flags=flags) as s:
             assert s.info()["resident"] == want
 

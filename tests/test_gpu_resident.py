@@ -82,7 +82,7 @@ def test_which_samplers_take_it():
     assert res([small8], intercept=True) == 1
     # beyond the small-lattice form: the fused sweep's tiles kept resident, and no form for 3-D
     assert res([big8]) == 4 and res([big4]) == 4 and res([vol]) == 0
-    assert res([big8], intercept=True) == 0 and res([big8], flags=g.FLAG_NO_RESIDENT) == 0
+    assert res([big8], intercept=True) == 4 and res([big8], flags=g.FLAG_NO_RESIDENT) == 0
     assert res([small8, small4]) == 0
     assert res([small8], algorithm=g.ALGO_PLAIN, precision=g.FP64) == 0
 
