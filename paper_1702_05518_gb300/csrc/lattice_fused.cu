@@ -16,6 +16,8 @@
 // and M2.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "gmrf_device.cuh"
 #include "gmrf_internal.h"
 #include "lattice_common.cuh"
@@ -561,8 +563,10 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4 && CP < 4) ? 
         accR[v] = 0;
         accA[v] = 0;
     }
-#pragma unroll 1
-    for (int c = 0; c < K; ++c) {
+    // One colour step per colour, the colour a compile-time constant (the lower-colour
+    // directions, whose edge terms enter the prior sum, are then known per direction).
+    auto colour_step = [&](auto colour) {
+        constexpr int c = decltype(colour)::value;
         const int e = K - 1 - c;
         const int lo_i = max(0, t.i0 - e), hi_i = min(Hl, t.i0 + TR + e);
         const int lo_j = max(0, t.j0 - e), hi_j = min(Wl, t.j0 + TC + e);
@@ -570,6 +574,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4 && CP < 4) ? 
         // lower-colour directions for this colour.
         int off[ND];
         T wl[ND];
+        bool lw[ND];  // lower-colour direction (its weight in wl is 1)
         if (E8) {
             const int ca = c >> 1, cb = c & 1;
 #pragma unroll
@@ -578,6 +583,7 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4 && CP < 4) ? 
                 const int cc = 2 * (ai & 1) + (bj & 1);
                 off[k] = ((cc - c) * SR + (ai >> 1)) * SC + (bj >> 1);
                 wl[k] = cc < c ? static_cast<T>(1) : static_cast<T>(0);
+                lw[k] = cc < c;
             }
         } else {
             const int o = (1 - 2 * c) * SR * SC;
@@ -586,7 +592,10 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4 && CP < 4) ? 
             off[2] = o;      // + p
             off[3] = o + SC;
 #pragma unroll
-            for (int k = 0; k < ND; ++k) wl[k] = static_cast<T>(c);
+            for (int k = 0; k < ND; ++k) {
+                wl[k] = static_cast<T>(c);
+                lw[k] = c != 0;
+            }
         }
         int n_rows, n_cols, first_u = 0, first_v = 0;
         if (E8) {
@@ -681,8 +690,10 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4 && CP < 4) ? 
                         T e2 = 0;
 #pragma unroll
                         for (int k = 0; k < ND; ++k) {
-                            const T df = xn[v] - nb[k][v];
-                            e2 += wv[k] * df * df;
+                            if (lw[k]) {  // the other directions' weights are 0: their terms add +0
+                                const T df = xn[v] - nb[k][v];
+                                e2 += wv[k] * df * df;
+                            }
                         }
                         accS[v] += (static_cast<T>(1) - rho) * d * xn[v] * xn[v] + rho * e2;
                         const T r = (yv - beta[v]) - xn[v];
@@ -693,6 +704,12 @@ __global__ void __launch_bounds__(NT, (NT == 512 && sizeof(T) == 4 && CP < 4) ? 
             }
         }
         __syncthreads();
+    };
+    colour_step(std::integral_constant<int, 0>{});
+    colour_step(std::integral_constant<int, 1>{});
+    if constexpr (K == 4) {
+        colour_step(std::integral_constant<int, 2>{});
+        colour_step(std::integral_constant<int, 3>{});
     }
 
     // Block reduction (all lanes hold the same chains): warp shuffle tree, then warps in order.
