@@ -5,16 +5,18 @@
 // to sweep.  Per sweep:
 //   * the K colour steps with the arithmetic of lattice_fused_fast (each owned site written to
 //     the next sweep's state buffer right after its step, the running mean and M2 updated in
-//     global memory on accumulated sweeps);
+//     global memory on accumulated sweeps; the colour a compile-time constant, so only the
+//     lower-colour directions' edge terms are formed);
 //   * the block's sums in that kernel's order to its tile partial, then the grid barrier
 //     (grid_barrier.cuh); while the other blocks finish, the block draws the normals of its
 //     staged sites for the next sweep;
 //   * every block draws tau | x and beta0, sigma^2 for every chain (warp 2v + which) from all tile
 //     partials, summed in the order of the hyperparameter kernel and drawn by hyper_draw with the
 //     batch's precomputed variates, so it holds the values the per-sweep path would have; block 0
-//     alone stores them and the traces; meanwhile the other warps stage again, through L2, the
-//     staged sites the tile does not own (its halo), which the neighbouring tiles have just
-//     written.
+//     alone stores them and the traces (with four chains per thread the partials are read from a
+//     copy laid out by field, TileResArgs::pm, so a warp's reads are consecutive); meanwhile the
+//     other warps stage again, through L2, the ring of staged sites around the tile (its halo),
+//     which the neighbouring tiles have just written.
 // The results equal the per-sweep path's bit for bit.  The state buffers alternate by sweep
 // number as on that path, so one barrier per sweep suffices.
 #include <cuda_runtime.h>
