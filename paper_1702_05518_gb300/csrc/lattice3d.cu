@@ -45,7 +45,6 @@
 // over blocks in FP64 by the draw kernel, each in a fixed order.
 #include <cuda_runtime.h>
 
-#include "f32x2.cuh"
 #include "gmrf_device.cuh"
 #include "gmrf_internal.h"
 
@@ -54,6 +53,52 @@ namespace {
 
 constexpr int k3Block = 256;
 
+// Two FP32 values (low half: the even chain) in one 64-bit register.
+using f2 = unsigned long long;
+
+__device__ __forceinline__ f2 pk(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// a * b + c, rounded once per lane
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Four chain values (two pairs) at p, 16-byte aligned.
+__device__ __forceinline__ void ld2x2(const float *p, f2 &a, f2 &b)
+{
+    const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(p);
+    a = t.x;
+    b = t.y;
+}
+__device__ __forceinline__ void st2x2(float *p, f2 a, f2 b) { *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(a, b); }
+
+__device__ __forceinline__ f2 splat(float v) { return pk(v, v); }
 __device__ __forceinline__ f2 lanes_f(uint32_t a, uint32_t b) { return pk(static_cast<float>(a), static_cast<float>(b)); }
 
 // The two Box-Muller pairs of one Philox block, (w.x, w.y) in the low lanes and (w.z, w.w) in
